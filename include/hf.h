@@ -1,0 +1,159 @@
+/*
+ * hf.h -- C ABI of the GB300 (sm_103a) Hirsch-Fye QMC / real-space DMFT library.
+ *
+ * Method: N. Bluemer and E. V. Gorelik, "Quantum Monte Carlo simulations of
+ * antiferromagnetism in ultracold fermions on optical lattices within real-space
+ * dynamical mean-field theory" (arXiv:1006.2716).
+ *   - eq. 1: trapped Hubbard model, hopping t, on-site U, trap V_i = V0 r_i^2, chemical
+ *     potential mu.
+ *   - eq. 2: lattice Green function [G(i w_n)]^{-1}_ij = t_ij + [i w_n + mu - V_i -
+ *     Sigma_i(i w_n)] delta_ij with a site-diagonal self-energy, one frequency at a time.
+ *   - "Model and Methods": one Anderson impurity problem per inequivalent site, solved by
+ *     Hirsch-Fye QMC at a fixed Trotter step dtau; importance sampling over many Markov
+ *     chains per impurity.
+ *
+ * Conventions shared by every entry point:
+ *   - Green functions are in the positive convention g(tau) = <T c(tau) c^dagger(0)>, so
+ *     g(0+) = 1 - n.  Imaginary times tau_m = m dtau, m = 0..L-1, L = round(beta / dtau).
+ *   - Spin index 0 = up (sigma = +1), 1 = down (sigma = -1).
+ *   - Every call returns an hf_status; nothing is thrown or exits across the ABI.  The text
+ *     of the last failure of a context is returned by hf_last_error.
+ *   - Device memory is never allocated by the library: hf_init takes a caller-owned device
+ *     workspace of hf_workspace_size bytes (256-byte aligned) and keeps its state in it;
+ *     the caller keeps that buffer alive until hf_free.  Host buffers passed to calls are
+ *     owned by the caller and only read or written during the call.
+ *   - All device work is queued on params.cuda_stream (a cudaStream_t; NULL = the legacy
+ *     default stream).  Calls that return host data synchronise that stream.
+ */
+#ifndef HF_H
+#define HF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HF_OK = 0,
+    HF_EINVAL = -1,    /* bad argument or parameter combination                        */
+    HF_ENOMEM = -2,    /* workspace too small                                          */
+    HF_ECUDA = -3,     /* a CUDA runtime call failed                                   */
+    HF_ETIMEOUT = -4,  /* a bounded device wait ran out                                */
+    HF_ENUMERIC = -5,  /* singular Dyson matrix or non-finite value detected on device */
+    HF_EBUSY = -6,     /* no free slot / resource                                      */
+    HF_ENOTREADY = -7  /* requested result is not available yet                        */
+} hf_status;
+
+typedef struct hf_ctx hf_ctx;
+
+/* Parameters of one trapped-lattice RDMFT problem (eq. 1 plus the QMC settings). */
+typedef struct hf_params {
+    int Lx, Ly;          /* geometry 0: Lx x Ly square; geometry 1: disc of radius Lx       */
+    int geometry;        /* 0 square (centre ((Lx-1)/2, (Ly-1)/2)), 1 site-centred disc     */
+    int periodic;        /* 1: periodic boundaries (square only); 0: open                   */
+    double t, U, V0, mu; /* eq. 1: hopping, interaction, trap strength, chemical potential  */
+    double beta, dtau;   /* inverse temperature, Trotter step; L = round(beta / dtau)       */
+    int n_matsubara;     /* Matsubara frequencies kept explicitly (paper: 500)              */
+    int chains_per_site; /* independent Markov chains per inequivalent site                 */
+    int precision;       /* 0: FP64 sweeps; 1: FP32 sweeps + FP64 refresh                   */
+    int refresh_every;   /* Dyson refresh after every refresh_every-th sweep of a chain     */
+    int delay_k;         /* delayed-update depth (0 or 1: rank-1 Sherman-Morrison)          */
+    int bin_size;        /* measured sweeps per bin                                         */
+    int max_bins;        /* bins kept per chain between clears                              */
+    int n_warmup, n_measure;  /* sweeps per hf_rdmft_step                                  */
+    uint64_t seed;       /* Philox key                                                      */
+    double h_seed;       /* staggered seed field of iteration 0                             */
+    double mix;          /* linear self-energy mixing                                       */
+    void* cuda_stream;   /* cudaStream_t used for every device operation                    */
+} hf_params;
+
+/* Bytes of device workspace hf_init needs for *p (*bytes set on HF_OK). */
+hf_status hf_workspace_size(const hf_params* p, size_t* bytes);
+
+/* Validate *p, build the lattice (eq. 1) and its C4v orbits, lay the state out in the
+ * caller's device workspace d_ws (ws_bytes >= hf_workspace_size), draw the initial Ising
+ * fields of every chain and seed Sigma_{i,sigma}(i w_n) = U/2 - sigma h_seed eps_i.
+ * *out receives a host handle released by hf_free. */
+hf_status hf_init(const hf_params* p, void* d_ws, size_t ws_bytes, hf_ctx** out);
+
+/* Number of inequivalent sites, chains, L, lattice sites N (any pointer may be NULL). */
+hf_status hf_get_sizes(const hf_ctx* ctx, int* n_sites, int* n_chains, int* L, int* N);
+
+/* Orbit tables: rep[n_sites] = lattice index of each inequivalent site; rep_of[N] =
+ * inequivalent index of every lattice site; flip[N] = 1 if that site sits on the other
+ * sublattice than its representative (its spins are exchanged).  Host buffers. */
+hf_status hf_get_orbits(const hf_ctx* ctx, int* rep, int* rep_of, int* flip);
+
+/* Set the Hartree-shifted bath g~0_sigma(tau_m), m = 0..L-1 (tau_0 = 0+), of one
+ * inequivalent site and spin from a host array of L doubles.  The next hf_sweep with
+ * refresh_first = 1 rebuilds every chain of that site from it (Dyson relation). */
+hf_status hf_set_g0(hf_ctx* ctx, int site, int spin, const double* g0_tau);
+
+/* Run n_warmup unmeasured then n_measure measured sweeps of every chain (asynchronous on
+ * the context stream).  refresh_first = 1 first recomputes G = [1 + (1 - g0)(e^V - 1)]^{-1} g0
+ * from the current bath and fields.  Per chain: sweep number w uses Philox counter
+ * (w, l, chain, site); after the sweep the chain's counter advances and a Dyson refresh runs
+ * when it is a multiple of refresh_every; measured sweeps then add to the current bin. */
+hf_status hf_sweep(hf_ctx* ctx, int n_warmup, int n_measure, int refresh_first);
+
+/* Zero all measurement bins and counters (the next measured sweep starts bin 0). */
+hf_status hf_clear_measurements(hf_ctx* ctx);
+
+/* Reduce the completed bins of every chain of one inequivalent site (synchronises):
+ * gtau[2][L] = G_sigma(tau_m), n[2] = densities, d = double occupancy, m = n_up - n_dn, each
+ * averaged over chains x bins; errs[2L + 4] = standard errors in the same order
+ * (gtau_up, gtau_dn, n_up, n_dn, d, m).  Any output pointer may be NULL. */
+hf_status hf_measure(hf_ctx* ctx, int site, double* gtau, double* n, double* d, double* m,
+                     double* errs);
+
+/* One full RDMFT iteration on the device: lattice step (eq. 2) for every frequency and
+ * spin, Weiss fields and their tau transform, warm-started QMC (n_warmup + n_measure sweeps),
+ * chain/bin reduction, tau -> i w transform, Sigma = 1/G0 - 1/G_imp and mixing.  Writes the
+ * wall time of the iteration to *iter_seconds (may be NULL).  Synchronises. */
+hf_status hf_rdmft_step(hf_ctx* ctx, double* iter_seconds);
+
+/* Self-energy of the inequivalent sites, [n_sites][2][n_matsubara] complex as interleaved
+ * (re, im) doubles; get copies it to the host, set replaces it from the host. */
+hf_status hf_get_sigma(hf_ctx* ctx, double* sigma);
+hf_status hf_set_sigma(hf_ctx* ctx, const double* sigma);
+
+/* Observables of the last hf_rdmft_step or hf_measure: per inequivalent site
+ * [n_sites][2L + 4] means and errors in the hf_measure order.  Synchronises. */
+hf_status hf_get_observables(hf_ctx* ctx, double* mean, double* err);
+
+/* Lattice-step output of the last hf_rdmft_step: G_ii(i w_n) of the inequivalent sites,
+ * [n_sites][2][n_matsubara] complex (re, im interleaved).  Synchronises. */
+hf_status hf_get_gloc(hf_ctx* ctx, double* gloc);
+
+/* Bath g~0(tau_m) currently set, [n_sites][2][L].  Synchronises. */
+hf_status hf_get_g0(hf_ctx* ctx, double* g0_tau);
+
+/* Checkpoint / resume: fields [n_chains][L] int8 (+-1), per-chain sweep counters
+ * [n_chains].  Setting fields invalidates G until the next refresh (hf_sweep with
+ * refresh_first = 1).  Synchronises. */
+hf_status hf_get_fields(hf_ctx* ctx, signed char* fields, uint32_t* sweep_counters);
+hf_status hf_set_fields(hf_ctx* ctx, const signed char* fields, const uint32_t* sweep_counters);
+
+/* Green-function matrices of one chain, [2][L][L] row-major doubles (converted from the
+ * single-precision state when precision = 1), and accepted-flip counters [n_chains]. */
+hf_status hf_get_green(hf_ctx* ctx, int chain, double* G);
+hf_status hf_get_accepts(hf_ctx* ctx, unsigned long long* accepts);
+
+/* Device time in milliseconds, from CUDA events recorded on the context stream, of the phases
+ * of the last hf_rdmft_step: ms[0] lattice step, ms[1] Weiss fields + i w -> tau, ms[2] QMC
+ * sweeps, ms[3] chain/bin reduction, ms[4] tau -> i w + self-energy update; ms[5] the QMC
+ * sweeps of the last hf_sweep.  A phase that has not run yet reads -1.  Synchronises. */
+hf_status hf_get_timings(hf_ctx* ctx, double* ms);
+
+/* Release the host handle (the device workspace stays the caller's). */
+void hf_free(hf_ctx* ctx);
+
+/* Text of the last error of ctx (or of the last hf_init failure if ctx is NULL). */
+const char* hf_last_error(const hf_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HF_H */

@@ -121,16 +121,18 @@ def matsubara(beta, nw):
     return (2.0 * np.arange(nw) + 1.0) * np.pi / beta
 
 
-def lattice_step(H0, mu, beta, sigma):
+def lattice_step(H0, mu, beta, sigma, n_index=None):
     """eq. 2: site-diagonal G_ii(i w_n) of [(i w_n + mu) 1 - H0 - diag(Sigma(i w_n))]^{-1}.
 
-    sigma: [nw, N] complex (one spin).  Returns [nw, N] complex.
+    sigma: [k, N] complex (one spin), the self-energy at the frequencies n_index (default
+    n = 0..k-1).  Returns [k, N] complex.
     """
-    nw, N = sigma.shape
-    w = matsubara(beta, nw)
-    out = np.zeros((nw, N), dtype=np.complex128)
+    k, N = sigma.shape
+    n_index = np.arange(k) if n_index is None else np.asarray(n_index)
+    w = (2.0 * n_index + 1.0) * np.pi / beta
+    out = np.zeros((k, N), dtype=np.complex128)
     eye = np.eye(N)
-    for n in range(nw):
-        M = (1j * w[n] + mu) * eye - H0 - np.diag(sigma[n])
-        out[n] = np.diag(np.linalg.inv(M))
+    for q in range(k):
+        M = (1j * w[q] + mu) * eye - H0 - np.diag(sigma[q])
+        out[q] = np.diag(np.linalg.inv(M))
     return out

@@ -1,0 +1,713 @@
+// hf_api.cu -- C ABI of the Hirsch-Fye QMC / RDMFT library (declared in include/hf.h).
+//
+// Host side of one context: validates parameters, builds the trapped lattice of eq. 1 and its
+// C4v orbits, lays the device state out inside the caller's workspace and sequences the
+// kernels of one RDMFT iteration ("Model and Methods": lattice step per Matsubara frequency,
+// one impurity problem per inequivalent site, many Markov chains per impurity).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+#include <chrono>
+
+#include "hf_internal.cuh"
+#include "k_lattice.cuh"
+
+namespace {
+
+thread_local std::string g_init_error;
+
+// ---------------------------------------------------------------------------------------
+// Lattice of eq. 1: sites, trap potential V_i = V0 r_i^2, nearest-neighbour hopping t.
+// Square: site (x, y) -> y * Lx + x, centre ((Lx-1)/2, (Ly-1)/2).  Disc: sites with
+// x^2 + y^2 <= R^2 in row order (y, then x), centre at the origin.  Orbits: the operations
+// (dx, dy) -> (+-dx, +-dy), (+-dy, +-dx) that map the site set onto itself; the representative
+// of an orbit is its smallest site index, inequivalent sites are numbered by increasing
+// representative; a site whose sublattice parity differs from its representative's carries
+// the spin exchange of an antiferromagnetic state.
+// ---------------------------------------------------------------------------------------
+struct HostLattice {
+    int N = 0;
+    int b = 0;                      // band half-width of H0 in this numbering
+    std::vector<int> x, y;
+    std::vector<double> dx, dy, V;
+    std::vector<int> parity, z;
+    std::vector<std::vector<int>> nbr;
+    std::vector<int> rep, rep_of, flip, site_rep;
+};
+
+bool build_lattice(const hf_params& p, HostLattice& lat, std::string& err) {
+    std::map<std::pair<int, int>, int> index;
+    double cx = 0.0, cy = 0.0;
+    if (p.geometry == 0) {
+        if (p.Lx < 1 || p.Ly < 1) { err = "Lx, Ly must be >= 1"; return false; }
+        for (int yy = 0; yy < p.Ly; ++yy)
+            for (int xx = 0; xx < p.Lx; ++xx) { lat.x.push_back(xx); lat.y.push_back(yy); }
+        cx = (p.Lx - 1) / 2.0;
+        cy = (p.Ly - 1) / 2.0;
+    } else if (p.geometry == 1) {
+        const int R = p.Lx;
+        if (R < 0) { err = "disc radius must be >= 0"; return false; }
+        for (int yy = -R; yy <= R; ++yy)
+            for (int xx = -R; xx <= R; ++xx)
+                if (xx * xx + yy * yy <= R * R) { lat.x.push_back(xx); lat.y.push_back(yy); }
+    } else {
+        err = "geometry must be 0 (square) or 1 (disc)";
+        return false;
+    }
+    lat.N = static_cast<int>(lat.x.size());
+    const int N = lat.N;
+    for (int i = 0; i < N; ++i) index[{lat.x[i], lat.y[i]}] = i;
+    lat.dx.resize(N); lat.dy.resize(N); lat.V.resize(N); lat.parity.resize(N); lat.z.resize(N);
+    lat.nbr.assign(N, {});
+    for (int i = 0; i < N; ++i) {
+        lat.dx[i] = lat.x[i] - cx;
+        lat.dy[i] = lat.y[i] - cy;
+        lat.V[i] = p.V0 * (lat.dx[i] * lat.dx[i] + lat.dy[i] * lat.dy[i]);
+        lat.parity[i] = (((lat.x[i] + lat.y[i]) % 2) + 2) % 2 == 0 ? 1 : -1;
+        const int off[4][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1}};
+        for (auto& o : off) {
+            int xn = lat.x[i] + o[0], yn = lat.y[i] + o[1];
+            if (p.periodic && p.geometry == 0) {
+                xn = ((xn % p.Lx) + p.Lx) % p.Lx;
+                yn = ((yn % p.Ly) + p.Ly) % p.Ly;
+            }
+            auto it = index.find({xn, yn});
+            if (it != index.end() && it->second != i) {
+                bool dup = false;
+                for (int j : lat.nbr[i]) dup |= (j == it->second);
+                if (!dup) lat.nbr[i].push_back(it->second);
+            }
+        }
+        lat.z[i] = static_cast<int>(lat.nbr[i].size());
+        for (int j : lat.nbr[i]) lat.b = std::max(lat.b, std::abs(j - i));
+    }
+    // orbits
+    std::vector<std::vector<int>> images;
+    for (int swap = 0; swap < 2; ++swap)
+        for (int sx = 1; sx >= -1; sx -= 2)
+            for (int sy = 1; sy >= -1; sy -= 2) {
+                std::vector<int> img(N);
+                bool ok = true;
+                for (int i = 0; i < N && ok; ++i) {
+                    const double a = (swap ? lat.dy[i] : lat.dx[i]) * sx;
+                    const double c = (swap ? lat.dx[i] : lat.dy[i]) * sy;
+                    const double xf = a + cx, yf = c + cy;
+                    const long xi = std::lround(xf), yi = std::lround(yf);
+                    if (std::fabs(xf - xi) > 1e-9 || std::fabs(yf - yi) > 1e-9) { ok = false; break; }
+                    auto it = index.find({static_cast<int>(xi), static_cast<int>(yi)});
+                    if (it == index.end()) { ok = false; break; }
+                    img[i] = it->second;
+                }
+                if (ok) images.push_back(img);
+            }
+    std::vector<int> rep_site(N);
+    for (int i = 0; i < N; ++i) {
+        int m = i;
+        for (auto& im : images) m = std::min(m, im[i]);
+        rep_site[i] = m;
+    }
+    lat.site_rep.assign(N, -1);
+    for (int i = 0; i < N; ++i)
+        if (rep_site[i] == i) {
+            lat.site_rep[i] = static_cast<int>(lat.rep.size());
+            lat.rep.push_back(i);
+        }
+    lat.rep_of.resize(N);
+    lat.flip.resize(N);
+    for (int i = 0; i < N; ++i) {
+        lat.rep_of[i] = lat.site_rep[rep_site[i]];
+        lat.flip[i] = lat.parity[i] != lat.parity[rep_site[i]] ? 1 : 0;
+    }
+    return true;
+}
+
+// Bump allocator over the caller's workspace (base == nullptr: size computation only).
+struct Carver {
+    char* base;
+    size_t off = 0;
+    explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+    template <class T>
+    T* take(size_t count) {
+        off = (off + 255) & ~static_cast<size_t>(255);
+        T* ptr = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return ptr;
+    }
+};
+
+}  // namespace
+
+struct hf_ctx {
+    hf_params p{};
+    HostLattice lat;
+    int L = 0, nsite = 0, nchain = 0, nw = 0;
+    double dtau = 0.0, lambda = 0.0;
+    double a_p = 0.0, a_m = 0.0, ev_p = 0.0, ev_m = 0.0;
+    cudaStream_t stream = nullptr;
+    int lat_batch = 0;              // matrices per lattice-step launch
+    uint32_t nmeas = 0;             // measured sweeps since the last clear (all chains)
+    std::string err;
+    // device state
+    double* gtau = nullptr;         // [nsite][2][L]
+    double* G = nullptr;            // [nchain][2][L*L]
+    float* Gf = nullptr;            // [nchain][2][L*L] (precision 1)
+    int8_t* s = nullptr;            // [nchain][L]
+    uint32_t* nsw = nullptr;        // [nchain]
+    uint32_t* nmeas_d = nullptr;    // [nchain]
+    unsigned long long* acc = nullptr;  // [nchain]
+    double* bins = nullptr;         // [nchain][max_bins][2L+3]
+    int* status = nullptr;          // [4]
+    double* obs_mean = nullptr;     // [nsite][2L+4]
+    double* obs_err = nullptr;      // [nsite][2L+4]
+    double2* sigma = nullptr;       // [nsite][2][nw]
+    double2* gloc = nullptr;
+    double2* weiss_inv = nullptr;
+    double2* gwt = nullptr;
+    double2* gimp = nullptr;
+    double2* sigma_new = nullptr;
+    double* c23 = nullptr;          // [nsite][2]
+    double* h0band = nullptr;       // [N][b+1]
+    int* rep_of = nullptr;          // [N]
+    int* flip = nullptr;            // [N]
+    int* site_rep = nullptr;        // [N]
+    double2* lat_scratch = nullptr; // [lat_batch][N][b+1]
+    // phase timing: events on the context stream (see hf_get_timings)
+    cudaEvent_t ev[9] = {};
+    bool ev_rdmft = false, ev_sweep = false;
+    ~hf_ctx() {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+};
+
+namespace {
+
+hf_status fail(hf_ctx* c, hf_status st, const std::string& msg) {
+    if (c) c->err = msg; else g_init_error = msg;
+    return st;
+}
+
+hf_status cuda_fail(hf_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, HF_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define HF_CUDA(ctx, call)                                             \
+    do {                                                               \
+        cudaError_t e_ = (call);                                       \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);     \
+    } while (0)
+
+hf_status validate(const hf_params& p, std::string& err) {
+    if (!(p.beta > 0.0) || !(p.dtau > 0.0)) { err = "beta and dtau must be > 0"; return HF_EINVAL; }
+    const double Lr = p.beta / p.dtau;
+    const int L = static_cast<int>(std::lround(Lr));
+    if (std::fabs(Lr - L) > 1e-9 * Lr) { err = "beta / dtau must be an integer"; return HF_EINVAL; }
+    if (p.precision == 0 && !hfk::qmc_f64_supported(L)) {
+        err = "FP64 sweeps support L in {8,12,16,20,24,32,40,48,64}, got " + std::to_string(L);
+        return HF_EINVAL;
+    }
+    if (p.precision == 1 && !hfk::qmc_f32_supported(L)) {
+        err = "FP32 sweeps support L in {16,32,64,128}, got " + std::to_string(L);
+        return HF_EINVAL;
+    }
+    if (p.precision != 0 && p.precision != 1) { err = "precision must be 0 or 1"; return HF_EINVAL; }
+    if (p.chains_per_site < 1) { err = "chains_per_site must be >= 1"; return HF_EINVAL; }
+    if (p.n_matsubara < 1 || p.n_matsubara > 100000) { err = "n_matsubara out of range"; return HF_EINVAL; }
+    if (p.bin_size < 1 || p.max_bins < 1) { err = "bin_size and max_bins must be >= 1"; return HF_EINVAL; }
+    if (p.refresh_every < 0) { err = "refresh_every must be >= 0"; return HF_EINVAL; }
+    if (p.precision == 1 && p.refresh_every < 1) {
+        err = "FP32 sweeps need a periodic FP64 refresh (refresh_every >= 1)";
+        return HF_EINVAL;
+    }
+    if (p.n_warmup < 0 || p.n_measure < 0) { err = "sweep counts must be >= 0"; return HF_EINVAL; }
+    if (!(p.U >= 0.0)) { err = "U must be >= 0"; return HF_EINVAL; }
+    if (!(p.mix > 0.0 && p.mix <= 1.0)) { err = "mix must be in (0, 1]"; return HF_EINVAL; }
+    if (!std::isfinite(p.t) || !std::isfinite(p.V0) || !std::isfinite(p.mu) || !std::isfinite(p.h_seed)) {
+        err = "non-finite model parameter";
+        return HF_EINVAL;
+    }
+    return HF_OK;
+}
+
+// Layout of the device state; returns total bytes.  base == nullptr computes sizes only.
+size_t layout(hf_ctx& c, void* base) {
+    Carver cv(base);
+    const int L = c.L, ns = c.nsite, nc = c.nchain, nw = c.nw, N = c.lat.N, bw = c.lat.b + 1;
+    c.gtau = cv.take<double>(static_cast<size_t>(ns) * 2 * L);
+    c.G = cv.take<double>(static_cast<size_t>(nc) * 2 * L * L);
+    c.Gf = c.p.precision == 1 ? cv.take<float>(static_cast<size_t>(nc) * 2 * L * L) : nullptr;
+    c.s = cv.take<int8_t>(static_cast<size_t>(nc) * L);
+    c.nsw = cv.take<uint32_t>(nc);
+    c.nmeas_d = cv.take<uint32_t>(nc);
+    c.acc = cv.take<unsigned long long>(nc);
+    c.bins = cv.take<double>(static_cast<size_t>(nc) * c.p.max_bins * (2 * L + 3));
+    c.status = cv.take<int>(4);
+    c.obs_mean = cv.take<double>(static_cast<size_t>(ns) * (2 * L + 4));
+    c.obs_err = cv.take<double>(static_cast<size_t>(ns) * (2 * L + 4));
+    const size_t nsw2 = static_cast<size_t>(ns) * 2 * nw;
+    c.sigma = cv.take<double2>(nsw2);
+    c.gloc = cv.take<double2>(nsw2);
+    c.weiss_inv = cv.take<double2>(nsw2);
+    c.gwt = cv.take<double2>(nsw2);
+    c.gimp = cv.take<double2>(nsw2);
+    c.sigma_new = cv.take<double2>(nsw2);
+    c.c23 = cv.take<double>(static_cast<size_t>(ns) * 2);
+    c.h0band = cv.take<double>(static_cast<size_t>(N) * bw);
+    c.rep_of = cv.take<int>(N);
+    c.flip = cv.take<int>(N);
+    c.site_rep = cv.take<int>(N);
+    c.lat_scratch = cv.take<double2>(static_cast<size_t>(c.lat_batch) * N * bw);
+    return cv.off + 256;
+}
+
+hf_status setup_sizes(hf_ctx& c, const hf_params* p) {
+    if (!p) return fail(nullptr, HF_EINVAL, "null params");
+    std::string err;
+    hf_status st = validate(*p, err);
+    if (st != HF_OK) return fail(nullptr, st, err);
+    c.p = *p;
+    if (!build_lattice(*p, c.lat, err)) return fail(nullptr, HF_EINVAL, err);
+    c.L = static_cast<int>(std::lround(p->beta / p->dtau));
+    c.nsite = static_cast<int>(c.lat.rep.size());
+    c.nchain = c.nsite * p->chains_per_site;
+    c.nw = p->n_matsubara;
+    // lattice step: as many (w_n, sigma) matrices per launch as fit in 1 GiB of band buffers
+    const size_t per = hfk::lattice_scratch_per_matrix(c.lat.N, c.lat.b);
+    const size_t cap = (static_cast<size_t>(1) << 30) / (per ? per : 1);
+    c.lat_batch = static_cast<int>(std::max<size_t>(1, std::min<size_t>(2 * c.nw, cap)));
+    return HF_OK;
+}
+
+hfk::QmcProblem make_problem(const hf_ctx& c, int n_warmup, int n_measure, int refresh_first) {
+    hfk::QmcProblem q{};
+    q.L = c.L;
+    q.cps = c.p.chains_per_site;
+    q.nchain = c.nchain;
+    q.block0 = 0;
+    q.seed_lo = static_cast<uint32_t>(c.p.seed & 0xFFFFFFFFull);
+    q.seed_hi = static_cast<uint32_t>(c.p.seed >> 32);
+    q.a_p = c.a_p;
+    q.a_m = c.a_m;
+    q.ev_p = c.ev_p;
+    q.ev_m = c.ev_m;
+    q.af_p = static_cast<float>(c.a_p);
+    q.af_m = static_cast<float>(c.a_m);
+    q.n_warmup = n_warmup;
+    q.n_measure = n_measure;
+    q.refresh_every = c.p.refresh_every;
+    q.bin_size = c.p.bin_size;
+    q.max_bins = c.p.max_bins;
+    q.refresh_first = refresh_first;
+    q.gtau = c.gtau;
+    q.G = c.G;
+    q.Gf = c.Gf;
+    q.s = c.s;
+    q.nsw = c.nsw;
+    q.nmeas = c.nmeas_d;
+    q.acc = c.acc;
+    q.bins = c.bins;
+    q.status = c.status;
+    return q;
+}
+
+hf_status check_status(hf_ctx* c) {
+    int st[4] = {0, 0, 0, 0};
+    HF_CUDA(c, cudaMemcpyAsync(st, c->status, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
+    HF_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (st[0] != 0) {
+        HF_CUDA(c, cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+        return fail(c, static_cast<hf_status>(st[0]),
+                    "device reported a numerical failure (singular Dyson matrix or non-finite value)");
+    }
+    return HF_OK;
+}
+
+hf_status launch_sweeps(hf_ctx* c, int n_warmup, int n_measure, int refresh_first) {
+    hfk::QmcBatch b{};
+    b.nprob = 1;
+    b.p[0] = make_problem(*c, n_warmup, n_measure, refresh_first);
+    cudaError_t e;
+    if (c->p.precision == 0) {
+        const int cpb = hfk::qmc_f64_chains_per_block(c->L);
+        b.nblocks = (c->nchain + cpb - 1) / cpb;
+        e = hfk::launch_qmc_f64(b, hfk::qmc_f64_smem_bytes(c->L), c->stream);
+    } else {
+        const int cpb = hfk::qmc_f32_chains_per_block(c->L);
+        b.nblocks = (c->nchain + cpb - 1) / cpb;
+        e = hfk::launch_qmc_f32(b, hfk::qmc_f32_smem_bytes(c->L), c->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "QMC sweep launch");
+    return HF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hf_status hf_workspace_size(const hf_params* p, size_t* bytes) {
+    if (!bytes) return fail(nullptr, HF_EINVAL, "null bytes pointer");
+    hf_ctx c;
+    hf_status st = setup_sizes(c, p);
+    if (st != HF_OK) return st;
+    *bytes = layout(c, nullptr);
+    return HF_OK;
+}
+
+hf_status hf_init(const hf_params* p, void* d_ws, size_t ws_bytes, hf_ctx** out) {
+    if (!out) return fail(nullptr, HF_EINVAL, "null output handle");
+    *out = nullptr;
+    hf_ctx* c = new (std::nothrow) hf_ctx();
+    if (!c) return fail(nullptr, HF_ENOMEM, "host allocation failed");
+    hf_status st = setup_sizes(*c, p);
+    if (st != HF_OK) { delete c; return st; }
+    const size_t need = layout(*c, nullptr);
+    if (!d_ws || ws_bytes < need) {
+        delete c;
+        return fail(nullptr, HF_ENOMEM, "workspace of " + std::to_string(ws_bytes) +
+                                            " bytes is smaller than the " + std::to_string(need) +
+                                            " bytes needed");
+    }
+    if ((reinterpret_cast<uintptr_t>(d_ws) & 255u) != 0) {
+        delete c;
+        return fail(nullptr, HF_EINVAL, "workspace must be 256-byte aligned");
+    }
+    layout(*c, d_ws);
+    c->stream = static_cast<cudaStream_t>(p->cuda_stream);
+    // a1: Trotter step and Hubbard-Stratonovich coupling (host libm)
+    c->dtau = p->beta / c->L;
+    c->lambda = std::acosh(std::exp(c->dtau * p->U / 2.0));
+    c->a_p = std::exp(-2.0 * c->lambda) - 1.0;
+    c->a_m = std::exp(2.0 * c->lambda) - 1.0;
+    c->ev_p = std::exp(c->lambda) - 1.0;
+    c->ev_m = std::exp(-c->lambda) - 1.0;
+
+    const int N = c->lat.N, bw = c->lat.b + 1, ns = c->nsite, nw = c->nw;
+    std::vector<double> h0(static_cast<size_t>(N) * bw, 0.0);
+    for (int k = 0; k < N; ++k) {
+        h0[static_cast<size_t>(k) * bw] = c->lat.V[k];
+        for (int j : c->lat.nbr[k])
+            if (j > k) h0[static_cast<size_t>(k) * bw + (j - k)] += -p->t;
+    }
+    std::vector<double> c23(static_cast<size_t>(ns) * 2);
+    std::vector<double2> sig(static_cast<size_t>(ns) * 2 * nw);
+    for (int i = 0; i < ns; ++i) {
+        const int r = c->lat.rep[i];
+        const double c2 = c->lat.V[r] - p->mu + p->U / 2.0;
+        c23[2 * i] = c2;
+        c23[2 * i + 1] = c2 * c2 + c->lat.z[r] * p->t * p->t;
+        for (int sp = 0; sp < 2; ++sp) {
+            const double sg = sp == 0 ? 1.0 : -1.0;
+            const double v = p->U / 2.0 - sg * p->h_seed * c->lat.parity[r];
+            for (int n = 0; n < nw; ++n) sig[(static_cast<size_t>(i) * 2 + sp) * nw + n] = make_double2(v, 0.0);
+        }
+    }
+    cudaStream_t st0 = c->stream;
+    auto up = [&](void* dst, const void* src, size_t n) {
+        return cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, st0);
+    };
+    cudaError_t e = up(c->h0band, h0.data(), h0.size() * sizeof(double));
+    if (e == cudaSuccess) e = up(c->rep_of, c->lat.rep_of.data(), N * sizeof(int));
+    if (e == cudaSuccess) e = up(c->flip, c->lat.flip.data(), N * sizeof(int));
+    if (e == cudaSuccess) e = up(c->site_rep, c->lat.site_rep.data(), N * sizeof(int));
+    if (e == cudaSuccess) e = up(c->c23, c23.data(), c23.size() * sizeof(double));
+    if (e == cudaSuccess) e = up(c->sigma, sig.data(), sig.size() * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->gtau, 0, sizeof(double) * ns * 2 * c->L, st0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->nsw, 0, sizeof(uint32_t) * c->nchain, st0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->nmeas_d, 0, sizeof(uint32_t) * c->nchain, st0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->acc, 0, sizeof(unsigned long long) * c->nchain, st0);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(c->bins, 0, sizeof(double) * c->nchain * p->max_bins * (2 * c->L + 3), st0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int) * 4, st0);
+    if (e == cudaSuccess)
+        e = hfk::launch_init_fields(c->s, c->nchain, p->chains_per_site, c->L,
+                                    static_cast<uint32_t>(p->seed & 0xFFFFFFFFull),
+                                    static_cast<uint32_t>(p->seed >> 32), st0);
+    for (int k = 0; k < 9 && e == cudaSuccess; ++k) e = cudaEventCreate(&c->ev[k]);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st0);
+    if (e != cudaSuccess) {
+        std::string m = std::string("hf_init device setup: ") + cudaGetErrorString(e);
+        delete c;
+        return fail(nullptr, HF_ECUDA, m);
+    }
+    *out = c;
+    return HF_OK;
+}
+
+hf_status hf_get_sizes(const hf_ctx* c, int* n_sites, int* n_chains, int* L, int* N) {
+    if (!c) return fail(nullptr, HF_EINVAL, "null context");
+    if (n_sites) *n_sites = c->nsite;
+    if (n_chains) *n_chains = c->nchain;
+    if (L) *L = c->L;
+    if (N) *N = c->lat.N;
+    return HF_OK;
+}
+
+hf_status hf_get_orbits(const hf_ctx* c, int* rep, int* rep_of, int* flip) {
+    if (!c) return fail(nullptr, HF_EINVAL, "null context");
+    if (rep) std::memcpy(rep, c->lat.rep.data(), sizeof(int) * c->nsite);
+    if (rep_of) std::memcpy(rep_of, c->lat.rep_of.data(), sizeof(int) * c->lat.N);
+    if (flip) std::memcpy(flip, c->lat.flip.data(), sizeof(int) * c->lat.N);
+    return HF_OK;
+}
+
+hf_status hf_set_g0(hf_ctx* c, int site, int spin, const double* g0_tau) {
+    if (!c) return fail(nullptr, HF_EINVAL, "null context");
+    if (site < 0 || site >= c->nsite || spin < 0 || spin > 1 || !g0_tau)
+        return fail(c, HF_EINVAL, "hf_set_g0: bad site, spin or pointer");
+    for (int m = 0; m < c->L; ++m)
+        if (!std::isfinite(g0_tau[m])) return fail(c, HF_EINVAL, "hf_set_g0: non-finite bath value");
+    HF_CUDA(c, cudaMemcpyAsync(c->gtau + (static_cast<size_t>(site) * 2 + spin) * c->L, g0_tau,
+                               sizeof(double) * c->L, cudaMemcpyHostToDevice, c->stream));
+    HF_CUDA(c, cudaStreamSynchronize(c->stream));
+    return HF_OK;
+}
+
+hf_status hf_get_g0(hf_ctx* c, double* g0_tau) {
+    if (!c || !g0_tau) return fail(c, HF_EINVAL, "hf_get_g0: null argument");
+    HF_CUDA(c, cudaMemcpyAsync(g0_tau, c->gtau, sizeof(double) * c->nsite * 2 * c->L,
+                               cudaMemcpyDeviceToHost, c->stream));
+    HF_CUDA(c, cudaStreamSynchronize(c->stream));
+    return HF_OK;
+}
+
+hf_status hf_sweep(hf_ctx* c, int n_warmup, int n_measure, int refresh_first) {
+    if (!c) return fail(nullptr, HF_EINVAL, "null context");
+    if (n_warmup < 0 || n_measure < 0) return fail(c, HF_EINVAL, "hf_sweep: negative sweep count");
+    const uint64_t cap = static_cast<uint64_t>(c->p.max_bins) * c->p.bin_size;
+    if (static_cast<uint64_t>(c->nmeas) + n_measure > cap)
+        return fail(c, HF_EINVAL, "hf_sweep: measurements would overflow max_bins * bin_size; "
+                                  "call hf_clear_measurements first");
+    HF_CUDA(c, cudaEventRecord(c->ev[7], c->stream));
+    hf_status st = launch_sweeps(c, n_warmup, n_measure, refresh_first);
+    if (st != HF_OK) return st;
+    HF_CUDA(c, cudaEventRecord(c->ev[8], c->stream));
+    c->ev_sweep = true;
+    c->nmeas += static_cast<uint32_t>(n_measure);
+    return HF_OK;
+}
+
+hf_status hf_clear_measurements(hf_ctx* c) {
+    if (!c) return fail(nullptr, HF_EINVAL, "null context");
+    HF_CUDA(c, cudaMemsetAsync(c->bins, 0, sizeof(double) * c->nchain * c->p.max_bins * (2 * c->L + 3),
+                               c->stream));
+    HF_CUDA(c, cudaMemsetAsync(c->nmeas_d, 0, sizeof(uint32_t) * c->nchain, c->stream));
+    c->nmeas = 0;
+    return HF_OK;
+}
+
+static hf_status reduce_all(hf_ctx* c) {
+    const int nb = static_cast<int>(c->nmeas / c->p.bin_size);
+    cudaError_t e = hfk::launch_reduce(c->bins, c->nsite, c->p.chains_per_site, c->L,
+                                       c->p.max_bins, nb, c->p.bin_size, c->obs_mean, c->obs_err,
+                                       c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "reduction launch");
+    return HF_OK;
+}
+
+hf_status hf_measure(hf_ctx* c, int site, double* gtau, double* n, double* d, double* m,
+                     double* errs) {
+    if (!c) return fail(nullptr, HF_EINVAL, "null context");
+    if (site < 0 || site >= c->nsite) return fail(c, HF_EINVAL, "hf_measure: bad site");
+    hf_status st = reduce_all(c);
+    if (st != HF_OK) return st;
+    const int K = 2 * c->L + 4;
+    std::vector<double> mean(K), err(K);
+    HF_CUDA(c, cudaMemcpyAsync(mean.data(), c->obs_mean + static_cast<size_t>(site) * K,
+                               sizeof(double) * K, cudaMemcpyDeviceToHost, c->stream));
+    HF_CUDA(c, cudaMemcpyAsync(err.data(), c->obs_err + static_cast<size_t>(site) * K,
+                               sizeof(double) * K, cudaMemcpyDeviceToHost, c->stream));
+    st = check_status(c);
+    if (st != HF_OK) return st;
+    const int L = c->L;
+    if (gtau) std::memcpy(gtau, mean.data(), sizeof(double) * 2 * L);
+    if (n) { n[0] = mean[2 * L]; n[1] = mean[2 * L + 1]; }
+    if (d) *d = mean[2 * L + 2];
+    if (m) *m = mean[2 * L + 3];
+    if (errs) std::memcpy(errs, err.data(), sizeof(double) * K);
+    return HF_OK;
+}
+
+hf_status hf_get_observables(hf_ctx* c, double* mean, double* err) {
+    if (!c) return fail(nullptr, HF_EINVAL, "null context");
+    const size_t K = static_cast<size_t>(c->nsite) * (2 * c->L + 4);
+    if (mean) HF_CUDA(c, cudaMemcpyAsync(mean, c->obs_mean, sizeof(double) * K, cudaMemcpyDeviceToHost, c->stream));
+    if (err) HF_CUDA(c, cudaMemcpyAsync(err, c->obs_err, sizeof(double) * K, cudaMemcpyDeviceToHost, c->stream));
+    HF_CUDA(c, cudaStreamSynchronize(c->stream));
+    return HF_OK;
+}
+
+hf_status hf_rdmft_step(hf_ctx* c, double* iter_seconds) {
+    if (!c) return fail(nullptr, HF_EINVAL, "null context");
+    const uint64_t cap = static_cast<uint64_t>(c->p.max_bins) * c->p.bin_size;
+    if (static_cast<uint64_t>(c->p.n_measure) > cap)
+        return fail(c, HF_EINVAL, "hf_rdmft_step: n_measure exceeds max_bins * bin_size");
+    auto t0 = std::chrono::steady_clock::now();
+    HF_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
+    // a9: lattice step, in chunks of lat_batch (w_n, sigma) matrices
+    hfk::LatticeArgs la{};
+    la.N = c->lat.N;
+    la.b = c->lat.b;
+    la.nw = c->nw;
+    la.beta = c->p.beta;
+    la.mu = c->p.mu;
+    la.h0band = c->h0band;
+    la.rep_of = c->rep_of;
+    la.flip = c->flip;
+    la.site_rep = c->site_rep;
+    la.sigma = c->sigma;
+    la.gloc = c->gloc;
+    la.scratch = c->lat_scratch;
+    la.status = c->status;
+    const int nq = 2 * c->nw;
+    for (int q0 = 0; q0 < nq; q0 += c->lat_batch) {
+        cudaError_t e = hfk::launch_lattice(la, q0, std::min(c->lat_batch, nq - q0), c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "lattice step launch");
+    }
+    // Weiss fields and the tau-grid bath
+    hfk::FourierArgs fa{};
+    fa.nsite = c->nsite;
+    fa.L = c->L;
+    fa.nw = c->nw;
+    fa.beta = c->p.beta;
+    fa.U = c->p.U;
+    fa.mix = c->p.mix;
+    fa.c23 = c->c23;
+    fa.gloc = c->gloc;
+    fa.sigma = c->sigma;
+    fa.weiss_inv = c->weiss_inv;
+    fa.gwt = c->gwt;
+    fa.gtau = c->gtau;
+    fa.obs_mean = c->obs_mean;
+    fa.gimp = c->gimp;
+    fa.sigma_new = c->sigma_new;
+    HF_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
+    cudaError_t e = hfk::launch_weiss_tau(fa, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "Weiss-field launch");
+    HF_CUDA(c, cudaEventRecord(c->ev[2], c->stream));
+    // impurities: warm-started chains, fresh bins
+    hf_status st = hf_clear_measurements(c);
+    if (st != HF_OK) return st;
+    HF_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
+    st = launch_sweeps(c, c->p.n_warmup, c->p.n_measure, 1);
+    if (st != HF_OK) return st;
+    HF_CUDA(c, cudaEventRecord(c->ev[4], c->stream));
+    c->nmeas = static_cast<uint32_t>(c->p.n_measure);
+    st = reduce_all(c);
+    if (st != HF_OK) return st;
+    HF_CUDA(c, cudaEventRecord(c->ev[5], c->stream));
+    e = hfk::launch_sigma_update(fa, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "self-energy update launch");
+    HF_CUDA(c, cudaEventRecord(c->ev[6], c->stream));
+    c->ev_rdmft = true;
+    st = check_status(c);
+    if (st != HF_OK) return st;
+    auto t1 = std::chrono::steady_clock::now();
+    if (iter_seconds) *iter_seconds = std::chrono::duration<double>(t1 - t0).count();
+    return HF_OK;
+}
+
+hf_status hf_get_sigma(hf_ctx* c, double* sigma) {
+    if (!c || !sigma) return fail(c, HF_EINVAL, "hf_get_sigma: null argument");
+    HF_CUDA(c, cudaMemcpyAsync(sigma, c->sigma, sizeof(double2) * c->nsite * 2 * c->nw,
+                               cudaMemcpyDeviceToHost, c->stream));
+    HF_CUDA(c, cudaStreamSynchronize(c->stream));
+    return HF_OK;
+}
+
+hf_status hf_set_sigma(hf_ctx* c, const double* sigma) {
+    if (!c || !sigma) return fail(c, HF_EINVAL, "hf_set_sigma: null argument");
+    HF_CUDA(c, cudaMemcpyAsync(c->sigma, sigma, sizeof(double2) * c->nsite * 2 * c->nw,
+                               cudaMemcpyHostToDevice, c->stream));
+    HF_CUDA(c, cudaStreamSynchronize(c->stream));
+    return HF_OK;
+}
+
+hf_status hf_get_gloc(hf_ctx* c, double* gloc) {
+    if (!c || !gloc) return fail(c, HF_EINVAL, "hf_get_gloc: null argument");
+    HF_CUDA(c, cudaMemcpyAsync(gloc, c->gloc, sizeof(double2) * c->nsite * 2 * c->nw,
+                               cudaMemcpyDeviceToHost, c->stream));
+    HF_CUDA(c, cudaStreamSynchronize(c->stream));
+    return HF_OK;
+}
+
+hf_status hf_get_fields(hf_ctx* c, signed char* fields, uint32_t* counters) {
+    if (!c) return fail(nullptr, HF_EINVAL, "null context");
+    if (fields)
+        HF_CUDA(c, cudaMemcpyAsync(fields, c->s, static_cast<size_t>(c->nchain) * c->L,
+                                   cudaMemcpyDeviceToHost, c->stream));
+    if (counters)
+        HF_CUDA(c, cudaMemcpyAsync(counters, c->nsw, sizeof(uint32_t) * c->nchain,
+                                   cudaMemcpyDeviceToHost, c->stream));
+    HF_CUDA(c, cudaStreamSynchronize(c->stream));
+    return HF_OK;
+}
+
+hf_status hf_set_fields(hf_ctx* c, const signed char* fields, const uint32_t* counters) {
+    if (!c) return fail(nullptr, HF_EINVAL, "null context");
+    if (fields) {
+        for (size_t i = 0; i < static_cast<size_t>(c->nchain) * c->L; ++i)
+            if (fields[i] != 1 && fields[i] != -1)
+                return fail(c, HF_EINVAL, "hf_set_fields: fields must be +1 or -1");
+        HF_CUDA(c, cudaMemcpyAsync(c->s, fields, static_cast<size_t>(c->nchain) * c->L,
+                                   cudaMemcpyHostToDevice, c->stream));
+    }
+    if (counters)
+        HF_CUDA(c, cudaMemcpyAsync(c->nsw, counters, sizeof(uint32_t) * c->nchain,
+                                   cudaMemcpyHostToDevice, c->stream));
+    HF_CUDA(c, cudaStreamSynchronize(c->stream));
+    return HF_OK;
+}
+
+hf_status hf_get_green(hf_ctx* c, int chain, double* G) {
+    if (!c || !G) return fail(c, HF_EINVAL, "hf_get_green: null argument");
+    if (chain < 0 || chain >= c->nchain) return fail(c, HF_EINVAL, "hf_get_green: bad chain");
+    const size_t LL = static_cast<size_t>(c->L) * c->L;
+    if (c->p.precision == 0) {
+        HF_CUDA(c, cudaMemcpyAsync(G, c->G + static_cast<size_t>(chain) * 2 * LL, sizeof(double) * 2 * LL,
+                                   cudaMemcpyDeviceToHost, c->stream));
+        HF_CUDA(c, cudaStreamSynchronize(c->stream));
+    } else {
+        std::vector<float> f(2 * LL);
+        HF_CUDA(c, cudaMemcpyAsync(f.data(), c->Gf + static_cast<size_t>(chain) * 2 * LL,
+                                   sizeof(float) * 2 * LL, cudaMemcpyDeviceToHost, c->stream));
+        HF_CUDA(c, cudaStreamSynchronize(c->stream));
+        for (size_t i = 0; i < 2 * LL; ++i) G[i] = f[i];
+    }
+    return HF_OK;
+}
+
+hf_status hf_get_accepts(hf_ctx* c, unsigned long long* accepts) {
+    if (!c || !accepts) return fail(c, HF_EINVAL, "hf_get_accepts: null argument");
+    HF_CUDA(c, cudaMemcpyAsync(accepts, c->acc, sizeof(unsigned long long) * c->nchain,
+                               cudaMemcpyDeviceToHost, c->stream));
+    HF_CUDA(c, cudaStreamSynchronize(c->stream));
+    return HF_OK;
+}
+
+hf_status hf_get_timings(hf_ctx* c, double* ms) {
+    if (!c || !ms) return fail(c, HF_EINVAL, "hf_get_timings: null argument");
+    const int pairs[6][2] = {{0, 1}, {1, 2}, {3, 4}, {4, 5}, {5, 6}, {7, 8}};
+    for (int k = 0; k < 6; ++k) {
+        ms[k] = -1.0;
+        const bool have = (k < 5) ? c->ev_rdmft : c->ev_sweep;
+        if (!have) continue;
+        HF_CUDA(c, cudaEventSynchronize(c->ev[pairs[k][1]]));
+        float t = 0.0f;
+        HF_CUDA(c, cudaEventElapsedTime(&t, c->ev[pairs[k][0]], c->ev[pairs[k][1]]));
+        ms[k] = t;
+    }
+    return HF_OK;
+}
+
+void hf_free(hf_ctx* c) { delete c; }
+
+const char* hf_last_error(const hf_ctx* c) {
+    return c ? c->err.c_str() : g_init_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+// hf_internal.cuh -- shared declarations of the sm_103a Hirsch-Fye QMC / RDMFT library.
+//
+// Device state of one context lives in a caller-owned workspace; the kernels below are
+// launched only by hf_api.cu.  Conventions follow include/hf.h (positive Green functions,
+// spin 0 = up).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/hf.h"
+
+namespace hfk {
+
+constexpr int kMaxProblems = 8;     // problems fused into one QMC launch
+constexpr int kBlock = 128;         // threads per QMC block (4 warps)
+constexpr int kMaxL64 = 64;         // largest slice count of the FP64 sweep
+constexpr int kMaxL32 = 128;        // largest slice count of the FP32 sweep
+
+// ---------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): counter-based generator keyed by
+// (seed_lo, seed_hi); the counter of proposal (sweep w, slice l) of chain c of site i is
+// (w, l, c, i); sweep 0xFFFFFFFF draws the initial fields.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 ctr, uint2 key) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            key.x += 0x9E3779B9u;
+            key.y += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, ctr.x);
+        const uint32_t lo0 = 0xD2511F53u * ctr.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, ctr.z);
+        const uint32_t lo1 = 0xCD9E8D57u * ctr.z;
+        ctr = make_uint4(hi1 ^ ctr.y ^ key.x, lo1, hi0 ^ ctr.w ^ key.y, lo0);
+    }
+    return ctr;
+}
+
+// 53-bit uniform in [0, 1): ((x << 32 | y) >> 11) * 2^-53.
+__device__ __forceinline__ double uniform53(uint4 x) {
+    const unsigned long long bits =
+        ((static_cast<unsigned long long>(x.x) << 32) | x.y) >> 11;
+    return static_cast<double>(bits) * 0x1p-53;
+}
+
+// 24-bit uniform in [0, 1) for the single-precision sweep: (x >> 8) * 2^-24.
+__device__ __forceinline__ float uniform24(uint4 x) {
+    return static_cast<float>(x.x >> 8) * 0x1p-24f;
+}
+
+// ---------------------------------------------------------------------------------------
+// One QMC problem (one context) as seen by the fused sweep kernel.
+// ---------------------------------------------------------------------------------------
+struct QmcProblem {
+    int L;                // time slices
+    int cps;              // chains per inequivalent site
+    int nchain;           // chains of this problem
+    int block0;           // first block of this problem in the launch
+    uint32_t seed_lo, seed_hi;
+    double a_p, a_m;      // e^{-2 lambda} - 1 (sigma s_l = +1), e^{+2 lambda} - 1 (= -1)
+    double ev_p, ev_m;    // e^{+lambda} - 1, e^{-lambda} - 1 (Dyson factors, sigma s = +-1)
+    float af_p, af_m;     // single-precision copies of a_p, a_m
+    int n_warmup, n_measure, refresh_every, bin_size, max_bins, refresh_first;
+    const double* gtau;   // [nsite][2][L]  bath g~0(tau_m)
+    double* G;            // [nchain][2][L*L] (FP64 state, or FP64 scratch of the FP32 path)
+    float* Gf;            // [nchain][2][L*L] FP32 state (precision 1) or nullptr
+    int8_t* s;            // [nchain][L]
+    uint32_t* nsw;        // [nchain] sweeps done
+    uint32_t* nmeas;      // [nchain] measurements since the last clear
+    unsigned long long* acc;  // [nchain] accepted flips
+    double* bins;         // [nchain][max_bins][2L+3]
+    int* status;          // [0]: error code (HF_ENUMERIC...), [1]: non-positive ratios seen
+};
+
+struct QmcBatch {
+    int nprob;
+    int nblocks;
+    QmcProblem p[kMaxProblems];
+};
+
+// Dynamic shared memory a block of the FP64 sweep needs for slice count L.
+size_t qmc_f64_smem_bytes(int L);
+bool qmc_f64_supported(int L);
+cudaError_t launch_qmc_f64(const QmcBatch& b, size_t smem, cudaStream_t st);
+int qmc_f64_chains_per_block(int L);
+
+size_t qmc_f32_smem_bytes(int L);
+bool qmc_f32_supported(int L);
+cudaError_t launch_qmc_f32(const QmcBatch& b, size_t smem, cudaStream_t st);
+int qmc_f32_chains_per_block(int L);
+cudaError_t launch_refresh_f64(const QmcProblem& p, int use_state_fields, cudaStream_t st);
+
+cudaError_t launch_init_fields(int8_t* s, int nchain, int cps, int L, uint32_t seed_lo,
+                               uint32_t seed_hi, cudaStream_t st);
+
+// Reduction of bins over chains: out_mean/out_err [nsite][2L+4].
+cudaError_t launch_reduce(const double* bins, int nsite, int cps, int L, int max_bins,
+                          int nbins_done, int bin_size, double* out_mean, double* out_err,
+                          cudaStream_t st);
+
+}  // namespace hfk

@@ -1,0 +1,43 @@
+// k_lattice.cuh -- arguments of the lattice-step (eq. 2) and transform kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace hfk {
+
+struct LatticeArgs {
+    int N, b, nw;             // lattice sites, band half-width, Matsubara frequencies
+    double beta, mu;
+    const double* h0band;     // [N][b+1]: H0[k+d][k] (d = 0: trap potential V_k)
+    const int* rep_of;        // [N] inequivalent index of each site
+    const int* flip;          // [N] 1: spins exchanged relative to the representative
+    const int* site_rep;      // [N] inequivalent index if the site is a representative, else -1
+    const double2* sigma;     // [nsite][2][nw]
+    double2* gloc;            // [nsite][2][nw] output G_ii of the representatives
+    double2* scratch;         // [nq][N][b+1] band factors of the matrices in flight
+    int* status;
+};
+
+size_t lattice_smem_per_warp(int b);
+int lattice_warps_per_block(int b);
+size_t lattice_scratch_per_matrix(int N, int b);
+cudaError_t launch_lattice(const LatticeArgs& a, int q0, int nq, cudaStream_t st);
+
+struct FourierArgs {
+    int nsite, L, nw;
+    double beta, U, mix;
+    const double* c23;        // [nsite][2]: tail coefficients c2, c3 of the shifted bath
+    const double2* gloc;      // [nsite][2][nw]
+    double2* sigma;           // [nsite][2][nw] (read, then mixed in place)
+    double2* weiss_inv;       // [nsite][2][nw]  1/G0 = 1/G_ii + Sigma
+    double2* gwt;             // [nsite][2][nw]  G~0 = 1/(1/G0 - U/2)
+    double* gtau;             // [nsite][2][L]   g~0(tau_m)
+    const double* obs_mean;   // [nsite][2L+4]   measured G(tau_m) (first 2L entries)
+    double2* gimp;            // [nsite][2][nw]  impurity G(i w_n)
+    double2* sigma_new;       // [nsite][2][nw]  unmixed 1/G0 - 1/G_imp
+};
+
+cudaError_t launch_weiss_tau(const FourierArgs& a, cudaStream_t st);
+cudaError_t launch_sigma_update(const FourierArgs& a, cudaStream_t st);
+
+}  // namespace hfk

@@ -1,0 +1,444 @@
+// k_qmc_f64.cu -- FP64 Hirsch-Fye QMC sweeps, resident in shared memory (sm_103a).
+//
+// One "team" (one warp for L <= 32, the whole 4-warp block for L > 32) owns one Markov chain
+// for the whole launch: its G_up, G_dn (L x L, FP64) stay in shared memory through
+// n_warmup + n_measure sweeps.  Per slice l of a sweep ("Model and Methods": Hirsch-Fye at
+// fixed dtau, with the single-flip ratio, Metropolis acceptance and Sherman-Morrison update):
+//     R_sigma = 1 + (1 - G_sigma[l][l]) (e^{-2 lambda sigma s_l} - 1),  accept iff u < R_up R_dn,
+//     G_sigma += (a_sigma / R_sigma) (G_sigma[:, l] - e_l) G_sigma[l, :].
+// The bath matrix g0[l][l'] = g~0(tau_l - tau_l') (antiperiodic) is never stored: the Dyson
+// refresh G = [1 + (1 - g0)(e^V - 1)]^{-1} g0 builds it on the fly from g~0(tau_m), factors
+// the matrix by Gaussian elimination with partial pivoting in shared memory and runs after
+// every refresh_every-th sweep of the chain.  Measured sweeps accumulate G(tau_m), n_sigma and
+// the double occupancy into the chain's current bin.
+//
+// GB300 has ~1 TFLOP/s of FP64 (DFMA and DMMA alike, 72x below FFMA), so this kernel is bound
+// by the FP64 pipe; it keeps the pipe busy with 12 chains per SM and issues no FP64 work that
+// the method does not need (the index arithmetic stays on the integer pipe).
+#include "hf_internal.cuh"
+
+namespace hfk {
+namespace {
+
+template <int TW>
+__device__ __forceinline__ void team_sync() {
+    if constexpr (TW == 1) {
+        __syncwarp();
+    } else {
+        __syncthreads();
+    }
+}
+
+// Shared-memory footprint of one team (bytes), 16-byte granular.
+__host__ __device__ constexpr size_t team_bytes(int L) {
+    return static_cast<size_t>(2 * L * L + 7 * L + 11) * 8 + 16 + ((L + 15) / 16) * 16;
+}
+
+template <int L>
+struct TeamSmem {
+    double* G0;    // [L*L]
+    double* G1;    // [L*L]
+    double* cr;    // [4L]: scaled column up/down, row up/down; refresh: multipliers, 1/pivot
+    double* u;     // [L]
+    double* bacc;  // [2L+3] current bin
+    double* red;   // [8]
+    int* piv;      // [4]
+    int8_t* s;     // [L]
+    __device__ explicit TeamSmem(unsigned char* base) {
+        double* d = reinterpret_cast<double*>(base);
+        G0 = d;
+        G1 = G0 + L * L;
+        cr = G1 + L * L;
+        u = cr + 4 * L;
+        bacc = u + L;
+        red = bacc + 2 * L + 3;
+        piv = reinterpret_cast<int*>(red + 8);
+        s = reinterpret_cast<int8_t*>(piv + 4);
+    }
+};
+
+// |x| ordering through the bit pattern (integer pipe): larger magnitude -> larger key.
+__device__ __forceinline__ unsigned long long mag_key(double x) {
+    return static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// Build A = 1 + (1 - g0) diag(e^{lambda sigma s_j} - 1) into A and g0 into B.
+template <int L, int TW>
+__device__ void build_dyson(const QmcProblem& P, const double* gt, const int8_t* s, int sigma,
+                            double* A, double* B, int tid) {
+    constexpr int T = 32 * TW;
+    for (int e = tid; e < L * L; e += T) {
+        const int i = e / L, j = e - (e / L) * L;
+        const int d = i - j;
+        const double g = (d >= 0) ? gt[d] : -gt[d + L];
+        const double ev = (sigma * s[j] > 0) ? P.ev_p : P.ev_m;
+        const double one = (i == j) ? 1.0 : 0.0;
+        A[e] = __dadd_rn(one, __dmul_rn(__dadd_rn(one, -g), ev));
+        B[e] = g;
+    }
+}
+
+// Solve A X = B in place (X overwrites B) by Gaussian elimination with partial pivoting.
+// Returns false if a pivot is exactly zero.
+template <int L, int TW>
+__device__ bool solve_dyson(double* A, double* B, double* f, int* piv, int tid) {
+    constexpr int T = 32 * TW;
+    bool ok = true;
+    for (int k = 0; k < L; ++k) {
+        if (tid < 32) {
+            unsigned long long best = 0ull;
+            int bi = L;  // sentinel: nothing found yet
+            for (int i = k + tid; i < L; i += 32) {
+                const unsigned long long key = mag_key(A[i * L + k]);
+                if (bi == L || key > best) {
+                    best = key;
+                    bi = i;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                // larger magnitude wins; ties go to the smaller row (first maximum)
+                if (oi != L && (bi == L || ob > best || (ob == best && oi < bi))) {
+                    best = ob;
+                    bi = oi;
+                }
+            }
+            if (tid == 0) {
+                piv[0] = bi;
+                piv[1] = (best == 0ull) ? 1 : 0;
+            }
+        }
+        team_sync<TW>();
+        const int p = piv[0];
+        if (piv[1]) ok = false;
+        if (p != k) {
+            for (int j = tid; j < 2 * L; j += T) {
+                double* M = (j < L) ? A : B;
+                const int jj = (j < L) ? j : j - L;
+                const double t = M[k * L + jj];
+                M[k * L + jj] = M[p * L + jj];
+                M[p * L + jj] = t;
+            }
+        }
+        team_sync<TW>();
+        const double inv = 1.0 / A[k * L + k];
+        for (int i = k + 1 + tid; i < L; i += T) f[i] = A[i * L + k] * inv;
+        team_sync<TW>();
+        // rows i > k of [A | B]: subtract f_i times row k (A columns j > k only)
+        const int rows = L - 1 - k;
+        for (int e = tid; e < rows * 2 * L; e += T) {
+            const int r = e / (2 * L);
+            const int j = e - r * (2 * L);
+            const int i = k + 1 + r;
+            if (j < L) {
+                if (j > k) A[i * L + j] = fma(-f[i], A[k * L + j], A[i * L + j]);
+            } else {
+                const int jj = j - L;
+                B[i * L + jj] = fma(-f[i], B[k * L + jj], B[i * L + jj]);
+            }
+        }
+        team_sync<TW>();
+    }
+    // back substitution, one column of B per thread (columns are independent)
+    for (int c = tid; c < L; c += T) {
+        for (int i = L - 1; i >= 0; --i) {
+            double acc = B[i * L + c];
+            for (int j = i + 1; j < L; ++j) acc = fma(-A[i * L + j], B[j * L + c], acc);
+            B[i * L + c] = acc / A[i * L + i];
+        }
+    }
+    team_sync<TW>();
+    return ok;
+}
+
+// Dyson refresh of both spins.  A_up is built in G1's buffer and G_up solved in G0; G_up is
+// parked in the chain's global G slot while A_dn (in G0) and G_dn (in G1) are formed, then
+// brought back.  Every thread reads back exactly the elements it parked.
+template <int L, int TW>
+__device__ void refresh_both(const QmcProblem& P, const TeamSmem<L>& S, const double* gt,
+                             double* Gg, int tid) {
+    constexpr int T = 32 * TW;
+    build_dyson<L, TW>(P, gt, S.s, +1, S.G1, S.G0, tid);
+    team_sync<TW>();
+    bool ok = solve_dyson<L, TW>(S.G1, S.G0, S.cr, S.piv, tid);
+    for (int e = tid; e < L * L; e += T) Gg[e] = S.G0[e];
+    team_sync<TW>();
+    build_dyson<L, TW>(P, gt + L, S.s, -1, S.G0, S.G1, tid);
+    team_sync<TW>();
+    ok = solve_dyson<L, TW>(S.G0, S.G1, S.cr, S.piv, tid) && ok;
+    for (int e = tid; e < L * L; e += T) S.G0[e] = Gg[e];
+    team_sync<TW>();
+    if (!ok && tid == 0) atomicExch(P.status, static_cast<int>(HF_ENUMERIC));
+}
+
+// Accumulate one measurement into bacc.
+template <int L, int TW>
+__device__ void measure(const TeamSmem<L>& S, int tid) {
+    constexpr int T = 32 * TW;
+    // G(tau_m) = (1/L) sum_l sgn G[(l+m) mod L][l]; thread m walks l in a skewed order so that
+    // the 32 lanes of a warp hit different banks.
+    for (int m = tid; m < L; m += T) {
+        double s0 = 0.0, s1 = 0.0;
+        for (int q = 0; q < L; ++q) {
+            int l = q + m;
+            if (l >= L) l -= L;
+            int r = l + m;
+            const bool wrap = r >= L;
+            if (wrap) r -= L;
+            const double x0 = S.G0[r * L + l], x1 = S.G1[r * L + l];
+            s0 = wrap ? s0 - x0 : s0 + x0;
+            s1 = wrap ? s1 - x1 : s1 + x1;
+        }
+        S.bacc[m] += s0 / L;
+        S.bacc[L + m] += s1 / L;
+    }
+    double nu = 0.0, nd = 0.0, db = 0.0;
+    for (int l = tid; l < L; l += T) {
+        const double a = 1.0 - S.G0[l * L + l];
+        const double b = 1.0 - S.G1[l * L + l];
+        nu += a;
+        nd += b;
+        db += a * b;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        nu += __shfl_xor_sync(0xffffffffu, nu, o);
+        nd += __shfl_xor_sync(0xffffffffu, nd, o);
+        db += __shfl_xor_sync(0xffffffffu, db, o);
+    }
+    if constexpr (TW > 1) {
+        const int w = tid >> 5;
+        if ((tid & 31) == 0) {
+            S.red[w] = nu;          // red has 8 slots; TW <= 4 uses red[0..3] and cr[0..7]
+            S.cr[w] = nd;
+            S.cr[4 + w] = db;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            nu = 0.0;
+            nd = 0.0;
+            db = 0.0;
+            for (int w2 = 0; w2 < TW; ++w2) {
+                nu += S.red[w2];
+                nd += S.cr[w2];
+                db += S.cr[4 + w2];
+            }
+        }
+    }
+    if (tid == 0) {
+        S.bacc[2 * L + 0] += nu / L;
+        S.bacc[2 * L + 1] += nd / L;
+        S.bacc[2 * L + 2] += db / L;
+    }
+    team_sync<TW>();
+}
+
+template <int L, int TW>
+__device__ void qmc_chain(const QmcProblem& P, int c, unsigned char* base, int tid) {
+    constexpr int T = 32 * TW;
+    constexpr int LL = L * L;
+    constexpr int W = 2 * L + 3;
+    const TeamSmem<L> S(base);
+    const int site = c / P.cps;
+    const int ch = c - site * P.cps;
+    const double* gt = P.gtau + static_cast<size_t>(site) * 2 * L;
+    double* Gg = P.G + static_cast<size_t>(c) * 2 * LL;
+    const uint2 key = make_uint2(P.seed_lo, P.seed_hi);
+
+    for (int l = tid; l < L; l += T) S.s[l] = P.s[static_cast<size_t>(c) * L + l];
+    uint32_t nsw = P.nsw[c];
+    uint32_t nmeas = P.nmeas[c];
+    unsigned long long acc = 0ull;
+    int cur_bin = static_cast<int>(nmeas / P.bin_size);
+    double* bins_c = P.bins + static_cast<size_t>(c) * P.max_bins * W;
+    for (int k = tid; k < W; k += T)
+        S.bacc[k] = (cur_bin < P.max_bins) ? bins_c[static_cast<size_t>(cur_bin) * W + k] : 0.0;
+    team_sync<TW>();
+    if (P.refresh_first) {
+        refresh_both<L, TW>(P, S, gt, Gg, tid);
+    } else {
+        for (int e = tid; e < LL; e += T) {
+            S.G0[e] = Gg[e];
+            S.G1[e] = Gg[LL + e];
+        }
+        team_sync<TW>();
+    }
+
+    const int nsweeps = P.n_warmup + P.n_measure;
+    for (int k = 0; k < nsweeps; ++k) {
+        for (int l = tid; l < L; l += T)
+            S.u[l] = uniform53(philox4x32_10(make_uint4(nsw, static_cast<uint32_t>(l),
+                                                        static_cast<uint32_t>(ch),
+                                                        static_cast<uint32_t>(site)), key));
+        team_sync<TW>();
+        for (int l = 0; l < L; ++l) {
+            const double g0 = S.G0[l * L + l];
+            const double g1 = S.G1[l * L + l];
+            const int sl = S.s[l];
+            const double au = (sl > 0) ? P.a_p : P.a_m;   // up:   sigma s_l = +s_l
+            const double ad = (sl > 0) ? P.a_m : P.a_p;   // down: sigma s_l = -s_l
+            const double Ru = __dadd_rn(1.0, __dmul_rn(__dadd_rn(1.0, -g0), au));
+            const double Rd = __dadd_rn(1.0, __dmul_rn(__dadd_rn(1.0, -g1), ad));
+            const double p = __dmul_rn(Ru, Rd);
+            if (!(p > 0.0) && tid == 0) atomicAdd(P.status + 1, 1);
+            if (S.u[l] < p) {
+                const double fu = au / Ru;
+                const double fd = ad / Rd;
+                for (int i = tid; i < L; i += T) {
+                    const double one = (i == l) ? 1.0 : 0.0;
+                    S.cr[i] = fu * (S.G0[i * L + l] - one);
+                    S.cr[L + i] = fd * (S.G1[i * L + l] - one);
+                    S.cr[2 * L + i] = S.G0[l * L + i];
+                    S.cr[3 * L + i] = S.G1[l * L + i];
+                }
+                team_sync<TW>();
+                if constexpr (T % L == 0) {
+                    // every thread stays on one column j: keep the row entries in registers
+                    const int j = tid % L;
+                    const double r0 = S.cr[2 * L + j], r1 = S.cr[3 * L + j];
+#pragma unroll 8
+                    for (int i = tid / L; i < L; i += T / L) {
+                        S.G0[i * L + j] = fma(S.cr[i], r0, S.G0[i * L + j]);
+                        S.G1[i * L + j] = fma(S.cr[L + i], r1, S.G1[i * L + j]);
+                    }
+                } else {
+                    int i = tid / L, j = tid - (tid / L) * L;
+#pragma unroll 4
+                    for (int e = tid; e < LL; e += T) {
+                        S.G0[e] = fma(S.cr[i], S.cr[2 * L + j], S.G0[e]);
+                        S.G1[e] = fma(S.cr[L + i], S.cr[3 * L + j], S.G1[e]);
+                        i += T / L;
+                        j += T % L;
+                        if (j >= L) {
+                            j -= L;
+                            ++i;
+                        }
+                    }
+                }
+                team_sync<TW>();
+                if (tid == 0) S.s[l] = static_cast<int8_t>(-sl);
+                ++acc;
+            }
+        }
+        ++nsw;
+        team_sync<TW>();
+        if (P.refresh_every > 0 && (nsw % static_cast<uint32_t>(P.refresh_every)) == 0u)
+            refresh_both<L, TW>(P, S, gt, Gg, tid);
+        if (k >= P.n_warmup) {
+            measure<L, TW>(S, tid);
+            ++nmeas;
+            if (nmeas % static_cast<uint32_t>(P.bin_size) == 0u) {
+                const int b = static_cast<int>(nmeas / P.bin_size) - 1;
+                for (int q = tid; q < W; q += T) {
+                    if (b < P.max_bins) bins_c[static_cast<size_t>(b) * W + q] = S.bacc[q];
+                    S.bacc[q] = 0.0;
+                }
+                team_sync<TW>();
+            }
+        }
+    }
+
+    // write the state back
+    cur_bin = static_cast<int>(nmeas / P.bin_size);
+    for (int q = tid; q < W; q += T)
+        if (cur_bin < P.max_bins) bins_c[static_cast<size_t>(cur_bin) * W + q] = S.bacc[q];
+    for (int e = tid; e < LL; e += T) {
+        Gg[e] = S.G0[e];
+        Gg[LL + e] = S.G1[e];
+    }
+    for (int l = tid; l < L; l += T) P.s[static_cast<size_t>(c) * L + l] = S.s[l];
+    if (tid == 0) {
+        P.nsw[c] = nsw;
+        P.nmeas[c] = nmeas;
+        P.acc[c] += acc;
+    }
+}
+
+template <int L>
+__device__ void run_block(const QmcProblem& P, int blk, unsigned char* smem) {
+    if constexpr (L <= 32) {
+        // four chains per block, one warp each
+        const int warp = threadIdx.x >> 5;
+        const int c = blk * 4 + warp;
+        if (c < P.nchain)
+            qmc_chain<L, 1>(P, c, smem + warp * team_bytes(L), threadIdx.x & 31);
+    } else {
+        if (blk < P.nchain) qmc_chain<L, 4>(P, blk, smem, threadIdx.x);
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) qmc_f64_kernel(const __grid_constant__ QmcBatch B) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    int pi = 0;
+    while (pi + 1 < B.nprob && static_cast<int>(blockIdx.x) >= B.p[pi + 1].block0) ++pi;
+    const QmcProblem& P = B.p[pi];
+    const int blk = static_cast<int>(blockIdx.x) - P.block0;
+    switch (P.L) {
+        case 8: run_block<8>(P, blk, smem); break;
+        case 12: run_block<12>(P, blk, smem); break;
+        case 16: run_block<16>(P, blk, smem); break;
+        case 20: run_block<20>(P, blk, smem); break;
+        case 24: run_block<24>(P, blk, smem); break;
+        case 32: run_block<32>(P, blk, smem); break;
+        case 40: run_block<40>(P, blk, smem); break;
+        case 48: run_block<48>(P, blk, smem); break;
+        case 64: run_block<64>(P, blk, smem); break;
+        default: break;
+    }
+}
+
+__global__ void init_fields_kernel(int8_t* s, int nchain, int cps, int L, uint32_t seed_lo,
+                                   uint32_t seed_hi) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nchain * L) return;
+    const int c = idx / L, l = idx - (idx / L) * L;
+    const int site = c / cps, ch = c - (c / cps) * cps;
+    const uint4 x = philox4x32_10(make_uint4(0xFFFFFFFFu, static_cast<uint32_t>(l),
+                                             static_cast<uint32_t>(ch),
+                                             static_cast<uint32_t>(site)),
+                                  make_uint2(seed_lo, seed_hi));
+    s[idx] = (x.x >> 31) ? static_cast<int8_t>(-1) : static_cast<int8_t>(1);
+}
+
+}  // namespace
+
+bool qmc_f64_supported(int L) {
+    switch (L) {
+        case 8: case 12: case 16: case 20: case 24: case 32: case 40: case 48: case 64:
+            return true;
+        default:
+            return false;
+    }
+}
+
+int qmc_f64_chains_per_block(int L) { return L <= 32 ? 4 : 1; }
+
+size_t qmc_f64_smem_bytes(int L) {
+    return L <= 32 ? 4 * team_bytes(L) : team_bytes(L);
+}
+
+cudaError_t launch_qmc_f64(const QmcBatch& b, size_t smem, cudaStream_t st) {
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(qmc_f64_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(4 * team_bytes(32) + 1024));
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    if (b.nblocks <= 0) return cudaSuccess;
+    qmc_f64_kernel<<<b.nblocks, kBlock, smem, st>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_fields(int8_t* s, int nchain, int cps, int L, uint32_t seed_lo,
+                               uint32_t seed_hi, cudaStream_t st) {
+    const int n = nchain * L;
+    if (n <= 0) return cudaSuccess;
+    init_fields_kernel<<<(n + 255) / 256, 256, 0, st>>>(s, nchain, cps, L, seed_lo, seed_hi);
+    return cudaGetLastError();
+}
+
+}  // namespace hfk

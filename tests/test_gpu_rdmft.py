@@ -1,0 +1,112 @@
+"""Parity of the CUDA RDMFT iteration (lattice step, transforms, impurities, self-energy)
+with the CPU oracle, through the C ABI.
+
+Bars: orbit tables bit-exact; lattice step G_ii(i w_n) within 1e-12 relative; bath g~0(tau)
+within 1e-12; impurity decisions identical; observables within 1e-10; self-energy within 1e-9
+relative (it divides by the measured Green function).
+"""
+import numpy as np
+import pytest
+
+from oracle.lattice import Lattice, lattice_step
+from oracle.rdmft import RDMFT
+from paper_1006_2716_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hf():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_1006_2716_gb300 import build as B
+
+    B.build()
+    from paper_1006_2716_gb300 import hf as H
+
+    return H
+
+
+def _oracle_for(cfg):
+    L = int(round(cfg["beta"] / cfg["dtau"]))
+    return RDMFT(cfg["Lx"], cfg.get("Ly"), geometry=cfg.get("geometry", 0),
+                 periodic=bool(cfg.get("periodic", 0)), t=cfg.get("t", 1.0), U=cfg["U"],
+                 V0=cfg["V0"], mu=cfg["mu"], beta=cfg["beta"], L=L, nw=cfg["n_matsubara"],
+                 chains=cfg["chains_per_site"], seed=cfg["seed"], h_seed=cfg["h_seed"],
+                 mix=cfg["mix"], n_warmup=cfg["n_warmup"], n_measure=cfg["n_measure"],
+                 refresh_every=cfg["refresh_every"], bin_size=cfg["bin_size"])
+
+
+@pytest.mark.parametrize("Lx,geom", [(6, 0), (20, 0), (30, 0), (40, 1), (7, 1)])
+def test_orbit_tables_bit_exact(hf, Lx, geom):
+    cfg = dict(wl.CONFIGS["square6"], Lx=Lx, Ly=Lx, geometry=geom, n_matsubara=4,
+               chains_per_site=1)
+    p = hf.make_params(cfg)
+    # sizes and orbit tables are host-side: a tiny context is enough
+    ctx = hf.Context(p)
+    rep, rep_of, flip = hf.hf_get_orbits(ctx.handle, ctx.n_sites, ctx.N)
+    lat = Lattice(Lx, Lx if geom == 0 else None, geometry=geom)
+    r2, ro2, f2 = lat.orbits()
+    assert np.array_equal(rep, r2) and np.array_equal(rep_of, ro2) and np.array_equal(flip, f2)
+    ctx.close()
+
+
+def test_rdmft_iteration_square6_full(hf):
+    """The 6x6 trap (U=4, V0=0.1, mu=2, beta=4, L=16), 1 chain/site, 500 + 2000 sweeps: two
+    complete iterations, each compared step by step with the oracle."""
+    cfg = dict(wl.CONFIGS["square6"])
+    ctx = hf.Context(hf.make_params(cfg))
+    ref = _oracle_for(cfg)
+    L, ns, nw = ctx.L, ctx.n_sites, ctx.nw
+    for it in range(2):
+        hf.hf_rdmft_step(ctx.handle)
+        mean, err = ref.iterate()
+        gloc = hf.hf_get_gloc(ctx.handle, ns, nw)
+        g0 = hf.hf_get_g0(ctx.handle, ns, L)
+        assert np.abs(gloc - ref.last["Gloc"]).max() < 1e-12 * np.abs(ref.last["Gloc"]).max()
+        assert np.abs(g0 - ref.last["g0_tau"][:, :, :L]).max() < 1e-12
+        f, cnt = hf.hf_get_fields(ctx.handle, ctx.n_chains, L)
+        assert np.array_equal(f, ref.fields.reshape(ctx.n_chains, L)), "iteration %d" % it
+        assert np.all(cnt == (it + 1) * 2500)
+        m_gpu, e_gpu = hf.hf_get_observables(ctx.handle, ns, L)
+        assert np.abs(m_gpu[:, :2 * L + 3] - mean).max() < 1e-10
+        assert np.abs(e_gpu[:, :2 * L + 3] - err).max() < 1e-10
+        sig = hf.hf_get_sigma(ctx.handle, ns, nw)
+        assert np.abs(sig - ref.sigma).max() < 1e-9 * np.abs(ref.sigma).max()
+    ctx.close()
+
+
+def test_lattice_step_square20_sampled_frequencies(hf):
+    """The 20x20 trap (N = 400, band half-width 20): one iteration's lattice step from the
+    seeded self-energy, every site of the sampled frequencies against a dense inverse."""
+    cfg = dict(wl.CONFIGS["square20"], chains_per_site=1, n_warmup=1, n_measure=2, bin_size=1,
+               max_bins=2)
+    ctx = hf.Context(hf.make_params(cfg))
+    hf.hf_rdmft_step(ctx.handle)
+    gloc = hf.hf_get_gloc(ctx.handle, ctx.n_sites, ctx.nw)
+    ref = _oracle_for(cfg)
+    full = ref.expand_sigma()
+    idx = np.array([0, 1, 57, 250, 499])
+    for sp in range(2):
+        g = lattice_step(ref.lat.H0, cfg["mu"], cfg["beta"], full[sp][idx], n_index=idx)
+        want = g[:, ref.reps]
+        got = gloc[:, sp, idx].T
+        assert np.abs(got - want).max() < 1e-12 * np.abs(want).max()
+    ctx.close()
+
+
+def test_lattice_step_disc_all_frequencies(hf):
+    """Site-centred disc (radius 6, N = 113): band from the row numbering of a disc."""
+    cfg = dict(wl.CONFIGS["square6"], Lx=6, geometry=1, V0=0.08, mu=1.0, n_matsubara=40,
+               chains_per_site=1, n_warmup=1, n_measure=2, bin_size=1, max_bins=2)
+    ctx = hf.Context(hf.make_params(cfg))
+    hf.hf_rdmft_step(ctx.handle)
+    gloc = hf.hf_get_gloc(ctx.handle, ctx.n_sites, ctx.nw)
+    ref = _oracle_for(cfg)
+    full = ref.expand_sigma()
+    for sp in range(2):
+        want = lattice_step(ref.lat.H0, cfg["mu"], cfg["beta"], full[sp])[:, ref.reps]
+        assert np.abs(gloc[:, sp, :].T - want).max() < 1e-12 * np.abs(want).max()
+    ctx.close()
