@@ -147,6 +147,27 @@ hf_status hf_get_accepts(hf_ctx* ctx, unsigned long long* accepts);
  * sweeps of the last hf_sweep.  A phase that has not run yet reads -1.  Synchronises. */
 hf_status hf_get_timings(hf_ctx* ctx, double* ms);
 
+/* Allocation-free lattice step.  The paper has no counterpart: this exists for callers that
+ * cannot allocate device memory at call time -- code running where a cudaMalloc would
+ * synchronise the device or is forbidden (inside a latency-critical loop, or under a host
+ * framework whose allocator owns all device memory and only hands out the caller's own input and
+ * output buffers).  It computes exactly what the lattice phase of hf_rdmft_step computes,
+ * G_ii(i w_n) = [(i w_n + mu) 1 - H0 - Sigma(i w_n)]^{-1}_ii of the inequivalent sites for every
+ * frequency and spin, but keeps its band buffers in a fixed 16 MiB device array inside the
+ * library instead of the workspace.
+ *   d_sigma: device, [n_sites][2][n_matsubara] complex (re, im interleaved), read only.
+ *   d_gloc:  device, same layout, written.
+ * The lattice tables come from ctx; work is queued on the context stream and the call
+ * synchronises it.  It allocates nothing (no cudaMalloc/cudaFree, no library allocator).
+ * Limits and sharing: a lattice whose band (N * (b + 1) * 16 bytes, b = band half-width) exceeds
+ * 16 MiB is rejected with HF_EINVAL; frequencies are processed in chunks that fit.  Every GPU
+ * that loads the library holds the 16 MiB until the process exits.  All calls share the one
+ * array, which keeps the last call's contents (every element is rewritten before it is read, so
+ * nothing needs clearing); calls that overlap on the GPU -- e.g. from two streams -- race.  The
+ * first call on a device looks the array's device address up (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture. */
+hf_status hf_lattice_step_noalloc(hf_ctx* ctx, const double* d_sigma, double* d_gloc);
+
 /* Release the host handle (the device workspace stays the caller's). */
 void hf_free(hf_ctx* ctx);
 

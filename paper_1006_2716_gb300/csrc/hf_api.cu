@@ -704,6 +704,35 @@ hf_status hf_get_timings(hf_ctx* c, double* ms) {
     return HF_OK;
 }
 
+hf_status hf_lattice_step_noalloc(hf_ctx* c, const double* d_sigma, double* d_gloc) {
+    if (!c) return fail(nullptr, HF_EINVAL, "null context");
+    if (!d_sigma || !d_gloc) return fail(c, HF_EINVAL, "hf_lattice_step_noalloc: null pointer");
+    const size_t per = hfk::lattice_scratch_per_matrix(c->lat.N, c->lat.b);
+    if (per > hfk::lattice_static_scratch_bytes())
+        return fail(c, HF_EINVAL,
+                    "hf_lattice_step_noalloc: one band of this lattice needs " + std::to_string(per) +
+                        " bytes of scratch, more than the " +
+                        std::to_string(hfk::lattice_static_scratch_bytes()) +
+                        "-byte static array holds; use hf_rdmft_step with a workspace instead");
+    hfk::LatticeArgs la{};
+    la.N = c->lat.N;
+    la.b = c->lat.b;
+    la.nw = c->nw;
+    la.beta = c->p.beta;
+    la.mu = c->p.mu;
+    la.h0band = c->h0band;
+    la.rep_of = c->rep_of;
+    la.flip = c->flip;
+    la.site_rep = c->site_rep;
+    la.sigma = reinterpret_cast<const double2*>(d_sigma);
+    la.gloc = reinterpret_cast<double2*>(d_gloc);
+    la.scratch = nullptr;
+    la.status = c->status;
+    cudaError_t e = hfk::launch_lattice_static(la, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "hf_lattice_step_noalloc launch");
+    return check_status(c);
+}
+
 void hf_free(hf_ctx* c) { delete c; }
 
 const char* hf_last_error(const hf_ctx* c) {

@@ -17,6 +17,8 @@
 //      which only touches entries of Z = M^{-1} inside the band, kept as a b x b window in
 //      shared memory.
 // Work per matrix ~1.5 N b^2 complex FMA instead of the dense (4/3) N^3.
+#include <algorithm>
+
 #include "hf_internal.cuh"
 #include "k_lattice.cuh"
 
@@ -168,6 +170,55 @@ cudaError_t launch_lattice(const LatticeArgs& a, int q0, int nq, cudaStream_t st
     const int blocks = (nq + wpb - 1) / wpb;
     lattice_kernel<<<blocks, 32 * wpb, smem, st>>>(a, q0, nq);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free variant: the band buffers live in a fixed device array of this file instead
+// of the caller's workspace.  Every GPU that loads the library holds the array until exit.
+// Each launch of the kernel overwrites every band element it later reads (step 1 assembles the
+// whole band), so nothing left over from an earlier call needs clearing; two calls that overlap
+// on the GPU would share the array and race.
+// ---------------------------------------------------------------------------------------
+constexpr size_t kStaticLatticeScratchBytes = static_cast<size_t>(16) << 20;   // 16 MiB
+static __device__ __align__(256) double2
+    g_lattice_scratch[kStaticLatticeScratchBytes / sizeof(double2)];
+
+size_t lattice_static_scratch_bytes() { return kStaticLatticeScratchBytes; }
+
+// Device address of g_lattice_scratch on the current device, looked up once per device (the
+// host-side symbol is only a stand-in and must never reach a kernel).
+static cudaError_t static_scratch_address(double2** out) {
+    constexpr int kMaxDevices = 64;
+    static double2* addr[kMaxDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    if (addr[dev] == nullptr) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_lattice_scratch);
+        if (e != cudaSuccess) return e;
+        addr[dev] = static_cast<double2*>(p);
+    }
+    *out = addr[dev];
+    return cudaSuccess;
+}
+
+cudaError_t launch_lattice_static(const LatticeArgs& a_in, cudaStream_t st) {
+    const size_t per = lattice_scratch_per_matrix(a_in.N, a_in.b);
+    if (per == 0 || per > kStaticLatticeScratchBytes) return cudaErrorInvalidValue;
+    double2* base = nullptr;
+    cudaError_t e = static_scratch_address(&base);
+    if (e != cudaSuccess) return e;
+    LatticeArgs a = a_in;
+    a.scratch = base;
+    const int chunk = static_cast<int>(kStaticLatticeScratchBytes / per);
+    const int nq = 2 * a.nw;
+    for (int q0 = 0; q0 < nq; q0 += chunk) {
+        e = launch_lattice(a, q0, std::min(chunk, nq - q0), st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace hfk

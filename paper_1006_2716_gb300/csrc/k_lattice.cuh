@@ -23,6 +23,11 @@ int lattice_warps_per_block(int b);
 size_t lattice_scratch_per_matrix(int N, int b);
 cudaError_t launch_lattice(const LatticeArgs& a, int q0, int nq, cudaStream_t st);
 
+// Lattice step over all 2 * nw matrices with the band buffers in a fixed 16 MiB device array
+// (a.scratch is ignored); rejects a lattice whose single band does not fit.
+size_t lattice_static_scratch_bytes();
+cudaError_t launch_lattice_static(const LatticeArgs& a, cudaStream_t st);
+
 struct FourierArgs {
     int nsite, L, nw;
     double beta, U, mix;

@@ -61,6 +61,7 @@ SIGNATURES = [
     ("hf_get_green", C.c_int, [_VP, C.c_int, _DP]),
     ("hf_get_accepts", C.c_int, [_VP, C.POINTER(C.c_ulonglong)]),
     ("hf_get_timings", C.c_int, [_VP, _DP]),
+    ("hf_lattice_step_noalloc", C.c_int, [_VP, _VP, _VP]),
     ("hf_free", None, [_VP]),
     ("hf_last_error", C.c_char_p, [_VP]),
 ]
@@ -213,6 +214,11 @@ def hf_get_timings(ctx):
     ms = np.zeros(6)
     _check(lib().hf_get_timings(ctx, _dp(ms)), ctx)
     return ms
+
+
+def hf_lattice_step_noalloc(ctx, d_sigma: int, d_gloc: int):
+    """d_sigma, d_gloc: device addresses of [n_sites][2][nw] complex128 buffers."""
+    _check(lib().hf_lattice_step_noalloc(ctx, C.c_void_p(d_sigma), C.c_void_p(d_gloc)), ctx)
 
 
 def hf_free(ctx):
