@@ -12,6 +12,7 @@
 #include <string>
 #include <utility>
 #include <vector>
+#include <algorithm>
 #include <chrono>
 
 #include "hf_internal.cuh"
@@ -151,6 +152,7 @@ struct hf_ctx {
     cudaStream_t stream = nullptr;
     int lat_batch = 0;              // matrices per lattice-step launch
     uint32_t nmeas = 0;             // measured sweeps since the last clear (all chains)
+    uint32_t nsw_host = 0;          // sweep counter shared by all chains (FP32 path)
     std::string err;
     // device state
     double* gtau = nullptr;         // [nsite][2][L]
@@ -327,21 +329,55 @@ hf_status check_status(hf_ctx* c) {
     return HF_OK;
 }
 
+// Mixed-precision sequence: FP32 sweep segments that end at the chains' next refresh point,
+// each followed by the FP64 refresh kernel, which also takes that sweep's measurement (the
+// measurement of a refresh sweep comes after the refresh, as in the FP64 path).
+hf_status launch_sweeps_f32(hf_ctx* c, int n_warmup, int n_measure, int refresh_first) {
+    hfk::QmcProblem q = make_problem(*c, n_warmup, n_measure, refresh_first);
+    cudaError_t e = cudaSuccess;
+    if (refresh_first) {
+        q.refresh_measure = 0;
+        e = hfk::launch_refresh_f64(q, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "FP64 refresh launch");
+    }
+    const int total = n_warmup + n_measure;
+    const uint32_t re = static_cast<uint32_t>(c->p.refresh_every);
+    uint32_t nsw = c->nsw_host;
+    for (int k = 0; k < total;) {
+        const int to_refresh = static_cast<int>(re - (nsw % re));
+        const int n = std::min(to_refresh, total - k);
+        const bool lands = (n == to_refresh);
+        hfk::QmcBatch b{};
+        b.nprob = 1;
+        b.p[0] = q;
+        b.p[0].nsweeps = n;
+        b.p[0].meas_from = std::max(0, n_warmup - k);
+        b.p[0].meas_to = std::max(b.p[0].meas_from, n - (lands ? 1 : 0));
+        b.nblocks = c->nchain;
+        e = hfk::launch_qmc_f32(b, hfk::qmc_f32_smem_bytes(c->L), c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "FP32 sweep launch");
+        if (lands) {
+            q.refresh_measure = (k + n - 1 >= n_warmup) ? 1 : 0;
+            e = hfk::launch_refresh_f64(q, c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "FP64 refresh launch");
+        }
+        k += n;
+        nsw += static_cast<uint32_t>(n);
+    }
+    c->nsw_host = nsw;
+    return HF_OK;
+}
+
 hf_status launch_sweeps(hf_ctx* c, int n_warmup, int n_measure, int refresh_first) {
+    if (c->p.precision == 1) return launch_sweeps_f32(c, n_warmup, n_measure, refresh_first);
     hfk::QmcBatch b{};
     b.nprob = 1;
     b.p[0] = make_problem(*c, n_warmup, n_measure, refresh_first);
-    cudaError_t e;
-    if (c->p.precision == 0) {
-        const int cpb = hfk::qmc_f64_chains_per_block(c->L);
-        b.nblocks = (c->nchain + cpb - 1) / cpb;
-        e = hfk::launch_qmc_f64(b, hfk::qmc_f64_smem_bytes(c->L), c->stream);
-    } else {
-        const int cpb = hfk::qmc_f32_chains_per_block(c->L);
-        b.nblocks = (c->nchain + cpb - 1) / cpb;
-        e = hfk::launch_qmc_f32(b, hfk::qmc_f32_smem_bytes(c->L), c->stream);
-    }
+    const int cpb = hfk::qmc_f64_chains_per_block(c->L);
+    b.nblocks = (c->nchain + cpb - 1) / cpb;
+    cudaError_t e = hfk::launch_qmc_f64(b, hfk::qmc_f64_smem_bytes(c->L), c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "QMC sweep launch");
+    c->nsw_host += static_cast<uint32_t>(n_warmup + n_measure);
     return HF_OK;
 }
 
@@ -656,9 +692,14 @@ hf_status hf_set_fields(hf_ctx* c, const signed char* fields, const uint32_t* co
         HF_CUDA(c, cudaMemcpyAsync(c->s, fields, static_cast<size_t>(c->nchain) * c->L,
                                    cudaMemcpyHostToDevice, c->stream));
     }
-    if (counters)
+    if (counters) {
+        for (int k = 1; k < c->nchain; ++k)
+            if (c->p.precision == 1 && counters[k] != counters[0])
+                return fail(c, HF_EINVAL, "hf_set_fields: the FP32 path needs equal sweep counters");
         HF_CUDA(c, cudaMemcpyAsync(c->nsw, counters, sizeof(uint32_t) * c->nchain,
                                    cudaMemcpyHostToDevice, c->stream));
+        c->nsw_host = counters[0];
+    }
     HF_CUDA(c, cudaStreamSynchronize(c->stream));
     return HF_OK;
 }

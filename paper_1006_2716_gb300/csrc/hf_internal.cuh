@@ -63,6 +63,9 @@ struct QmcProblem {
     double ev_p, ev_m;    // e^{+lambda} - 1, e^{-lambda} - 1 (Dyson factors, sigma s = +-1)
     float af_p, af_m;     // single-precision copies of a_p, a_m
     int n_warmup, n_measure, refresh_every, bin_size, max_bins, refresh_first;
+    // single-precision path only: sweeps of this launch and the measured local range
+    int nsweeps, meas_from, meas_to;
+    int refresh_measure;  // refresh kernel: add a measurement after the refresh
     const double* gtau;   // [nsite][2][L]  bath g~0(tau_m)
     double* G;            // [nchain][2][L*L] (FP64 state, or FP64 scratch of the FP32 path)
     float* Gf;            // [nchain][2][L*L] FP32 state (precision 1) or nullptr
@@ -90,7 +93,10 @@ size_t qmc_f32_smem_bytes(int L);
 bool qmc_f32_supported(int L);
 cudaError_t launch_qmc_f32(const QmcBatch& b, size_t smem, cudaStream_t st);
 int qmc_f32_chains_per_block(int L);
-cudaError_t launch_refresh_f64(const QmcProblem& p, int use_state_fields, cudaStream_t st);
+// FP64 Dyson refresh of every chain of one problem (L <= 128): writes G (FP64) and, when
+// p.Gf is set, its FP32 copy; measures afterwards when p.refresh_measure is set.
+size_t refresh_f64_smem_bytes(int L);
+cudaError_t launch_refresh_f64(const QmcProblem& p, cudaStream_t st);
 
 cudaError_t launch_init_fields(int8_t* s, int nchain, int cps, int L, uint32_t seed_lo,
                                uint32_t seed_hi, cudaStream_t st);

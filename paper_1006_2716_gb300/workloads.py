@@ -33,7 +33,8 @@ CONFIGS = {
                      n_warmup=500, n_measure=2000, refresh_every=10, bin_size=100, seed=2,
                      h_seed=0.1, mix=0.5),
     "square30": dict(Lx=30, Ly=30, geometry=0, periodic=0, t=1.0, U=8.0, V0=0.03, mu=4.2571,
-                     beta=16.0, dtau=0.125, n_matsubara=500, chains_per_site=16, n_warmup=500,
+                     beta=16.0, dtau=0.125, precision=1, n_matsubara=500, chains_per_site=16,
+                     n_warmup=500,
                      n_measure=2000, refresh_every=1, bin_size=100, seed=4, h_seed=0.1,
                      mix=0.5),
 }
