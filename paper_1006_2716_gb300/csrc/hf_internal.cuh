@@ -45,6 +45,11 @@ __device__ __forceinline__ double uniform53(uint4 x) {
     return static_cast<double>(bits) * 0x1p-53;
 }
 
+// The 53 bits of that uniform as an integer (u = bits * 2^-53).
+__device__ __forceinline__ unsigned long long uniform_bits53(uint4 x) {
+    return ((static_cast<unsigned long long>(x.x) << 32) | x.y) >> 11;
+}
+
 // 24-bit uniform in [0, 1) for the single-precision sweep: (x >> 8) * 2^-24.
 __device__ __forceinline__ float uniform24(uint4 x) {
     return static_cast<float>(x.x >> 8) * 0x1p-24f;

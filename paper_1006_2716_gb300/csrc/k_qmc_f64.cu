@@ -39,7 +39,7 @@ struct TeamSmem {
     double* G0;    // [L*L]
     double* G1;    // [L*L]
     double* cr;    // [4L]: scaled column up/down, row up/down; refresh: multipliers, 1/pivot
-    double* u;     // [L]
+    unsigned long long* ub;  // [L] 53-bit uniforms as integers
     double* bacc;  // [2L+3] current bin
     double* red;   // [8]
     int* piv;      // [4]
@@ -49,8 +49,8 @@ struct TeamSmem {
         G0 = d;
         G1 = G0 + L * L;
         cr = G1 + L * L;
-        u = cr + 4 * L;
-        bacc = u + L;
+        ub = reinterpret_cast<unsigned long long*>(cr + 4 * L);
+        bacc = reinterpret_cast<double*>(ub + L);
         red = bacc + 2 * L + 3;
         piv = reinterpret_cast<int*>(red + 8);
         s = reinterpret_cast<int8_t*>(piv + 4);
@@ -60,6 +60,41 @@ struct TeamSmem {
 // |x| ordering through the bit pattern (integer pipe): larger magnitude -> larger key.
 __device__ __forceinline__ unsigned long long mag_key(double x) {
     return static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// Single-precision view of a double built on the integer pipe from its bit pattern (mantissa
+// truncated to 23 bits, |relative error| < 2^-23; magnitudes outside the float range flush
+// to 0 or saturate to FLT_MAX, which only widens the decision guard below).
+__device__ __forceinline__ float f32_of(double x) {
+    const int hi = __double2hiint(x);
+    const unsigned lo = static_cast<unsigned>(__double2loint(x));
+    const int e = ((hi >> 20) & 0x7FF) - 1023 + 127;
+    const unsigned sign = static_cast<unsigned>(hi) & 0x80000000u;
+    const unsigned mant = ((static_cast<unsigned>(hi) & 0xFFFFFu) << 3) | (lo >> 29);
+    if (e <= 0) return __int_as_float(static_cast<int>(sign));
+    if (e >= 255) return __int_as_float(static_cast<int>(sign | 0x7F7FFFFFu));
+    return __int_as_float(static_cast<int>(sign | (static_cast<unsigned>(e) << 23) | mant));
+}
+
+// Double from a (normal, nonzero) float's bit pattern, integer pipe only.
+__device__ __forceinline__ double f64_of(float f) {
+    const unsigned b = static_cast<unsigned>(__float_as_int(f));
+    const unsigned sign = b & 0x80000000u;
+    const unsigned e = ((b >> 23) & 0xFFu) + (1023u - 127u);
+    const unsigned mant = b & 0x7FFFFFu;
+    return __hiloint2double(static_cast<int>(sign | (e << 20) | (mant >> 3)),
+                            static_cast<int>(mant << 29));
+}
+
+// 1/R to ~1 ulp: FP32 reciprocal seed (22 bits) and two Newton steps in FP64 (4 DFMA)
+// instead of a full IEEE division.  R is a flip ratio: finite, normal, |R| well inside the float
+// range.
+__device__ __forceinline__ double recip64(double R, float Rf) {
+    double r = f64_of(__frcp_rn(Rf));
+    double e = fma(-R, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-R, r, 1.0);
+    return fma(r, e, r);
 }
 
 // Build A = 1 + (1 - g0) diag(e^{lambda sigma s_j} - 1) into A and g0 into B.
@@ -125,6 +160,7 @@ __device__ bool solve_dyson(double* A, double* B, double* f, int* piv, int tid) 
         team_sync<TW>();
         const double inv = 1.0 / A[k * L + k];
         for (int i = k + 1 + tid; i < L; i += T) f[i] = A[i * L + k] * inv;
+        if (tid == 0) f[L + k] = inv;   // kept for the back substitution
         team_sync<TW>();
         // rows i > k of [A | B]: subtract f_i times row k (A columns j > k only)
         const int rows = L - 1 - k;
@@ -146,7 +182,7 @@ __device__ bool solve_dyson(double* A, double* B, double* f, int* piv, int tid) 
         for (int i = L - 1; i >= 0; --i) {
             double acc = B[i * L + c];
             for (int j = i + 1; j < L; ++j) acc = fma(-A[i * L + j], B[j * L + c], acc);
-            B[i * L + c] = acc / A[i * L + i];
+            B[i * L + c] = acc * f[L + i];
         }
     }
     team_sync<TW>();
@@ -269,9 +305,9 @@ __device__ void qmc_chain(const QmcProblem& P, int c, unsigned char* base, int t
     const int nsweeps = P.n_warmup + P.n_measure;
     for (int k = 0; k < nsweeps; ++k) {
         for (int l = tid; l < L; l += T)
-            S.u[l] = uniform53(philox4x32_10(make_uint4(nsw, static_cast<uint32_t>(l),
-                                                        static_cast<uint32_t>(ch),
-                                                        static_cast<uint32_t>(site)), key));
+            S.ub[l] = uniform_bits53(philox4x32_10(make_uint4(nsw, static_cast<uint32_t>(l),
+                                                              static_cast<uint32_t>(ch),
+                                                              static_cast<uint32_t>(site)), key));
         team_sync<TW>();
         for (int l = 0; l < L; ++l) {
             const double g0 = S.G0[l * L + l];
@@ -279,13 +315,43 @@ __device__ void qmc_chain(const QmcProblem& P, int c, unsigned char* base, int t
             const int sl = S.s[l];
             const double au = (sl > 0) ? P.a_p : P.a_m;   // up:   sigma s_l = +s_l
             const double ad = (sl > 0) ? P.a_m : P.a_p;   // down: sigma s_l = -s_l
-            const double Ru = __dadd_rn(1.0, __dmul_rn(__dadd_rn(1.0, -g0), au));
-            const double Rd = __dadd_rn(1.0, __dmul_rn(__dadd_rn(1.0, -g1), ad));
-            const double p = __dmul_rn(Ru, Rd);
-            if (!(p > 0.0) && tid == 0) atomicAdd(P.status + 1, 1);
-            if (S.u[l] < p) {
-                const double fu = au / Ru;
-                const double fd = ad / Rd;
+            const float auf = (sl > 0) ? P.af_p : P.af_m;
+            const float adf = (sl > 0) ? P.af_m : P.af_p;
+            // Metropolis test u < R_up R_dn.  An FP32 estimate decides whenever |u - p| exceeds
+            // twice a bound on its error; otherwise the FP64 product decides.  Either way the
+            // outcome is that of the FP64 arithmetic.  Error of the estimate: g truncated to 23
+            // bits (2^-23 |g|), 1 - g and a rounded (2^-24), one fused rounding of R (2^-24 |R|)
+            // give |R - Rf| <= 2^-21 (|a|(|1-g| + |g| + 1) + |Rf|) =: eR; the product adds
+            // eRu (|Rdf| + eRd) + |Ruf| eRd + 2^-24 |pf|, and u carries 2^-24.
+            const unsigned long long ubits = S.ub[l];
+            const float uf = static_cast<float>(static_cast<unsigned>(ubits >> 29)) * 0x1p-24f;
+            const float g0f = f32_of(g0), g1f = f32_of(g1);
+            const float Ruf = fmaf(1.0f - g0f, auf, 1.0f);
+            const float Rdf = fmaf(1.0f - g1f, adf, 1.0f);
+            const float pf = Ruf * Rdf;
+            const float eRu = 0x1p-21f * (fabsf(auf) * (fabsf(1.0f - g0f) + fabsf(g0f) + 1.0f) + fabsf(Ruf));
+            const float eRd = 0x1p-21f * (fabsf(adf) * (fabsf(1.0f - g1f) + fabsf(g1f) + 1.0f) + fabsf(Rdf));
+            const float guard = 2.0f * (eRu * (fabsf(Rdf) + eRd) + fabsf(Ruf) * eRd +
+                                        0x1p-24f * (fabsf(pf) + 1.0f));
+            bool accept;
+            double Ru = 0.0, Rd = 0.0;
+            if (fabsf(uf - pf) > guard) {
+                accept = uf < pf;
+                if (!(pf > 0.0f) && tid == 0) atomicAdd(P.status + 1, 1);
+                if (accept) {
+                    Ru = __dadd_rn(1.0, __dmul_rn(__dadd_rn(1.0, -g0), au));
+                    Rd = __dadd_rn(1.0, __dmul_rn(__dadd_rn(1.0, -g1), ad));
+                }
+            } else {
+                Ru = __dadd_rn(1.0, __dmul_rn(__dadd_rn(1.0, -g0), au));
+                Rd = __dadd_rn(1.0, __dmul_rn(__dadd_rn(1.0, -g1), ad));
+                const double p = __dmul_rn(Ru, Rd);
+                if (!(p > 0.0) && tid == 0) atomicAdd(P.status + 1, 1);
+                accept = static_cast<double>(ubits) * 0x1p-53 < p;
+            }
+            if (accept) {
+                const double fu = au * recip64(Ru, Ruf);
+                const double fd = ad * recip64(Rd, Rdf);
                 for (int i = tid; i < L; i += T) {
                     const double one = (i == l) ? 1.0 : 0.0;
                     S.cr[i] = fu * (S.G0[i * L + l] - one);
@@ -369,7 +435,7 @@ __device__ void run_block(const QmcProblem& P, int blk, unsigned char* smem) {
     }
 }
 
-__global__ void __launch_bounds__(kBlock) qmc_f64_kernel(const __grid_constant__ QmcBatch B) {
+__global__ void __launch_bounds__(kBlock, 3) qmc_f64_kernel(const __grid_constant__ QmcBatch B) {
     extern __shared__ __align__(16) unsigned char smem[];
     int pi = 0;
     while (pi + 1 < B.nprob && static_cast<int>(blockIdx.x) >= B.p[pi + 1].block0) ++pi;
