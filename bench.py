@@ -203,7 +203,7 @@ def run_ours(args):
 
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)
-    cfg = dict(CFG)
+    cfg = dict(CFG, precision=args.precision, team_warps=args.team_warps)
     if args.sweeps:
         # short QMC launch for profiling captures only (not a benchmark value)
         cfg.update(n_warmup=args.sweeps // 5, n_measure=args.sweeps - args.sweeps // 5,
@@ -321,6 +321,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
+    ap.add_argument("--team-warps", type=int, default=0, choices=[0, 1, 2, 4],
+                    help="warps per Markov chain (0: library default)")
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 2],
+                    help="sweep arithmetic: 0 FP64, 2 FP32 pairs (both with FP64 refresh)")
     ap.add_argument("--sweeps", type=int, default=0,
                     help="profiling only: override sweeps per iteration (result is not a bench value)")
     args = ap.parse_args()

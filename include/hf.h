@@ -57,9 +57,12 @@ typedef struct hf_params {
     double beta, dtau;   /* inverse temperature, Trotter step; L = round(beta / dtau)       */
     int n_matsubara;     /* Matsubara frequencies kept explicitly (paper: 500)              */
     int chains_per_site; /* independent Markov chains per inequivalent site                 */
-    int precision;       /* 0: FP64 sweeps; 1: FP32 sweeps + FP64 refresh                   */
+    int precision;       /* 0: FP64 sweeps; 1: FP32 sweeps + FP64 refresh; 2: FP32-pair     */
+                         /* ("double-float", 48-bit significand) sweeps + FP64 refresh      */
     int refresh_every;   /* Dyson refresh after every refresh_every-th sweep of a chain     */
     int delay_k;         /* delayed-update depth (0 or 1: rank-1 Sherman-Morrison)          */
+    int team_warps;      /* FP64-class sweeps: warps per Markov chain, 1, 2 or 4 (0: default */
+                         /* 1 for L <= 32, 4 above); picked per L by the autotuner          */
     int bin_size;        /* measured sweeps per bin                                         */
     int max_bins;        /* bins kept per chain between clears                              */
     int n_warmup, n_measure;  /* sweeps per hf_rdmft_step                                  */
@@ -137,7 +140,8 @@ hf_status hf_get_fields(hf_ctx* ctx, signed char* fields, uint32_t* sweep_counte
 hf_status hf_set_fields(hf_ctx* ctx, const signed char* fields, const uint32_t* sweep_counters);
 
 /* Green-function matrices of one chain, [2][L][L] row-major doubles (converted from the
- * single-precision state when precision = 1), and accepted-flip counters [n_chains]. */
+ * single-precision or FP32-pair state when precision = 1 or 2), and accepted-flip counters
+ * [n_chains]. */
 hf_status hf_get_green(hf_ctx* ctx, int chain, double* G);
 hf_status hf_get_accepts(hf_ctx* ctx, unsigned long long* accepts);
 
@@ -146,6 +150,34 @@ hf_status hf_get_accepts(hf_ctx* ctx, unsigned long long* accepts);
  * sweeps, ms[3] chain/bin reduction, ms[4] tau -> i w + self-energy update; ms[5] the QMC
  * sweeps of the last hf_sweep.  A phase that has not run yet reads -1.  Synchronises. */
 hf_status hf_get_timings(hf_ctx* ctx, double* ms);
+
+/* ---- Batches: uneven-L problems in one fused launch, graph-captured iterations -------------
+ * A batch groups 1..8 contexts that share one stream, one sweep form (precision 0 or 2, not 1)
+ * and the same n_warmup / n_measure -- e.g. one RDMFT run per temperature of a scan, each with its
+ * own L.  The impurity sweeps of all of them run as a single launch of the fused sweep kernel
+ * (problems ordered by L, largest first, so the longest chains start first); every other phase
+ * of an iteration stays per context.  The caller keeps the contexts alive until hf_batch_free. */
+typedef struct hf_batch hf_batch;
+
+/* use_graph = 1: from the second hf_batch_rdmft_step on, the whole iteration (lattice steps,
+ * transforms, fused sweeps, reductions, self-energy updates) is replayed from one CUDA graph
+ * captured on the first replayed call; the contexts' stream must then be a created stream (not
+ * the legacy default stream), else HF_EINVAL. */
+hf_status hf_batch_create(hf_ctx* const* ctxs, int n, int use_graph, hf_batch** out);
+
+/* Fused sweeps of every context (asynchronous; same semantics per context as hf_sweep). */
+hf_status hf_batch_sweep(hf_batch* b, int n_warmup, int n_measure, int refresh_first);
+
+/* One RDMFT iteration of every context of the batch (as hf_rdmft_step for each); writes the
+ * device time of the whole batched iteration in milliseconds to *gpu_ms (may be NULL).
+ * Synchronises. */
+hf_status hf_batch_rdmft_step(hf_batch* b, double* gpu_ms);
+
+/* Device time (ms) of the last hf_batch_sweep or hf_batch_rdmft_step.  Synchronises. */
+hf_status hf_batch_elapsed(hf_batch* b, double* gpu_ms);
+
+void hf_batch_free(hf_batch* b);
+const char* hf_batch_last_error(const hf_batch* b);
 
 /* Allocation-free lattice step.  The paper has no counterpart: this exists for callers that
  * cannot allocate device memory at call time -- code running where a cudaMalloc would

@@ -1,0 +1,72 @@
+"""Autotuner of the sweep kernels: for each slice count L, the arithmetic form of the FP64-class
+sweeps (0 = FP64, 2 = FP32 pairs with FP64 refresh; both meet the FP64 parity bar) and the
+number of warps per Markov chain that give the most proposals per second on this GPU.
+
+Each candidate runs the real fused sweep kernel on a probe problem with the target number of
+chains (one impurity, random bath, fields from the seed) and is timed with CUDA events on the
+context stream (hf_get_timings).  Results are cached per GPU name in ``_build/autotune.json``.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import numpy as np
+
+from . import hf
+from . import workloads as wl
+
+_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
+
+
+def candidates(L, forms=(0, 2)):
+    tws = (1, 2, 4) if L <= 32 else (2, 4)
+    return [(f, tw) for f in forms for tw in tws]
+
+
+def _probe(L, chains, form, tw, sweeps, device, stream):
+    beta = 0.25 * L
+    cfg = dict(Lx=1, Ly=1, geometry=0, U=8.0, V0=0.0, mu=4.0, beta=beta, dtau=0.25,
+               n_matsubara=4, chains_per_site=chains, precision=form, team_warps=tw,
+               refresh_every=10, bin_size=max(1, sweeps), max_bins=1, n_warmup=0,
+               n_measure=sweeps, seed=12345)
+    ctx = hf.Context(hf.make_params(cfg), device=device, stream=stream)
+    bath = wl.random_baths(L, 1, beta, L)[0]
+    hf.hf_set_g0(ctx.handle, 0, 0, bath[0])
+    hf.hf_set_g0(ctx.handle, 0, 1, bath[1])
+    hf.hf_sweep(ctx.handle, 2, 0, 1)                     # warm-up (module load, attributes)
+    best = np.inf
+    for _ in range(2):
+        hf.hf_sweep(ctx.handle, sweeps, 0, 0)
+        best = min(best, hf.hf_get_timings(ctx.handle)[5])
+    ctx.close()
+    return best / sweeps                                  # ms per sweep of all chains
+
+
+def tune(Ls, chains, forms=(0, 2), sweeps=30, device="cuda:0", stream=None, use_cache=True):
+    """{L: {"precision": f, "team_warps": tw, "ms_per_sweep": t, "table": {...}}} for every L."""
+    import torch
+
+    name = torch.cuda.get_device_name(torch.device(device))
+    cache = {}
+    if use_cache and os.path.exists(_CACHE):
+        try:
+            cache = json.load(open(_CACHE))
+        except (OSError, ValueError):
+            cache = {}
+    out = {}
+    for L in Ls:
+        key = "%s|L=%d|chains=%d|forms=%s" % (name, L, chains, ",".join(map(str, forms)))
+        if key not in cache:
+            table = {}
+            for form, tw in candidates(L, forms):
+                table["%d/%d" % (form, tw)] = _probe(L, chains, form, tw, sweeps, device, stream)
+            pick = min(table, key=table.get)
+            f, tw = map(int, pick.split("/"))
+            cache[key] = {"precision": f, "team_warps": tw, "ms_per_sweep": table[pick],
+                          "table": table}
+        out[L] = cache[key]
+    if use_cache:
+        os.makedirs(os.path.dirname(_CACHE), exist_ok=True)
+        json.dump(cache, open(_CACHE, "w"), indent=1, sort_keys=True)
+    return out

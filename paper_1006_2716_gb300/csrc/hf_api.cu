@@ -195,6 +195,7 @@ hf_status fail(hf_ctx* c, hf_status st, const std::string& msg) {
 }
 
 hf_status cuda_fail(hf_ctx* c, cudaError_t e, const char* what) {
+    (void)cudaGetLastError();   // consume it, so that a later launch check does not see it again
     return fail(c, HF_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
@@ -209,7 +210,7 @@ hf_status validate(const hf_params& p, std::string& err) {
     const double Lr = p.beta / p.dtau;
     const int L = static_cast<int>(std::lround(Lr));
     if (std::fabs(Lr - L) > 1e-9 * Lr) { err = "beta / dtau must be an integer"; return HF_EINVAL; }
-    if (p.precision == 0 && !hfk::qmc_f64_supported(L)) {
+    if ((p.precision == 0 || p.precision == 2) && !hfk::qmc_f64_supported(L)) {
         err = "FP64 sweeps support L in {8,12,16,20,24,32,40,48,64}, got " + std::to_string(L);
         return HF_EINVAL;
     }
@@ -217,8 +218,13 @@ hf_status validate(const hf_params& p, std::string& err) {
         err = "FP32 sweeps support L in {16,32,64,128}, got " + std::to_string(L);
         return HF_EINVAL;
     }
-    if (p.precision != 0 && p.precision != 1) { err = "precision must be 0 or 1"; return HF_EINVAL; }
+    if (p.precision < 0 || p.precision > 2) { err = "precision must be 0, 1 or 2"; return HF_EINVAL; }
     if (p.chains_per_site < 1) { err = "chains_per_site must be >= 1"; return HF_EINVAL; }
+    if (!(p.team_warps == 0 || p.team_warps == 1 || p.team_warps == 2 || p.team_warps == 4) ||
+        (L > 32 && p.team_warps == 1)) {
+        err = "team_warps must be 0 (default), 1, 2 or 4, and >= 2 for L > 32";
+        return HF_EINVAL;
+    }
     if (p.n_matsubara < 1 || p.n_matsubara > 100000) { err = "n_matsubara out of range"; return HF_EINVAL; }
     if (p.bin_size < 1 || p.max_bins < 1) { err = "bin_size and max_bins must be >= 1"; return HF_EINVAL; }
     if (p.refresh_every < 0) { err = "refresh_every must be >= 0"; return HF_EINVAL; }
@@ -299,12 +305,15 @@ hfk::QmcProblem make_problem(const hf_ctx& c, int n_warmup, int n_measure, int r
     q.ev_m = c.ev_m;
     q.af_p = static_cast<float>(c.a_p);
     q.af_m = static_cast<float>(c.a_m);
+    q.afl_p = static_cast<float>(c.a_p - static_cast<double>(q.af_p));
+    q.afl_m = static_cast<float>(c.a_m - static_cast<double>(q.af_m));
     q.n_warmup = n_warmup;
     q.n_measure = n_measure;
     q.refresh_every = c.p.refresh_every;
     q.bin_size = c.p.bin_size;
     q.max_bins = c.p.max_bins;
     q.refresh_first = refresh_first;
+    q.team_warps = c.p.team_warps > 0 ? c.p.team_warps : hfk::qmc_default_team_warps(c.L);
     q.gtau = c.gtau;
     q.G = c.G;
     q.Gf = c.Gf;
@@ -373,12 +382,63 @@ hf_status launch_sweeps(hf_ctx* c, int n_warmup, int n_measure, int refresh_firs
     hfk::QmcBatch b{};
     b.nprob = 1;
     b.p[0] = make_problem(*c, n_warmup, n_measure, refresh_first);
-    const int cpb = hfk::qmc_f64_chains_per_block(c->L);
+    const int tw = b.p[0].team_warps;
+    const int cpb = hfk::qmc_f64_chains_per_block(c->L, tw);
     b.nblocks = (c->nchain + cpb - 1) / cpb;
-    cudaError_t e = hfk::launch_qmc_f64(b, hfk::qmc_f64_smem_bytes(c->L), c->stream);
+    const size_t smem = hfk::qmc_f64_smem_bytes(c->L, tw);
+    cudaError_t e = (c->p.precision == 2) ? hfk::launch_qmc_df64(b, smem, c->stream)
+                                          : hfk::launch_qmc_f64(b, smem, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "QMC sweep launch");
     c->nsw_host += static_cast<uint32_t>(n_warmup + n_measure);
     return HF_OK;
+}
+
+hfk::LatticeArgs lattice_args(const hf_ctx& c) {
+    hfk::LatticeArgs la{};
+    la.N = c.lat.N;
+    la.b = c.lat.b;
+    la.nw = c.nw;
+    la.beta = c.p.beta;
+    la.mu = c.p.mu;
+    la.h0band = c.h0band;
+    la.rep_of = c.rep_of;
+    la.flip = c.flip;
+    la.site_rep = c.site_rep;
+    la.sigma = c.sigma;
+    la.gloc = c.gloc;
+    la.scratch = c.lat_scratch;
+    la.status = c.status;
+    return la;
+}
+
+hf_status enqueue_lattice(hf_ctx* c) {
+    const hfk::LatticeArgs la = lattice_args(*c);
+    const int nq = 2 * c->nw;
+    for (int q0 = 0; q0 < nq; q0 += c->lat_batch) {
+        cudaError_t e = hfk::launch_lattice(la, q0, std::min(c->lat_batch, nq - q0), c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "lattice step launch");
+    }
+    return HF_OK;
+}
+
+hfk::FourierArgs fourier_args(const hf_ctx& c) {
+    hfk::FourierArgs fa{};
+    fa.nsite = c.nsite;
+    fa.L = c.L;
+    fa.nw = c.nw;
+    fa.beta = c.p.beta;
+    fa.U = c.p.U;
+    fa.mix = c.p.mix;
+    fa.c23 = c.c23;
+    fa.gloc = c.gloc;
+    fa.sigma = c.sigma;
+    fa.weiss_inv = c.weiss_inv;
+    fa.gwt = c.gwt;
+    fa.gtau = c.gtau;
+    fa.obs_mean = c.obs_mean;
+    fa.gimp = c.gimp;
+    fa.sigma_new = c.sigma_new;
+    return fa;
 }
 
 }  // namespace
@@ -466,6 +526,7 @@ hf_status hf_init(const hf_params* p, void* d_ws, size_t ws_bytes, hf_ctx** out)
     for (int k = 0; k < 9 && e == cudaSuccess; ++k) e = cudaEventCreate(&c->ev[k]);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st0);
     if (e != cudaSuccess) {
+        (void)cudaGetLastError();
         std::string m = std::string("hf_init device setup: ") + cudaGetErrorString(e);
         delete c;
         return fail(nullptr, HF_ECUDA, m);
@@ -585,42 +646,10 @@ hf_status hf_rdmft_step(hf_ctx* c, double* iter_seconds) {
     auto t0 = std::chrono::steady_clock::now();
     HF_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
     // a9: lattice step, in chunks of lat_batch (w_n, sigma) matrices
-    hfk::LatticeArgs la{};
-    la.N = c->lat.N;
-    la.b = c->lat.b;
-    la.nw = c->nw;
-    la.beta = c->p.beta;
-    la.mu = c->p.mu;
-    la.h0band = c->h0band;
-    la.rep_of = c->rep_of;
-    la.flip = c->flip;
-    la.site_rep = c->site_rep;
-    la.sigma = c->sigma;
-    la.gloc = c->gloc;
-    la.scratch = c->lat_scratch;
-    la.status = c->status;
-    const int nq = 2 * c->nw;
-    for (int q0 = 0; q0 < nq; q0 += c->lat_batch) {
-        cudaError_t e = hfk::launch_lattice(la, q0, std::min(c->lat_batch, nq - q0), c->stream);
-        if (e != cudaSuccess) return cuda_fail(c, e, "lattice step launch");
-    }
+    hf_status st0 = enqueue_lattice(c);
+    if (st0 != HF_OK) return st0;
     // Weiss fields and the tau-grid bath
-    hfk::FourierArgs fa{};
-    fa.nsite = c->nsite;
-    fa.L = c->L;
-    fa.nw = c->nw;
-    fa.beta = c->p.beta;
-    fa.U = c->p.U;
-    fa.mix = c->p.mix;
-    fa.c23 = c->c23;
-    fa.gloc = c->gloc;
-    fa.sigma = c->sigma;
-    fa.weiss_inv = c->weiss_inv;
-    fa.gwt = c->gwt;
-    fa.gtau = c->gtau;
-    fa.obs_mean = c->obs_mean;
-    fa.gimp = c->gimp;
-    fa.sigma_new = c->sigma_new;
+    const hfk::FourierArgs fa = fourier_args(*c);
     HF_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
     cudaError_t e = hfk::launch_weiss_tau(fa, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "Weiss-field launch");
@@ -712,6 +741,13 @@ hf_status hf_get_green(hf_ctx* c, int chain, double* G) {
         HF_CUDA(c, cudaMemcpyAsync(G, c->G + static_cast<size_t>(chain) * 2 * LL, sizeof(double) * 2 * LL,
                                    cudaMemcpyDeviceToHost, c->stream));
         HF_CUDA(c, cudaStreamSynchronize(c->stream));
+    } else if (c->p.precision == 2) {
+        std::vector<float> f(4 * LL);   // (hi, lo) pairs
+        HF_CUDA(c, cudaMemcpyAsync(f.data(), c->G + static_cast<size_t>(chain) * 2 * LL,
+                                   sizeof(double) * 2 * LL, cudaMemcpyDeviceToHost, c->stream));
+        HF_CUDA(c, cudaStreamSynchronize(c->stream));
+        for (size_t i = 0; i < 2 * LL; ++i)
+            G[i] = static_cast<double>(f[2 * i]) + static_cast<double>(f[2 * i + 1]);
     } else {
         std::vector<float> f(2 * LL);
         HF_CUDA(c, cudaMemcpyAsync(f.data(), c->Gf + static_cast<size_t>(chain) * 2 * LL,
@@ -773,6 +809,183 @@ hf_status hf_lattice_step_noalloc(hf_ctx* c, const double* d_sigma, double* d_gl
     if (e != cudaSuccess) return cuda_fail(c, e, "hf_lattice_step_noalloc launch");
     return check_status(c);
 }
+
+// ----------------------------------------------------------------------------------------------
+// Batches: several contexts (e.g. one RDMFT run per temperature, uneven L) whose impurity sweeps
+// run as one fused launch, and whose whole iteration is captured once into a CUDA graph.
+// ----------------------------------------------------------------------------------------------
+struct hf_batch {
+    std::vector<hf_ctx*> ctx;     // in launch order: most expensive chains first
+    cudaStream_t stream = nullptr;
+    int use_graph = 0;
+    int iterations = 0;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::string err;
+    ~hf_batch() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+    }
+};
+
+static hf_status bfail(hf_batch* b, hf_status st, const std::string& m) {
+    if (st == HF_ECUDA) (void)cudaGetLastError();
+    if (b) b->err = m; else g_init_error = m;
+    return st;
+}
+
+// One fused launch of the sweeps of every context in the batch.
+static hf_status enqueue_batch_qmc(hf_batch* b, int n_warmup, int n_measure, int refresh_first) {
+    hfk::QmcBatch qb{};
+    qb.nprob = static_cast<int>(b->ctx.size());
+    size_t smem = 0;
+    int blocks = 0;
+    for (int i = 0; i < qb.nprob; ++i) {
+        hf_ctx* c = b->ctx[i];
+        qb.p[i] = make_problem(*c, n_warmup, n_measure, refresh_first);
+        qb.p[i].block0 = blocks;
+        const int tw = qb.p[i].team_warps;
+        const int cpb = hfk::qmc_f64_chains_per_block(c->L, tw);
+        blocks += (c->nchain + cpb - 1) / cpb;
+        smem = std::max(smem, hfk::qmc_f64_smem_bytes(c->L, tw));
+    }
+    qb.nblocks = blocks;
+    const cudaError_t e = (b->ctx[0]->p.precision == 2) ? hfk::launch_qmc_df64(qb, smem, b->stream)
+                                                        : hfk::launch_qmc_f64(qb, smem, b->stream);
+    if (e != cudaSuccess) return bfail(b, HF_ECUDA, std::string("fused sweep launch: ") + cudaGetErrorString(e));
+    return HF_OK;
+}
+
+// Every device operation of one batched RDMFT iteration, in stream order (capturable).
+static hf_status enqueue_batch_iteration(hf_batch* b) {
+    for (hf_ctx* c : b->ctx) {
+        hf_status st = enqueue_lattice(c);
+        if (st != HF_OK) return bfail(b, st, c->err);
+        const cudaError_t e = hfk::launch_weiss_tau(fourier_args(*c), b->stream);
+        if (e != cudaSuccess) return bfail(b, HF_ECUDA, "Weiss-field launch");
+        cudaError_t e1 = cudaMemsetAsync(c->bins, 0, sizeof(double) * c->nchain * c->p.max_bins * (2 * c->L + 3), b->stream);
+        cudaError_t e2 = cudaMemsetAsync(c->nmeas_d, 0, sizeof(uint32_t) * c->nchain, b->stream);
+        if (e1 != cudaSuccess || e2 != cudaSuccess) return bfail(b, HF_ECUDA, "bin clear");
+    }
+    const int nw = b->ctx[0]->p.n_warmup, nm = b->ctx[0]->p.n_measure;
+    hf_status st = enqueue_batch_qmc(b, nw, nm, 1);
+    if (st != HF_OK) return st;
+    for (hf_ctx* c : b->ctx) {
+        const int nb = c->p.n_measure / c->p.bin_size;
+        cudaError_t e = hfk::launch_reduce(c->bins, c->nsite, c->p.chains_per_site, c->L, c->p.max_bins, nb,
+                                           c->p.bin_size, c->obs_mean, c->obs_err, b->stream);
+        if (e == cudaSuccess) e = hfk::launch_sigma_update(fourier_args(*c), b->stream);
+        if (e != cudaSuccess) return bfail(b, HF_ECUDA, "reduction / self-energy launch");
+    }
+    return HF_OK;
+}
+
+hf_status hf_batch_create(hf_ctx* const* ctxs, int n, int use_graph, hf_batch** out) {
+    if (!out) return bfail(nullptr, HF_EINVAL, "null output handle");
+    *out = nullptr;
+    if (!ctxs || n < 1 || n > hfk::kMaxProblems)
+        return bfail(nullptr, HF_EINVAL, "hf_batch_create: need 1.." + std::to_string(hfk::kMaxProblems) + " contexts");
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i]) return bfail(nullptr, HF_EINVAL, "hf_batch_create: null context");
+        if (ctxs[i]->stream != ctxs[0]->stream)
+            return bfail(nullptr, HF_EINVAL, "hf_batch_create: contexts must share one stream");
+        if (ctxs[i]->p.precision == 1 || ctxs[i]->p.precision != ctxs[0]->p.precision)
+            return bfail(nullptr, HF_EINVAL, "hf_batch_create: contexts must all use precision 0 or all 2");
+        if (ctxs[i]->p.n_warmup != ctxs[0]->p.n_warmup || ctxs[i]->p.n_measure != ctxs[0]->p.n_measure)
+            return bfail(nullptr, HF_EINVAL, "hf_batch_create: contexts must share n_warmup and n_measure");
+        if (ctxs[i]->p.n_measure > ctxs[i]->p.max_bins * ctxs[i]->p.bin_size)
+            return bfail(nullptr, HF_EINVAL, "hf_batch_create: n_measure exceeds max_bins * bin_size");
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) return bfail(nullptr, HF_EINVAL, "hf_batch_create: repeated context");
+    }
+    if (use_graph && ctxs[0]->stream == nullptr)
+        return bfail(nullptr, HF_EINVAL,
+                     "hf_batch_create: graph capture needs the contexts on a created (non-default) stream");
+    hf_batch* b = new (std::nothrow) hf_batch();
+    if (!b) return bfail(nullptr, HF_ENOMEM, "host allocation failed");
+    b->ctx.assign(ctxs, ctxs + n);
+    // longest chains first: cost per chain ~ L^3 (sweeps of L proposals, L^2 updates each)
+    std::stable_sort(b->ctx.begin(), b->ctx.end(), [](const hf_ctx* a, const hf_ctx* c2) {
+        return a->L > c2->L;
+    });
+    b->stream = ctxs[0]->stream;
+    b->use_graph = use_graph;
+    if (cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess) {
+        delete b;
+        return bfail(nullptr, HF_ECUDA, "event creation failed");
+    }
+    *out = b;
+    return HF_OK;
+}
+
+hf_status hf_batch_sweep(hf_batch* b, int n_warmup, int n_measure, int refresh_first) {
+    if (!b) return bfail(nullptr, HF_EINVAL, "null batch");
+    if (n_warmup < 0 || n_measure < 0) return bfail(b, HF_EINVAL, "negative sweep count");
+    for (hf_ctx* c : b->ctx)
+        if (static_cast<uint64_t>(c->nmeas) + n_measure > static_cast<uint64_t>(c->p.max_bins) * c->p.bin_size)
+            return bfail(b, HF_EINVAL, "hf_batch_sweep: measurements would overflow max_bins * bin_size");
+    if (cudaEventRecord(b->ev0, b->stream) != cudaSuccess) return bfail(b, HF_ECUDA, "event record");
+    hf_status st = enqueue_batch_qmc(b, n_warmup, n_measure, refresh_first);
+    if (st != HF_OK) return st;
+    if (cudaEventRecord(b->ev1, b->stream) != cudaSuccess) return bfail(b, HF_ECUDA, "event record");
+    for (hf_ctx* c : b->ctx) {
+        c->nmeas += static_cast<uint32_t>(n_measure);
+        c->nsw_host += static_cast<uint32_t>(n_warmup + n_measure);
+    }
+    return HF_OK;
+}
+
+hf_status hf_batch_rdmft_step(hf_batch* b, double* gpu_ms) {
+    if (!b) return bfail(nullptr, HF_EINVAL, "null batch");
+    if (cudaEventRecord(b->ev0, b->stream) != cudaSuccess) return bfail(b, HF_ECUDA, "event record");
+    if (!b->use_graph || b->iterations == 0) {
+        // first iteration runs uncaptured (it also sets the kernels' launch attributes)
+        hf_status st = enqueue_batch_iteration(b);
+        if (st != HF_OK) return st;
+    } else {
+        if (!b->exec) {
+            cudaGraph_t g = nullptr;
+            if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+                return bfail(b, HF_ECUDA, "stream capture could not start");
+            hf_status st = enqueue_batch_iteration(b);
+            const cudaError_t ec = cudaStreamEndCapture(b->stream, &g);
+            if (st != HF_OK) { if (g) cudaGraphDestroy(g); return st; }
+            if (ec != cudaSuccess) return bfail(b, HF_ECUDA, std::string("capture: ") + cudaGetErrorString(ec));
+            const cudaError_t ei = cudaGraphInstantiate(&b->exec, g, 0);
+            cudaGraphDestroy(g);
+            if (ei != cudaSuccess) { b->exec = nullptr; return bfail(b, HF_ECUDA, "graph instantiation failed"); }
+        }
+        if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess) return bfail(b, HF_ECUDA, "graph launch failed");
+    }
+    if (cudaEventRecord(b->ev1, b->stream) != cudaSuccess) return bfail(b, HF_ECUDA, "event record");
+    for (hf_ctx* c : b->ctx) {
+        c->nmeas = static_cast<uint32_t>(c->p.n_measure);
+        c->nsw_host += static_cast<uint32_t>(c->p.n_warmup + c->p.n_measure);
+        hf_status st = check_status(c);
+        if (st != HF_OK) return bfail(b, st, c->err);
+    }
+    ++b->iterations;
+    if (gpu_ms) {
+        float t = 0.0f;
+        if (cudaEventElapsedTime(&t, b->ev0, b->ev1) != cudaSuccess) return bfail(b, HF_ECUDA, "event timing");
+        *gpu_ms = t;
+    }
+    return HF_OK;
+}
+
+hf_status hf_batch_elapsed(hf_batch* b, double* gpu_ms) {
+    if (!b || !gpu_ms) return bfail(b, HF_EINVAL, "null argument");
+    if (cudaEventSynchronize(b->ev1) != cudaSuccess) return bfail(b, HF_ECUDA, "event sync");
+    float t = 0.0f;
+    if (cudaEventElapsedTime(&t, b->ev0, b->ev1) != cudaSuccess) return bfail(b, HF_ECUDA, "event timing");
+    *gpu_ms = t;
+    return HF_OK;
+}
+
+void hf_batch_free(hf_batch* b) { delete b; }
+
+const char* hf_batch_last_error(const hf_batch* b) { return b ? b->err.c_str() : g_init_error.c_str(); }
 
 void hf_free(hf_ctx* c) { delete c; }
 

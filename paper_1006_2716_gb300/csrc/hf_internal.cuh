@@ -66,11 +66,13 @@ struct QmcProblem {
     uint32_t seed_lo, seed_hi;
     double a_p, a_m;      // e^{-2 lambda} - 1 (sigma s_l = +1), e^{+2 lambda} - 1 (= -1)
     double ev_p, ev_m;    // e^{+lambda} - 1, e^{-lambda} - 1 (Dyson factors, sigma s = +-1)
-    float af_p, af_m;     // single-precision copies of a_p, a_m
+    float af_p, af_m;     // single-precision copies of a_p, a_m (rounded to nearest)
+    float afl_p, afl_m;   // remainders: a_p ~ af_p + afl_p as a double-float
     int n_warmup, n_measure, refresh_every, bin_size, max_bins, refresh_first;
     // single-precision path only: sweeps of this launch and the measured local range
     int nsweeps, meas_from, meas_to;
     int refresh_measure;  // refresh kernel: add a measurement after the refresh
+    int team_warps;       // FP64 / FP32-pair sweeps: warps per chain (1, 2, 4; >= 2 for L > 32)
     const double* gtau;   // [nsite][2][L]  bath g~0(tau_m)
     double* G;            // [nchain][2][L*L] (FP64 state, or FP64 scratch of the FP32 path)
     float* Gf;            // [nchain][2][L*L] FP32 state (precision 1) or nullptr
@@ -88,11 +90,15 @@ struct QmcBatch {
     QmcProblem p[kMaxProblems];
 };
 
-// Dynamic shared memory a block of the FP64 sweep needs for slice count L.
-size_t qmc_f64_smem_bytes(int L);
+// FP64 and FP32-pair sweeps: blocks of kBlock threads hold 4 / team_warps chains.
+size_t qmc_f64_smem_bytes(int L, int team_warps);
 bool qmc_f64_supported(int L);
 cudaError_t launch_qmc_f64(const QmcBatch& b, size_t smem, cudaStream_t st);
-int qmc_f64_chains_per_block(int L);
+int qmc_f64_chains_per_block(int L, int team_warps);
+int qmc_default_team_warps(int L);
+
+// FP32-pair ("double-float") sweeps with FP64 refresh: same layout and L set as the FP64 kernel.
+cudaError_t launch_qmc_df64(const QmcBatch& b, size_t smem, cudaStream_t st);
 
 size_t qmc_f32_smem_bytes(int L);
 bool qmc_f32_supported(int L);

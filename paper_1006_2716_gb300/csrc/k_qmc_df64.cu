@@ -1,0 +1,374 @@
+// k_qmc_df64.cu -- Hirsch-Fye sweeps with G held as FP32 pairs (sm_103a).
+//
+// Same method and schedule as the FP64 kernel (one team per Markov chain, G_up/G_dn resident in
+// shared memory for all sweeps; per slice: single-flip ratio, Metropolis test, Sherman-Morrison
+// update; FP64 Dyson refresh every refresh_every sweeps; measurement into bins), but the state
+// and all sweep arithmetic use "double-float" numbers x = hi + lo (two floats, |lo| <= ulp(hi),
+// a 48-bit significand), evaluated with error-free transformations on the FP32 pipe:
+//   TwoSum (Knuth): s = fl(a + b), e = (a - (s - b')) + (b - b') with b' = s - a, exact a + b = s + e;
+//   TwoProd (with FMA): p = fl(a b), e = fma(a, b, -p), exact a b = p + e.
+// On GB300 the FP32 pipe retires 72x more FMA than the FP64 pipe, so the Sherman-Morrison update
+// (2 L^2 multiply-adds per accepted flip) costs ~15 FP32 instructions per element instead of one
+// FP64 instruction at 1/64 of the issue rate.  What stays in FP64: the Dyson refresh (the
+// method's re-anchoring step), and the Metropolis test whenever the FP32 estimate of R_up R_dn
+// is within its error bound of u -- then the ratio is evaluated in FP64 from the exactly
+// representable hi + lo, so every decision is the one FP64 arithmetic takes on the stored G.
+// Accuracy: each update adds an absolute error ~2^-47 max|G|; between two refreshes (at most a
+// few hundred updates) this stays ~1e-13 of max|G|.
+#include "qmc_common.cuh"
+
+namespace hfk {
+namespace {
+
+using namespace qmc;
+
+// ------------------------------ double-float arithmetic -------------------------------------
+// The _rn intrinsics keep every product and sum separately rounded (no contraction), which the
+// error-free transformations rely on.
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return make_float2(s, e);
+}
+__device__ __forceinline__ float2 fast_two_sum(float a, float b) {   // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+// x + y with absolute error <= ~2^-47 (|x| + |y|)
+__device__ __forceinline__ float2 df_add(float2 x, float2 y) {
+    const float2 s = two_sum(x.x, y.x);
+    return fast_two_sum(s.x, __fadd_rn(s.y, __fadd_rn(x.y, y.y)));
+}
+__device__ __forceinline__ float2 df_neg(float2 x) { return make_float2(-x.x, -x.y); }
+__device__ __forceinline__ float2 df_mul(float2 x, float2 y) {
+    const float p = __fmul_rn(x.x, y.x);
+    float e = fmaf(x.x, y.x, -p);
+    e = fmaf(x.x, y.y, e);
+    e = fmaf(x.y, y.x, e);
+    return fast_two_sum(p, e);
+}
+// z + x y
+__device__ __forceinline__ float2 df_fma(float2 x, float2 y, float2 z) {
+    const float p = __fmul_rn(x.x, y.x);
+    float e = fmaf(x.x, y.x, -p);
+    e = fmaf(x.x, y.y, e);
+    e = fmaf(x.y, y.x, e);
+    const float2 s = two_sum(z.x, p);
+    return fast_two_sum(s.x, __fadd_rn(s.y, __fadd_rn(e, z.y)));
+}
+// exact double value of a double-float (hi + lo has at most 48 significant bits)
+__device__ __forceinline__ double df_to_d(float2 x) {
+    return static_cast<double>(x.x) + static_cast<double>(x.y);
+}
+// split of a double: hi = 23-bit truncation (integer pipe), lo = the remainder
+__device__ __forceinline__ float2 d_to_df(double x) {
+    const float h = f32_of(x);
+    const double hd = (h == 0.0f) ? 0.0 : f64_of(h);
+    return make_float2(h, f32_of(x - hd));
+}
+// 1 / R: FP32 seed and two Newton steps in double-float
+__device__ __forceinline__ float2 df_recip(float2 R) {
+    const float2 one = make_float2(1.0f, 0.0f);
+    float2 r = make_float2(__frcp_rn(R.x), 0.0f);
+    for (int it = 0; it < 2; ++it) {
+        const float2 e = df_add(one, df_neg(df_mul(R, r)));
+        r = df_add(r, df_mul(r, e));
+    }
+    return r;
+}
+
+// Dyson refresh of both spins in FP64 (as the FP64 kernel), then the FP64 result is split into
+// double-floats in place.  The two G buffers hold 8 bytes per element in either format.
+template <int L, int TW>
+__device__ void refresh_both_df(const QmcProblem& P, const TeamSmem<L>& S, const double* gt,
+                                double* Gg, int tid) {
+    constexpr int T = 32 * TW;
+    float2* X0 = reinterpret_cast<float2*>(S.G0);
+    float2* X1 = reinterpret_cast<float2*>(S.G1);
+    build_dyson<L, TW>(P, gt, S.s, +1, S.G1, S.G0, tid);
+    team_sync<TW>();
+    bool ok = solve_dyson<L, TW>(S.G1, S.G0, S.cr, S.piv, tid);
+    for (int e = tid; e < L * L; e += T) Gg[e] = S.G0[e];        // park FP64 G_up
+    team_sync<TW>();
+    build_dyson<L, TW>(P, gt + L, S.s, -1, S.G0, S.G1, tid);
+    team_sync<TW>();
+    ok = solve_dyson<L, TW>(S.G0, S.G1, S.cr, S.piv, tid) && ok;
+    for (int e = tid; e < L * L; e += T) {
+        X0[e] = d_to_df(Gg[e]);
+        X1[e] = d_to_df(S.G1[e]);
+    }
+    team_sync<TW>();
+    if (!ok && tid == 0) atomicExch(P.status, static_cast<int>(HF_ENUMERIC));
+}
+
+template <int L, int TW>
+__device__ void measure_df(const TeamSmem<L>& S, int tid) {
+    constexpr int T = 32 * TW;
+    const float2* G0 = reinterpret_cast<const float2*>(S.G0);
+    const float2* G1 = reinterpret_cast<const float2*>(S.G1);
+    for (int m = tid; m < L; m += T) {
+        float2 s0 = make_float2(0.0f, 0.0f), s1 = make_float2(0.0f, 0.0f);
+        for (int q = 0; q < L; ++q) {
+            int l = q + m;
+            if (l >= L) l -= L;
+            int r = l + m;
+            const bool wrap = r >= L;
+            if (wrap) r -= L;
+            const float2 x0 = G0[r * L + l], x1 = G1[r * L + l];
+            s0 = df_add(s0, wrap ? df_neg(x0) : x0);
+            s1 = df_add(s1, wrap ? df_neg(x1) : x1);
+        }
+        S.bacc[m] += df_to_d(s0) / L;
+        S.bacc[L + m] += df_to_d(s1) / L;
+    }
+    double nu = 0.0, nd = 0.0, db = 0.0;
+    for (int l = tid; l < L; l += T) {
+        const double a = 1.0 - df_to_d(G0[l * L + l]);
+        const double b = 1.0 - df_to_d(G1[l * L + l]);
+        nu += a;
+        nd += b;
+        db += a * b;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        nu += __shfl_xor_sync(0xffffffffu, nu, o);
+        nd += __shfl_xor_sync(0xffffffffu, nd, o);
+        db += __shfl_xor_sync(0xffffffffu, db, o);
+    }
+    if constexpr (TW > 1) {
+        const int w = tid >> 5;
+        if ((tid & 31) == 0) {
+            S.red[w] = nu;
+            S.cr[w] = nd;
+            S.cr[4 + w] = db;
+        }
+        team_sync<TW>();
+        if (tid == 0) {
+            nu = 0.0;
+            nd = 0.0;
+            db = 0.0;
+            for (int w2 = 0; w2 < TW; ++w2) {
+                nu += S.red[w2];
+                nd += S.cr[w2];
+                db += S.cr[4 + w2];
+            }
+        }
+    }
+    if (tid == 0) {
+        S.bacc[2 * L + 0] += nu / L;
+        S.bacc[2 * L + 1] += nd / L;
+        S.bacc[2 * L + 2] += db / L;
+    }
+    team_sync<TW>();
+}
+
+template <int L, int TW>
+__device__ void df_chain(const QmcProblem& P, int c, unsigned char* base, int tid) {
+    constexpr int T = 32 * TW;
+    constexpr int LL = L * L;
+    constexpr int W = 2 * L + 3;
+    const TeamSmem<L> S(base);
+    float2* G0 = reinterpret_cast<float2*>(S.G0);
+    float2* G1 = reinterpret_cast<float2*>(S.G1);
+    float2* cr = reinterpret_cast<float2*>(S.cr);
+    const int site = c / P.cps;
+    const int ch = c - site * P.cps;
+    const double* gt = P.gtau + static_cast<size_t>(site) * 2 * L;
+    double* Gg = P.G + static_cast<size_t>(c) * 2 * LL;   // 8 bytes per element, pairs here
+    float2* Gp = reinterpret_cast<float2*>(Gg);
+    const uint2 key = make_uint2(P.seed_lo, P.seed_hi);
+    const float2 a_p = make_float2(P.af_p, P.afl_p), a_m = make_float2(P.af_m, P.afl_m);
+    const float2 one = make_float2(1.0f, 0.0f);
+
+    for (int l = tid; l < L; l += T) S.s[l] = P.s[static_cast<size_t>(c) * L + l];
+    uint32_t nsw = P.nsw[c];
+    uint32_t nmeas = P.nmeas[c];
+    unsigned long long acc = 0ull;
+    int cur_bin = static_cast<int>(nmeas / P.bin_size);
+    double* bins_c = P.bins + static_cast<size_t>(c) * P.max_bins * W;
+    for (int k = tid; k < W; k += T)
+        S.bacc[k] = (cur_bin < P.max_bins) ? bins_c[static_cast<size_t>(cur_bin) * W + k] : 0.0;
+    team_sync<TW>();
+    if (P.refresh_first) {
+        refresh_both_df<L, TW>(P, S, gt, Gg, tid);
+    } else {
+        for (int e = tid; e < LL; e += T) {
+            G0[e] = Gp[e];
+            G1[e] = Gp[LL + e];
+        }
+        team_sync<TW>();
+    }
+
+    const int nsweeps = P.n_warmup + P.n_measure;
+    for (int k = 0; k < nsweeps; ++k) {
+        for (int l = tid; l < L; l += T)
+            S.ub[l] = uniform_bits53(philox4x32_10(make_uint4(nsw, static_cast<uint32_t>(l),
+                                                              static_cast<uint32_t>(ch),
+                                                              static_cast<uint32_t>(site)), key));
+        team_sync<TW>();
+        for (int l = 0; l < L; ++l) {
+            const float2 g0 = G0[l * L + l];
+            const float2 g1 = G1[l * L + l];
+            const int sl = S.s[l];
+            const float auf = (sl > 0) ? P.af_p : P.af_m;   // up:   sigma s_l = +s_l
+            const float adf = (sl > 0) ? P.af_m : P.af_p;   // down: sigma s_l = -s_l
+            // FP32 estimate of the Metropolis test with the error bound of the FP64 kernel
+            // (the pair's hi part is within 2^-24 of its value, inside the 2^-23 term)
+            const unsigned long long ubits = S.ub[l];
+            const float uf = static_cast<float>(static_cast<unsigned>(ubits >> 29)) * 0x1p-24f;
+            const float Ruf = fmaf(1.0f - g0.x, auf, 1.0f);
+            const float Rdf = fmaf(1.0f - g1.x, adf, 1.0f);
+            const float pf = Ruf * Rdf;
+            const float eRu = 0x1p-21f * (fabsf(auf) * (fabsf(1.0f - g0.x) + fabsf(g0.x) + 1.0f) + fabsf(Ruf));
+            const float eRd = 0x1p-21f * (fabsf(adf) * (fabsf(1.0f - g1.x) + fabsf(g1.x) + 1.0f) + fabsf(Rdf));
+            const float guard = 2.0f * (eRu * (fabsf(Rdf) + eRd) + fabsf(Ruf) * eRd +
+                                        0x1p-24f * (fabsf(pf) + 1.0f));
+            bool accept;
+            if (fabsf(uf - pf) > guard) {
+                accept = uf < pf;
+                if (!(pf > 0.0f) && tid == 0) atomicAdd(P.status + 1, 1);
+            } else {
+                const double au = (sl > 0) ? P.a_p : P.a_m;
+                const double ad = (sl > 0) ? P.a_m : P.a_p;
+                const double Ru = __dadd_rn(1.0, __dmul_rn(__dadd_rn(1.0, -df_to_d(g0)), au));
+                const double Rd = __dadd_rn(1.0, __dmul_rn(__dadd_rn(1.0, -df_to_d(g1)), ad));
+                const double p = __dmul_rn(Ru, Rd);
+                if (!(p > 0.0) && tid == 0) atomicAdd(P.status + 1, 1);
+                accept = static_cast<double>(ubits) * 0x1p-53 < p;
+            }
+            if (accept) {
+                // f_sigma = a_sigma / R_sigma in double-float
+                const float2 au2 = (sl > 0) ? a_p : a_m;
+                const float2 ad2 = (sl > 0) ? a_m : a_p;
+                const float2 Ru = df_add(one, df_mul(df_add(one, df_neg(g0)), au2));
+                const float2 Rd = df_add(one, df_mul(df_add(one, df_neg(g1)), ad2));
+                const float2 fu = df_mul(au2, df_recip(Ru));
+                const float2 fd = df_mul(ad2, df_recip(Rd));
+                for (int i = tid; i < L; i += T) {
+                    float2 x0 = G0[i * L + l], x1 = G1[i * L + l];
+                    if (i == l) {
+                        x0 = df_add(x0, df_neg(one));
+                        x1 = df_add(x1, df_neg(one));
+                    }
+                    cr[i] = df_mul(fu, x0);
+                    cr[L + i] = df_mul(fd, x1);
+                    cr[2 * L + i] = G0[l * L + i];
+                    cr[3 * L + i] = G1[l * L + i];
+                }
+                team_sync<TW>();
+                if constexpr (T % L == 0) {
+                    const int j = tid % L;
+                    const float2 r0 = cr[2 * L + j], r1 = cr[3 * L + j];
+#pragma unroll 4
+                    for (int i = tid / L; i < L; i += T / L) {
+                        G0[i * L + j] = df_fma(cr[i], r0, G0[i * L + j]);
+                        G1[i * L + j] = df_fma(cr[L + i], r1, G1[i * L + j]);
+                    }
+                } else {
+                    int i = tid / L, j = tid - (tid / L) * L;
+#pragma unroll 2
+                    for (int e = tid; e < LL; e += T) {
+                        G0[e] = df_fma(cr[i], cr[2 * L + j], G0[e]);
+                        G1[e] = df_fma(cr[L + i], cr[3 * L + j], G1[e]);
+                        i += T / L;
+                        j += T % L;
+                        if (j >= L) {
+                            j -= L;
+                            ++i;
+                        }
+                    }
+                }
+                team_sync<TW>();
+                if (tid == 0) S.s[l] = static_cast<int8_t>(-sl);
+                ++acc;
+            }
+        }
+        ++nsw;
+        team_sync<TW>();
+        if (P.refresh_every > 0 && (nsw % static_cast<uint32_t>(P.refresh_every)) == 0u)
+            refresh_both_df<L, TW>(P, S, gt, Gg, tid);
+        if (k >= P.n_warmup) {
+            measure_df<L, TW>(S, tid);
+            ++nmeas;
+            if (nmeas % static_cast<uint32_t>(P.bin_size) == 0u) {
+                const int b = static_cast<int>(nmeas / P.bin_size) - 1;
+                for (int q = tid; q < W; q += T) {
+                    if (b < P.max_bins) bins_c[static_cast<size_t>(b) * W + q] = S.bacc[q];
+                    S.bacc[q] = 0.0;
+                }
+                team_sync<TW>();
+            }
+        }
+    }
+
+    cur_bin = static_cast<int>(nmeas / P.bin_size);
+    for (int q = tid; q < W; q += T)
+        if (cur_bin < P.max_bins) bins_c[static_cast<size_t>(cur_bin) * W + q] = S.bacc[q];
+    for (int e = tid; e < LL; e += T) {
+        Gp[e] = G0[e];
+        Gp[LL + e] = G1[e];
+    }
+    for (int l = tid; l < L; l += T) P.s[static_cast<size_t>(c) * L + l] = S.s[l];
+    if (tid == 0) {
+        P.nsw[c] = nsw;
+        P.nmeas[c] = nmeas;
+        P.acc[c] += acc;
+    }
+}
+
+template <int L, int TW>
+__device__ void run_team_df(const QmcProblem& P, int blk, unsigned char* smem) {
+    constexpr int per_block = kBlock / (32 * TW);
+    const int team = static_cast<int>(threadIdx.x) / (32 * TW);
+    const int c = blk * per_block + team;
+    if (c < P.nchain)
+        df_chain<L, TW>(P, c, smem + team * team_bytes(L), static_cast<int>(threadIdx.x) % (32 * TW));
+}
+
+template <int L>
+__device__ void run_block_df(const QmcProblem& P, int blk, unsigned char* smem) {
+    const int tw = P.team_warps;
+    if constexpr (L <= 32) {
+        if (tw == 1) run_team_df<L, 1>(P, blk, smem);
+        else if (tw == 2) run_team_df<L, 2>(P, blk, smem);
+        else run_team_df<L, 4>(P, blk, smem);
+    } else {
+        if (tw == 2) run_team_df<L, 2>(P, blk, smem);
+        else run_team_df<L, 4>(P, blk, smem);
+    }
+}
+
+__global__ void __launch_bounds__(kBlock, 3) qmc_df64_kernel(const __grid_constant__ QmcBatch B) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    int pi = 0;
+    while (pi + 1 < B.nprob && static_cast<int>(blockIdx.x) >= B.p[pi + 1].block0) ++pi;
+    const QmcProblem& P = B.p[pi];
+    const int blk = static_cast<int>(blockIdx.x) - P.block0;
+    switch (P.L) {
+        case 8: run_block_df<8>(P, blk, smem); break;
+        case 12: run_block_df<12>(P, blk, smem); break;
+        case 16: run_block_df<16>(P, blk, smem); break;
+        case 20: run_block_df<20>(P, blk, smem); break;
+        case 24: run_block_df<24>(P, blk, smem); break;
+        case 32: run_block_df<32>(P, blk, smem); break;
+        case 40: run_block_df<40>(P, blk, smem); break;
+        case 48: run_block_df<48>(P, blk, smem); break;
+        case 64: run_block_df<64>(P, blk, smem); break;
+        default: break;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_qmc_df64(const QmcBatch& b, size_t smem, cudaStream_t st) {
+    // the largest block (two-warp teams at L = 64) needs ~136 KB; set what this launch asks for
+    cudaError_t e = cudaFuncSetAttribute(qmc_df64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    if (b.nblocks <= 0) return cudaSuccess;
+    qmc_df64_kernel<<<b.nblocks, kBlock, smem, st>>>(b);
+    return cudaGetLastError();
+}
+
+}  // namespace hfk

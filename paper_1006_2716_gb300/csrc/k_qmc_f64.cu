@@ -15,179 +15,13 @@
 // GB300 has ~1 TFLOP/s of FP64 (DFMA and DMMA alike, 72x below FFMA), so this kernel is bound
 // by the FP64 pipe; it keeps the pipe busy with 12 chains per SM and issues no FP64 work that
 // the method does not need (the index arithmetic stays on the integer pipe).
-#include "hf_internal.cuh"
+#include "qmc_common.cuh"
 
 namespace hfk {
 namespace {
 
-template <int TW>
-__device__ __forceinline__ void team_sync() {
-    if constexpr (TW == 1) {
-        __syncwarp();
-    } else {
-        __syncthreads();
-    }
-}
+using namespace qmc;
 
-// Shared-memory footprint of one team (bytes), 16-byte granular.
-__host__ __device__ constexpr size_t team_bytes(int L) {
-    return static_cast<size_t>(2 * L * L + 7 * L + 11) * 8 + 16 + ((L + 15) / 16) * 16;
-}
-
-template <int L>
-struct TeamSmem {
-    double* G0;    // [L*L]
-    double* G1;    // [L*L]
-    double* cr;    // [4L]: scaled column up/down, row up/down; refresh: multipliers, 1/pivot
-    unsigned long long* ub;  // [L] 53-bit uniforms as integers
-    double* bacc;  // [2L+3] current bin
-    double* red;   // [8]
-    int* piv;      // [4]
-    int8_t* s;     // [L]
-    __device__ explicit TeamSmem(unsigned char* base) {
-        double* d = reinterpret_cast<double*>(base);
-        G0 = d;
-        G1 = G0 + L * L;
-        cr = G1 + L * L;
-        ub = reinterpret_cast<unsigned long long*>(cr + 4 * L);
-        bacc = reinterpret_cast<double*>(ub + L);
-        red = bacc + 2 * L + 3;
-        piv = reinterpret_cast<int*>(red + 8);
-        s = reinterpret_cast<int8_t*>(piv + 4);
-    }
-};
-
-// |x| ordering through the bit pattern (integer pipe): larger magnitude -> larger key.
-__device__ __forceinline__ unsigned long long mag_key(double x) {
-    return static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7FFFFFFFFFFFFFFFull;
-}
-
-// Single-precision view of a double built on the integer pipe from its bit pattern (mantissa
-// truncated to 23 bits, |relative error| < 2^-23; magnitudes outside the float range flush
-// to 0 or saturate to FLT_MAX, which only widens the decision guard below).
-__device__ __forceinline__ float f32_of(double x) {
-    const int hi = __double2hiint(x);
-    const unsigned lo = static_cast<unsigned>(__double2loint(x));
-    const int e = ((hi >> 20) & 0x7FF) - 1023 + 127;
-    const unsigned sign = static_cast<unsigned>(hi) & 0x80000000u;
-    const unsigned mant = ((static_cast<unsigned>(hi) & 0xFFFFFu) << 3) | (lo >> 29);
-    if (e <= 0) return __int_as_float(static_cast<int>(sign));
-    if (e >= 255) return __int_as_float(static_cast<int>(sign | 0x7F7FFFFFu));
-    return __int_as_float(static_cast<int>(sign | (static_cast<unsigned>(e) << 23) | mant));
-}
-
-// Double from a (normal, nonzero) float's bit pattern, integer pipe only.
-__device__ __forceinline__ double f64_of(float f) {
-    const unsigned b = static_cast<unsigned>(__float_as_int(f));
-    const unsigned sign = b & 0x80000000u;
-    const unsigned e = ((b >> 23) & 0xFFu) + (1023u - 127u);
-    const unsigned mant = b & 0x7FFFFFu;
-    return __hiloint2double(static_cast<int>(sign | (e << 20) | (mant >> 3)),
-                            static_cast<int>(mant << 29));
-}
-
-// 1/R to ~1 ulp: FP32 reciprocal seed (22 bits) and two Newton steps in FP64 (4 DFMA)
-// instead of a full IEEE division.  R is a flip ratio: finite, normal, |R| well inside the float
-// range.
-__device__ __forceinline__ double recip64(double R, float Rf) {
-    double r = f64_of(__frcp_rn(Rf));
-    double e = fma(-R, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-R, r, 1.0);
-    return fma(r, e, r);
-}
-
-// Build A = 1 + (1 - g0) diag(e^{lambda sigma s_j} - 1) into A and g0 into B.
-template <int L, int TW>
-__device__ void build_dyson(const QmcProblem& P, const double* gt, const int8_t* s, int sigma,
-                            double* A, double* B, int tid) {
-    constexpr int T = 32 * TW;
-    for (int e = tid; e < L * L; e += T) {
-        const int i = e / L, j = e - (e / L) * L;
-        const int d = i - j;
-        const double g = (d >= 0) ? gt[d] : -gt[d + L];
-        const double ev = (sigma * s[j] > 0) ? P.ev_p : P.ev_m;
-        const double one = (i == j) ? 1.0 : 0.0;
-        A[e] = __dadd_rn(one, __dmul_rn(__dadd_rn(one, -g), ev));
-        B[e] = g;
-    }
-}
-
-// Solve A X = B in place (X overwrites B) by Gaussian elimination with partial pivoting.
-// Returns false if a pivot is exactly zero.
-template <int L, int TW>
-__device__ bool solve_dyson(double* A, double* B, double* f, int* piv, int tid) {
-    constexpr int T = 32 * TW;
-    bool ok = true;
-    for (int k = 0; k < L; ++k) {
-        if (tid < 32) {
-            unsigned long long best = 0ull;
-            int bi = L;  // sentinel: nothing found yet
-            for (int i = k + tid; i < L; i += 32) {
-                const unsigned long long key = mag_key(A[i * L + k]);
-                if (bi == L || key > best) {
-                    best = key;
-                    bi = i;
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                // larger magnitude wins; ties go to the smaller row (first maximum)
-                if (oi != L && (bi == L || ob > best || (ob == best && oi < bi))) {
-                    best = ob;
-                    bi = oi;
-                }
-            }
-            if (tid == 0) {
-                piv[0] = bi;
-                piv[1] = (best == 0ull) ? 1 : 0;
-            }
-        }
-        team_sync<TW>();
-        const int p = piv[0];
-        if (piv[1]) ok = false;
-        if (p != k) {
-            for (int j = tid; j < 2 * L; j += T) {
-                double* M = (j < L) ? A : B;
-                const int jj = (j < L) ? j : j - L;
-                const double t = M[k * L + jj];
-                M[k * L + jj] = M[p * L + jj];
-                M[p * L + jj] = t;
-            }
-        }
-        team_sync<TW>();
-        const double inv = 1.0 / A[k * L + k];
-        for (int i = k + 1 + tid; i < L; i += T) f[i] = A[i * L + k] * inv;
-        if (tid == 0) f[L + k] = inv;   // kept for the back substitution
-        team_sync<TW>();
-        // rows i > k of [A | B]: subtract f_i times row k (A columns j > k only)
-        const int rows = L - 1 - k;
-        for (int e = tid; e < rows * 2 * L; e += T) {
-            const int r = e / (2 * L);
-            const int j = e - r * (2 * L);
-            const int i = k + 1 + r;
-            if (j < L) {
-                if (j > k) A[i * L + j] = fma(-f[i], A[k * L + j], A[i * L + j]);
-            } else {
-                const int jj = j - L;
-                B[i * L + jj] = fma(-f[i], B[k * L + jj], B[i * L + jj]);
-            }
-        }
-        team_sync<TW>();
-    }
-    // back substitution, one column of B per thread (columns are independent)
-    for (int c = tid; c < L; c += T) {
-        for (int i = L - 1; i >= 0; --i) {
-            double acc = B[i * L + c];
-            for (int j = i + 1; j < L; ++j) acc = fma(-A[i * L + j], B[j * L + c], acc);
-            B[i * L + c] = acc * f[L + i];
-        }
-    }
-    team_sync<TW>();
-    return ok;
-}
 
 // Dyson refresh of both spins.  A_up is built in G1's buffer and G_up solved in G0; G_up is
 // parked in the chain's global G slot while A_dn (in G0) and G_dn (in G1) are formed, then
@@ -251,7 +85,7 @@ __device__ void measure(const TeamSmem<L>& S, int tid) {
             S.cr[w] = nd;
             S.cr[4 + w] = db;
         }
-        __syncthreads();
+        team_sync<TW>();
         if (tid == 0) {
             nu = 0.0;
             nd = 0.0;
@@ -422,16 +256,25 @@ __device__ void qmc_chain(const QmcProblem& P, int c, unsigned char* base, int t
     }
 }
 
+template <int L, int TW>
+__device__ void run_team(const QmcProblem& P, int blk, unsigned char* smem) {
+    constexpr int per_block = kBlock / (32 * TW);
+    const int team = static_cast<int>(threadIdx.x) / (32 * TW);
+    const int c = blk * per_block + team;
+    if (c < P.nchain)
+        qmc_chain<L, TW>(P, c, smem + team * team_bytes(L), static_cast<int>(threadIdx.x) % (32 * TW));
+}
+
 template <int L>
 __device__ void run_block(const QmcProblem& P, int blk, unsigned char* smem) {
+    const int tw = P.team_warps;
     if constexpr (L <= 32) {
-        // four chains per block, one warp each
-        const int warp = threadIdx.x >> 5;
-        const int c = blk * 4 + warp;
-        if (c < P.nchain)
-            qmc_chain<L, 1>(P, c, smem + warp * team_bytes(L), threadIdx.x & 31);
+        if (tw == 1) run_team<L, 1>(P, blk, smem);
+        else if (tw == 2) run_team<L, 2>(P, blk, smem);
+        else run_team<L, 4>(P, blk, smem);
     } else {
-        if (blk < P.nchain) qmc_chain<L, 4>(P, blk, smem, threadIdx.x);
+        if (tw == 2) run_team<L, 2>(P, blk, smem);
+        else run_team<L, 4>(P, blk, smem);
     }
 }
 
@@ -479,21 +322,18 @@ bool qmc_f64_supported(int L) {
     }
 }
 
-int qmc_f64_chains_per_block(int L) { return L <= 32 ? 4 : 1; }
+int qmc_default_team_warps(int L) { return L <= 32 ? 1 : 4; }
+int qmc_f64_chains_per_block(int L, int team_warps) { (void)L; return 4 / team_warps; }
 
-size_t qmc_f64_smem_bytes(int L) {
-    return L <= 32 ? 4 * team_bytes(L) : team_bytes(L);
+size_t qmc_f64_smem_bytes(int L, int team_warps) {
+    return static_cast<size_t>(4 / team_warps) * team_bytes(L);
 }
 
 cudaError_t launch_qmc_f64(const QmcBatch& b, size_t smem, cudaStream_t st) {
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(qmc_f64_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(4 * team_bytes(32) + 1024));
-        if (e != cudaSuccess) return e;
-        attr_done = true;
-    }
+    // the largest block (two-warp teams at L = 64) needs ~136 KB; set what this launch asks for
+    cudaError_t e = cudaFuncSetAttribute(qmc_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
     if (b.nblocks <= 0) return cudaSuccess;
     qmc_f64_kernel<<<b.nblocks, kBlock, smem, st>>>(b);
     return cudaGetLastError();

@@ -30,7 +30,8 @@ class hf_params(C.Structure):
         ("t", C.c_double), ("U", C.c_double), ("V0", C.c_double), ("mu", C.c_double),
         ("beta", C.c_double), ("dtau", C.c_double),
         ("n_matsubara", C.c_int), ("chains_per_site", C.c_int), ("precision", C.c_int),
-        ("refresh_every", C.c_int), ("delay_k", C.c_int), ("bin_size", C.c_int),
+        ("refresh_every", C.c_int), ("delay_k", C.c_int), ("team_warps", C.c_int),
+        ("bin_size", C.c_int),
         ("max_bins", C.c_int), ("n_warmup", C.c_int), ("n_measure", C.c_int),
         ("seed", C.c_uint64), ("h_seed", C.c_double), ("mix", C.c_double),
         ("cuda_stream", C.c_void_p),
@@ -62,6 +63,12 @@ SIGNATURES = [
     ("hf_get_accepts", C.c_int, [_VP, C.POINTER(C.c_ulonglong)]),
     ("hf_get_timings", C.c_int, [_VP, _DP]),
     ("hf_lattice_step_noalloc", C.c_int, [_VP, _VP, _VP]),
+    ("hf_batch_create", C.c_int, [C.POINTER(_VP), C.c_int, C.c_int, C.POINTER(_VP)]),
+    ("hf_batch_sweep", C.c_int, [_VP, C.c_int, C.c_int, C.c_int]),
+    ("hf_batch_rdmft_step", C.c_int, [_VP, _DP]),
+    ("hf_batch_elapsed", C.c_int, [_VP, _DP]),
+    ("hf_batch_free", None, [_VP]),
+    ("hf_batch_last_error", C.c_char_p, [_VP]),
     ("hf_free", None, [_VP]),
     ("hf_last_error", C.c_char_p, [_VP]),
 ]
@@ -221,6 +228,44 @@ def hf_lattice_step_noalloc(ctx, d_sigma: int, d_gloc: int):
     _check(lib().hf_lattice_step_noalloc(ctx, C.c_void_p(d_sigma), C.c_void_p(d_gloc)), ctx)
 
 
+def _bcheck(st, b=None):
+    if st != HF_OK:
+        msg = lib().hf_batch_last_error(b)
+        raise HFError(st, msg.decode() if msg else "")
+
+
+def hf_batch_create(handles, use_graph=1):
+    arr = (C.c_void_p * len(handles))(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    out = C.c_void_p()
+    _bcheck(lib().hf_batch_create(arr, len(handles), int(use_graph), C.byref(out)))
+    return out
+
+
+def hf_batch_sweep(b, n_warmup, n_measure, refresh_first):
+    _bcheck(lib().hf_batch_sweep(b, int(n_warmup), int(n_measure), int(refresh_first)), b)
+
+
+def hf_batch_rdmft_step(b):
+    t = C.c_double()
+    _bcheck(lib().hf_batch_rdmft_step(b, C.byref(t)), b)
+    return t.value
+
+
+def hf_batch_elapsed(b):
+    t = C.c_double()
+    _bcheck(lib().hf_batch_elapsed(b, C.byref(t)), b)
+    return t.value
+
+
+def hf_batch_free(b):
+    lib().hf_batch_free(b)
+
+
+def hf_batch_last_error(b=None):
+    m = lib().hf_batch_last_error(b)
+    return m.decode() if m else ""
+
+
 def hf_free(ctx):
     lib().hf_free(ctx)
 
@@ -251,6 +296,7 @@ def make_params(cfg: dict, stream=None, **over) -> hf_params:
     p.precision = int(d.get("precision", 0))
     p.refresh_every = int(d.get("refresh_every", 10))
     p.delay_k = int(d.get("delay_k", 1))
+    p.team_warps = int(d.get("team_warps", 0))
     p.bin_size = int(d.get("bin_size", 100))
     p.n_warmup = int(d.get("n_warmup", 500))
     p.n_measure = int(d.get("n_measure", 2000))

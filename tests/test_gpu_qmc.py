@@ -1,7 +1,8 @@
-"""Parity of the FP64 CUDA Hirsch-Fye path with the CPU oracle, through the C ABI.
+"""Parity of the FP64-class CUDA Hirsch-Fye paths with the CPU oracle, through the C ABI.
 
-Bar (FP64 path): identical accept decisions under the same Philox stream (fields compared after
-every sweep), G within 1e-10 of the oracle relative to max|G|, measurement bins within 1e-10.
+precision 0 = FP64 sweeps, precision 2 = FP32-pair sweeps with FP64 refresh.  Bar for both:
+identical accept decisions under the same Philox stream (fields compared after every sweep), G
+within 1e-10 of the oracle relative to max|G|, measurement bins within 1e-10.
 """
 import numpy as np
 import pytest
@@ -67,12 +68,15 @@ def test_initial_fields_bit_exact(hf):
         assert np.array_equal(f[c], o.init_fields(cfg["seed"], site, ch, ctx.L))
 
 
+@pytest.mark.parametrize("team_warps", [0, 2, 4])
+@pytest.mark.parametrize("precision", [0, 2])
 @pytest.mark.parametrize("L,beta", [(8, 2.0), (12, 3.0), (16, 4.0), (20, 5.0), (24, 6.0),
                                     (32, 8.0), (40, 10.0), (48, 12.0), (64, 16.0)])
-def test_sweeps_identical_decisions(hf, L, beta):
+def test_sweeps_identical_decisions(hf, L, beta, precision, team_warps):
     cps, re, nsweep, bs = 2, 7, 24, 4
     ctx, cfg = _ctx(hf, chains_per_site=cps, beta=beta, dtau=0.25, U=6.0, refresh_every=re,
-                    bin_size=bs, max_bins=nsweep // bs, seed=1234 + L)
+                    bin_size=bs, max_bins=nsweep // bs, seed=1234 + L, precision=precision,
+                    team_warps=team_warps)
     assert ctx.L == L
     baths = wl.random_baths(L, ctx.n_sites, beta, L)
     for i in range(ctx.n_sites):
@@ -114,10 +118,13 @@ def test_sweeps_identical_decisions(hf, L, beta):
     ctx.close()
 
 
-def test_u0_is_bitwise_g0(hf):
+@pytest.mark.parametrize("precision", [0, 2])
+def test_u0_is_bitwise_g0(hf, precision):
+    # FP64 path: G = G0 bit for bit; FP32-pair path: G0 split into hi + lo (two 24-bit
+    # truncations, relative error < 2^-46) and then left exactly unchanged by every (zero) update
     L, beta = 16, 4.0
     ctx, cfg = _ctx(hf, chains_per_site=2, U=0.0, beta=beta, dtau=0.25, refresh_every=3,
-                    bin_size=5, max_bins=2)
+                    bin_size=5, max_bins=2, precision=precision)
     baths = wl.random_baths(99, ctx.n_sites, beta, L)
     for i in range(ctx.n_sites):
         for sp in range(2):
@@ -128,15 +135,21 @@ def test_u0_is_bitwise_g0(hf):
     for c in range(ctx.n_chains):
         G = hf.hf_get_green(ctx.handle, c, L)
         site = c // 2
-        assert np.array_equal(G[0], o.build_g0(baths[site, 0]))
-        assert np.array_equal(G[1], o.build_g0(baths[site, 1]))
+        for sp in range(2):
+            g0 = o.build_g0(baths[site, sp])
+            if precision == 0:
+                assert np.array_equal(G[sp], g0)
+            else:
+                assert np.all(np.abs(G[sp] - g0) <= 2.0 ** -45 * np.abs(g0))
     ctx.close()
 
 
-def test_full_size_batch_sampled_chains(hf):
+@pytest.mark.parametrize("precision,team_warps", [(0, 0), (2, 0), (2, 2), (2, 4)])
+def test_full_size_batch_sampled_chains(hf, precision, team_warps):
     """The bench's workload shape (20x20 trap: 55 sites x 32 chains, L = 32) in the bench's
-    launch configuration; a sample of chains is replayed by the oracle."""
-    cfg = dict(wl.CONFIGS["square20"], n_warmup=6, n_measure=20, bin_size=10, max_bins=2)
+    launch configurations; a sample of chains is replayed by the oracle."""
+    cfg = dict(wl.CONFIGS["square20"], n_warmup=6, n_measure=20, bin_size=10, max_bins=2,
+               precision=precision, team_warps=team_warps)
     ctx = hf.Context(hf.make_params(cfg))
     L = ctx.L
     assert (ctx.n_sites, ctx.n_chains, L) == (55, 1760, 32)

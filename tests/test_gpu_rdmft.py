@@ -53,10 +53,12 @@ def test_orbit_tables_bit_exact(hf, Lx, geom):
     ctx.close()
 
 
-def test_rdmft_iteration_square6_full(hf):
+@pytest.mark.parametrize("precision", [0, 2])
+def test_rdmft_iteration_square6_full(hf, precision):
     """The 6x6 trap (U=4, V0=0.1, mu=2, beta=4, L=16), 1 chain/site, 500 + 2000 sweeps: two
-    complete iterations, each compared step by step with the oracle."""
-    cfg = dict(wl.CONFIGS["square6"])
+    complete iterations, each compared step by step with the oracle (FP64 and FP32-pair
+    sweeps)."""
+    cfg = dict(wl.CONFIGS["square6"], precision=precision)
     ctx = hf.Context(hf.make_params(cfg))
     ref = _oracle_for(cfg)
     L, ns, nw = ctx.L, ctx.n_sites, ctx.nw
