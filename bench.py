@@ -47,14 +47,6 @@ def dist_env():
     return rank, world, local
 
 
-def qmc_flops(L, nchain, sweeps, accepts, n_measure, n_refresh):
-    """Algorithmic FP64 flops of the fused QMC kernel: 10 per proposal (ratio and test),
-    4 L^2 per accepted flip (two rank-1 updates), 2 L^2 per measurement, 2 (8/3) L^3 per
-    refresh (both spins)."""
-    return (10.0 * L * nchain * sweeps + 4.0 * L * L * accepts + 2.0 * L * L * nchain * n_measure
-            + 2.0 * (8.0 / 3.0) * L ** 3 * nchain * n_refresh)
-
-
 # ---------------------------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------------------------
@@ -183,6 +175,58 @@ def run_reference(args):
     return 0
 
 
+FP32_PEAK_TFLOPS = 2.0 * 128 * 152 * 2.07e9 / 1e12   # 128 FFMA/clk/SM
+DF_OPS_PER_FMA = 15                                  # FP32-pipe ops of one double-float multiply-add
+
+
+def qmc_roofline(form, L, nchain, sweeps, accepts, n_measure, n_refresh, qmc_s, kernel):
+    """Roofline of the fused QMC kernel for one launch.
+
+    form 0 (FP64): every flop runs on the FP64 pipe; peak = nominal FP64 (2 DFMA/clk/SM).
+    form 2 (FP32 pairs): the refresh runs on the FP64 pipe, the sweep arithmetic on the FP32 pipe
+    at DF_OPS_PER_FMA ops per FP64-equivalent multiply-add; peak = the FP64-equivalent rate if
+    both pipes ran flat out and overlapped (algorithmic flops / max of the two pipe times)."""
+    f_ratio = 10.0 * L * nchain * sweeps
+    f_upd = 4.0 * L * L * accepts
+    f_meas = 2.0 * L * L * nchain * n_measure
+    f_ref = 2.0 * (8.0 / 3.0) * L ** 3 * nchain * n_refresh
+    total = f_ratio + f_upd + f_meas + f_ref
+    achieved = total / qmc_s / 1e12
+    if form == 0:
+        peak, src = FP64_PEAK_TFLOPS, "FP64 nominal: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz"
+    else:
+        t64 = f_ref / (FP64_PEAK_TFLOPS * 1e12)
+        t32 = (f_ratio + f_upd + f_meas) / 2.0 * DF_OPS_PER_FMA / (FP32_PEAK_TFLOPS * 1e12 / 2.0)
+        peak = total / max(t64, t32) / 1e12
+        src = ("mixed-pipe roof: refresh on FP64 (2 DFMA/clk/SM), pair arithmetic on FP32 "
+               "(128 FFMA/clk/SM, %d ops per FP64-equivalent FMA), both at 2.07 GHz, overlapped"
+               % DF_OPS_PER_FMA)
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None, "kernel": kernel, "peak_source": src}
+
+
+def _time_iterations(hf, ctx, stream, flush, steps):
+    import numpy as np
+    import torch
+
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ms_steps, qmc_ms, phase = [], [], np.zeros(5)
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()                       # evict L2 between timed steps
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        hf.hf_rdmft_step(ctx.handle)
+        ev1.record(stream)
+        ev1.synchronize()
+        ms_steps.append(ev0.elapsed_time(ev1))
+        t = hf.hf_get_timings(ctx.handle)
+        phase += t[:5]
+        qmc_ms.append(t[2])
+    return ms_steps, qmc_ms, phase
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -199,11 +243,18 @@ def run_ours(args):
         cpu = {"value": 1760 * 2500 * 32 / t_cpu, "unit": "proposals/s", "cores": 1,
                "kind": "oracle", "sample": sample}
     torch.cuda.set_device(local)
-    from paper_1006_2716_gb300 import hf
+    from paper_1006_2716_gb300 import autotune, hf
 
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)
-    cfg = dict(CFG, precision=args.precision, team_warps=args.team_warps)
+    L = 32
+    if args.precision < 0:
+        # chosen form: autotuned over both FP64-parity forms and the team widths
+        tune = autotune.tune_workload("square20", CFG, forms=(0, 2), device=dev, stream=stream)
+        form, tw = tune["precision"], tune["team_warps"]
+    else:
+        form, tw, tune = args.precision, args.team_warps, None
+    cfg = dict(CFG, precision=form, team_warps=tw)
     if args.sweeps:
         # short QMC launch for profiling captures only (not a benchmark value)
         cfg.update(n_warmup=args.sweeps // 5, n_measure=args.sweeps - args.sweeps // 5,
@@ -213,6 +264,7 @@ def run_ours(args):
     L, ns, nc, nw = ctx.L, ctx.n_sites, ctx.n_chains, ctx.nw
     sweeps = cfg["n_warmup"] + cfg["n_measure"]
     proposals = nc * sweeps * L
+    n_refresh = 1 + sweeps // cfg["refresh_every"]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
 
     def barrier():
@@ -224,22 +276,8 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     barrier()
     clocks = ClockSampler(local)
-    ms_steps, qmc_ms, phase = [], [], np.zeros(5)
     acc0 = hf.hf_get_accepts(ctx.handle, nc).sum()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    for _ in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.zero_()                       # evict L2 between timed steps
-        torch.cuda.synchronize(dev)
-        ev0.record(stream)
-        hf.hf_rdmft_step(ctx.handle)
-        ev1.record(stream)
-        ev1.synchronize()
-        ms_steps.append(ev0.elapsed_time(ev1))
-        t = hf.hf_get_timings(ctx.handle)
-        phase += t[:5]
-        qmc_ms.append(t[2])
+    ms_steps, qmc_ms, phase = _time_iterations(hf, ctx, stream, flush, args.steps)
     torch.cuda.synchronize(dev)
     barrier()
     clk = clocks.stop()
@@ -278,39 +316,101 @@ def run_ours(args):
         e2e_s = float(tt.item())
     e2e = {"value": proposals * world / e2e_s, "unit": "proposals/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h}
+    kernel = "qmc_df64_kernel" if form == 2 else "qmc_f64_kernel"
+    roofline = qmc_roofline(form, L, nc, sweeps, accepts / args.steps, cfg["n_measure"],
+                            n_refresh, statistics.mean(qmc_ms) / 1e3, kernel)
+    roofline["acceptance"] = accepts / (args.steps * proposals)
+    ctx.close()
 
-    # roofline of the dominant kernel (the fused QMC sweep kernel), FP64 ALU bound
-    n_refresh = 1 + sweeps // cfg["refresh_every"]
-    flops = qmc_flops(L, nc, sweeps, accepts / args.steps, cfg["n_measure"], n_refresh)
-    qmc_s = statistics.mean(qmc_ms) / 1e3
-    achieved = flops / qmc_s / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "kernel": "qmc_f64_kernel", "acceptance": accepts / (args.steps * proposals),
-                "peak_source": "FP64 nominal: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz"}
-    # our kernels per iteration: lattice step (chunks of <= 1 GiB of band buffers), Weiss/tau,
-    # QMC, reduction, self-energy update
+    # the plain FP64 per-impurity form beside the chosen form (same workload, device-timed)
+    fp64_form = None
+    if form != 0 and not args.sweeps and not args.no_fp64_form:
+        c0 = hf.Context(hf.make_params(dict(CFG, precision=0, team_warps=0)), device=dev,
+                        stream=stream)
+        for _ in range(2):
+            hf.hf_rdmft_step(c0.handle)
+        a0 = hf.hf_get_accepts(c0.handle, nc).sum()
+        ms0, q0, _ = _time_iterations(hf, c0, stream, flush, 2)
+        acc_0 = int(hf.hf_get_accepts(c0.handle, nc).sum() - a0)
+        fp64_form = {"value": proposals / (statistics.mean(ms0) / 1e3), "unit": "proposals/s",
+                     "ms_per_step": statistics.mean(ms0),
+                     "roofline": qmc_roofline(0, L, nc, sweeps, acc_0 / 2, cfg["n_measure"],
+                                              n_refresh, statistics.mean(q0) / 1e3,
+                                              "qmc_f64_kernel")}
+        c0.close()
+
     per_matrix = ctx.N * (20 + 1) * 16
     launches_per_step = -(-2 * nw // max(1, min(2 * nw, (1 << 30) // per_matrix))) + 4
+    dtype = "f64" if form == 0 else "f32x2+f64"
     line = {"metric": METRIC, "value": value, "unit": "proposals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "global_batch": nc * world, "seq_len": L,
-                       "parallelism": "replicas%d" % world,
+                       "parallelism": "replicas%d" % world, "sweep_form": form,
+                       "team_warps": tw if tw else "default",
                        "l2": "flushed (256 MB write) between timed steps"},
             "rdmft_iteration_ms": ms_per_step,
             "phase_ms": dict(zip(["lattice", "weiss_tau", "qmc", "reduce", "sigma"],
                                  [float(x) for x in phase / args.steps])),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches_per_step * args.steps, "clocks": clk}
+            "gpu_launches": launches_per_step * args.steps, "clocks": clk,
+            "fp64_form": fp64_form, "autotune": tune}
     if args.sweeps:
         line["profile_case"] = "sweeps overridden to %d: not a benchmark value" % args.sweeps
     if rank == 0:
         print(json.dumps(line))
-    ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_scan20(args):
+    """Batched uneven-L temperature scan: the 20x20 trap at beta = 5, 8, 10, 16 (L = 20, 32, 40,
+    64), 1760 chains each, one fused graph-captured launch per iteration, sweep form and team
+    width autotuned per L."""
+    import torch
+
+    from paper_1006_2716_gb300 import autotune, hf
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    betas = wl.SCAN20_BETAS
+    Ls = [int(round(b / 0.25)) for b in betas]
+    tune = {L: autotune.tune_workload("scan20_beta%g" % b, dict(CFG, beta=b), forms=(2,),
+                                      device=dev, stream=stream) for b, L in zip(betas, Ls)}
+    ctxs = [hf.Context(hf.make_params(dict(CFG, beta=b, precision=2,
+                                           team_warps=tune[L]["team_warps"])),
+                       device=dev, stream=stream) for b, L in zip(betas, Ls)]
+    batch = hf.hf_batch_create([c.handle for c in ctxs], 1)
+    for _ in range(max(args.warmup, 2)):      # first call plain, second captures the graph
+        hf.hf_batch_rdmft_step(batch)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ms = []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        torch.cuda.synchronize(dev)
+        ms.append(hf.hf_batch_rdmft_step(batch))
+    proposals = sum(c.n_chains * 2500 * c.L for c in ctxs)
+    ms_per = statistics.mean(ms)
+    line = {"metric": METRIC, "value": proposals / (ms_per / 1e3), "unit": "proposals/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32x2+f64", "data": "synthetic",
+            "config": {"workload": "scan20: 20x20 trap at beta 5/8/10/16 (L 20/32/40/64), "
+                                   "4 x 1760 chains in one fused graph-captured launch, "
+                                   "500+2000 sweeps; one step = one batched RDMFT iteration",
+                       "l2": "flushed (256 MB write) between timed steps"},
+            "autotune": {str(L): tune[L] for L in Ls}}
+    print(json.dumps(line))
+    hf.hf_batch_free(batch)
+    for c in ctxs:
+        c.close()
     return 0
 
 
@@ -323,13 +423,19 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--team-warps", type=int, default=0, choices=[0, 1, 2, 4],
                     help="warps per Markov chain (0: library default)")
-    ap.add_argument("--precision", type=int, default=0, choices=[0, 2],
-                    help="sweep arithmetic: 0 FP64, 2 FP32 pairs (both with FP64 refresh)")
+    ap.add_argument("--precision", type=int, default=-1, choices=[-1, 0, 2],
+                    help="sweep arithmetic: 0 FP64, 2 FP32 pairs (both with FP64 refresh); "
+                         "-1 (default): the autotuner picks form and team width")
+    ap.add_argument("--workload", default="square20", choices=["square20", "scan20"])
+    ap.add_argument("--no-fp64-form", action="store_true",
+                    help="skip the plain FP64 form measured beside the chosen form")
     ap.add_argument("--sweeps", type=int, default=0,
                     help="profiling only: override sweeps per iteration (result is not a bench value)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "scan20":
+        return run_scan20(args)
     return run_ours(args)
 
 

@@ -2,9 +2,10 @@
 sweeps (0 = FP64, 2 = FP32 pairs with FP64 refresh; both meet the FP64 parity bar) and the
 number of warps per Markov chain that give the most proposals per second on this GPU.
 
-Each candidate runs the real fused sweep kernel on a probe problem with the target number of
-chains (one impurity, random bath, fields from the seed) and is timed with CUDA events on the
-context stream (hf_get_timings).  Results are cached per GPU name in ``_build/autotune.json``.
+Each candidate runs the real fused sweep kernel and is timed with CUDA events on the context
+stream (hf_get_timings): ``tune_workload`` probes a workload configuration itself (its own lattice
+step supplies the baths, so acceptance rates match the real run); ``tune`` probes a synthetic
+single-impurity problem per L.  Results are cached per GPU name in ``_build/autotune.json``.
 """
 from __future__ import annotations
 
@@ -41,6 +42,49 @@ def _probe(L, chains, form, tw, sweeps, device, stream):
         best = min(best, hf.hf_get_timings(ctx.handle)[5])
     ctx.close()
     return best / sweeps                                  # ms per sweep of all chains
+
+
+def _probe_workload(cfg, form, tw, sweeps, device, stream):
+    c = dict(cfg, precision=form, team_warps=tw, n_warmup=0, n_measure=2, bin_size=1,
+             max_bins=2)
+    ctx = hf.Context(hf.make_params(c), device=device, stream=stream)
+    hf.hf_rdmft_step(ctx.handle)                          # the workload's own baths
+    hf.hf_sweep(ctx.handle, 100, 0, 0)                    # towards equilibrium acceptance
+    best = np.inf
+    for _ in range(2):
+        hf.hf_sweep(ctx.handle, sweeps, 0, 0)
+        best = min(best, hf.hf_get_timings(ctx.handle)[5])
+    ctx.close()
+    return best / sweeps
+
+
+def tune_workload(name, cfg, forms=(0, 2), sweeps=40, device="cuda:0", stream=None,
+                  use_cache=True):
+    """Best (form, team width) for one workload configuration, probed on that workload: the
+    context runs its own first lattice step, so the chains sweep the workload's real baths."""
+    import torch
+
+    L = int(round(cfg["beta"] / cfg["dtau"]))
+    gpu = torch.cuda.get_device_name(torch.device(device))
+    cache = {}
+    if use_cache and os.path.exists(_CACHE):
+        try:
+            cache = json.load(open(_CACHE))
+        except (OSError, ValueError):
+            cache = {}
+    key = "%s|%s|L=%d|forms=%s" % (gpu, name, L, ",".join(map(str, forms)))
+    if key not in cache:
+        table = {}
+        for form, tw in candidates(L, forms):
+            table["%d/%d" % (form, tw)] = _probe_workload(cfg, form, tw, sweeps, device, stream)
+        pick = min(table, key=table.get)
+        f, tw = map(int, pick.split("/"))
+        cache[key] = {"precision": f, "team_warps": tw, "ms_per_sweep": table[pick],
+                      "table": table}
+    if use_cache:
+        os.makedirs(os.path.dirname(_CACHE), exist_ok=True)
+        json.dump(cache, open(_CACHE, "w"), indent=1, sort_keys=True)
+    return cache[key]
 
 
 def tune(Ls, chains, forms=(0, 2), sweeps=30, device="cuda:0", stream=None, use_cache=True):
