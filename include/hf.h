@@ -117,6 +117,11 @@ hf_status hf_measure(hf_ctx* ctx, int site, double* gtau, double* n, double* d, 
  * wall time of the iteration to *iter_seconds (may be NULL).  Synchronises. */
 hf_status hf_rdmft_step(hf_ctx* ctx, double* iter_seconds);
 
+/* The first two phases of hf_rdmft_step alone: lattice step (eq. 2) from the current
+ * self-energy, Weiss fields and the tau-grid baths g~0(tau_m) of every inequivalent site
+ * (readable with hf_get_g0 / hf_get_gloc); no sweeps.  Synchronises. */
+hf_status hf_compute_baths(hf_ctx* ctx);
+
 /* Self-energy of the inequivalent sites, [n_sites][2][n_matsubara] complex as interleaved
  * (re, im) doubles; get copies it to the host, set replaces it from the host. */
 hf_status hf_get_sigma(hf_ctx* ctx, double* sigma);
@@ -178,6 +183,78 @@ hf_status hf_batch_elapsed(hf_batch* b, double* gpu_ms);
 
 void hf_batch_free(hf_batch* b);
 const char* hf_batch_last_error(const hf_batch* b);
+
+/* ---- Serving: continuously batched impurity solves ----------------------------------------
+ * A service object accepts Hirsch-Fye impurity solves (one inequivalent site of one RDMFT run,
+ * its bath g~0(tau) and L) from any host thread.  A scheduler thread inside the library admits
+ * queued requests in arrival order whenever the device memory they need (chains x (2 L^2 FP64
+ * entries + fields + bins), first-fit in the caller's device pool) and one of its streams are
+ * free; up to requests_per_launch admitted requests share one launch of the fused sweep kernel,
+ * and launches on different streams overlap on the GPU, so requests that arrive while others run
+ * start without waiting for them.  The Ising fields and sweep counters of each (run, site) key
+ * stay on the device between its requests (warm start; a key's next request waits for its
+ * previous one); with more keys than max_keys the least recently used idle key is dropped and
+ * its next request starts cold.  Chains are keyed by (seed, site, chain) and computed exactly as
+ * in a context of their own, so a result does not depend on which requests shared its launch.
+ * No device code waits or polls: all waiting is on the host, with timeouts. */
+typedef struct hf_srv hf_srv;
+
+typedef struct hf_srv_params {
+    int chains_per_request;   /* Markov chains per impurity solve                           */
+    int n_warmup, n_measure;  /* sweeps per solve (n_measure a multiple of bin_size)        */
+    int refresh_every;        /* FP64 Dyson refresh cadence (sweeps)                        */
+    int bin_size;             /* measured sweeps per bin                                    */
+    int precision;            /* 0 FP64 sweeps, 2 FP32-pair sweeps (both FP64 refresh)      */
+    int team_warps;           /* warps per chain (0: default)                               */
+    int max_L;                /* largest L admitted (<= 64)                                 */
+    int max_inflight;         /* requests on the device at once                             */
+    int max_keys;             /* warm-start records kept on the device                      */
+    int n_streams;            /* concurrent launches                                        */
+    int requests_per_launch;  /* requests fused into one launch (<= 16; 0: 16)              */
+} hf_srv_params;
+
+typedef struct hf_request {
+    int run, site;            /* warm-start key; site is also the Philox site word          */
+    int L;                    /* time slices, supported L <= max_L                          */
+    double beta, U;           /* dtau = beta / L, cosh(lambda) = exp(dtau U / 2)            */
+    uint64_t seed;            /* Philox key of this run's chains                            */
+    double g0_tau[2][64];     /* Hartree-shifted bath, g0_tau[spin][m], m < L               */
+} hf_request;
+
+typedef struct hf_result {
+    uint64_t ticket;
+    int status;               /* HF_OK or the failure of this solve                         */
+    int L;
+    int warm;                 /* 1 if the chains continued from kept fields                 */
+    uint32_t sweeps_done;     /* sweep counter of chain 0 after this solve                  */
+    double gtau[2][64];       /* G_sigma(tau_m), mean over chains x bins                    */
+    double n[2], d, m;        /* densities, double occupancy, n_up - n_dn                   */
+    double err[2 * 64 + 4];   /* standard errors: gtau_up[L], gtau_dn[L], n_up, n_dn, d, m  */
+    double latency_s;         /* submit -> result available                                 */
+} hf_result;
+
+typedef struct hf_srv_stats_t {
+    int queued, inflight, peak_inflight, warm_keys;
+    uint64_t completed;
+    size_t bytes_in_use, peak_bytes, arena_bytes;
+} hf_srv_stats_t;
+
+/* Device pool bytes for the warm-start store plus max_inflight requests at max_L. */
+hf_status hf_srv_workspace_size(const hf_srv_params* p, size_t* bytes);
+/* Starts the service on the current device with the caller's 256-byte-aligned device pool
+ * (kept alive by the caller until hf_srv_free).  Creates its own streams and pinned host
+ * staging. */
+hf_status hf_srv_create(const hf_srv_params* p, void* d_pool, size_t pool_bytes, hf_srv** out);
+/* Queues a solve (copied); returns at once with a ticket. */
+hf_status hf_srv_submit(hf_srv* s, const hf_request* r, uint64_t* ticket);
+/* HF_OK and *out filled once the ticket's result exists (then forgotten), HF_ENOTREADY before. */
+hf_status hf_srv_poll(hf_srv* s, uint64_t ticket, hf_result* out);
+/* As hf_srv_poll, waiting up to timeout_s seconds (HF_ETIMEOUT after). */
+hf_status hf_srv_wait(hf_srv* s, uint64_t ticket, double timeout_s, hf_result* out);
+hf_status hf_srv_stats(hf_srv* s, hf_srv_stats_t* out);
+/* Drops queued requests, lets admitted launches finish, stops the scheduler thread. */
+void hf_srv_free(hf_srv* s);
+const char* hf_srv_last_error(const hf_srv* s);
 
 /* Allocation-free lattice step.  The paper has no counterpart: this exists for callers that
  * cannot allocate device memory at call time -- code running where a cudaMalloc would

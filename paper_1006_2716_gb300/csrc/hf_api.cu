@@ -676,6 +676,15 @@ hf_status hf_rdmft_step(hf_ctx* c, double* iter_seconds) {
     return HF_OK;
 }
 
+hf_status hf_compute_baths(hf_ctx* c) {
+    if (!c) return fail(nullptr, HF_EINVAL, "null context");
+    hf_status st = enqueue_lattice(c);
+    if (st != HF_OK) return st;
+    const cudaError_t e = hfk::launch_weiss_tau(fourier_args(*c), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "Weiss-field launch");
+    return check_status(c);
+}
+
 hf_status hf_get_sigma(hf_ctx* c, double* sigma) {
     if (!c || !sigma) return fail(c, HF_EINVAL, "hf_get_sigma: null argument");
     HF_CUDA(c, cudaMemcpyAsync(sigma, c->sigma, sizeof(double2) * c->nsite * 2 * c->nw,

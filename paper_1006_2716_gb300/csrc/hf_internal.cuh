@@ -12,7 +12,7 @@
 
 namespace hfk {
 
-constexpr int kMaxProblems = 8;     // problems fused into one QMC launch
+constexpr int kMaxProblems = 16;    // problems fused into one QMC launch
 constexpr int kBlock = 128;         // threads per QMC block (4 warps)
 constexpr int kMaxL64 = 64;         // largest slice count of the FP64 sweep
 constexpr int kMaxL32 = 128;        // largest slice count of the FP32 sweep
@@ -73,6 +73,7 @@ struct QmcProblem {
     int nsweeps, meas_from, meas_to;
     int refresh_measure;  // refresh kernel: add a measurement after the refresh
     int team_warps;       // FP64 / FP32-pair sweeps: warps per chain (1, 2, 4; >= 2 for L > 32)
+    int site0;            // Philox site word = site0 + local site (served requests: the key's site)
     const double* gtau;   // [nsite][2][L]  bath g~0(tau_m)
     double* G;            // [nchain][2][L*L] (FP64 state, or FP64 scratch of the FP32 path)
     float* Gf;            // [nchain][2][L*L] FP32 state (precision 1) or nullptr
@@ -110,7 +111,7 @@ size_t refresh_f64_smem_bytes(int L);
 cudaError_t launch_refresh_f64(const QmcProblem& p, cudaStream_t st);
 
 cudaError_t launch_init_fields(int8_t* s, int nchain, int cps, int L, uint32_t seed_lo,
-                               uint32_t seed_hi, cudaStream_t st);
+                               uint32_t seed_hi, cudaStream_t st, int site0 = 0);
 
 // Reduction of bins over chains: out_mean/out_err [nsite][2L+4].
 cudaError_t launch_reduce(const double* bins, int nsite, int cps, int L, int max_bins,

@@ -203,7 +203,7 @@ __device__ void df_chain(const QmcProblem& P, int c, unsigned char* base, int ti
         for (int l = tid; l < L; l += T)
             S.ub[l] = uniform_bits53(philox4x32_10(make_uint4(nsw, static_cast<uint32_t>(l),
                                                               static_cast<uint32_t>(ch),
-                                                              static_cast<uint32_t>(site)), key));
+                                                              static_cast<uint32_t>(P.site0 + site)), key));
         team_sync<TW>();
         for (int l = 0; l < L; ++l) {
             const float2 g0 = G0[l * L + l];

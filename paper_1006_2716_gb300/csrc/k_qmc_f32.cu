@@ -117,7 +117,7 @@ __device__ void sweep32_chain(const QmcProblem& P, int c, unsigned char* base) {
         for (int l = tid; l < L; l += kT32)
             u[l] = uniform24(philox4x32_10(make_uint4(nsw, static_cast<uint32_t>(l),
                                                       static_cast<uint32_t>(ch),
-                                                      static_cast<uint32_t>(site)), key));
+                                                      static_cast<uint32_t>(P.site0 + site)), key));
         __syncthreads();
         for (int l = 0; l < L; ++l) {
             const float g0 = G0[l * L + l], g1 = G1[l * L + l];

@@ -141,7 +141,7 @@ __device__ void qmc_chain(const QmcProblem& P, int c, unsigned char* base, int t
         for (int l = tid; l < L; l += T)
             S.ub[l] = uniform_bits53(philox4x32_10(make_uint4(nsw, static_cast<uint32_t>(l),
                                                               static_cast<uint32_t>(ch),
-                                                              static_cast<uint32_t>(site)), key));
+                                                              static_cast<uint32_t>(P.site0 + site)), key));
         team_sync<TW>();
         for (int l = 0; l < L; ++l) {
             const double g0 = S.G0[l * L + l];
@@ -299,11 +299,11 @@ __global__ void __launch_bounds__(kBlock, 3) qmc_f64_kernel(const __grid_constan
 }
 
 __global__ void init_fields_kernel(int8_t* s, int nchain, int cps, int L, uint32_t seed_lo,
-                                   uint32_t seed_hi) {
+                                   uint32_t seed_hi, int site0) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= nchain * L) return;
     const int c = idx / L, l = idx - (idx / L) * L;
-    const int site = c / cps, ch = c - (c / cps) * cps;
+    const int site = site0 + c / cps, ch = c - (c / cps) * cps;
     const uint4 x = philox4x32_10(make_uint4(0xFFFFFFFFu, static_cast<uint32_t>(l),
                                              static_cast<uint32_t>(ch),
                                              static_cast<uint32_t>(site)),
@@ -340,10 +340,10 @@ cudaError_t launch_qmc_f64(const QmcBatch& b, size_t smem, cudaStream_t st) {
 }
 
 cudaError_t launch_init_fields(int8_t* s, int nchain, int cps, int L, uint32_t seed_lo,
-                               uint32_t seed_hi, cudaStream_t st) {
+                               uint32_t seed_hi, cudaStream_t st, int site0) {
     const int n = nchain * L;
     if (n <= 0) return cudaSuccess;
-    init_fields_kernel<<<(n + 255) / 256, 256, 0, st>>>(s, nchain, cps, L, seed_lo, seed_hi);
+    init_fields_kernel<<<(n + 255) / 256, 256, 0, st>>>(s, nchain, cps, L, seed_lo, seed_hi, site0);
     return cudaGetLastError();
 }
 

@@ -38,6 +38,39 @@ class hf_params(C.Structure):
     ]
 
 
+class hf_srv_params(C.Structure):
+    _fields_ = [
+        ("chains_per_request", C.c_int), ("n_warmup", C.c_int), ("n_measure", C.c_int),
+        ("refresh_every", C.c_int), ("bin_size", C.c_int), ("precision", C.c_int),
+        ("team_warps", C.c_int), ("max_L", C.c_int), ("max_inflight", C.c_int),
+        ("max_keys", C.c_int), ("n_streams", C.c_int), ("requests_per_launch", C.c_int),
+    ]
+
+
+class hf_request(C.Structure):
+    _fields_ = [
+        ("run", C.c_int), ("site", C.c_int), ("L", C.c_int), ("beta", C.c_double),
+        ("U", C.c_double), ("seed", C.c_uint64), ("g0_tau", (C.c_double * 64) * 2),
+    ]
+
+
+class hf_result(C.Structure):
+    _fields_ = [
+        ("ticket", C.c_uint64), ("status", C.c_int), ("L", C.c_int), ("warm", C.c_int),
+        ("sweeps_done", C.c_uint32), ("gtau", (C.c_double * 64) * 2), ("n", C.c_double * 2),
+        ("d", C.c_double), ("m", C.c_double), ("err", C.c_double * 132),
+        ("latency_s", C.c_double),
+    ]
+
+
+class hf_srv_stats_t(C.Structure):
+    _fields_ = [
+        ("queued", C.c_int), ("inflight", C.c_int), ("peak_inflight", C.c_int),
+        ("warm_keys", C.c_int), ("completed", C.c_uint64), ("bytes_in_use", C.c_size_t),
+        ("peak_bytes", C.c_size_t), ("arena_bytes", C.c_size_t),
+    ]
+
+
 _lib = None
 
 # (name, restype, argtypes) of every entry point declared in include/hf.h
@@ -52,6 +85,7 @@ SIGNATURES = [
     ("hf_clear_measurements", C.c_int, [_VP]),
     ("hf_measure", C.c_int, [_VP, C.c_int, _DP, _DP, _DP, _DP, _DP]),
     ("hf_rdmft_step", C.c_int, [_VP, _DP]),
+    ("hf_compute_baths", C.c_int, [_VP]),
     ("hf_get_sigma", C.c_int, [_VP, _DP]),
     ("hf_set_sigma", C.c_int, [_VP, _DP]),
     ("hf_get_observables", C.c_int, [_VP, _DP, _DP]),
@@ -69,6 +103,14 @@ SIGNATURES = [
     ("hf_batch_elapsed", C.c_int, [_VP, _DP]),
     ("hf_batch_free", None, [_VP]),
     ("hf_batch_last_error", C.c_char_p, [_VP]),
+    ("hf_srv_workspace_size", C.c_int, [C.POINTER(hf_srv_params), C.POINTER(C.c_size_t)]),
+    ("hf_srv_create", C.c_int, [C.POINTER(hf_srv_params), _VP, C.c_size_t, C.POINTER(_VP)]),
+    ("hf_srv_submit", C.c_int, [_VP, C.POINTER(hf_request), C.POINTER(C.c_uint64)]),
+    ("hf_srv_poll", C.c_int, [_VP, C.c_uint64, C.POINTER(hf_result)]),
+    ("hf_srv_wait", C.c_int, [_VP, C.c_uint64, C.c_double, C.POINTER(hf_result)]),
+    ("hf_srv_stats", C.c_int, [_VP, C.POINTER(hf_srv_stats_t)]),
+    ("hf_srv_free", None, [_VP]),
+    ("hf_srv_last_error", C.c_char_p, [_VP]),
     ("hf_free", None, [_VP]),
     ("hf_last_error", C.c_char_p, [_VP]),
 ]
@@ -156,6 +198,10 @@ def hf_rdmft_step(ctx):
     t = C.c_double()
     _check(lib().hf_rdmft_step(ctx, C.byref(t)), ctx)
     return t.value
+
+
+def hf_compute_baths(ctx):
+    _check(lib().hf_compute_baths(ctx), ctx)
 
 
 def hf_get_sigma(ctx, n_sites, nw):
@@ -264,6 +310,104 @@ def hf_batch_free(b):
 def hf_batch_last_error(b=None):
     m = lib().hf_batch_last_error(b)
     return m.decode() if m else ""
+
+
+def _scheck(st, srv=None):
+    if st != HF_OK:
+        msg = lib().hf_srv_last_error(srv)
+        raise HFError(st, msg.decode() if msg else "")
+
+
+def hf_srv_workspace_size(p: hf_srv_params) -> int:
+    n = C.c_size_t()
+    _scheck(lib().hf_srv_workspace_size(C.byref(p), C.byref(n)))
+    return n.value
+
+
+def hf_srv_create(p: hf_srv_params, d_pool: int, nbytes: int):
+    h = C.c_void_p()
+    _scheck(lib().hf_srv_create(C.byref(p), C.c_void_p(d_pool), nbytes, C.byref(h)))
+    return h
+
+
+def make_request(run, site, L, beta, U, seed, g0_tau):
+    r = hf_request()
+    r.run, r.site, r.L, r.beta, r.U, r.seed = int(run), int(site), int(L), float(beta), float(U), int(seed)
+    g = np.asarray(g0_tau, dtype=np.float64)
+    for sp in range(2):
+        for m in range(L):
+            r.g0_tau[sp][m] = g[sp, m]
+    return r
+
+
+def hf_srv_submit(srv, req: hf_request) -> int:
+    t = C.c_uint64()
+    _scheck(lib().hf_srv_submit(srv, C.byref(req), C.byref(t)), srv)
+    return t.value
+
+
+def _result_dict(r: hf_result):
+    L = r.L
+    return {"ticket": r.ticket, "status": r.status, "L": L, "warm": r.warm,
+            "sweeps_done": r.sweeps_done, "latency_s": r.latency_s,
+            "gtau": np.array([[r.gtau[sp][m] for m in range(L)] for sp in range(2)]),
+            "n": np.array([r.n[0], r.n[1]]), "d": r.d, "m": r.m,
+            "err": np.array([r.err[k] for k in range(2 * L + 4)])}
+
+
+def hf_srv_poll(srv, ticket):
+    r = hf_result()
+    st = lib().hf_srv_poll(srv, C.c_uint64(ticket), C.byref(r))
+    if st == HF_ENOTREADY:
+        return None
+    _scheck(st, srv)
+    return _result_dict(r)
+
+
+def hf_srv_wait(srv, ticket, timeout_s=60.0):
+    r = hf_result()
+    _scheck(lib().hf_srv_wait(srv, C.c_uint64(ticket), float(timeout_s), C.byref(r)), srv)
+    return _result_dict(r)
+
+
+def hf_srv_stats(srv):
+    s = hf_srv_stats_t()
+    _scheck(lib().hf_srv_stats(srv, C.byref(s)), srv)
+    return {k: getattr(s, k) for k, _ in hf_srv_stats_t._fields_}
+
+
+def hf_srv_free(srv):
+    lib().hf_srv_free(srv)
+
+
+def hf_srv_last_error(srv=None):
+    m = lib().hf_srv_last_error(srv)
+    return m.decode() if m else ""
+
+
+class Server:
+    """Owns the device pool (a torch uint8 CUDA tensor) and the service handle."""
+
+    def __init__(self, params: hf_srv_params, device="cuda:0", pool_bytes=None):
+        import torch
+
+        need = hf_srv_workspace_size(params)
+        n = max(int(pool_bytes or 0), need)
+        self.pool = torch.empty(n + 256, dtype=torch.uint8, device=torch.device(device))
+        base = self.pool.data_ptr()
+        aligned = (base + 255) & ~255
+        self.handle = hf_srv_create(params, aligned, n + 256 - (aligned - base))
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            hf_srv_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def hf_free(ctx):
