@@ -414,6 +414,98 @@ def run_scan20(args):
     return 0
 
 
+def run_disc40(args):
+    """Serving: impurity solves for the radius-40 disc (5025 sites, 663 inequivalent, U = 8)
+    from 4 concurrent RDMFT runs at (beta, V0) = (8, .010), (10, .010), (16, .010), (8, .015),
+    i.e. L = 32, 40, 64, 32; 16 chains x (200 + 1000) sweeps per solve.  Baths come from each
+    run's own lattice step.  Capacity = all 2652 solves submitted at once; then Poisson streams at
+    0.5 / 0.7 / 0.9 of capacity over warm keys give p50 / p99 latency."""
+    import numpy as np
+    import torch
+
+    from paper_1006_2716_gb300 import hf
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    runs = [(8.0, 0.010), (10.0, 0.010), (16.0, 0.010), (8.0, 0.015)]
+    baths, Ls = [], []
+    for beta, V0 in runs:
+        cfg = dict(Lx=40, geometry=1, U=8.0, V0=V0, mu=4.0, beta=beta, dtau=0.25,
+                   chains_per_site=1, n_warmup=1, n_measure=1, bin_size=1, max_bins=1,
+                   precision=2, seed=7)
+        ctx = hf.Context(hf.make_params(cfg), device=dev)
+        hf.hf_compute_baths(ctx.handle)
+        baths.append(hf.hf_get_g0(ctx.handle, ctx.n_sites, ctx.L))
+        Ls.append(ctx.L)
+        nsite = ctx.n_sites
+        ctx.close()
+    sp = hf.hf_srv_params()
+    for k, v in dict(chains_per_request=16, n_warmup=200, n_measure=1000, refresh_every=10,
+                     bin_size=100, precision=2, team_warps=0, max_L=64, max_inflight=160,
+                     max_keys=len(runs) * nsite, n_streams=12, requests_per_launch=16).items():
+        setattr(sp, k, v)
+    srv = hf.Server(sp, device=dev)
+
+    def req(run, site):
+        beta = runs[run][0]
+        return hf.make_request(run, site, Ls[run], beta, 8.0, 1000 + run, baths[run][site])
+
+    # one solve on an idle service: the per-impurity latency floor
+    t = hf.hf_srv_submit(srv.handle, req(0, 0))
+    alone = hf.hf_srv_wait(srv.handle, t, 600)["latency_s"]
+    # capacity: every (run, site) solve at once (cold keys)
+    keys = [(r, s) for s in range(nsite) for r in range(len(runs))]
+    t0 = time.perf_counter()
+    tickets = [hf.hf_srv_submit(srv.handle, req(r, s)) for r, s in keys]
+    lat_cap = [hf.hf_srv_wait(srv.handle, tk, 600)["latency_s"] for tk in tickets]
+    cap_s = time.perf_counter() - t0
+    capacity = len(keys) / cap_s
+    rng = np.random.default_rng(5)
+    loads = []
+    n_req = args.serve_requests
+    for frac in (0.5, 0.7, 0.9):
+        rate = frac * capacity
+        pick = rng.integers(0, len(keys), n_req)
+        gaps = rng.exponential(1.0 / rate, n_req)
+        tks = []
+        t_start = time.perf_counter()
+        t_next = t_start
+        for i in range(n_req):
+            t_next += gaps[i]
+            while time.perf_counter() < t_next:
+                time.sleep(min(2e-4, max(0.0, t_next - time.perf_counter())))
+            r, s = keys[pick[i]]
+            tks.append(hf.hf_srv_submit(srv.handle, req(r, s)))
+        res = [hf.hf_srv_wait(srv.handle, tk, 600) for tk in tks]
+        wall = time.perf_counter() - t_start
+        lat = np.array([x["latency_s"] for x in res])
+        loads.append({"offered_fraction": frac, "offered_solves_per_s": rate,
+                      "achieved_solves_per_s": n_req / wall, "p50_s": float(np.percentile(lat, 50)),
+                      "p99_s": float(np.percentile(lat, 99)),
+                      "warm_fraction": float(np.mean([x["warm"] for x in res]))})
+    st = hf.hf_srv_stats(srv.handle)
+    srv.close()
+    line = {"metric": "p50/p99 solve latency and solves/s (served)", "value": capacity,
+            "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": cap_s * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32x2+f64", "data": "synthetic",
+            "config": {"workload": "disc40: site-centred disc r=40 (5025 sites, 663 inequivalent), "
+                                   "U=8, mu=4, 4 runs (beta,V0)=(8,.010),(10,.010),(16,.010),(8,.015) "
+                                   "-> L 32/40/64/32; 16 chains x (200+1000) sweeps per solve",
+                       "inflight_cap": sp.max_inflight, "streams": sp.n_streams},
+            "alone_latency_s": alone, "per_impurity_solves_per_s": 1.0 / alone,
+            "capacity_solves_per_s": capacity,
+            "capacity_latency_p50_s": float(np.percentile(lat_cap, 50)),
+            "capacity_latency_p99_s": float(np.percentile(lat_cap, 99)),
+            "poisson": loads, "peak_inflight": st["peak_inflight"],
+            "peak_device_bytes": st["peak_bytes"]}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -426,7 +518,9 @@ def main():
     ap.add_argument("--precision", type=int, default=-1, choices=[-1, 0, 2],
                     help="sweep arithmetic: 0 FP64, 2 FP32 pairs (both with FP64 refresh); "
                          "-1 (default): the autotuner picks form and team width")
-    ap.add_argument("--workload", default="square20", choices=["square20", "scan20"])
+    ap.add_argument("--workload", default="square20", choices=["square20", "scan20", "disc40"])
+    ap.add_argument("--serve-requests", type=int, default=600,
+                    help="disc40: requests per Poisson load level")
     ap.add_argument("--no-fp64-form", action="store_true",
                     help="skip the plain FP64 form measured beside the chosen form")
     ap.add_argument("--sweeps", type=int, default=0,
@@ -436,6 +530,8 @@ def main():
         return run_reference(args)
     if args.workload == "scan20":
         return run_scan20(args)
+    if args.workload == "disc40":
+        return run_disc40(args)
     return run_ours(args)
 
 
