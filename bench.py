@@ -251,10 +251,10 @@ def run_ours(args):
     if args.precision < 0:
         # chosen form: autotuned over both FP64-parity forms and the team widths
         tune = autotune.tune_workload("square20", CFG, forms=(0, 2), device=dev, stream=stream)
-        form, tw = tune["precision"], tune["team_warps"]
+        form, tw, dk = tune["precision"], tune["team_warps"], tune["delay_k"]
     else:
-        form, tw, tune = args.precision, args.team_warps, None
-    cfg = dict(CFG, precision=form, team_warps=tw)
+        form, tw, dk, tune = args.precision, args.team_warps, args.delay_k, None
+    cfg = dict(CFG, precision=form, team_warps=tw, delay_k=dk)
     if args.sweeps:
         # short QMC launch for profiling captures only (not a benchmark value)
         cfg.update(n_warmup=args.sweeps // 5, n_measure=args.sweeps - args.sweeps // 5,
@@ -348,7 +348,7 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "global_batch": nc * world, "seq_len": L,
                        "parallelism": "replicas%d" % world, "sweep_form": form,
-                       "team_warps": tw if tw else "default",
+                       "team_warps": tw if tw else "default", "delay_k": dk,
                        "l2": "flushed (256 MB write) between timed steps"},
             "rdmft_iteration_ms": ms_per_step,
             "phase_ms": dict(zip(["lattice", "weiss_tau", "qmc", "reduce", "sigma"],
@@ -384,7 +384,8 @@ def run_scan20(args):
     tune = {L: autotune.tune_workload("scan20_beta%g" % b, dict(CFG, beta=b), forms=(2,),
                                       device=dev, stream=stream) for b, L in zip(betas, Ls)}
     ctxs = [hf.Context(hf.make_params(dict(CFG, beta=b, precision=2,
-                                           team_warps=tune[L]["team_warps"])),
+                                           team_warps=tune[L]["team_warps"],
+                                           delay_k=tune[L]["delay_k"])),
                        device=dev, stream=stream) for b, L in zip(betas, Ls)]
     batch = hf.hf_batch_create([c.handle for c in ctxs], 1)
     for _ in range(max(args.warmup, 2)):      # first call plain, second captures the graph
@@ -515,6 +516,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--team-warps", type=int, default=0, choices=[0, 1, 2, 4],
                     help="warps per Markov chain (0: library default)")
+    ap.add_argument("--delay-k", type=int, default=1, choices=[1, 4, 8, 16, 32],
+                    help="delayed-update depth (FP32-pair form)")
     ap.add_argument("--precision", type=int, default=-1, choices=[-1, 0, 2],
                     help="sweep arithmetic: 0 FP64, 2 FP32 pairs (both with FP64 refresh); "
                          "-1 (default): the autotuner picks form and team width")

@@ -60,7 +60,9 @@ typedef struct hf_params {
     int precision;       /* 0: FP64 sweeps; 1: FP32 sweeps + FP64 refresh; 2: FP32-pair     */
                          /* ("double-float", 48-bit significand) sweeps + FP64 refresh      */
     int refresh_every;   /* Dyson refresh after every refresh_every-th sweep of a chain     */
-    int delay_k;         /* delayed-update depth (0 or 1: rank-1 Sherman-Morrison)          */
+    int delay_k;         /* delayed-update depth: 0/1 rank-1 Sherman-Morrison; 4, 8, 16, 32  */
+                         /* (precision 2, one warp per chain): accepted flips gathered as    */
+                         /* rank-k corrections                                              */
     int team_warps;      /* FP64-class sweeps: warps per Markov chain, 1, 2 or 4 (0: default */
                          /* 1 for L <= 32, 4 above); picked per L by the autotuner          */
     int bin_size;        /* measured sweeps per bin                                         */
@@ -149,6 +151,10 @@ hf_status hf_set_fields(hf_ctx* ctx, const signed char* fields, const uint32_t* 
  * [n_chains]. */
 hf_status hf_get_green(hf_ctx* ctx, int chain, double* G);
 hf_status hf_get_accepts(hf_ctx* ctx, unsigned long long* accepts);
+
+/* Waits for the context stream and reports any failure the device recorded (numerical, or a
+ * self-check of a checking build).  */
+hf_status hf_sync(hf_ctx* ctx);
 
 /* Device time in milliseconds, from CUDA events recorded on the context stream, of the phases
  * of the last hf_rdmft_step: ms[0] lattice step, ms[1] Weiss fields + i w -> tau, ms[2] QMC

@@ -1,6 +1,7 @@
 """Autotuner of the sweep kernels: for each slice count L, the arithmetic form of the FP64-class
-sweeps (0 = FP64, 2 = FP32 pairs with FP64 refresh; both meet the FP64 parity bar) and the
-number of warps per Markov chain that give the most proposals per second on this GPU.
+sweeps (0 = FP64, 2 = FP32 pairs with FP64 refresh; both meet the FP64 parity bar), the number of
+warps per Markov chain and the delayed-update depth k in {1, 4, 8, 16, 32} (FP32-pair form) that
+give the most proposals per second on this GPU.
 
 Each candidate runs the real fused sweep kernel and is timed with CUDA events on the context
 stream (hf_get_timings): ``tune_workload`` probes a workload configuration itself (its own lattice
@@ -20,15 +21,34 @@ from . import workloads as wl
 _CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 
+DELAYS = (1, 4, 8, 16, 32)
+
+
+def _fits(L, tw, k):
+    # per-block shared memory of the FP32-pair kernel: (4 / tw) chains x (G pair buffers and
+    # scratch + delayed-update buffers), limit 227 KB
+    team = (2 * L * L + 7 * L + 11) * 8 + 16 + ((L + 15) // 16) * 16
+    delayed = (4 * k * L + 2 * L) * 8 if k > 1 else 0
+    return (4 // tw) * (team + delayed) <= 227 * 1024
+
+
 def candidates(L, forms=(0, 2)):
+    """(form, warps per chain, delay depth) triples.  Delayed updates exist in the FP32-pair form
+    and run with one warp per chain (L <= 32)."""
     tws = (1, 2, 4) if L <= 32 else (2, 4)
-    return [(f, tw) for f in forms for tw in tws]
+    out = []
+    for f in forms:
+        for tw in tws:
+            for k in (DELAYS if (f == 2 and tw == 1) else (1,)):
+                if f == 0 or _fits(L, tw, k):
+                    out.append((f, tw, k))
+    return out
 
 
-def _probe(L, chains, form, tw, sweeps, device, stream):
+def _probe(L, chains, form, tw, k, sweeps, device, stream):
     beta = 0.25 * L
     cfg = dict(Lx=1, Ly=1, geometry=0, U=8.0, V0=0.0, mu=4.0, beta=beta, dtau=0.25,
-               n_matsubara=4, chains_per_site=chains, precision=form, team_warps=tw,
+               n_matsubara=4, chains_per_site=chains, precision=form, team_warps=tw, delay_k=k,
                refresh_every=10, bin_size=max(1, sweeps), max_bins=1, n_warmup=0,
                n_measure=sweeps, seed=12345)
     ctx = hf.Context(hf.make_params(cfg), device=device, stream=stream)
@@ -44,8 +64,8 @@ def _probe(L, chains, form, tw, sweeps, device, stream):
     return best / sweeps                                  # ms per sweep of all chains
 
 
-def _probe_workload(cfg, form, tw, sweeps, device, stream):
-    c = dict(cfg, precision=form, team_warps=tw, n_warmup=0, n_measure=2, bin_size=1,
+def _probe_workload(cfg, form, tw, k, sweeps, device, stream):
+    c = dict(cfg, precision=form, team_warps=tw, delay_k=k, n_warmup=0, n_measure=2, bin_size=1,
              max_bins=2)
     ctx = hf.Context(hf.make_params(c), device=device, stream=stream)
     hf.hf_rdmft_step(ctx.handle)                          # the workload's own baths
@@ -72,14 +92,15 @@ def tune_workload(name, cfg, forms=(0, 2), sweeps=40, device="cuda:0", stream=No
             cache = json.load(open(_CACHE))
         except (OSError, ValueError):
             cache = {}
-    key = "%s|%s|L=%d|forms=%s" % (gpu, name, L, ",".join(map(str, forms)))
+    key = "%s|%s|L=%d|forms=%s|v3" % (gpu, name, L, ",".join(map(str, forms)))
     if key not in cache:
         table = {}
-        for form, tw in candidates(L, forms):
-            table["%d/%d" % (form, tw)] = _probe_workload(cfg, form, tw, sweeps, device, stream)
+        for form, tw, k in candidates(L, forms):
+            table["%d/%d/%d" % (form, tw, k)] = _probe_workload(cfg, form, tw, k, sweeps, device,
+                                                                stream)
         pick = min(table, key=table.get)
-        f, tw = map(int, pick.split("/"))
-        cache[key] = {"precision": f, "team_warps": tw, "ms_per_sweep": table[pick],
+        f, tw, k = map(int, pick.split("/"))
+        cache[key] = {"precision": f, "team_warps": tw, "delay_k": k, "ms_per_sweep": table[pick],
                       "table": table}
     if use_cache:
         os.makedirs(os.path.dirname(_CACHE), exist_ok=True)
@@ -100,15 +121,16 @@ def tune(Ls, chains, forms=(0, 2), sweeps=30, device="cuda:0", stream=None, use_
             cache = {}
     out = {}
     for L in Ls:
-        key = "%s|L=%d|chains=%d|forms=%s" % (name, L, chains, ",".join(map(str, forms)))
+        key = "%s|L=%d|chains=%d|forms=%s|v3" % (name, L, chains, ",".join(map(str, forms)))
         if key not in cache:
             table = {}
-            for form, tw in candidates(L, forms):
-                table["%d/%d" % (form, tw)] = _probe(L, chains, form, tw, sweeps, device, stream)
+            for form, tw, k in candidates(L, forms):
+                table["%d/%d/%d" % (form, tw, k)] = _probe(L, chains, form, tw, k, sweeps, device,
+                                                           stream)
             pick = min(table, key=table.get)
-            f, tw = map(int, pick.split("/"))
-            cache[key] = {"precision": f, "team_warps": tw, "ms_per_sweep": table[pick],
-                          "table": table}
+            f, tw, k = map(int, pick.split("/"))
+            cache[key] = {"precision": f, "team_warps": tw, "delay_k": k,
+                          "ms_per_sweep": table[pick], "table": table}
         out[L] = cache[key]
     if use_cache:
         os.makedirs(os.path.dirname(_CACHE), exist_ok=True)

@@ -13,10 +13,14 @@ from concurrent.futures import ThreadPoolExecutor
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-BUILD = os.path.join(HERE, "_build")
+# HF_BUILD_DIR selects the output folder (the self-checking build, HF_DEBUG_SMEM=1, goes to its
+# own folder so that it never replaces the production library)
+BUILD = os.path.join(HERE, os.environ.get("HF_BUILD_DIR", "_build"))
 LIB = os.path.join(BUILD, "libhfqmc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
+if os.environ.get("HF_DEBUG_SMEM"):
+    FLAGS.append("-DHF_DEBUG_SMEM")
 
 
 def _nvcc():

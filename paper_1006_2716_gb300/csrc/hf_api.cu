@@ -220,10 +220,30 @@ hf_status validate(const hf_params& p, std::string& err) {
     }
     if (p.precision < 0 || p.precision > 2) { err = "precision must be 0, 1 or 2"; return HF_EINVAL; }
     if (p.chains_per_site < 1) { err = "chains_per_site must be >= 1"; return HF_EINVAL; }
+    if (!(p.delay_k == 0 || p.delay_k == 1 || p.delay_k == 4 || p.delay_k == 8 || p.delay_k == 16 ||
+          p.delay_k == 32) || (p.delay_k > 1 && p.precision != 2)) {
+        err = "delay_k must be 0/1 (rank-1) or, for FP32-pair sweeps (precision 2), 4, 8, 16 or 32";
+        return HF_EINVAL;
+    }
     if (!(p.team_warps == 0 || p.team_warps == 1 || p.team_warps == 2 || p.team_warps == 4) ||
         (L > 32 && p.team_warps == 1)) {
         err = "team_warps must be 0 (default), 1, 2 or 4, and >= 2 for L > 32";
         return HF_EINVAL;
+    }
+    if (p.delay_k > 1 && (p.team_warps > 1 || (p.team_warps == 0 && hfk::qmc_default_team_warps(L) > 1))) {
+        err = "delay_k > 1 runs with one warp per chain only (team_warps = 1, L <= 32)";
+        return HF_EINVAL;
+    }
+    if (p.precision != 1) {
+        const int tw = p.team_warps > 0 ? p.team_warps : hfk::qmc_default_team_warps(L);
+        const size_t smem = (p.precision == 2) ? hfk::qmc_df64_smem_bytes(L, tw, p.delay_k)
+                                               : hfk::qmc_f64_smem_bytes(L, tw);
+        if (smem > static_cast<size_t>(227) * 1024) {
+            err = "team_warps / delay_k need " + std::to_string(smem) +
+                  " bytes of shared memory per block (limit 232448); use more warps per chain or a "
+                  "smaller delay_k";
+            return HF_EINVAL;
+        }
     }
     if (p.n_matsubara < 1 || p.n_matsubara > 100000) { err = "n_matsubara out of range"; return HF_EINVAL; }
     if (p.bin_size < 1 || p.max_bins < 1) { err = "bin_size and max_bins must be >= 1"; return HF_EINVAL; }
@@ -314,6 +334,7 @@ hfk::QmcProblem make_problem(const hf_ctx& c, int n_warmup, int n_measure, int r
     q.max_bins = c.p.max_bins;
     q.refresh_first = refresh_first;
     q.team_warps = c.p.team_warps > 0 ? c.p.team_warps : hfk::qmc_default_team_warps(c.L);
+    q.delay_k = c.p.delay_k > 1 ? c.p.delay_k : 1;
     q.gtau = c.gtau;
     q.G = c.G;
     q.Gf = c.Gf;
@@ -332,6 +353,9 @@ hf_status check_status(hf_ctx* c) {
     HF_CUDA(c, cudaStreamSynchronize(c->stream));
     if (st[0] != 0) {
         HF_CUDA(c, cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+        if (st[0] == HF_EINVAL)   // only the self-checking build reports this
+            return fail(c, HF_EINVAL, "device self-check failed at line " + std::to_string(st[2]) +
+                                          " (value " + std::to_string(st[3]) + ")");
         return fail(c, static_cast<hf_status>(st[0]),
                     "device reported a numerical failure (singular Dyson matrix or non-finite value)");
     }
@@ -385,7 +409,8 @@ hf_status launch_sweeps(hf_ctx* c, int n_warmup, int n_measure, int refresh_firs
     const int tw = b.p[0].team_warps;
     const int cpb = hfk::qmc_f64_chains_per_block(c->L, tw);
     b.nblocks = (c->nchain + cpb - 1) / cpb;
-    const size_t smem = hfk::qmc_f64_smem_bytes(c->L, tw);
+    const size_t smem = (c->p.precision == 2) ? hfk::qmc_df64_smem_bytes(c->L, tw, b.p[0].delay_k)
+                                              : hfk::qmc_f64_smem_bytes(c->L, tw);
     cudaError_t e = (c->p.precision == 2) ? hfk::launch_qmc_df64(b, smem, c->stream)
                                           : hfk::launch_qmc_f64(b, smem, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "QMC sweep launch");
@@ -775,6 +800,11 @@ hf_status hf_get_accepts(hf_ctx* c, unsigned long long* accepts) {
     return HF_OK;
 }
 
+hf_status hf_sync(hf_ctx* c) {
+    if (!c) return fail(nullptr, HF_EINVAL, "null context");
+    return check_status(c);
+}
+
 hf_status hf_get_timings(hf_ctx* c, double* ms) {
     if (!c || !ms) return fail(c, HF_EINVAL, "hf_get_timings: null argument");
     const int pairs[6][2] = {{0, 1}, {1, 2}, {3, 4}, {4, 5}, {5, 6}, {7, 8}};
@@ -857,7 +887,8 @@ static hf_status enqueue_batch_qmc(hf_batch* b, int n_warmup, int n_measure, int
         const int tw = qb.p[i].team_warps;
         const int cpb = hfk::qmc_f64_chains_per_block(c->L, tw);
         blocks += (c->nchain + cpb - 1) / cpb;
-        smem = std::max(smem, hfk::qmc_f64_smem_bytes(c->L, tw));
+        smem = std::max(smem, c->p.precision == 2 ? hfk::qmc_df64_smem_bytes(c->L, tw, qb.p[i].delay_k)
+                                                  : hfk::qmc_f64_smem_bytes(c->L, tw));
     }
     qb.nblocks = blocks;
     const cudaError_t e = (b->ctx[0]->p.precision == 2) ? hfk::launch_qmc_df64(qb, smem, b->stream)

@@ -74,6 +74,7 @@ struct QmcProblem {
     int refresh_measure;  // refresh kernel: add a measurement after the refresh
     int team_warps;       // FP64 / FP32-pair sweeps: warps per chain (1, 2, 4; >= 2 for L > 32)
     int site0;            // Philox site word = site0 + local site (served requests: the key's site)
+    int delay_k;          // FP32-pair sweeps: delayed-update depth (<= 1: rank-1 updates)
     const double* gtau;   // [nsite][2][L]  bath g~0(tau_m)
     double* G;            // [nchain][2][L*L] (FP64 state, or FP64 scratch of the FP32 path)
     float* Gf;            // [nchain][2][L*L] FP32 state (precision 1) or nullptr
@@ -100,6 +101,7 @@ int qmc_default_team_warps(int L);
 
 // FP32-pair ("double-float") sweeps with FP64 refresh: same layout and L set as the FP64 kernel.
 cudaError_t launch_qmc_df64(const QmcBatch& b, size_t smem, cudaStream_t st);
+size_t qmc_df64_smem_bytes(int L, int team_warps, int delay_k);
 
 size_t qmc_f32_smem_bytes(int L);
 bool qmc_f32_supported(int L);

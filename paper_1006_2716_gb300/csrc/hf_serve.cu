@@ -278,6 +278,7 @@ hf_status start_launch(hf_srv* S, Launch& Lh) {
         q.max_bins = S->nb;
         q.refresh_first = 1;
         q.team_warps = p.team_warps > 0 ? p.team_warps : hfk::qmc_default_team_warps(L);
+        q.delay_k = 1;
         if (L > 32 && q.team_warps == 1) q.team_warps = 2;
         q.gtau = b.gtau;
         q.G = b.G;
@@ -289,7 +290,8 @@ hf_status start_launch(hf_srv* S, Launch& Lh) {
         q.status = b.status;
         const int cpb = hfk::qmc_f64_chains_per_block(L, q.team_warps);
         blocks += (cps + cpb - 1) / cpb;
-        smem = std::max(smem, hfk::qmc_f64_smem_bytes(L, q.team_warps));
+        smem = std::max(smem, p.precision == 2 ? hfk::qmc_df64_smem_bytes(L, q.team_warps, 1)
+                                               : hfk::qmc_f64_smem_bytes(L, q.team_warps));
     }
     qb.nblocks = blocks;
     if (e == cudaSuccess)

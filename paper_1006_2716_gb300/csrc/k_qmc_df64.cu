@@ -161,6 +161,51 @@ __device__ void measure_df(const TeamSmem<L>& S, int tid) {
     team_sync<TW>();
 }
 
+// Delayed updates: per spin, the pending columns u_q (stored transposed, Ut[q][i]) and rows
+// v_q (V[q][j]) of the accepted flips since the last flush, and the current diagonal.
+__host__ __device__ constexpr size_t delayed_bytes(int L, int K) {
+    return K > 1 ? static_cast<size_t>(4 * K * L + 2 * L) * sizeof(float2) : 0;
+}
+
+// G += sum_q u_q v_q^T in accept order (the same multiply-adds, in the same order, as the
+// rank-1 path applies them), then reload the diagonal.
+template <int L, int TW>
+__device__ void df_flush(float2* G0, float2* G1, const float2* Ut0, const float2* Ut1,
+                         const float2* V0, const float2* V1, int m, float2* dg0, float2* dg1,
+                         int tid) {
+    constexpr int T = 32 * TW;
+    if constexpr (T % L == 0) {
+        const int j = tid % L;
+#pragma unroll 4
+        for (int i = tid / L; i < L; i += T / L) {
+            float2 a0 = G0[i * L + j], a1 = G1[i * L + j];
+            for (int q = 0; q < m; ++q) {
+                a0 = df_fma(Ut0[q * L + i], V0[q * L + j], a0);
+                a1 = df_fma(Ut1[q * L + i], V1[q * L + j], a1);
+            }
+            G0[i * L + j] = a0;
+            G1[i * L + j] = a1;
+        }
+    } else {
+        for (int e = tid; e < L * L; e += T) {
+            const int i = e / L, j = e - (e / L) * L;
+            float2 a0 = G0[e], a1 = G1[e];
+            for (int q = 0; q < m; ++q) {
+                a0 = df_fma(Ut0[q * L + i], V0[q * L + j], a0);
+                a1 = df_fma(Ut1[q * L + i], V1[q * L + j], a1);
+            }
+            G0[e] = a0;
+            G1[e] = a1;
+        }
+    }
+    team_sync<TW>();
+    for (int i = tid; i < L; i += T) {
+        dg0[i] = G0[i * L + i];
+        dg1[i] = G1[i * L + i];
+    }
+    team_sync<TW>();
+}
+
 template <int L, int TW>
 __device__ void df_chain(const QmcProblem& P, int c, unsigned char* base, int tid) {
     constexpr int T = 32 * TW;
@@ -178,7 +223,31 @@ __device__ void df_chain(const QmcProblem& P, int c, unsigned char* base, int ti
     const uint2 key = make_uint2(P.seed_lo, P.seed_hi);
     const float2 a_p = make_float2(P.af_p, P.afl_p), a_m = make_float2(P.af_m, P.afl_m);
     const float2 one = make_float2(1.0f, 0.0f);
+    const int K = P.delay_k > 1 ? P.delay_k : 1;
+    float2* Ut0 = reinterpret_cast<float2*>(base + team_bytes(L));   // [K][L]
+    float2* Ut1 = Ut0 + K * L;
+    float2* V0 = Ut1 + K * L;                                         // [K][L]
+    float2* V1 = V0 + K * L;
+    float2* dg0 = V1 + K * L;                                         // [L]
+    float2* dg1 = dg0 + L;
 
+#ifdef HF_DEBUG_SMEM
+    {   // self-check: this team's region [base, base + team + delayed) inside the dynamic window
+        extern __shared__ __align__(16) unsigned char smem[];
+        unsigned dyn;
+        asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+        const long off = base - smem;
+        const long end = off + static_cast<long>(team_bytes(L) + delayed_bytes(L, P.delay_k));
+        if (off < 0 || end > static_cast<long>(dyn)) {
+            if (tid == 0) {
+                atomicExch(P.status + 2, __LINE__);
+                atomicExch(P.status + 3, static_cast<int>(end));
+                atomicExch(P.status, static_cast<int>(HF_EINVAL));
+            }
+            return;
+        }
+    }
+#endif
     for (int l = tid; l < L; l += T) S.s[l] = P.s[static_cast<size_t>(c) * L + l];
     uint32_t nsw = P.nsw[c];
     uint32_t nmeas = P.nmeas[c];
@@ -204,10 +273,16 @@ __device__ void df_chain(const QmcProblem& P, int c, unsigned char* base, int ti
             S.ub[l] = uniform_bits53(philox4x32_10(make_uint4(nsw, static_cast<uint32_t>(l),
                                                               static_cast<uint32_t>(ch),
                                                               static_cast<uint32_t>(P.site0 + site)), key));
+        int m = 0;                  // pending delayed updates
+        if (K > 1)
+            for (int i = tid; i < L; i += T) {
+                dg0[i] = G0[i * L + i];
+                dg1[i] = G1[i * L + i];
+            }
         team_sync<TW>();
         for (int l = 0; l < L; ++l) {
-            const float2 g0 = G0[l * L + l];
-            const float2 g1 = G1[l * L + l];
+            const float2 g0 = (K > 1) ? dg0[l] : G0[l * L + l];
+            const float2 g1 = (K > 1) ? dg1[l] : G1[l * L + l];
             const int sl = S.s[l];
             const float auf = (sl > 0) ? P.af_p : P.af_m;   // up:   sigma s_l = +s_l
             const float adf = (sl > 0) ? P.af_m : P.af_p;   // down: sigma s_l = -s_l
@@ -243,6 +318,52 @@ __device__ void df_chain(const QmcProblem& P, int c, unsigned char* base, int ti
                 const float2 Rd = df_add(one, df_mul(df_add(one, df_neg(g1)), ad2));
                 const float2 fu = df_mul(au2, df_recip(Ru));
                 const float2 fd = df_mul(ad2, df_recip(Rd));
+                if (K > 1) {
+#ifdef HF_DEBUG_SMEM
+                    if (m < 0 || m >= K) {   // self-check: append slot inside the buffers
+                        if (tid == 0) {
+                            atomicExch(P.status + 2, __LINE__);
+                            atomicExch(P.status + 3, m);
+                            atomicExch(P.status, static_cast<int>(HF_EINVAL));
+                        }
+                        m = 0;
+                    }
+#endif
+                    // every thread of the team has read dg[l] for this decision before any
+                    // diagonal or pending slot is written (threads run ahead through rejections)
+                    team_sync<TW>();
+                    // current column l and row l = stale values + pending products, in accept
+                    // order; append u = f (G[:, l] - e_l), v = G[l, :]; update the diagonal
+                    for (int i = tid; i < L; i += T) {
+                        float2 c0 = G0[i * L + l], c1 = G1[i * L + l];
+                        float2 r0 = G0[l * L + i], r1 = G1[l * L + i];
+                        for (int q = 0; q < m; ++q) {
+                            c0 = df_fma(Ut0[q * L + i], V0[q * L + l], c0);
+                            c1 = df_fma(Ut1[q * L + i], V1[q * L + l], c1);
+                            r0 = df_fma(Ut0[q * L + l], V0[q * L + i], r0);
+                            r1 = df_fma(Ut1[q * L + l], V1[q * L + i], r1);
+                        }
+                        if (i == l) {
+                            c0 = df_add(c0, df_neg(one));
+                            c1 = df_add(c1, df_neg(one));
+                        }
+                        const float2 u0 = df_mul(fu, c0), u1 = df_mul(fd, c1);
+                        Ut0[m * L + i] = u0;
+                        Ut1[m * L + i] = u1;
+                        V0[m * L + i] = r0;
+                        V1[m * L + i] = r1;
+                        dg0[i] = df_fma(u0, r0, dg0[i]);
+                        dg1[i] = df_fma(u1, r1, dg1[i]);
+                    }
+                    team_sync<TW>();
+                    if (tid == 0) S.s[l] = static_cast<int8_t>(-sl);
+                    ++acc;
+                    if (++m == K) {
+                        df_flush<L, TW>(G0, G1, Ut0, Ut1, V0, V1, m, dg0, dg1, tid);
+                        m = 0;
+                    }
+                    continue;
+                }
                 for (int i = tid; i < L; i += T) {
                     float2 x0 = G0[i * L + l], x1 = G1[i * L + l];
                     if (i == l) {
@@ -282,6 +403,7 @@ __device__ void df_chain(const QmcProblem& P, int c, unsigned char* base, int ti
                 ++acc;
             }
         }
+        if (K > 1 && m > 0) df_flush<L, TW>(G0, G1, Ut0, Ut1, V0, V1, m, dg0, dg1, tid);
         ++nsw;
         team_sync<TW>();
         if (P.refresh_every > 0 && (nsw % static_cast<uint32_t>(P.refresh_every)) == 0u)
@@ -320,8 +442,9 @@ __device__ void run_team_df(const QmcProblem& P, int blk, unsigned char* smem) {
     constexpr int per_block = kBlock / (32 * TW);
     const int team = static_cast<int>(threadIdx.x) / (32 * TW);
     const int c = blk * per_block + team;
+    const size_t stride = team_bytes(L) + delayed_bytes(L, P.delay_k);
     if (c < P.nchain)
-        df_chain<L, TW>(P, c, smem + team * team_bytes(L), static_cast<int>(threadIdx.x) % (32 * TW));
+        df_chain<L, TW>(P, c, smem + team * stride, static_cast<int>(threadIdx.x) % (32 * TW));
 }
 
 template <int L>
@@ -358,6 +481,10 @@ __global__ void __launch_bounds__(kBlock, 3) qmc_df64_kernel(const __grid_consta
 }
 
 }  // namespace
+
+size_t qmc_df64_smem_bytes(int L, int team_warps, int delay_k) {
+    return static_cast<size_t>(4 / team_warps) * (team_bytes(L) + delayed_bytes(L, delay_k));
+}
 
 cudaError_t launch_qmc_df64(const QmcBatch& b, size_t smem, cudaStream_t st) {
     // the largest block (two-warp teams at L = 64) needs ~136 KB; set what this launch asks for

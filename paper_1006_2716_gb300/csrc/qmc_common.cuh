@@ -11,7 +11,11 @@ namespace qmc {
 
 // A team of TW warps owns one chain; a 128-thread block holds 4 / TW teams.  One-warp teams
 // synchronise with __syncwarp, the whole-block team with __syncthreads, two-warp teams with the
-// named barrier 1 + team index over their 64 threads.
+// named barrier 1 + team index over their 64 threads.  The named barrier uses the non-aligned
+// form (arrivals counted per thread, defined even if a warp reaches it diverged) after an
+// explicit __syncwarp: the compiler does not treat inline assembly as a barrier, so it does not
+// reconverge a warp before it, and the aligned form with a partially converged warp lets the two
+// warps of a team fall out of step.
 template <int TW>
 __device__ __forceinline__ void team_sync() {
     if constexpr (TW == 1) {
@@ -19,7 +23,8 @@ __device__ __forceinline__ void team_sync() {
     } else if constexpr (TW * 32 == kBlock) {
         __syncthreads();
     } else {
-        asm volatile("bar.sync %0, %1;" ::"r"(1 + static_cast<int>(threadIdx.x) / (32 * TW)),
+        __syncwarp();
+        asm volatile("barrier.sync %0, %1;" ::"r"(1 + static_cast<int>(threadIdx.x) / (32 * TW)),
                      "r"(32 * TW)
                      : "memory");
     }

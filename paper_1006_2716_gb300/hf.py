@@ -12,7 +12,7 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libhfqmc.so")
+LIB_PATH = os.path.join(_HERE, os.environ.get("HF_BUILD_DIR", "_build"), "libhfqmc.so")
 
 HF_OK, HF_EINVAL, HF_ENOMEM, HF_ECUDA, HF_ETIMEOUT, HF_ENUMERIC, HF_EBUSY, HF_ENOTREADY = (
     0, -1, -2, -3, -4, -5, -6, -7)
@@ -96,6 +96,7 @@ SIGNATURES = [
     ("hf_get_green", C.c_int, [_VP, C.c_int, _DP]),
     ("hf_get_accepts", C.c_int, [_VP, C.POINTER(C.c_ulonglong)]),
     ("hf_get_timings", C.c_int, [_VP, _DP]),
+    ("hf_sync", C.c_int, [_VP]),
     ("hf_lattice_step_noalloc", C.c_int, [_VP, _VP, _VP]),
     ("hf_batch_create", C.c_int, [C.POINTER(_VP), C.c_int, C.c_int, C.POINTER(_VP)]),
     ("hf_batch_sweep", C.c_int, [_VP, C.c_int, C.c_int, C.c_int]),
@@ -261,6 +262,10 @@ def hf_get_accepts(ctx, n_chains):
     a = np.zeros(n_chains, dtype=np.uint64)
     _check(lib().hf_get_accepts(ctx, a.ctypes.data_as(C.POINTER(C.c_ulonglong))), ctx)
     return a
+
+
+def hf_sync(ctx):
+    _check(lib().hf_sync(ctx), ctx)
 
 
 def hf_get_timings(ctx):

@@ -63,6 +63,10 @@ def test_workspace_size_and_orbit_counts(lib):
     (dict(team_warps=3), "team_warps"),
     (dict(beta=16.0, dtau=0.25, team_warps=1), "team_warps"),
     (dict(precision=3), "precision"),
+    (dict(delay_k=4), "delay_k"),
+    (dict(precision=2, delay_k=5), "delay_k"),
+    (dict(precision=2, beta=8.0, dtau=0.25, team_warps=2, delay_k=4), "one warp per chain"),
+    (dict(precision=2, beta=16.0, dtau=0.25, delay_k=8), "one warp per chain"),
 ])
 def test_invalid_params_rejected(lib, over, frag):
     p = hf.make_params(wl.CONFIGS["square6"], **over)

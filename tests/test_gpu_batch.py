@@ -126,5 +126,5 @@ def test_autotuner_picks_a_valid_configuration(hf):
 
     res = autotune.tune([20, 64], chains=64, sweeps=6, use_cache=False)
     for L, r in res.items():
-        assert (r["precision"], r["team_warps"]) in autotune.candidates(L)
+        assert (r["precision"], r["team_warps"], r["delay_k"]) in autotune.candidates(L)
         assert r["ms_per_sweep"] == min(r["table"].values()) > 0

@@ -175,6 +175,36 @@ def test_full_size_batch_sampled_chains(hf, precision, team_warps):
     ctx.close()
 
 
+@pytest.mark.parametrize("L,beta,team_warps", [(8, 2.0, 1), (16, 4.0, 1), (20, 5.0, 1),
+                                               (32, 8.0, 1)])
+def test_delayed_updates_bitwise_equal_rank1(hf, L, beta, team_warps):
+    """Rank-k delayed updates apply the same pair multiply-adds in the same order as rank-1
+    updates, so every delay depth gives bit-for-bit the rank-1 result."""
+    ref = None
+    for k in (1, 4, 8, 16, 32):
+        ctx, cfg = _ctx(hf, chains_per_site=2, beta=beta, dtau=0.25, U=7.0, refresh_every=5,
+                        bin_size=4, max_bins=3, seed=77, precision=2, delay_k=k,
+                        team_warps=team_warps)
+        baths = wl.random_baths(3 * L, ctx.n_sites, beta, L)
+        for i in range(ctx.n_sites):
+            for sp in range(2):
+                hf.hf_set_g0(ctx.handle, i, sp, baths[i, sp])
+        hf.hf_sweep(ctx.handle, 3, 12, 1)
+        out = (hf.hf_get_fields(ctx.handle, ctx.n_chains, L)[0],
+               hf.hf_get_accepts(ctx.handle, ctx.n_chains),
+               [hf.hf_get_green(ctx.handle, c, L) for c in (0, ctx.n_chains - 1)],
+               [hf.hf_measure(ctx.handle, i, L)[0] for i in range(ctx.n_sites)])
+        ctx.close()
+        if ref is None:
+            ref = out
+            continue
+        assert np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1]), k
+        for a, b in zip(out[2], ref[2]):
+            assert np.array_equal(a, b), k
+        for a, b in zip(out[3], ref[3]):
+            assert np.array_equal(a, b), k
+
+
 def test_resume_from_checkpoint_is_bitwise(hf):
     """Fields + sweep counters saved at a refresh boundary reproduce the uninterrupted run."""
     L, beta = 16, 4.0
