@@ -117,7 +117,8 @@ def _oracle_sample(q, n_chains, n_freq):
         Gd, _ = o.dyson(g0d, s, -1, lam)
         bins = np.zeros((cfg["n_measure"] // cfg["bin_size"], 2 * L + 3))
         o.run_chain(lam, g0u, g0d, cfg["seed"], c, 0, 0, cfg["n_warmup"], cfg["n_measure"],
-                    cfg["refresh_every"], cfg["bin_size"], s, Gu, Gd, bins)
+                    cfg["refresh_every"], cfg["bin_size"], s, Gu, Gd, bins,
+                    refresh_stagger=cfg.get("refresh_stagger", 0))
     t_qmc = (time.perf_counter() - t0) * (1760.0 / n_chains)
     q.put((t_lat, t_qmc))
 
@@ -250,11 +251,13 @@ def run_ours(args):
     L = 32
     if args.precision < 0:
         # chosen form: autotuned over both FP64-parity forms and the team widths
-        tune = autotune.tune_workload("square20", CFG, forms=(0, 2), device=dev, stream=stream)
+        tune = autotune.tune_workload("square20" if args.refresh_stagger == 0 else "square20_stagger",
+                                      dict(CFG, refresh_stagger=args.refresh_stagger),
+                                      forms=(0, 2), device=dev, stream=stream)
         form, tw, dk = tune["precision"], tune["team_warps"], tune["delay_k"]
     else:
         form, tw, dk, tune = args.precision, args.team_warps, args.delay_k, None
-    cfg = dict(CFG, precision=form, team_warps=tw, delay_k=dk)
+    cfg = dict(CFG, precision=form, team_warps=tw, delay_k=dk, refresh_stagger=args.refresh_stagger)
     if args.sweeps:
         # short QMC launch for profiling captures only (not a benchmark value)
         cfg.update(n_warmup=args.sweeps // 5, n_measure=args.sweeps - args.sweeps // 5,
@@ -325,7 +328,8 @@ def run_ours(args):
     # the plain FP64 per-impurity form beside the chosen form (same workload, device-timed)
     fp64_form = None
     if form != 0 and not args.sweeps and not args.no_fp64_form:
-        c0 = hf.Context(hf.make_params(dict(CFG, precision=0, team_warps=0)), device=dev,
+        c0 = hf.Context(hf.make_params(dict(CFG, precision=0, team_warps=0,
+                                            refresh_stagger=args.refresh_stagger)), device=dev,
                         stream=stream)
         for _ in range(2):
             hf.hf_rdmft_step(c0.handle)
@@ -349,6 +353,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "global_batch": nc * world, "seq_len": L,
                        "parallelism": "replicas%d" % world, "sweep_form": form,
                        "team_warps": tw if tw else "default", "delay_k": dk,
+                       "refresh_stagger": args.refresh_stagger,
                        "l2": "flushed (256 MB write) between timed steps"},
             "rdmft_iteration_ms": ms_per_step,
             "phase_ms": dict(zip(["lattice", "weiss_tau", "qmc", "reduce", "sigma"],
@@ -522,6 +527,9 @@ def main():
                     help="sweep arithmetic: 0 FP64, 2 FP32 pairs (both with FP64 refresh); "
                          "-1 (default): the autotuner picks form and team width")
     ap.add_argument("--workload", default="square20", choices=["square20", "scan20", "disc40"])
+    ap.add_argument("--refresh-stagger", type=int, default=0, choices=[0, 1],
+                    help="1: per-chain refresh phases; 0 (default): every chain refreshes on the "
+                         "same sweeps")
     ap.add_argument("--serve-requests", type=int, default=600,
                     help="disc40: requests per Poisson load level")
     ap.add_argument("--no-fp64-form", action="store_true",

@@ -60,6 +60,11 @@ typedef struct hf_params {
     int precision;       /* 0: FP64 sweeps; 1: FP32 sweeps + FP64 refresh; 2: FP32-pair     */
                          /* ("double-float", 48-bit significand) sweeps + FP64 refresh      */
     int refresh_every;   /* Dyson refresh after every refresh_every-th sweep of a chain     */
+    int refresh_stagger; /* 0: a chain refreshes when its sweep counter n is a multiple of   */
+                         /* refresh_every; 1: when n + site + chain is (site, chain = the    */
+                         /* Philox counter words), so the FP64 refreshes of chains that run  */
+                         /* side by side fall on different sweeps; needs precision 0 or 2    */
+                         /* unless refresh_every is 1                                       */
     int delay_k;         /* delayed-update depth: 0/1 rank-1 Sherman-Morrison; 4, 8, 16, 32  */
                          /* (precision 2, one warp per chain): accepted flips gathered as    */
                          /* rank-k corrections                                              */
@@ -209,6 +214,7 @@ typedef struct hf_srv_params {
     int chains_per_request;   /* Markov chains per impurity solve                           */
     int n_warmup, n_measure;  /* sweeps per solve (n_measure a multiple of bin_size)        */
     int refresh_every;        /* FP64 Dyson refresh cadence (sweeps)                        */
+    int refresh_stagger;      /* 1: per-chain refresh phases, as hf_params.refresh_stagger  */
     int bin_size;             /* measured sweeps per bin                                    */
     int precision;            /* 0 FP64 sweeps, 2 FP32-pair sweeps (both FP64 refresh)      */
     int team_warps;           /* warps per chain (0: default)                               */

@@ -63,7 +63,7 @@ def lib():
             L.hfo_measure.restype = None
             L.hfo_run_chain.argtypes = [C.c_int, C.c_double, dp, dp, C.c_uint64, C.c_uint32,
                                         C.c_uint32, u32p, C.c_int, C.c_int, C.c_int, C.c_int,
-                                        i8p, dp, dp, dp]
+                                        C.c_int, i8p, dp, dp, dp]
             L.hfo_run_chain.restype = C.c_long
             L.hfo_brute_force.argtypes = [C.c_int, C.c_double, dp, dp, dp]
             L.hfo_brute_force.restype = C.c_int
@@ -152,15 +152,16 @@ def measure(Gup, Gdn):
 
 
 def run_chain(lam, g0up, g0dn, seed, site, chain, nsw, n_warmup, n_measure,
-              refresh_every, bin_size, s, Gup, Gdn, bins):
-    """In place on s, Gup, Gdn, bins ([nbins, 2L+3]).  Returns (accepts, new nsw)."""
+              refresh_every, bin_size, s, Gup, Gdn, bins, refresh_stagger=0):
+    """In place on s, Gup, Gdn, bins ([nbins, 2L+3]).  Returns (accepts, new nsw).
+    refresh_stagger=1 offsets the chain's refresh sweeps by (site + chain) % refresh_every."""
     L = s.shape[0]
     g0up = _f64(g0up)
     g0dn = _f64(g0dn)
     n = C.c_uint32(nsw)
     acc = lib().hfo_run_chain(L, lam, _p(g0up, C.c_double), _p(g0dn, C.c_double), seed,
                               site, chain, C.byref(n), n_warmup, n_measure, refresh_every,
-                              bin_size, _p(s, C.c_int8), _p(Gup, C.c_double),
+                              int(refresh_stagger), bin_size, _p(s, C.c_int8), _p(Gup, C.c_double),
                               _p(Gdn, C.c_double), _p(bins, C.c_double))
     if acc < 0:
         raise FloatingPointError("singular Dyson refresh")

@@ -228,15 +228,18 @@ void hfo_measure(int L, const double* Gup, const double* Gdn, double* acc)
 
 long hfo_run_chain(int L, double lambda, const double* g0up, const double* g0dn,
                    uint64_t seed, uint32_t site, uint32_t chain, uint32_t* nsw,
-                   int n_warmup, int n_measure, int refresh_every, int bin_size,
-                   int8_t* s, double* Gup, double* Gdn, double* bins)
+                   int n_warmup, int n_measure, int refresh_every, int refresh_stagger,
+                   int bin_size, int8_t* s, double* Gup, double* Gdn, double* bins)
 {
     long accepted = 0;
     const int W = 2 * L + 3;
+    uint32_t phase = 0u;
+    if (refresh_every > 0 && refresh_stagger)
+        phase = (site + chain) % (uint32_t)refresh_every;
     for (int k = 0; k < n_warmup + n_measure; ++k) {
         accepted += hfo_sweep(L, lambda, seed, site, chain, *nsw, s, Gup, Gdn);
         *nsw += 1u;
-        if (refresh_every > 0 && (*nsw % (uint32_t)refresh_every) == 0u) {
+        if (refresh_every > 0 && ((*nsw + phase) % (uint32_t)refresh_every) == 0u) {
             if (hfo_dyson(L, g0up, s, +1, lambda, Gup, 0) != 0) return -1;
             if (hfo_dyson(L, g0dn, s, -1, lambda, Gdn, 0) != 0) return -1;
         }

@@ -72,15 +72,17 @@ int hfo_sweep(int L, double lambda, uint64_t seed, uint32_t site, uint32_t chain
 void hfo_measure(int L, const double* Gup, const double* Gdn, double* acc);
 
 /* Run one chain: for k in [0, n_warmup + n_measure): sweep number *nsw, then
- * (*nsw)++, a Dyson refresh of both spins whenever *nsw % refresh_every == 0, and,
- * for k >= n_warmup, a measurement added to bin (k - n_warmup) / bin_size of
- * bins[nbins][2L+3] (bins must be zeroed by the caller when a fresh run starts).
+ * (*nsw)++, a Dyson refresh of both spins whenever (*nsw + phase) % refresh_every == 0
+ * (phase = 0, or (site + chain) % refresh_every when refresh_stagger is 1: the refresh
+ * interval is the same for every chain, its offset differs), and, for k >= n_warmup, a
+ * measurement added to bin (k - n_warmup) / bin_size of bins[nbins][2L+3] (bins must be
+ * zeroed by the caller when a fresh run starts).
  * Gup/Gdn must hold the Green functions that belong to s on entry.
  * Returns accepted flips, or -1 on a singular refresh. */
 long hfo_run_chain(int L, double lambda, const double* g0up, const double* g0dn,
                    uint64_t seed, uint32_t site, uint32_t chain, uint32_t* nsw,
-                   int n_warmup, int n_measure, int refresh_every, int bin_size,
-                   int8_t* s, double* Gup, double* Gdn, double* bins);
+                   int n_warmup, int n_measure, int refresh_every, int refresh_stagger,
+                   int bin_size, int8_t* s, double* Gup, double* Gdn, double* bins);
 
 /* Exact discretised averages by enumeration of all 2^L field configurations
  * (L <= 20): weights w(s) = det A_up(s) det A_dn(s), observables as hfo_measure.

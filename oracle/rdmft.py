@@ -22,7 +22,7 @@ from .lattice import Lattice, lattice_step
 class RDMFT:
     def __init__(self, Lx, Ly=None, geometry=0, periodic=False, t=1.0, U=4.0, V0=0.1, mu=2.0,
                  beta=4.0, L=16, nw=500, chains=1, seed=1, h_seed=0.1, mix=0.5,
-                 n_warmup=500, n_measure=2000, refresh_every=10, bin_size=100):
+                 n_warmup=500, n_measure=2000, refresh_every=10, bin_size=100, refresh_stagger=0):
         self.lat = Lattice(Lx, Ly, geometry=geometry, periodic=periodic, t=t, V0=V0)
         self.reps, self.rep_of, self.flip = self.lat.orbits()
         self.U, self.mu, self.beta, self.L, self.nw = U, mu, beta, L, nw
@@ -30,6 +30,7 @@ class RDMFT:
         self.chains, self.seed, self.mix = chains, seed, mix
         self.n_warmup, self.n_measure = n_warmup, n_measure
         self.refresh_every, self.bin_size = refresh_every, bin_size
+        self.refresh_stagger = refresh_stagger
         self.dtau, self.lam = core.constants(beta, U, L)
         ns = len(self.reps)
         self.nsite = ns
@@ -92,7 +93,7 @@ class RDMFT:
                 acc, nsw = core.run_chain(self.lam, g0up, g0dn, self.seed, i, c,
                                           int(self.nsw[i, c]), self.n_warmup, self.n_measure,
                                           self.refresh_every, self.bin_size, s, Gup, Gdn,
-                                          bins[i, c])
+                                          bins[i, c], refresh_stagger=self.refresh_stagger)
                 self.nsw[i, c] = nsw
                 self.accepts[i, c] += acc
                 self.G_last[i, c, 0] = Gup

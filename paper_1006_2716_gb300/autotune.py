@@ -4,8 +4,8 @@ warps per Markov chain and the delayed-update depth k in {1, 4, 8, 16, 32} (FP32
 give the most proposals per second on this GPU.
 
 Each candidate runs the real fused sweep kernel and is timed with CUDA events on the context
-stream (hf_get_timings): ``tune_workload`` probes a workload configuration itself (its own lattice
-step supplies the baths, so acceptance rates match the real run); ``tune`` probes a synthetic
+stream (hf_get_timings): ``tune_workload`` runs whole RDMFT iterations of a workload configuration
+(its own baths, measurement cadence and acceptance rates); ``tune`` probes a synthetic
 single-impurity problem per L.  Results are cached per GPU name in ``_build/autotune.json``.
 """
 from __future__ import annotations
@@ -64,24 +64,26 @@ def _probe(L, chains, form, tw, k, sweeps, device, stream):
     return best / sweeps                                  # ms per sweep of all chains
 
 
-def _probe_workload(cfg, form, tw, k, sweeps, device, stream):
-    c = dict(cfg, precision=form, team_warps=tw, delay_k=k, n_warmup=0, n_measure=2, bin_size=1,
-             max_bins=2)
+def _probe_workload(cfg, form, tw, k, iterations, device, stream):
+    """ms per sweep of the QMC phase of a full RDMFT iteration of the workload itself (its own
+    warm-up/measurement mix, refresh cadence and equilibrium acceptance); best of the iterations
+    after the first."""
+    c = dict(cfg, precision=form, team_warps=tw, delay_k=k)
     ctx = hf.Context(hf.make_params(c), device=device, stream=stream)
-    hf.hf_rdmft_step(ctx.handle)                          # the workload's own baths
-    hf.hf_sweep(ctx.handle, 100, 0, 0)                    # towards equilibrium acceptance
     best = np.inf
-    for _ in range(2):
-        hf.hf_sweep(ctx.handle, sweeps, 0, 0)
-        best = min(best, hf.hf_get_timings(ctx.handle)[5])
+    for it in range(iterations):
+        hf.hf_rdmft_step(ctx.handle)
+        if it > 0:
+            best = min(best, hf.hf_get_timings(ctx.handle)[2])
     ctx.close()
-    return best / sweeps
+    return best / (c["n_warmup"] + c["n_measure"])
 
 
-def tune_workload(name, cfg, forms=(0, 2), sweeps=40, device="cuda:0", stream=None,
+def tune_workload(name, cfg, forms=(0, 2), iterations=2, device="cuda:0", stream=None,
                   use_cache=True):
-    """Best (form, team width) for one workload configuration, probed on that workload: the
-    context runs its own first lattice step, so the chains sweep the workload's real baths."""
+    """Best (form, team width, delay depth) for one workload configuration, probed on that
+    workload: each candidate runs whole RDMFT iterations of it (lattice step, sweeps with the
+    workload's measurement cadence, reduction, self-energy update)."""
     import torch
 
     L = int(round(cfg["beta"] / cfg["dtau"]))
@@ -92,12 +94,12 @@ def tune_workload(name, cfg, forms=(0, 2), sweeps=40, device="cuda:0", stream=No
             cache = json.load(open(_CACHE))
         except (OSError, ValueError):
             cache = {}
-    key = "%s|%s|L=%d|forms=%s|v3" % (gpu, name, L, ",".join(map(str, forms)))
+    key = "%s|%s|L=%d|forms=%s|v4" % (gpu, name, L, ",".join(map(str, forms)))
     if key not in cache:
         table = {}
         for form, tw, k in candidates(L, forms):
-            table["%d/%d/%d" % (form, tw, k)] = _probe_workload(cfg, form, tw, k, sweeps, device,
-                                                                stream)
+            table["%d/%d/%d" % (form, tw, k)] = _probe_workload(cfg, form, tw, k, iterations,
+                                                                device, stream)
         pick = min(table, key=table.get)
         f, tw, k = map(int, pick.split("/"))
         cache[key] = {"precision": f, "team_warps": tw, "delay_k": k, "ms_per_sweep": table[pick],

@@ -252,6 +252,12 @@ hf_status validate(const hf_params& p, std::string& err) {
         err = "FP32 sweeps need a periodic FP64 refresh (refresh_every >= 1)";
         return HF_EINVAL;
     }
+    if (!(p.refresh_stagger == 0 || p.refresh_stagger == 1) ||
+        (p.refresh_stagger == 1 && p.precision == 1 && p.refresh_every > 1)) {
+        err = "refresh_stagger must be 0 or 1; staggered phases need fused refreshes (precision 0 "
+              "or 2) unless refresh_every is 1";
+        return HF_EINVAL;
+    }
     if (p.n_warmup < 0 || p.n_measure < 0) { err = "sweep counts must be >= 0"; return HF_EINVAL; }
     if (!(p.U >= 0.0)) { err = "U must be >= 0"; return HF_EINVAL; }
     if (!(p.mix > 0.0 && p.mix <= 1.0)) { err = "mix must be in (0, 1]"; return HF_EINVAL; }
@@ -330,6 +336,7 @@ hfk::QmcProblem make_problem(const hf_ctx& c, int n_warmup, int n_measure, int r
     q.n_warmup = n_warmup;
     q.n_measure = n_measure;
     q.refresh_every = c.p.refresh_every;
+    q.refresh_stagger = c.p.refresh_stagger;
     q.bin_size = c.p.bin_size;
     q.max_bins = c.p.max_bins;
     q.refresh_first = refresh_first;

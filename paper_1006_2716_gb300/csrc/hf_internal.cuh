@@ -75,6 +75,7 @@ struct QmcProblem {
     int team_warps;       // FP64 / FP32-pair sweeps: warps per chain (1, 2, 4; >= 2 for L > 32)
     int site0;            // Philox site word = site0 + local site (served requests: the key's site)
     int delay_k;          // FP32-pair sweeps: delayed-update depth (<= 1: rank-1 updates)
+    int refresh_stagger;  // 1: chain (site, c) refreshes when nsw + site + c = 0 mod refresh_every
     const double* gtau;   // [nsite][2][L]  bath g~0(tau_m)
     double* G;            // [nchain][2][L*L] (FP64 state, or FP64 scratch of the FP32 path)
     float* Gf;            // [nchain][2][L*L] FP32 state (precision 1) or nullptr

@@ -208,6 +208,7 @@ hf_status validate_srv(const hf_srv_params* p, std::string& e) {
     if (p->n_warmup < 0 || p->n_measure < 1) { e = "need n_warmup >= 0 and n_measure >= 1"; return HF_EINVAL; }
     if (p->bin_size < 1 || p->n_measure % p->bin_size != 0) { e = "n_measure must be a multiple of bin_size"; return HF_EINVAL; }
     if (p->refresh_every < 0) { e = "refresh_every must be >= 0"; return HF_EINVAL; }
+    if (p->refresh_stagger != 0 && p->refresh_stagger != 1) { e = "refresh_stagger must be 0 or 1"; return HF_EINVAL; }
     if (p->precision != 0 && p->precision != 2) { e = "precision must be 0 (FP64) or 2 (FP32 pairs)"; return HF_EINVAL; }
     if (!hfk::qmc_f64_supported(p->max_L)) { e = "max_L must be one of 8,12,16,20,24,32,40,48,64"; return HF_EINVAL; }
     if (p->max_keys < 1 || p->n_streams < 1 || p->n_streams > 64) { e = "max_keys >= 1 and 1 <= n_streams <= 64 required"; return HF_EINVAL; }
@@ -274,6 +275,7 @@ hf_status start_launch(hf_srv* S, Launch& Lh) {
         q.n_warmup = p.n_warmup;
         q.n_measure = p.n_measure;
         q.refresh_every = p.refresh_every;
+        q.refresh_stagger = p.refresh_stagger;
         q.bin_size = p.bin_size;
         q.max_bins = S->nb;
         q.refresh_first = 1;

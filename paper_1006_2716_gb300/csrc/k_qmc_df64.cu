@@ -250,6 +250,14 @@ __device__ void df_chain(const QmcProblem& P, int c, unsigned char* base, int ti
 #endif
     for (int l = tid; l < L; l += T) S.s[l] = P.s[static_cast<size_t>(c) * L + l];
     uint32_t nsw = P.nsw[c];
+    // refresh phase: with staggering, chain (site, ch) refreshes when nsw + site + ch is a
+    // multiple of refresh_every, so the chains sharing an SM do not all wait on the FP64 pipe
+    // in the same sweep
+    const uint32_t rphase =
+        (P.refresh_stagger && P.refresh_every > 0)
+            ? (static_cast<uint32_t>(P.site0 + site) + static_cast<uint32_t>(ch)) %
+                  static_cast<uint32_t>(P.refresh_every)
+            : 0u;
     uint32_t nmeas = P.nmeas[c];
     unsigned long long acc = 0ull;
     int cur_bin = static_cast<int>(nmeas / P.bin_size);
@@ -406,7 +414,7 @@ __device__ void df_chain(const QmcProblem& P, int c, unsigned char* base, int ti
         if (K > 1 && m > 0) df_flush<L, TW>(G0, G1, Ut0, Ut1, V0, V1, m, dg0, dg1, tid);
         ++nsw;
         team_sync<TW>();
-        if (P.refresh_every > 0 && (nsw % static_cast<uint32_t>(P.refresh_every)) == 0u)
+        if (P.refresh_every > 0 && ((nsw + rphase) % static_cast<uint32_t>(P.refresh_every)) == 0u)
             refresh_both_df<L, TW>(P, S, gt, Gg, tid);
         if (k >= P.n_warmup) {
             measure_df<L, TW>(S, tid);

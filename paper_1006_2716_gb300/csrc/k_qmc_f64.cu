@@ -119,6 +119,14 @@ __device__ void qmc_chain(const QmcProblem& P, int c, unsigned char* base, int t
 
     for (int l = tid; l < L; l += T) S.s[l] = P.s[static_cast<size_t>(c) * L + l];
     uint32_t nsw = P.nsw[c];
+    // refresh phase: with staggering, chain (site, ch) refreshes when nsw + site + ch is a
+    // multiple of refresh_every, so the chains sharing an SM do not all wait on the FP64 pipe
+    // in the same sweep
+    const uint32_t rphase =
+        (P.refresh_stagger && P.refresh_every > 0)
+            ? (static_cast<uint32_t>(P.site0 + site) + static_cast<uint32_t>(ch)) %
+                  static_cast<uint32_t>(P.refresh_every)
+            : 0u;
     uint32_t nmeas = P.nmeas[c];
     unsigned long long acc = 0ull;
     int cur_bin = static_cast<int>(nmeas / P.bin_size);
@@ -224,7 +232,7 @@ __device__ void qmc_chain(const QmcProblem& P, int c, unsigned char* base, int t
         }
         ++nsw;
         team_sync<TW>();
-        if (P.refresh_every > 0 && (nsw % static_cast<uint32_t>(P.refresh_every)) == 0u)
+        if (P.refresh_every > 0 && ((nsw + rphase) % static_cast<uint32_t>(P.refresh_every)) == 0u)
             refresh_both<L, TW>(P, S, gt, Gg, tid);
         if (k >= P.n_warmup) {
             measure<L, TW>(S, tid);

@@ -11,11 +11,11 @@ namespace qmc {
 
 // A team of TW warps owns one chain; a 128-thread block holds 4 / TW teams.  One-warp teams
 // synchronise with __syncwarp, the whole-block team with __syncthreads, two-warp teams with the
-// named barrier 1 + team index over their 64 threads.  The named barrier uses the non-aligned
-// form (arrivals counted per thread, defined even if a warp reaches it diverged) after an
-// explicit __syncwarp: the compiler does not treat inline assembly as a barrier, so it does not
-// reconverge a warp before it, and the aligned form with a partially converged warp lets the two
-// warps of a team fall out of step.
+// named barrier 1 + team index over their 64 threads.  Every call site is reached by all threads
+// of the team in the same order (the control flow around it depends only on shared data that
+// all of them read before any thread of the team writes it); the explicit __syncwarp
+// reconverges the warp, since the compiler does not treat inline assembly as a barrier, so the
+// aligned form of the named barrier applies.
 template <int TW>
 __device__ __forceinline__ void team_sync() {
     if constexpr (TW == 1) {
@@ -24,7 +24,7 @@ __device__ __forceinline__ void team_sync() {
         __syncthreads();
     } else {
         __syncwarp();
-        asm volatile("barrier.sync %0, %1;" ::"r"(1 + static_cast<int>(threadIdx.x) / (32 * TW)),
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + static_cast<int>(threadIdx.x) / (32 * TW)),
                      "r"(32 * TW)
                      : "memory");
     }

@@ -30,7 +30,8 @@ class hf_params(C.Structure):
         ("t", C.c_double), ("U", C.c_double), ("V0", C.c_double), ("mu", C.c_double),
         ("beta", C.c_double), ("dtau", C.c_double),
         ("n_matsubara", C.c_int), ("chains_per_site", C.c_int), ("precision", C.c_int),
-        ("refresh_every", C.c_int), ("delay_k", C.c_int), ("team_warps", C.c_int),
+        ("refresh_every", C.c_int), ("refresh_stagger", C.c_int), ("delay_k", C.c_int),
+        ("team_warps", C.c_int),
         ("bin_size", C.c_int),
         ("max_bins", C.c_int), ("n_warmup", C.c_int), ("n_measure", C.c_int),
         ("seed", C.c_uint64), ("h_seed", C.c_double), ("mix", C.c_double),
@@ -41,7 +42,8 @@ class hf_params(C.Structure):
 class hf_srv_params(C.Structure):
     _fields_ = [
         ("chains_per_request", C.c_int), ("n_warmup", C.c_int), ("n_measure", C.c_int),
-        ("refresh_every", C.c_int), ("bin_size", C.c_int), ("precision", C.c_int),
+        ("refresh_every", C.c_int), ("refresh_stagger", C.c_int), ("bin_size", C.c_int),
+        ("precision", C.c_int),
         ("team_warps", C.c_int), ("max_L", C.c_int), ("max_inflight", C.c_int),
         ("max_keys", C.c_int), ("n_streams", C.c_int), ("requests_per_launch", C.c_int),
     ]
@@ -444,6 +446,7 @@ def make_params(cfg: dict, stream=None, **over) -> hf_params:
     p.chains_per_site = int(d.get("chains_per_site", 1))
     p.precision = int(d.get("precision", 0))
     p.refresh_every = int(d.get("refresh_every", 10))
+    p.refresh_stagger = int(d.get("refresh_stagger", 0))
     p.delay_k = int(d.get("delay_k", 1))
     p.team_warps = int(d.get("team_warps", 0))
     p.bin_size = int(d.get("bin_size", 100))

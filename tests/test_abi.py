@@ -60,6 +60,8 @@ def test_workspace_size_and_orbit_counts(lib):
     (dict(U=-1.0), "U must"),
     (dict(geometry=5), "geometry"),
     (dict(precision=1, beta=4.0, dtau=0.25, refresh_every=0), "refresh"),
+    (dict(precision=1, beta=4.0, dtau=0.25, refresh_every=5, refresh_stagger=1), "stagger"),
+    (dict(refresh_stagger=2), "stagger"),
     (dict(team_warps=3), "team_warps"),
     (dict(beta=16.0, dtau=0.25, team_warps=1), "team_warps"),
     (dict(precision=3), "precision"),

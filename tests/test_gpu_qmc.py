@@ -34,12 +34,13 @@ def _ctx(hf, **over):
 
 
 class OracleChain:
-    def __init__(self, seed, site, ch, L, lam, gup, gdn, refresh_every):
+    def __init__(self, seed, site, ch, L, lam, gup, gdn, refresh_every, stagger=0):
         self.g0u, self.g0d = o.build_g0(gup), o.build_g0(gdn)
         self.s = o.init_fields(seed, site, ch, L)
         self.Gu, _ = o.dyson(self.g0u, self.s, 1, lam)
         self.Gd, _ = o.dyson(self.g0d, self.s, -1, lam)
         self.seed, self.site, self.ch, self.lam, self.re = seed, site, ch, lam, refresh_every
+        self.phase = (site + ch) % refresh_every if (stagger and refresh_every > 0) else 0
         self.nsw = 0
         self.acc = 0
         self.meas = []
@@ -48,7 +49,7 @@ class OracleChain:
         self.acc += o.sweep(self.lam, self.seed, self.site, self.ch, self.nsw, self.s, self.Gu,
                             self.Gd)
         self.nsw += 1
-        if self.re > 0 and self.nsw % self.re == 0:
+        if self.re > 0 and (self.nsw + self.phase) % self.re == 0:
             self.Gu, _ = o.dyson(self.g0u, self.s, 1, self.lam)
             self.Gd, _ = o.dyson(self.g0d, self.s, -1, self.lam)
         if measure:
@@ -68,15 +69,16 @@ def test_initial_fields_bit_exact(hf):
         assert np.array_equal(f[c], o.init_fields(cfg["seed"], site, ch, ctx.L))
 
 
+@pytest.mark.parametrize("stagger", [0, 1])
 @pytest.mark.parametrize("team_warps", [0, 2, 4])
 @pytest.mark.parametrize("precision", [0, 2])
 @pytest.mark.parametrize("L,beta", [(8, 2.0), (12, 3.0), (16, 4.0), (20, 5.0), (24, 6.0),
                                     (32, 8.0), (40, 10.0), (48, 12.0), (64, 16.0)])
-def test_sweeps_identical_decisions(hf, L, beta, precision, team_warps):
+def test_sweeps_identical_decisions(hf, L, beta, precision, team_warps, stagger):
     cps, re, nsweep, bs = 2, 7, 24, 4
     ctx, cfg = _ctx(hf, chains_per_site=cps, beta=beta, dtau=0.25, U=6.0, refresh_every=re,
                     bin_size=bs, max_bins=nsweep // bs, seed=1234 + L, precision=precision,
-                    team_warps=team_warps)
+                    team_warps=team_warps, refresh_stagger=stagger)
     assert ctx.L == L
     baths = wl.random_baths(L, ctx.n_sites, beta, L)
     for i in range(ctx.n_sites):
@@ -84,7 +86,7 @@ def test_sweeps_identical_decisions(hf, L, beta, precision, team_warps):
             hf.hf_set_g0(ctx.handle, i, sp, baths[i, sp])
     _, lam = o.constants(beta, 6.0, L)
     ref = [OracleChain(cfg["seed"], c // cps, c % cps, L, lam, baths[c // cps, 0],
-                       baths[c // cps, 1], re) for c in range(ctx.n_chains)]
+                       baths[c // cps, 1], re, stagger) for c in range(ctx.n_chains)]
     for k in range(nsweep):
         hf.hf_sweep(ctx.handle, 0, 1, 1 if k == 0 else 0)
         fields, cnt = hf.hf_get_fields(ctx.handle, ctx.n_chains, L)
@@ -165,7 +167,7 @@ def test_full_size_batch_sampled_chains(hf, precision, team_warps):
     for c in (0, 1, 31, 32, 777, 1000, 1728, 1759):
         site, ch = divmod(c, 32)
         r = OracleChain(cfg["seed"], site, ch, L, lam, baths[site, 0], baths[site, 1],
-                        cfg["refresh_every"])
+                        cfg["refresh_every"], cfg.get("refresh_stagger", 0))
         for k in range(26):
             r.sweep(k >= 6)
         assert np.array_equal(fields[c], r.s)

@@ -67,14 +67,15 @@ def test_same_result_alone_and_in_the_mix(hf):
     assert ra["d"] == rb["d"] and ra["m"] == rb["m"] and ra["warm"] == rb["warm"] == 0
 
 
-@pytest.mark.parametrize("precision,L", [(0, 32), (2, 32), (2, 64)])
-def test_served_solve_equals_context_path_with_warm_start(hf, precision, L):
+@pytest.mark.parametrize("precision,L,stagger", [(0, 32, 0), (2, 32, 0), (0, 32, 1), (2, 64, 1)])
+def test_served_solve_equals_context_path_with_warm_start(hf, precision, L, stagger):
     cps, nw, nm, bs, seed, site = 8, 10, 40, 10, 123, 0
     beta = 0.25 * L
     srv = hf.Server(_params(hf, precision=precision, chains_per_request=cps, n_warmup=nw,
-                            n_measure=nm, bin_size=bs))
+                            n_measure=nm, bin_size=bs, refresh_stagger=stagger))
     cfg = dict(wl.CONFIGS["square6"], Lx=1, Ly=1, beta=beta, dtau=0.25, U=8.0, precision=precision,
-               chains_per_site=cps, bin_size=bs, max_bins=nm // bs, seed=seed, n_matsubara=4)
+               chains_per_site=cps, bin_size=bs, max_bins=nm // bs, seed=seed, n_matsubara=4,
+               refresh_stagger=stagger)
     ctx = hf.Context(hf.make_params(cfg))
     for it in range(2):                      # cold start, then warm start with a new bath
         bath = wl.random_baths(50 + it, 1, beta, L)[0]

@@ -213,9 +213,11 @@ def test_qmc_atomic_limit_within_error():
     assert np.max(z) < 4.5
 
 
-def test_run_chain_refresh_and_bins():
-    # cadence: a refresh exactly when the sweep counter hits a multiple of refresh_every;
-    # bins hold sums of bin_size measurements
+@pytest.mark.parametrize("stagger,refresh_at", [(0, (10, 20, 30)), (1, (7, 17, 27))])
+def test_run_chain_refresh_and_bins(stagger, refresh_at):
+    # cadence: a refresh exactly when the sweep counter hits a multiple of refresh_every
+    # (staggered: site 1 + chain 2 moves the counter by 3, so the refreshes come after sweeps
+    # 7, 17, 27); bins hold sums of bin_size measurements
     L, beta, U = 16, 4.0, 4.0
     gt = wl.random_baths(8, 1, beta, L)[0]
     g0u, g0d = o.build_g0(gt[0]), o.build_g0(gt[1])
@@ -224,9 +226,10 @@ def test_run_chain_refresh_and_bins():
     Gu, _ = o.dyson(g0u, s, 1, lam)
     Gd, _ = o.dyson(g0d, s, -1, lam)
     bins = np.zeros((3, 2 * L + 3))
-    acc, nsw = o.run_chain(lam, g0u, g0d, 3, 1, 2, 0, 5, 30, 10, 10, s, Gu, Gd, bins)
+    acc, nsw = o.run_chain(lam, g0u, g0d, 3, 1, 2, 0, 5, 30, 10, 10, s, Gu, Gd, bins,
+                           refresh_stagger=stagger)
     assert nsw == 35
-    # after sweep 35 the last refresh was at 30: replay by hand from a copy
+    # replay by hand from a copy
     s2 = o.init_fields(3, 1, 2, L)
     Hu, _ = o.dyson(g0u, s2, 1, lam)
     Hd, _ = o.dyson(g0d, s2, -1, lam)
@@ -234,7 +237,7 @@ def test_run_chain_refresh_and_bins():
     ref = np.zeros((3, 2 * L + 3))
     for k in range(35):
         acc2 += o.sweep(lam, 3, 1, 2, k, s2, Hu, Hd)
-        if (k + 1) % 10 == 0:
+        if k + 1 in refresh_at:
             Hu, _ = o.dyson(g0u, s2, 1, lam)
             Hd, _ = o.dyson(g0d, s2, -1, lam)
         if k >= 5:
@@ -242,6 +245,7 @@ def test_run_chain_refresh_and_bins():
     assert acc == acc2
     assert np.array_equal(s, s2)
     assert np.abs(bins - ref).max() < 1e-13
+    assert np.array_equal(Gu, Hu) and np.array_equal(Gd, Hd)
     # a measurement is an average of L diagonals: density = 1 - G(0+)
     m = o.measure(Hu, Hd)
     assert abs(m[2 * L] - (1 - m[0])) < 1e-14
