@@ -8,13 +8,15 @@
 //   TwoSum (Knuth): s = fl(a + b), e = (a - (s - b')) + (b - b') with b' = s - a, exact a + b = s + e;
 //   TwoProd (with FMA): p = fl(a b), e = fma(a, b, -p), exact a b = p + e.
 // On GB300 the FP32 pipe retires 72x more FMA than the FP64 pipe, so the Sherman-Morrison update
-// (2 L^2 multiply-adds per accepted flip) costs ~15 FP32 instructions per element instead of one
-// FP64 instruction at 1/64 of the issue rate.  What stays in FP64: the Dyson refresh (the
+// (2 L^2 multiply-adds per accepted flip) costs ~12 FP32 instructions per element (the pair is
+// renormalised once per sweep, not after every update) instead of one FP64 instruction at 1/64
+// of the issue rate.  What stays in FP64: the Dyson refresh (the
 // method's re-anchoring step), and the Metropolis test whenever the FP32 estimate of R_up R_dn
 // is within its error bound of u -- then the ratio is evaluated in FP64 from the exactly
 // representable hi + lo, so every decision is the one FP64 arithmetic takes on the stored G.
-// Accuracy: each update adds an absolute error ~2^-47 max|G|; between two refreshes (at most a
-// few hundred updates) this stays ~1e-13 of max|G|.
+// Accuracy: each update adds an absolute error ~2^-47 max|G| (a few times that while lo is
+// unnormalised within a sweep); between two refreshes (at most a few hundred updates) this stays
+// ~1e-13 of max|G|.
 #include "qmc_common.cuh"
 
 namespace hfk {
@@ -48,15 +50,21 @@ __device__ __forceinline__ float2 df_mul(float2 x, float2 y) {
     e = fmaf(x.y, y.x, e);
     return fast_two_sum(p, e);
 }
-// z + x y
-__device__ __forceinline__ float2 df_fma(float2 x, float2 y, float2 z) {
+// z + x y without the final renormalisation: the Sherman-Morrison updates of a sweep leave lo
+// unnormalised (it grows by at most half an ulp of hi per update, so after the <= L updates of
+// one sweep |lo| <= (L/2 + 1) ulp(hi) and its own rounding stays ~L 2^-48 |hi|); every element
+// is renormalised by df_norm at the end of each sweep, and each diagonal element is
+// renormalised before it enters a Metropolis test.
+__device__ __forceinline__ float2 df_fma_lazy(float2 x, float2 y, float2 z) {
     const float p = __fmul_rn(x.x, y.x);
     float e = fmaf(x.x, y.x, -p);
     e = fmaf(x.x, y.y, e);
     e = fmaf(x.y, y.x, e);
     const float2 s = two_sum(z.x, p);
-    return fast_two_sum(s.x, __fadd_rn(s.y, __fadd_rn(e, z.y)));
+    return make_float2(s.x, __fadd_rn(s.y, __fadd_rn(e, z.y)));
 }
+// hi + lo -> (fl(hi + lo), exact remainder): the same number, normalised
+__device__ __forceinline__ float2 df_norm(float2 x) { return two_sum(x.x, x.y); }
 // exact double value of a double-float (hi + lo has at most 48 significant bits)
 __device__ __forceinline__ double df_to_d(float2 x) {
     return static_cast<double>(x.x) + static_cast<double>(x.y);
@@ -180,8 +188,8 @@ __device__ void df_flush(float2* G0, float2* G1, const float2* Ut0, const float2
         for (int i = tid / L; i < L; i += T / L) {
             float2 a0 = G0[i * L + j], a1 = G1[i * L + j];
             for (int q = 0; q < m; ++q) {
-                a0 = df_fma(Ut0[q * L + i], V0[q * L + j], a0);
-                a1 = df_fma(Ut1[q * L + i], V1[q * L + j], a1);
+                a0 = df_fma_lazy(Ut0[q * L + i], V0[q * L + j], a0);
+                a1 = df_fma_lazy(Ut1[q * L + i], V1[q * L + j], a1);
             }
             G0[i * L + j] = a0;
             G1[i * L + j] = a1;
@@ -191,8 +199,8 @@ __device__ void df_flush(float2* G0, float2* G1, const float2* Ut0, const float2
             const int i = e / L, j = e - (e / L) * L;
             float2 a0 = G0[e], a1 = G1[e];
             for (int q = 0; q < m; ++q) {
-                a0 = df_fma(Ut0[q * L + i], V0[q * L + j], a0);
-                a1 = df_fma(Ut1[q * L + i], V1[q * L + j], a1);
+                a0 = df_fma_lazy(Ut0[q * L + i], V0[q * L + j], a0);
+                a1 = df_fma_lazy(Ut1[q * L + i], V1[q * L + j], a1);
             }
             G0[e] = a0;
             G1[e] = a1;
@@ -206,7 +214,82 @@ __device__ void df_flush(float2* G0, float2* G1, const float2* Ut0, const float2
     team_sync<TW>();
 }
 
+// Rank-1 update of both spins, G_s[i][j] += u_s[i] v_s[j] with u = cr[0..L) / cr[L..2L) and
+// v = cr[2L..3L) / cr[3L..4L).  Each thread takes its elements in groups of up to 8: all loads
+// of a group, then the group's arithmetic, then its stores.  The compiler cannot prove that the
+// G stores miss the cr loads, so it would otherwise run one element's dependent pair
+// arithmetic after another; the grouping gives it 16 independent chains.
 template <int L, int TW>
+__device__ __forceinline__ void df_rank1(float2* G0, float2* G1, const float2* cr, int tid) {
+    constexpr int T = 32 * TW;
+    if constexpr (T % L == 0) {
+        // one column j per thread; rows i0, i0 + STEP, ...
+        constexpr int STEP = T / L, NR = (L + STEP - 1) / STEP, GB = NR < 8 ? NR : 8;
+        const int j = tid % L, i0 = tid / L;
+        if (STEP > L && i0 >= L) return;
+        const float2 r0 = cr[2 * L + j], r1 = cr[3 * L + j];
+        for (int b = 0; b < NR; b += GB) {
+            float2 a0[GB], a1[GB], c0[GB], c1[GB];
+#pragma unroll
+            for (int k = 0; k < GB; ++k) {
+                const int i = i0 + (b + k) * STEP;
+                a0[k] = G0[i * L + j];
+                a1[k] = G1[i * L + j];
+                c0[k] = cr[i];
+                c1[k] = cr[L + i];
+            }
+#pragma unroll
+            for (int k = 0; k < GB; ++k) {
+                a0[k] = df_fma_lazy(c0[k], r0, a0[k]);
+                a1[k] = df_fma_lazy(c1[k], r1, a1[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < GB; ++k) {
+                const int i = i0 + (b + k) * STEP;
+                G0[i * L + j] = a0[k];
+                G1[i * L + j] = a1[k];
+            }
+        }
+    } else {
+        // elements e = tid + n T, n = 0 .. NE-1 (the last group ragged)
+        constexpr int NE = (L * L + T - 1) / T, GB = NE < 8 ? NE : 8;
+        for (int b = 0; b < NE; b += GB) {
+            float2 a0[GB], a1[GB], c0[GB], c1[GB], v0[GB], v1[GB];
+#pragma unroll
+            for (int k = 0; k < GB; ++k) {
+                const int e = tid + (b + k) * T;
+                if (e < L * L) {
+                    const int i = e / L, j = e - (e / L) * L;
+                    a0[k] = G0[e];
+                    a1[k] = G1[e];
+                    c0[k] = cr[i];
+                    c1[k] = cr[L + i];
+                    v0[k] = cr[2 * L + j];
+                    v1[k] = cr[3 * L + j];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < GB; ++k) {
+                if (tid + (b + k) * T < L * L) {
+                    a0[k] = df_fma_lazy(c0[k], v0[k], a0[k]);
+                    a1[k] = df_fma_lazy(c1[k], v1[k], a1[k]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < GB; ++k) {
+                const int e = tid + (b + k) * T;
+                if (e < L * L) {
+                    G0[e] = a0[k];
+                    G1[e] = a1[k];
+                }
+            }
+        }
+    }
+}
+
+// DLY: delayed rank-k updates (P.delay_k > 1); the rank-1 instantiation carries none of their
+// buffers or branches.
+template <int L, int TW, bool DLY>
 __device__ void df_chain(const QmcProblem& P, int c, unsigned char* base, int tid) {
     constexpr int T = 32 * TW;
     constexpr int LL = L * L;
@@ -223,7 +306,7 @@ __device__ void df_chain(const QmcProblem& P, int c, unsigned char* base, int ti
     const uint2 key = make_uint2(P.seed_lo, P.seed_hi);
     const float2 a_p = make_float2(P.af_p, P.afl_p), a_m = make_float2(P.af_m, P.afl_m);
     const float2 one = make_float2(1.0f, 0.0f);
-    const int K = P.delay_k > 1 ? P.delay_k : 1;
+    const int K = DLY ? P.delay_k : 1;
     float2* Ut0 = reinterpret_cast<float2*>(base + team_bytes(L));   // [K][L]
     float2* Ut1 = Ut0 + K * L;
     float2* V0 = Ut1 + K * L;                                         // [K][L]
@@ -282,15 +365,15 @@ __device__ void df_chain(const QmcProblem& P, int c, unsigned char* base, int ti
                                                               static_cast<uint32_t>(ch),
                                                               static_cast<uint32_t>(P.site0 + site)), key));
         int m = 0;                  // pending delayed updates
-        if (K > 1)
+        if constexpr (DLY)
             for (int i = tid; i < L; i += T) {
                 dg0[i] = G0[i * L + i];
                 dg1[i] = G1[i * L + i];
             }
         team_sync<TW>();
         for (int l = 0; l < L; ++l) {
-            const float2 g0 = (K > 1) ? dg0[l] : G0[l * L + l];
-            const float2 g1 = (K > 1) ? dg1[l] : G1[l * L + l];
+            const float2 g0 = df_norm(DLY ? dg0[l] : G0[l * L + l]);
+            const float2 g1 = df_norm(DLY ? dg1[l] : G1[l * L + l]);
             const int sl = S.s[l];
             const float auf = (sl > 0) ? P.af_p : P.af_m;   // up:   sigma s_l = +s_l
             const float adf = (sl > 0) ? P.af_m : P.af_p;   // down: sigma s_l = -s_l
@@ -326,7 +409,7 @@ __device__ void df_chain(const QmcProblem& P, int c, unsigned char* base, int ti
                 const float2 Rd = df_add(one, df_mul(df_add(one, df_neg(g1)), ad2));
                 const float2 fu = df_mul(au2, df_recip(Ru));
                 const float2 fd = df_mul(ad2, df_recip(Rd));
-                if (K > 1) {
+                if constexpr (DLY) {
 #ifdef HF_DEBUG_SMEM
                     if (m < 0 || m >= K) {   // self-check: append slot inside the buffers
                         if (tid == 0) {
@@ -346,10 +429,10 @@ __device__ void df_chain(const QmcProblem& P, int c, unsigned char* base, int ti
                         float2 c0 = G0[i * L + l], c1 = G1[i * L + l];
                         float2 r0 = G0[l * L + i], r1 = G1[l * L + i];
                         for (int q = 0; q < m; ++q) {
-                            c0 = df_fma(Ut0[q * L + i], V0[q * L + l], c0);
-                            c1 = df_fma(Ut1[q * L + i], V1[q * L + l], c1);
-                            r0 = df_fma(Ut0[q * L + l], V0[q * L + i], r0);
-                            r1 = df_fma(Ut1[q * L + l], V1[q * L + i], r1);
+                            c0 = df_fma_lazy(Ut0[q * L + i], V0[q * L + l], c0);
+                            c1 = df_fma_lazy(Ut1[q * L + i], V1[q * L + l], c1);
+                            r0 = df_fma_lazy(Ut0[q * L + l], V0[q * L + i], r0);
+                            r1 = df_fma_lazy(Ut1[q * L + l], V1[q * L + i], r1);
                         }
                         if (i == l) {
                             c0 = df_add(c0, df_neg(one));
@@ -360,8 +443,8 @@ __device__ void df_chain(const QmcProblem& P, int c, unsigned char* base, int ti
                         Ut1[m * L + i] = u1;
                         V0[m * L + i] = r0;
                         V1[m * L + i] = r1;
-                        dg0[i] = df_fma(u0, r0, dg0[i]);
-                        dg1[i] = df_fma(u1, r1, dg1[i]);
+                        dg0[i] = df_fma_lazy(u0, r0, dg0[i]);
+                        dg1[i] = df_fma_lazy(u1, r1, dg1[i]);
                     }
                     team_sync<TW>();
                     if (tid == 0) S.s[l] = static_cast<int8_t>(-sl);
@@ -370,48 +453,36 @@ __device__ void df_chain(const QmcProblem& P, int c, unsigned char* base, int ti
                         df_flush<L, TW>(G0, G1, Ut0, Ut1, V0, V1, m, dg0, dg1, tid);
                         m = 0;
                     }
-                    continue;
-                }
-                for (int i = tid; i < L; i += T) {
-                    float2 x0 = G0[i * L + l], x1 = G1[i * L + l];
-                    if (i == l) {
-                        x0 = df_add(x0, df_neg(one));
-                        x1 = df_add(x1, df_neg(one));
-                    }
-                    cr[i] = df_mul(fu, x0);
-                    cr[L + i] = df_mul(fd, x1);
-                    cr[2 * L + i] = G0[l * L + i];
-                    cr[3 * L + i] = G1[l * L + i];
-                }
-                team_sync<TW>();
-                if constexpr (T % L == 0) {
-                    const int j = tid % L;
-                    const float2 r0 = cr[2 * L + j], r1 = cr[3 * L + j];
-#pragma unroll 8
-                    for (int i = tid / L; i < L; i += T / L) {
-                        G0[i * L + j] = df_fma(cr[i], r0, G0[i * L + j]);
-                        G1[i * L + j] = df_fma(cr[L + i], r1, G1[i * L + j]);
-                    }
                 } else {
-                    int i = tid / L, j = tid - (tid / L) * L;
-#pragma unroll 4
-                    for (int e = tid; e < LL; e += T) {
-                        G0[e] = df_fma(cr[i], cr[2 * L + j], G0[e]);
-                        G1[e] = df_fma(cr[L + i], cr[3 * L + j], G1[e]);
-                        i += T / L;
-                        j += T % L;
-                        if (j >= L) {
-                            j -= L;
-                            ++i;
+                    for (int i = tid; i < L; i += T) {
+                        float2 x0 = G0[i * L + l], x1 = G1[i * L + l];
+                        if (i == l) {
+                            x0 = df_add(x0, df_neg(one));
+                            x1 = df_add(x1, df_neg(one));
                         }
+                        cr[i] = df_mul(fu, x0);
+                        cr[L + i] = df_mul(fd, x1);
+                        cr[2 * L + i] = G0[l * L + i];
+                        cr[3 * L + i] = G1[l * L + i];
                     }
+                    team_sync<TW>();
+                    df_rank1<L, TW>(G0, G1, cr, tid);
+                    team_sync<TW>();
+                    if (tid == 0) S.s[l] = static_cast<int8_t>(-sl);
+                    ++acc;
                 }
-                team_sync<TW>();
-                if (tid == 0) S.s[l] = static_cast<int8_t>(-sl);
-                ++acc;
             }
         }
-        if (K > 1 && m > 0) df_flush<L, TW>(G0, G1, Ut0, Ut1, V0, V1, m, dg0, dg1, tid);
+        if constexpr (DLY) {
+            if (m > 0) df_flush<L, TW>(G0, G1, Ut0, Ut1, V0, V1, m, dg0, dg1, tid);
+        }
+        // renormalise every element after the sweep's lazy updates (threads may still be reading
+        // diagonals of the last proposals until the barrier)
+        team_sync<TW>();
+        for (int e = tid; e < LL; e += T) {
+            G0[e] = df_norm(G0[e]);
+            G1[e] = df_norm(G1[e]);
+        }
         ++nsw;
         team_sync<TW>();
         if (P.refresh_every > 0 && ((nsw + rphase) % static_cast<uint32_t>(P.refresh_every)) == 0u)
@@ -451,8 +522,15 @@ __device__ void run_team_df(const QmcProblem& P, int blk, unsigned char* smem) {
     const int team = static_cast<int>(threadIdx.x) / (32 * TW);
     const int c = blk * per_block + team;
     const size_t stride = team_bytes(L) + delayed_bytes(L, P.delay_k);
-    if (c < P.nchain)
-        df_chain<L, TW>(P, c, smem + team * stride, static_cast<int>(threadIdx.x) % (32 * TW));
+    if (c >= P.nchain) return;
+    const int tid = static_cast<int>(threadIdx.x) % (32 * TW);
+    if constexpr (TW == 1) {   // delayed updates run with one warp per chain
+        if (P.delay_k > 1) {
+            df_chain<L, TW, true>(P, c, smem + team * stride, tid);
+            return;
+        }
+    }
+    df_chain<L, TW, false>(P, c, smem + team * stride, tid);
 }
 
 template <int L>

@@ -43,6 +43,78 @@ __device__ void refresh_both(const QmcProblem& P, const TeamSmem<L>& S, const do
     if (!ok && tid == 0) atomicExch(P.status, static_cast<int>(HF_ENUMERIC));
 }
 
+// Rank-1 update of both spins, G_s[i][j] += u_s[i] v_s[j] (u = cr[0..L) / cr[L..2L),
+// v = cr[2L..3L) / cr[3L..4L)), one DFMA per element.  Each thread takes its elements in groups
+// -- all loads, then the DFMAs, then the stores -- because the compiler cannot prove that the G
+// stores miss the cr loads and would otherwise serialise the elements.
+template <int L, int TW>
+__device__ __forceinline__ void rank1(double* G0, double* G1, const double* cr, int tid) {
+    constexpr int T = 32 * TW;
+    if constexpr (T % L == 0) {
+        // one column j per thread (its row entries stay in registers); rows i0, i0 + STEP, ...
+        constexpr int STEP = T / L, NR = (L + STEP - 1) / STEP, GB = NR < 8 ? NR : 8;
+        const int j = tid % L, i0 = tid / L;
+        if (STEP > L && i0 >= L) return;
+        const double r0 = cr[2 * L + j], r1 = cr[3 * L + j];
+        for (int b = 0; b < NR; b += GB) {
+            double a0[GB], a1[GB], c0[GB], c1[GB];
+#pragma unroll
+            for (int k = 0; k < GB; ++k) {
+                const int i = i0 + (b + k) * STEP;
+                a0[k] = G0[i * L + j];
+                a1[k] = G1[i * L + j];
+                c0[k] = cr[i];
+                c1[k] = cr[L + i];
+            }
+#pragma unroll
+            for (int k = 0; k < GB; ++k) {
+                a0[k] = fma(c0[k], r0, a0[k]);
+                a1[k] = fma(c1[k], r1, a1[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < GB; ++k) {
+                const int i = i0 + (b + k) * STEP;
+                G0[i * L + j] = a0[k];
+                G1[i * L + j] = a1[k];
+            }
+        }
+    } else {
+        // elements e = tid + n T (the last group ragged), groups of up to 4 (register budget)
+        constexpr int NE = (L * L + T - 1) / T, GB = NE < 4 ? NE : 4;
+        for (int b = 0; b < NE; b += GB) {
+            double a0[GB], a1[GB], c0[GB], c1[GB], v0[GB], v1[GB];
+#pragma unroll
+            for (int k = 0; k < GB; ++k) {
+                const int e = tid + (b + k) * T;
+                if (e < L * L) {
+                    const int i = e / L, j = e - (e / L) * L;
+                    a0[k] = G0[e];
+                    a1[k] = G1[e];
+                    c0[k] = cr[i];
+                    c1[k] = cr[L + i];
+                    v0[k] = cr[2 * L + j];
+                    v1[k] = cr[3 * L + j];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < GB; ++k) {
+                if (tid + (b + k) * T < L * L) {
+                    a0[k] = fma(c0[k], v0[k], a0[k]);
+                    a1[k] = fma(c1[k], v1[k], a1[k]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < GB; ++k) {
+                const int e = tid + (b + k) * T;
+                if (e < L * L) {
+                    G0[e] = a0[k];
+                    G1[e] = a1[k];
+                }
+            }
+        }
+    }
+}
+
 // Accumulate one measurement into bacc.
 template <int L, int TW>
 __device__ void measure(const TeamSmem<L>& S, int tid) {
@@ -202,29 +274,7 @@ __device__ void qmc_chain(const QmcProblem& P, int c, unsigned char* base, int t
                     S.cr[3 * L + i] = S.G1[l * L + i];
                 }
                 team_sync<TW>();
-                if constexpr (T % L == 0) {
-                    // every thread stays on one column j: keep the row entries in registers
-                    const int j = tid % L;
-                    const double r0 = S.cr[2 * L + j], r1 = S.cr[3 * L + j];
-#pragma unroll 8
-                    for (int i = tid / L; i < L; i += T / L) {
-                        S.G0[i * L + j] = fma(S.cr[i], r0, S.G0[i * L + j]);
-                        S.G1[i * L + j] = fma(S.cr[L + i], r1, S.G1[i * L + j]);
-                    }
-                } else {
-                    int i = tid / L, j = tid - (tid / L) * L;
-#pragma unroll 4
-                    for (int e = tid; e < LL; e += T) {
-                        S.G0[e] = fma(S.cr[i], S.cr[2 * L + j], S.G0[e]);
-                        S.G1[e] = fma(S.cr[L + i], S.cr[3 * L + j], S.G1[e]);
-                        i += T / L;
-                        j += T % L;
-                        if (j >= L) {
-                            j -= L;
-                            ++i;
-                        }
-                    }
-                }
+                rank1<L, TW>(S.G0, S.G1, S.cr, tid);
                 team_sync<TW>();
                 if (tid == 0) S.s[l] = static_cast<int8_t>(-sl);
                 ++acc;
