@@ -47,6 +47,25 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x, device):
+    """Largest x over the ranks of the default process group (x itself on one rank): the slowest
+    replica sets a job's time."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, seconds, world):
+    """Whole-job rate of `world` replicas that each process units_per_rank units, timed by the
+    slowest rank's seconds."""
+    return units_per_rank * world / seconds
+
+
 # ---------------------------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------------------------
@@ -177,7 +196,27 @@ def run_reference(args):
 
 
 FP32_PEAK_TFLOPS = 2.0 * 128 * 152 * 2.07e9 / 1e12   # 128 FFMA/clk/SM
-DF_OPS_PER_FMA = 15                                  # FP32-pipe ops of one double-float multiply-add
+DF_OPS_PER_FMA = 12          # FP32-pipe ops of one double-float multiply-add (lazy renormalisation)
+# DRAM bytes (read + write) of one full-size launch (2500 sweeps of all 1760 chains), from one
+# ncu capture of the kernel built from sources with this sha256 prefix (profiles/
+# qmc_df64_kernel_square20.md); a kernel whose sources changed since reports null.
+MEASURED_TRAFFIC = {"qmc_df64_kernel": (1.72e6 + 1.08e6, "79bb9b9d42a84886")}
+KERNEL_SOURCES = {"qmc_df64_kernel": ("k_qmc_df64.cu", "qmc_common.cuh", "hf_internal.cuh"),
+                  "qmc_f64_kernel": ("k_qmc_f64.cu", "qmc_common.cuh", "hf_internal.cuh")}
+
+
+def measured_traffic(kernel):
+    """Bytes per launch from the last ncu capture of this kernel, or None if it has changed."""
+    import hashlib
+
+    if kernel not in MEASURED_TRAFFIC:
+        return None
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_1006_2716_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    nbytes, digest = MEASURED_TRAFFIC[kernel]
+    return nbytes if h.hexdigest().startswith(digest) else None
 
 
 def qmc_roofline(form, L, nchain, sweeps, accepts, n_measure, n_refresh, qmc_s, kernel):
@@ -203,7 +242,8 @@ def qmc_roofline(form, L, nchain, sweeps, accepts, n_measure, n_refresh, qmc_s, 
                "(128 FFMA/clk/SM, %d ops per FP64-equivalent FMA), both at 2.07 GHz, overlapped"
                % DF_OPS_PER_FMA)
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None, "kernel": kernel, "peak_source": src}
+            "frac": achieved / peak, "traffic": measured_traffic(kernel), "kernel": kernel,
+            "peak_source": src}
 
 
 def _time_iterations(hf, ctx, stream, flush, steps):
@@ -285,13 +325,9 @@ def run_ours(args):
     barrier()
     clk = clocks.stop()
     accepts = int(hf.hf_get_accepts(ctx.handle, nc).sum() - acc0)
-    ms_total = sum(ms_steps)
-    if world > 1:
-        tt = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(tt.item())
+    ms_total = max_over_ranks(sum(ms_steps), dev)
     ms_per_step = ms_total / args.steps
-    value = proposals * world / (ms_per_step / 1e3)
+    value = job_throughput(proposals, ms_per_step / 1e3, world)
 
     # end to end through the public API with host buffers: H2D self-energy, iteration,
     # D2H observables and self-energy, every step
@@ -312,12 +348,9 @@ def run_ours(args):
                                     obs[ns * (2 * L + 4):].ctypes.data_as(hf._DP))
         hf.lib().hf_get_sigma(ctx.handle, sig_np.ctypes.data_as(hf._DP))
     torch.cuda.synchronize(dev)
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    if world > 1:
-        tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e = {"value": proposals * world / e2e_s, "unit": "proposals/s", "h2d_bytes_per_step": h2d,
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, dev)
+    e2e = {"value": job_throughput(proposals, e2e_s, world), "unit": "proposals/s",
+           "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h}
     kernel = "qmc_df64_kernel" if form == 2 else "qmc_f64_kernel"
     roofline = qmc_roofline(form, L, nc, sweeps, accepts / args.steps, cfg["n_measure"],

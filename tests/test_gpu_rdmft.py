@@ -113,3 +113,30 @@ def test_lattice_step_disc_all_frequencies(hf):
         want = lattice_step(ref.lat.H0, cfg["mu"], cfg["beta"], full[sp])[:, ref.reps]
         assert np.abs(gloc[:, sp, :].T - want).max() < 1e-12 * np.abs(want).max()
     ctx.close()
+
+
+@pytest.mark.parametrize("geom,Lx", [(0, 6), (1, 6)])
+def test_compute_baths_from_a_set_self_energy(hf, geom, Lx):
+    """hf_set_sigma + hf_compute_baths (lattice step, Weiss fields, iw -> tau with tails) against
+    the oracle's steps, for an arbitrary causal self-energy (Im Sigma <= 0 on w_n > 0)."""
+    cfg = dict(wl.CONFIGS["square6"], Lx=Lx, Ly=Lx, geometry=geom, V0=0.08, mu=1.3,
+               n_matsubara=64, chains_per_site=1, n_warmup=1, n_measure=2, bin_size=1, max_bins=2)
+    ctx = hf.Context(hf.make_params(cfg))
+    ns, nw, L = ctx.n_sites, ctx.nw, ctx.L
+    rng = np.random.default_rng(7 + geom)
+    wn = (2 * np.arange(nw) + 1) * np.pi / cfg["beta"]
+    sig = (cfg["U"] / 2 + rng.uniform(-0.5, 0.5, (ns, 2, 1))
+           - 1j * rng.uniform(0.05, 0.6, (ns, 2, 1)) / (1.0 + wn[None, None, :]))
+    hf.hf_set_sigma(ctx.handle, sig)
+    hf.hf_compute_baths(ctx.handle)
+    ref = _oracle_for(cfg)
+    ref.sigma = sig.copy()
+    full = ref.expand_sigma()
+    Gloc = np.zeros((ns, 2, nw), dtype=np.complex128)
+    for sp in range(2):
+        Gloc[:, sp, :] = lattice_step(ref.lat.H0, cfg["mu"], cfg["beta"], full[sp])[:, ref.reps].T
+    _, gw_t = ref.weiss(Gloc)
+    want = ref.bath_tau(gw_t)[:, :, :L]
+    assert np.abs(hf.hf_get_gloc(ctx.handle, ns, nw) - Gloc).max() < 1e-12 * np.abs(Gloc).max()
+    assert np.abs(hf.hf_get_g0(ctx.handle, ns, L) - want).max() < 1e-12
+    ctx.close()
