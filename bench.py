@@ -403,6 +403,73 @@ def run_ours(args):
     return 0
 
 
+def run_square30(args):
+    """Mixed precision on the 30x30 trap (120 inequivalent sites x 16 chains, L = 128): FP32
+    sweeps with FP32 accumulation, an FP64 Dyson refresh (and the measurement) after every
+    sweep; one step = one RDMFT iteration (500 + 2000 sweeps)."""
+    import torch
+
+    from paper_1006_2716_gb300 import hf
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    cfg = dict(wl.CONFIGS["square30"])
+    ctx = hf.Context(hf.make_params(cfg), device=dev, stream=stream)
+    L, nc, ns, nw = ctx.L, ctx.n_chains, ctx.n_sites, ctx.nw
+    sweeps = cfg["n_warmup"] + cfg["n_measure"]
+    proposals = nc * sweeps * L
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        hf.hf_rdmft_step(ctx.handle)
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    acc0 = hf.hf_get_accepts(ctx.handle, nc).sum()
+    ms_steps, qmc_ms, phase = _time_iterations(hf, ctx, stream, flush, args.steps)
+    clk = clocks.stop()
+    accepts = int(hf.hf_get_accepts(ctx.handle, nc).sum() - acc0) / args.steps
+    ms_per = statistics.mean(ms_steps)
+    qmc_s = statistics.mean(qmc_ms) / 1e3
+    # FP64 refresh (a separate kernel after every sweep) and FP32 sweeps run one after the
+    # other: roof time = FP64-pipe time of the refresh flops + FP32-pipe time of the rest
+    f_ref = 2.0 * (8.0 / 3.0) * L ** 3 * nc * sweeps
+    f_sweep = 10.0 * L * nc * sweeps + 4.0 * L * L * accepts + 2.0 * L * L * nc * cfg["n_measure"]
+    t_roof = f_ref / (FP64_PEAK_TFLOPS * 1e12) + f_sweep / (FP32_PEAK_TFLOPS * 1e12)
+    achieved = (f_ref + f_sweep) / qmc_s / 1e12
+    peak = (f_ref + f_sweep) / t_roof / 1e12
+    line = {"metric": METRIC, "value": proposals / (ms_per / 1e3), "unit": "proposals/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "square30: 30x30 open trap, U=8, V0=0.03, mu=%.4f, beta=16, "
+                                   "dtau=0.125 (L=128), 120 inequivalent sites x 16 chains, "
+                                   "500+2000 FP32 sweeps, FP64 refresh every sweep, 500 Matsubara "
+                                   "frequencies; one step = one RDMFT iteration" % cfg["mu"],
+                       "l2": "flushed (256 MB write) between timed steps"},
+            "rdmft_iteration_ms": ms_per,
+            "phase_ms": dict(zip(["lattice", "weiss_tau", "qmc", "reduce", "sigma"],
+                                 [float(x) for x in phase / args.steps])),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         # the refresh inverts G^{-1} by Gauss-Jordan: 2 L^3 executed flops per
+                         # spin against the 2 (8/3) L^3 of the algorithmic Dyson solve counted above
+                         "executed_tflops": (0.75 * f_ref + f_sweep) / qmc_s / 1e12,
+                         "kernel": "refresh_f64_kernel + qmc_f32_kernel",
+                         "peak_source": "FP64 refresh flops at nominal FP64 (2 DFMA/clk/SM) plus "
+                                        "sweep flops at FP32 (128 FFMA/clk/SM), not overlapped",
+                         "acceptance": accepts / proposals},
+            # per iteration: an FP32 sweep launch and an FP64 refresh launch per sweep, the first
+            # refresh, lattice step, Weiss/tau, reduction, self-energy update
+            "gpu_launches": (2 * sweeps + 5) * args.steps,
+            "clocks": clk}
+    print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
 def run_scan20(args):
     """Batched uneven-L temperature scan: the 20x20 trap at beta = 5, 8, 10, 16 (L = 20, 32, 40,
     64), 1760 chains each, one fused graph-captured launch per iteration, sweep form and team
@@ -559,7 +626,8 @@ def main():
     ap.add_argument("--precision", type=int, default=-1, choices=[-1, 0, 2],
                     help="sweep arithmetic: 0 FP64, 2 FP32 pairs (both with FP64 refresh); "
                          "-1 (default): the autotuner picks form and team width")
-    ap.add_argument("--workload", default="square20", choices=["square20", "scan20", "disc40"])
+    ap.add_argument("--workload", default="square20",
+                    choices=["square20", "scan20", "square30", "disc40"])
     ap.add_argument("--refresh-stagger", type=int, default=0, choices=[0, 1],
                     help="1: per-chain refresh phases; 0 (default): every chain refreshes on the "
                          "same sweeps")
@@ -576,6 +644,8 @@ def main():
         return run_scan20(args)
     if args.workload == "disc40":
         return run_disc40(args)
+    if args.workload == "square30":
+        return run_square30(args)
     return run_ours(args)
 
 

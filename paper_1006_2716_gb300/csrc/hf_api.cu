@@ -158,6 +158,8 @@ struct hf_ctx {
     double* gtau = nullptr;         // [nsite][2][L]
     double* G = nullptr;            // [nchain][2][L*L]
     float* Gf = nullptr;            // [nchain][2][L*L] (precision 1)
+    double* g0inv = nullptr;        // [nsite][2][L*L] (precision 1)
+    bool g0inv_stale = true;        // the baths changed since g0inv was computed
     int8_t* s = nullptr;            // [nchain][L]
     uint32_t* nsw = nullptr;        // [nchain]
     uint32_t* nmeas_d = nullptr;    // [nchain]
@@ -275,6 +277,7 @@ size_t layout(hf_ctx& c, void* base) {
     c.gtau = cv.take<double>(static_cast<size_t>(ns) * 2 * L);
     c.G = cv.take<double>(static_cast<size_t>(nc) * 2 * L * L);
     c.Gf = c.p.precision == 1 ? cv.take<float>(static_cast<size_t>(nc) * 2 * L * L) : nullptr;
+    c.g0inv = c.p.precision == 1 ? cv.take<double>(static_cast<size_t>(ns) * 2 * L * L) : nullptr;
     c.s = cv.take<int8_t>(static_cast<size_t>(nc) * L);
     c.nsw = cv.take<uint32_t>(nc);
     c.nmeas_d = cv.take<uint32_t>(nc);
@@ -345,6 +348,7 @@ hfk::QmcProblem make_problem(const hf_ctx& c, int n_warmup, int n_measure, int r
     q.gtau = c.gtau;
     q.G = c.G;
     q.Gf = c.Gf;
+    q.g0inv = c.g0inv;
     q.s = c.s;
     q.nsw = c.nsw;
     q.nmeas = c.nmeas_d;
@@ -375,6 +379,11 @@ hf_status check_status(hf_ctx* c) {
 hf_status launch_sweeps_f32(hf_ctx* c, int n_warmup, int n_measure, int refresh_first) {
     hfk::QmcProblem q = make_problem(*c, n_warmup, n_measure, refresh_first);
     cudaError_t e = cudaSuccess;
+    if (c->g0inv_stale) {
+        e = hfk::launch_g0_inverse(q, c->nsite, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "g0 inverse launch");
+        c->g0inv_stale = false;
+    }
     if (refresh_first) {
         q.refresh_measure = 0;
         e = hfk::launch_refresh_f64(q, c->stream);
@@ -593,6 +602,7 @@ hf_status hf_set_g0(hf_ctx* c, int site, int spin, const double* g0_tau) {
     HF_CUDA(c, cudaMemcpyAsync(c->gtau + (static_cast<size_t>(site) * 2 + spin) * c->L, g0_tau,
                                sizeof(double) * c->L, cudaMemcpyHostToDevice, c->stream));
     HF_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->g0inv_stale = true;
     return HF_OK;
 }
 
@@ -685,6 +695,7 @@ hf_status hf_rdmft_step(hf_ctx* c, double* iter_seconds) {
     HF_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
     cudaError_t e = hfk::launch_weiss_tau(fa, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "Weiss-field launch");
+    c->g0inv_stale = true;
     HF_CUDA(c, cudaEventRecord(c->ev[2], c->stream));
     // impurities: warm-started chains, fresh bins
     hf_status st = hf_clear_measurements(c);
@@ -714,6 +725,7 @@ hf_status hf_compute_baths(hf_ctx* c) {
     if (st != HF_OK) return st;
     const cudaError_t e = hfk::launch_weiss_tau(fourier_args(*c), c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "Weiss-field launch");
+    c->g0inv_stale = true;
     return check_status(c);
 }
 

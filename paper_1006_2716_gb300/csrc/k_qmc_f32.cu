@@ -1,13 +1,13 @@
 // k_qmc_f32.cu -- mixed-precision Hirsch-Fye QMC (sm_103a): FP32 sweeps, FP64 Dyson refresh.
 //
-// Sweeps (single-flip ratio, Metropolis test, Sherman-Morrison update of "Model and Methods"
-// with the ratio of the benchmark spec) run in FP32 with FP32 accumulation, so that G_up and G_dn of
-// a chain with L = 128 (2 x 64 KiB) stay in shared memory.  The refresh
-// G = [1 + (1 - g0)(e^V - 1)]^{-1} g0 runs in FP64 in its own kernel: A (L x L FP64, 128 KiB at
-// L = 128) is LU-factored with partial pivoting in shared memory and the right-hand side g0
-// (rebuilt from g~0(tau) on the fly) is solved in blocks of 32 columns.  The refresh writes the
-// FP64 G (used for the measurement that follows a refresh) and its FP32 copy (the sweep state).
-// One block of 256 threads per chain in both kernels.
+// Sweeps (single-flip ratio, Metropolis test and Sherman-Morrison update of the Hirsch-Fye
+// algorithm named in "Model and Methods") run in FP32 with FP32 accumulation, so that G_up and
+// G_dn of a chain with L = 128 (2 x 64 KiB) stay in shared memory.  The refresh
+// G = [1 + (1 - g0)(e^V - 1)]^{-1} g0 runs in FP64 in its own kernel, as the in-place
+// Gauss-Jordan inversion of G^{-1} = g0^{-1} e^V - (e^V - 1) (L x L FP64, 128 KiB at L = 128,
+// in shared memory), with g0^{-1} computed once per bath.  The refresh writes the FP64 G (used
+// for the measurement that follows a refresh) and its FP32 copy (the sweep state).  One block
+// of 256 threads per chain in both kernels.
 #include <algorithm>
 
 #include "hf_internal.cuh"
@@ -16,7 +16,6 @@ namespace hfk {
 namespace {
 
 constexpr int kT32 = 256;   // threads per block
-constexpr int kRhsBlock = 32;
 
 // --------------------------------------------------------------------------------------------
 // FP32 sweep kernel
@@ -197,15 +196,204 @@ __global__ void __launch_bounds__(kT32) qmc_f32_kernel(const __grid_constant__ Q
 }
 
 // --------------------------------------------------------------------------------------------
-// FP64 refresh kernel (one block per chain, both spins)
+// FP64 refresh (one block per chain, both spins) by way of the inverse Green function.
+// A G = g0 with A = 1 + (1 - g0) D, D = diag(e^V - 1), gives G^{-1} = g0^{-1} A =
+// g0^{-1} e^V - D.  With g0^{-1} computed once per bath (g0_inverse_kernel), a refresh is one
+// in-place Gauss-Jordan inversion of M = g0^{-1} e^V - D: L^3 FP64 multiply-adds, against the
+// (4/3) L^3 of factoring A and solving for the L columns of g0, and every elimination step is a
+// full-width rank-1 update that all threads share evenly.
 // --------------------------------------------------------------------------------------------
 __host__ __device__ constexpr size_t refresh_bytes(int L) {
-    // A[L*L] f64, B[L*32] f64, f[L] f64, red[32] f64, perm[L] int, flag[4] int
-    return static_cast<size_t>(L * L + L * kRhsBlock + L + 32) * 8 + static_cast<size_t>(L + 4) * 4;
+    // M[L*L] f64, fcol[L] f64, red[32] f64, scal[2] f64, piv[L] int, flag[4] int
+    return static_cast<size_t>(L * L + L + 32 + 2) * 8 + static_cast<size_t>(L + 4) * 4;
 }
 
 __device__ __forceinline__ unsigned long long mag64(double x) {
     return static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+struct GjScratch {
+    double* M;      // [L][L] the matrix, inverted in place
+    double* fcol;   // [L] the pivot column of the current step
+    double* red;    // [32] reduction scratch
+    double* scal;   // [2] reciprocal of the pivot
+    int* piv;       // [L] pivot row of each step
+    int* flag;      // [4] pivot row, zero-pivot flag
+};
+
+template <int L>
+__device__ GjScratch gj_scratch(unsigned char* smem) {
+    GjScratch g;
+    g.M = reinterpret_cast<double*>(smem);
+    g.fcol = g.M + L * L;
+    g.red = g.fcol + L;
+    g.scal = g.red + 32;
+    g.piv = reinterpret_cast<int*>(g.scal + 2);
+    g.flag = g.piv + L;
+    return g;
+}
+
+// In-place Gauss-Jordan inversion of the row-major L x L matrix g.M with partial pivoting by
+// rows, by kT32 threads: each step takes the largest |M[i][k]|, i >= k, as pivot, swaps it into
+// row k, scales row k by its reciprocal, moves column k out and subtracts its multiples of row
+// k from every other row; the column order is restored at the end.  Each thread owns column
+// tid % L and rows tid / L + n (kT32 / L); its rows go in register groups of up to 8 (all
+// loads, then the multiply-adds, then the stores).  Returns false if a pivot column was zero.
+template <int L>
+__device__ bool gj_invert(const GjScratch& g, int tid) {
+    constexpr int STEP = kT32 / L, NR = L / STEP, GB = NR < 8 ? NR : 8;
+    static_assert(kT32 % L == 0 && NR * STEP == L && NR % GB == 0, "thread layout");
+    double* M = g.M;
+    const int j = tid % L, i0 = tid / L;
+    bool ok = true;
+    for (int k = 0; k < L; ++k) {
+        if (tid < 32) {
+            unsigned long long best = 0ull;
+            int bi = L;
+            for (int i = k + tid; i < L; i += 32) {
+                const unsigned long long key = mag64(M[i * L + k]);
+                if (bi == L || key > best) {
+                    best = key;
+                    bi = i;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (oi != L && (bi == L || ob > best || (ob == best && oi < bi))) {
+                    best = ob;
+                    bi = oi;
+                }
+            }
+            if (tid == 0) {
+                g.piv[k] = bi;
+                g.flag[0] = bi;
+                g.flag[1] = (best == 0ull) ? 1 : 0;
+                g.scal[0] = 1.0 / M[bi * L + k];
+            }
+        }
+        __syncthreads();
+        const int p = g.flag[0];
+        if (g.flag[1]) ok = false;
+        if (p != k) {
+            for (int jj = tid; jj < L; jj += kT32) {
+                const double t = M[k * L + jj];
+                M[k * L + jj] = M[p * L + jj];
+                M[p * L + jj] = t;
+            }
+            __syncthreads();
+        }
+        const double pinv = g.scal[0];
+        // disjoint elements: row k (scaled; its diagonal becomes the reciprocal) and the rest of
+        // column k (copied out and zeroed)
+        for (int jj = tid; jj < L; jj += kT32) {
+            const double x = M[k * L + jj];
+            M[k * L + jj] = (jj == k) ? pinv : x * pinv;
+        }
+        for (int i = tid; i < L; i += kT32) {
+            if (i != k) {
+                g.fcol[i] = M[i * L + k];
+                M[i * L + k] = 0.0;
+            } else {
+                g.fcol[i] = 0.0;   // row k subtracts nothing from itself
+            }
+        }
+        __syncthreads();
+        const double rk = M[k * L + j];
+        for (int b = 0; b < NR; b += GB) {
+            double a[GB], f[GB];
+#pragma unroll
+            for (int q = 0; q < GB; ++q) {
+                const int i = i0 + (b + q) * STEP;
+                a[q] = M[i * L + j];
+                f[q] = g.fcol[i];
+            }
+#pragma unroll
+            for (int q = 0; q < GB; ++q) a[q] = fma(-f[q], rk, a[q]);
+#pragma unroll
+            for (int q = 0; q < GB; ++q) {
+                const int i = i0 + (b + q) * STEP;
+                if (i != k) M[i * L + j] = a[q];
+            }
+        }
+        __syncthreads();
+    }
+    for (int k = L - 1; k >= 0; --k) {   // undo the row swaps as column swaps, last first
+        const int p = g.piv[k];
+        if (p != k) {
+            for (int i = tid; i < L; i += kT32) {
+                const double t = M[i * L + k];
+                M[i * L + k] = M[i * L + p];
+                M[i * L + p] = t;
+            }
+            __syncthreads();
+        }
+    }
+    return ok;
+}
+
+// g0^{-1} of every inequivalent site and spin: one block per (site, spin) builds the
+// antiperiodic bath matrix g0[l][l'] = g~0(tau_l - tau_l') from g~0(tau_m) and inverts it.
+template <int L>
+__device__ void g0_inverse_block(const QmcProblem& P, int blk, unsigned char* smem) {
+    const int tid = threadIdx.x;
+    const GjScratch g = gj_scratch<L>(smem);
+    const double* gt = P.gtau + static_cast<size_t>(blk) * L;
+    for (int e = tid; e < L * L; e += kT32) {
+        const int i = e / L, j = e - (e / L) * L;
+        const int d = i - j;
+        g.M[e] = (d >= 0) ? gt[d] : -gt[d + L];
+    }
+    __syncthreads();
+    const bool ok = gj_invert<L>(g, tid);
+    double* out = P.g0inv + static_cast<size_t>(blk) * L * L;
+    for (int e = tid; e < L * L; e += kT32) out[e] = g.M[e];
+    if (!ok && tid == 0) atomicExch(P.status, static_cast<int>(HF_ENUMERIC));
+}
+
+__global__ void __launch_bounds__(kT32) g0_inverse_kernel(const QmcProblem P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    switch (P.L) {
+        case 16: g0_inverse_block<16>(P, blockIdx.x, smem); break;
+        case 32: g0_inverse_block<32>(P, blockIdx.x, smem); break;
+        case 64: g0_inverse_block<64>(P, blockIdx.x, smem); break;
+        case 128: g0_inverse_block<128>(P, blockIdx.x, smem); break;
+        default: break;
+    }
+}
+
+// G_sigma = M^{-1}, M = g0^{-1} e^{V_sigma} - (e^{V_sigma} - 1) (columns scaled by the fields)
+template <int L>
+__device__ bool refresh_chain(const QmcProblem& P, int c, unsigned char* smem) {
+    const int tid = threadIdx.x;
+    const GjScratch g = gj_scratch<L>(smem);
+    constexpr int LL = L * L;
+    const int site = c / P.cps;
+    const int8_t* s = P.s + static_cast<size_t>(c) * L;
+    double* Gout = P.G + static_cast<size_t>(c) * 2 * LL;
+    float* Gf = P.Gf ? P.Gf + static_cast<size_t>(c) * 2 * LL : nullptr;
+    const double ex_p = 1.0 + P.ev_p, ex_m = 1.0 + P.ev_m;
+    bool ok = true;
+    for (int sp = 0; sp < 2; ++sp) {
+        const int sigma = sp == 0 ? 1 : -1;
+        const double* gi = P.g0inv + (static_cast<size_t>(site) * 2 + sp) * LL;
+        for (int e = tid; e < LL; e += kT32) {
+            const int i = e / L, j = e - (e / L) * L;
+            const bool up = sigma * s[j] > 0;
+            const double m = gi[e] * (up ? ex_p : ex_m);
+            g.M[e] = (i == j) ? m - (up ? P.ev_p : P.ev_m) : m;
+        }
+        __syncthreads();
+        ok = gj_invert<L>(g, tid) && ok;
+        for (int e = tid; e < LL; e += kT32) {
+            const double x = g.M[e];
+            Gout[static_cast<size_t>(sp) * LL + e] = x;
+            if (Gf) Gf[static_cast<size_t>(sp) * LL + e] = static_cast<float>(x);
+        }
+        __syncthreads();
+    }
+    return ok;
 }
 
 __global__ void __launch_bounds__(kT32) refresh_f64_kernel(const QmcProblem P) {
@@ -214,124 +402,17 @@ __global__ void __launch_bounds__(kT32) refresh_f64_kernel(const QmcProblem P) {
     const int c = blockIdx.x;
     if (c >= P.nchain) return;
     const int tid = threadIdx.x;
-    double* A = reinterpret_cast<double*>(smem);
-    double* B = A + L * L;
-    double* f = B + L * kRhsBlock;
-    double* red = f + L;
-    int* perm = reinterpret_cast<int*>(red + 32);
-    int* flag = perm + L;
-    const int site = c / P.cps;
     const int LL = L * L;
-    const int8_t* s = P.s + static_cast<size_t>(c) * L;
-    double* Gout = P.G + static_cast<size_t>(c) * 2 * LL;
-    float* Gf = P.Gf ? P.Gf + static_cast<size_t>(c) * 2 * LL : nullptr;
     bool ok = true;
-    for (int sp = 0; sp < 2; ++sp) {
-        const int sigma = sp == 0 ? 1 : -1;
-        const double* gt = P.gtau + (static_cast<size_t>(site) * 2 + sp) * L;
-        // A = 1 + (1 - g0) diag(e^{lambda sigma s_j} - 1)
-        for (int e = tid; e < LL; e += kT32) {
-            const int i = e / L, j = e - (e / L) * L;
-            const int d = i - j;
-            const double g = (d >= 0) ? gt[d] : -gt[d + L];
-            const double ev = (sigma * s[j] > 0) ? P.ev_p : P.ev_m;
-            const double one = (i == j) ? 1.0 : 0.0;
-            A[e] = __dadd_rn(one, __dmul_rn(__dadd_rn(one, -g), ev));
-        }
-        for (int i = tid; i < L; i += kT32) perm[i] = i;
-        __syncthreads();
-        // LU with partial pivoting, in place (unit-lower multipliers below the diagonal)
-        for (int k = 0; k < L; ++k) {
-            if (tid < 32) {
-                unsigned long long best = 0ull;
-                int bi = L;
-                for (int i = k + tid; i < L; i += 32) {
-                    const unsigned long long key = mag64(A[i * L + k]);
-                    if (bi == L || key > best) {
-                        best = key;
-                        bi = i;
-                    }
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
-                    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                    if (oi != L && (bi == L || ob > best || (ob == best && oi < bi))) {
-                        best = ob;
-                        bi = oi;
-                    }
-                }
-                if (tid == 0) {
-                    flag[0] = bi;
-                    flag[1] = (best == 0ull) ? 1 : 0;
-                    if (bi != k) {
-                        const int t = perm[k];
-                        perm[k] = perm[bi];
-                        perm[bi] = t;
-                    }
-                }
-            }
-            __syncthreads();
-            const int p = flag[0];
-            if (flag[1]) ok = false;
-            if (p != k)
-                for (int jj = tid; jj < L; jj += kT32) {
-                    const double t = A[k * L + jj];
-                    A[k * L + jj] = A[p * L + jj];
-                    A[p * L + jj] = t;
-                }
-            __syncthreads();
-            const double inv = 1.0 / A[k * L + k];
-            for (int i = k + 1 + tid; i < L; i += kT32) {
-                const double m = A[i * L + k] * inv;
-                f[i] = m;
-                A[i * L + k] = m;
-            }
-            __syncthreads();
-            const int rows = L - 1 - k, cols = L - 1 - k;
-            for (int e = tid; e < rows * cols; e += kT32) {
-                const int r = e / cols;
-                const int i = k + 1 + r, jj = k + 1 + (e - r * cols);
-                A[i * L + jj] = fma(-f[i], A[k * L + jj], A[i * L + jj]);
-            }
-            __syncthreads();
-        }
-        // solve for g0 in blocks of 32 columns: X = U^{-1} L^{-1} P g0
-        for (int c0 = 0; c0 < L; c0 += kRhsBlock) {
-            const int nc = min(kRhsBlock, L - c0);
-            for (int e = tid; e < L * nc; e += kT32) {
-                const int i = e / nc, cc = e - (e / nc) * nc;
-                const int r = perm[i], col = c0 + cc;
-                const int d = r - col;
-                B[i * kRhsBlock + cc] = (d >= 0) ? gt[d] : -gt[d + L];
-            }
-            __syncthreads();
-            for (int k = 0; k < L; ++k) {        // forward, unit lower
-                for (int e = tid; e < (L - 1 - k) * nc; e += kT32) {
-                    const int r = e / nc, cc = e - r * nc;
-                    const int i = k + 1 + r;
-                    B[i * kRhsBlock + cc] = fma(-A[i * L + k], B[k * kRhsBlock + cc], B[i * kRhsBlock + cc]);
-                }
-                __syncthreads();
-            }
-            for (int k = L - 1; k >= 0; --k) {   // backward, upper
-                if (tid < nc) B[k * kRhsBlock + tid] = B[k * kRhsBlock + tid] / A[k * L + k];
-                __syncthreads();
-                for (int e = tid; e < k * nc; e += kT32) {
-                    const int i = e / nc, cc = e - (e / nc) * nc;
-                    B[i * kRhsBlock + cc] = fma(-A[i * L + k], B[k * kRhsBlock + cc], B[i * kRhsBlock + cc]);
-                }
-                __syncthreads();
-            }
-            for (int e = tid; e < L * nc; e += kT32) {
-                const int i = e / nc, cc = e - (e / nc) * nc;
-                const double x = B[i * kRhsBlock + cc];
-                Gout[static_cast<size_t>(sp) * LL + i * L + c0 + cc] = x;
-                if (Gf) Gf[static_cast<size_t>(sp) * LL + i * L + c0 + cc] = static_cast<float>(x);
-            }
-            __syncthreads();
-        }
+    switch (L) {
+        case 16: ok = refresh_chain<16>(P, c, smem); break;
+        case 32: ok = refresh_chain<32>(P, c, smem); break;
+        case 64: ok = refresh_chain<64>(P, c, smem); break;
+        case 128: ok = refresh_chain<128>(P, c, smem); break;
+        default: break;
     }
+    double* red = reinterpret_cast<double*>(smem) + LL + L;
+    double* Gout = P.G + static_cast<size_t>(c) * 2 * LL;
     if (!ok && tid == 0) atomicExch(P.status, static_cast<int>(HF_ENUMERIC));
     if (!P.refresh_measure) return;
     // measurement from the FP64 G just written (this block wrote it; block-wide visibility)
@@ -410,6 +491,16 @@ cudaError_t launch_qmc_f32(const QmcBatch& b, size_t smem, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     if (b.nblocks <= 0) return cudaSuccess;
     qmc_f32_kernel<<<b.nblocks, kT32, smem, st>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_g0_inverse(const QmcProblem& p, int nsite, cudaStream_t st) {
+    const size_t smem = refresh_bytes(p.L);
+    cudaError_t e = cudaFuncSetAttribute(g0_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(refresh_bytes(128)));
+    if (e != cudaSuccess) return e;
+    if (nsite <= 0) return cudaSuccess;
+    g0_inverse_kernel<<<2 * nsite, kT32, smem, st>>>(p);
     return cudaGetLastError();
 }
 

@@ -51,7 +51,8 @@ def test_init_fields_top_bit():
 
 
 def test_constants_closed_form():
-    # cosh(lambda) = exp(dtau U / 2); the survey's printed lambdas for dtau = 0.25
+    # cosh(lambda) = exp(dtau U / 2); at dtau = 0.25: lambda = acosh(e^0.5) = 1.08504 (U = 4)
+    # and acosh(e^1) = 1.65745 (U = 8)
     dt, lam = o.constants(4.0, 4.0, 16)
     assert dt == 0.25
     assert abs(np.cosh(lam) - np.exp(0.5)) < 1e-14
