@@ -27,7 +27,7 @@ DELAYS = (1, 4, 8, 16, 32)
 def _fits(L, tw, k):
     # per-block shared memory of the FP32-pair kernel: (4 / tw) chains x (G pair buffers and
     # scratch + delayed-update buffers), limit 227 KB
-    team = (2 * L * L + 7 * L + 11) * 8 + 16 + ((L + 15) // 16) * 16
+    team = ((2 * L * L + 7 * L + 11) * 8 + 16 + ((L + 15) // 16) * 16 + 15) // 16 * 16
     delayed = (4 * k * L + 2 * L) * 8 if k > 1 else 0
     return (4 // tw) * (team + delayed) <= 227 * 1024
 

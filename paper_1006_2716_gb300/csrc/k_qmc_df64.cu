@@ -24,6 +24,17 @@ namespace {
 
 using namespace qmc;
 
+// Shared-memory placement of G[i][j] (8-byte elements, rows of L): for L a power of two the
+// column pairs of row i are permuted by XOR with i mod 8, so that a column gather G[i][l],
+// i = 0..L-1, spreads over the banks (at most 2-way conflicts instead of 32-way) while every
+// column pair stays one aligned 16-byte unit; other L keep the dense order.
+template <int L>
+constexpr int kSW = ((L & (L - 1)) == 0 && L >= 8) ? ((L / 2 < 8 ? L / 2 : 8) - 1) : 0;
+template <int L>
+__device__ __forceinline__ int gx(int i, int j) {
+    return i * L + ((((j >> 1) ^ (i & kSW<L>)) << 1) | (j & 1));
+}
+
 // ------------------------------ double-float arithmetic -------------------------------------
 // The _rn intrinsics keep every product and sum separately rounded (no contraction), which the
 // error-free transformations rely on.
@@ -84,8 +95,9 @@ __device__ __forceinline__ float2 df_recip(float2 R) {
     return df_add(r, df_mul(r, e));
 }
 
-// Dyson refresh of both spins in FP64 (as the FP64 kernel), then the FP64 result is split into
-// double-floats in place.  The two G buffers hold 8 bytes per element in either format.
+// Dyson refresh of both spins in FP64 (as the FP64 kernel, on dense L x L matrices in the two
+// G buffers), each result parked in the chain's global slot, then split into double-floats in
+// the permuted placement.
 template <int L, int TW>
 __device__ void refresh_both_df(const QmcProblem& P, const TeamSmem<L>& S, const double* gt,
                                 double* Gg, int tid) {
@@ -95,14 +107,17 @@ __device__ void refresh_both_df(const QmcProblem& P, const TeamSmem<L>& S, const
     build_dyson<L, TW>(P, gt, S.s, +1, S.G1, S.G0, tid);
     team_sync<TW>();
     bool ok = solve_dyson<L, TW>(S.G1, S.G0, S.cr, S.piv, tid);
-    for (int e = tid; e < L * L; e += T) Gg[e] = S.G0[e];        // park FP64 G_up
+    for (int e = tid; e < L * L; e += T) Gg[e] = S.G0[e];            // park FP64 G_up
     team_sync<TW>();
     build_dyson<L, TW>(P, gt + L, S.s, -1, S.G0, S.G1, tid);
     team_sync<TW>();
     ok = solve_dyson<L, TW>(S.G0, S.G1, S.cr, S.piv, tid) && ok;
+    for (int e = tid; e < L * L; e += T) Gg[L * L + e] = S.G1[e];    // park FP64 G_dn
+    team_sync<TW>();
     for (int e = tid; e < L * L; e += T) {
-        X0[e] = d_to_df(Gg[e]);
-        X1[e] = d_to_df(S.G1[e]);
+        const int i = e / L, j = e - (e / L) * L;
+        X0[gx<L>(i, j)] = d_to_df(Gg[e]);
+        X1[gx<L>(i, j)] = d_to_df(Gg[L * L + e]);
     }
     team_sync<TW>();
     if (!ok && tid == 0) atomicExch(P.status, static_cast<int>(HF_ENUMERIC));
@@ -121,7 +136,7 @@ __device__ void measure_df(const TeamSmem<L>& S, int tid) {
             int r = l + m;
             const bool wrap = r >= L;
             if (wrap) r -= L;
-            const float2 x0 = G0[r * L + l], x1 = G1[r * L + l];
+            const float2 x0 = G0[gx<L>(r, l)], x1 = G1[gx<L>(r, l)];
             s0 = df_add(s0, wrap ? df_neg(x0) : x0);
             s1 = df_add(s1, wrap ? df_neg(x1) : x1);
         }
@@ -130,8 +145,8 @@ __device__ void measure_df(const TeamSmem<L>& S, int tid) {
     }
     double nu = 0.0, nd = 0.0, db = 0.0;
     for (int l = tid; l < L; l += T) {
-        const double a = 1.0 - df_to_d(G0[l * L + l]);
-        const double b = 1.0 - df_to_d(G1[l * L + l]);
+        const double a = 1.0 - df_to_d(G0[gx<L>(l, l)]);
+        const double b = 1.0 - df_to_d(G1[gx<L>(l, l)]);
         nu += a;
         nd += b;
         db += a * b;
@@ -186,68 +201,77 @@ __device__ void df_flush(float2* G0, float2* G1, const float2* Ut0, const float2
         const int j = tid % L;
 #pragma unroll 4
         for (int i = tid / L; i < L; i += T / L) {
-            float2 a0 = G0[i * L + j], a1 = G1[i * L + j];
+            float2 a0 = G0[gx<L>(i, j)], a1 = G1[gx<L>(i, j)];
             for (int q = 0; q < m; ++q) {
                 a0 = df_fma_lazy(Ut0[q * L + i], V0[q * L + j], a0);
                 a1 = df_fma_lazy(Ut1[q * L + i], V1[q * L + j], a1);
             }
-            G0[i * L + j] = a0;
-            G1[i * L + j] = a1;
+            G0[gx<L>(i, j)] = a0;
+            G1[gx<L>(i, j)] = a1;
         }
     } else {
         for (int e = tid; e < L * L; e += T) {
             const int i = e / L, j = e - (e / L) * L;
-            float2 a0 = G0[e], a1 = G1[e];
+            float2 a0 = G0[gx<L>(i, j)], a1 = G1[gx<L>(i, j)];
             for (int q = 0; q < m; ++q) {
                 a0 = df_fma_lazy(Ut0[q * L + i], V0[q * L + j], a0);
                 a1 = df_fma_lazy(Ut1[q * L + i], V1[q * L + j], a1);
             }
-            G0[e] = a0;
-            G1[e] = a1;
+            G0[gx<L>(i, j)] = a0;
+            G1[gx<L>(i, j)] = a1;
         }
     }
     team_sync<TW>();
     for (int i = tid; i < L; i += T) {
-        dg0[i] = G0[i * L + i];
-        dg1[i] = G1[i * L + i];
+        dg0[i] = G0[gx<L>(i, i)];
+        dg1[i] = G1[gx<L>(i, i)];
     }
     team_sync<TW>();
 }
 
 // Rank-1 update of both spins, G_s[i][j] += u_s[i] v_s[j] with u = cr[0..L) / cr[L..2L) and
-// v = cr[2L..3L) / cr[3L..4L).  Each thread takes its elements in groups of up to 8: all loads
-// of a group, then the group's arithmetic, then its stores.  The compiler cannot prove that the
-// G stores miss the cr loads, so it would otherwise run one element's dependent pair
-// arithmetic after another; the grouping gives it 16 independent chains.
+// v = cr[2L..3L) / cr[3L..4L).  Each thread takes its elements in groups of up to 8 rows: all
+// loads of a group, then the group's arithmetic, then its stores.  The compiler cannot prove
+// that the G stores miss the cr loads, so it would otherwise run one element's dependent pair
+// arithmetic after another.  Where the team's threads tile the matrix in column pairs, a thread
+// owns two adjacent columns: one 128-bit load and store per row and spin, and each u[i] serves
+// two elements.
 template <int L, int TW>
 __device__ __forceinline__ void df_rank1(float2* G0, float2* G1, const float2* cr, int tid) {
     constexpr int T = 32 * TW;
-    if constexpr (T % L == 0) {
-        // one column j per thread; rows i0, i0 + STEP, ...
-        constexpr int STEP = T / L, NR = (L + STEP - 1) / STEP, GB = NR < 8 ? NR : 8;
-        const int j = tid % L, i0 = tid / L;
+    if constexpr ((2 * T) % L == 0) {
+        // column pair (j, j + 1), j = 2 (tid % (L/2)); rows i0, i0 + STEP, ...
+        constexpr int NCP = L / 2, STEP = T / NCP, NR = (L + STEP - 1) / STEP;
+        constexpr int GB = NR < 8 ? NR : 8;
+        const int j = 2 * (tid % NCP), i0 = tid / NCP;
         if (STEP > L && i0 >= L) return;
-        const float2 r0 = cr[2 * L + j], r1 = cr[3 * L + j];
+        const float4 r0 = *reinterpret_cast<const float4*>(cr + 2 * L + j);
+        const float4 r1 = *reinterpret_cast<const float4*>(cr + 3 * L + j);
         for (int b = 0; b < NR; b += GB) {
-            float2 a0[GB], a1[GB], c0[GB], c1[GB];
+            float4 a0[GB], a1[GB];
+            float2 c0[GB], c1[GB];
 #pragma unroll
             for (int k = 0; k < GB; ++k) {
                 const int i = i0 + (b + k) * STEP;
-                a0[k] = G0[i * L + j];
-                a1[k] = G1[i * L + j];
+                a0[k] = *reinterpret_cast<const float4*>(G0 + gx<L>(i, j));
+                a1[k] = *reinterpret_cast<const float4*>(G1 + gx<L>(i, j));
                 c0[k] = cr[i];
                 c1[k] = cr[L + i];
             }
 #pragma unroll
             for (int k = 0; k < GB; ++k) {
-                a0[k] = df_fma_lazy(c0[k], r0, a0[k]);
-                a1[k] = df_fma_lazy(c1[k], r1, a1[k]);
+                const float2 x0 = df_fma_lazy(c0[k], make_float2(r0.x, r0.y), make_float2(a0[k].x, a0[k].y));
+                const float2 y0 = df_fma_lazy(c0[k], make_float2(r0.z, r0.w), make_float2(a0[k].z, a0[k].w));
+                const float2 x1 = df_fma_lazy(c1[k], make_float2(r1.x, r1.y), make_float2(a1[k].x, a1[k].y));
+                const float2 y1 = df_fma_lazy(c1[k], make_float2(r1.z, r1.w), make_float2(a1[k].z, a1[k].w));
+                a0[k] = make_float4(x0.x, x0.y, y0.x, y0.y);
+                a1[k] = make_float4(x1.x, x1.y, y1.x, y1.y);
             }
 #pragma unroll
             for (int k = 0; k < GB; ++k) {
                 const int i = i0 + (b + k) * STEP;
-                G0[i * L + j] = a0[k];
-                G1[i * L + j] = a1[k];
+                *reinterpret_cast<float4*>(G0 + gx<L>(i, j)) = a0[k];
+                *reinterpret_cast<float4*>(G1 + gx<L>(i, j)) = a1[k];
             }
         }
     } else {
@@ -260,8 +284,8 @@ __device__ __forceinline__ void df_rank1(float2* G0, float2* G1, const float2* c
                 const int e = tid + (b + k) * T;
                 if (e < L * L) {
                     const int i = e / L, j = e - (e / L) * L;
-                    a0[k] = G0[e];
-                    a1[k] = G1[e];
+                    a0[k] = G0[gx<L>(i, j)];
+                    a1[k] = G1[gx<L>(i, j)];
                     c0[k] = cr[i];
                     c1[k] = cr[L + i];
                     v0[k] = cr[2 * L + j];
@@ -279,8 +303,9 @@ __device__ __forceinline__ void df_rank1(float2* G0, float2* G1, const float2* c
             for (int k = 0; k < GB; ++k) {
                 const int e = tid + (b + k) * T;
                 if (e < L * L) {
-                    G0[e] = a0[k];
-                    G1[e] = a1[k];
+                    const int i = e / L, j = e - (e / L) * L;
+                    G0[gx<L>(i, j)] = a0[k];
+                    G1[gx<L>(i, j)] = a1[k];
                 }
             }
         }
@@ -321,7 +346,7 @@ __device__ void df_chain(const QmcProblem& P, int c, unsigned char* base, int ti
         asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
         const long off = base - smem;
         const long end = off + static_cast<long>(team_bytes(L) + delayed_bytes(L, P.delay_k));
-        if (off < 0 || end > static_cast<long>(dyn)) {
+        if (off < 0 || end > static_cast<long>(dyn) || (off & 15) != 0) {
             if (tid == 0) {
                 atomicExch(P.status + 2, __LINE__);
                 atomicExch(P.status + 3, static_cast<int>(end));
@@ -352,8 +377,9 @@ __device__ void df_chain(const QmcProblem& P, int c, unsigned char* base, int ti
         refresh_both_df<L, TW>(P, S, gt, Gg, tid);
     } else {
         for (int e = tid; e < LL; e += T) {
-            G0[e] = Gp[e];
-            G1[e] = Gp[LL + e];
+            const int i = e / L, j = e - (e / L) * L;
+            G0[gx<L>(i, j)] = Gp[e];
+            G1[gx<L>(i, j)] = Gp[LL + e];
         }
         team_sync<TW>();
     }
@@ -367,13 +393,13 @@ __device__ void df_chain(const QmcProblem& P, int c, unsigned char* base, int ti
         int m = 0;                  // pending delayed updates
         if constexpr (DLY)
             for (int i = tid; i < L; i += T) {
-                dg0[i] = G0[i * L + i];
-                dg1[i] = G1[i * L + i];
+                dg0[i] = G0[gx<L>(i, i)];
+                dg1[i] = G1[gx<L>(i, i)];
             }
         team_sync<TW>();
         for (int l = 0; l < L; ++l) {
-            const float2 g0 = df_norm(DLY ? dg0[l] : G0[l * L + l]);
-            const float2 g1 = df_norm(DLY ? dg1[l] : G1[l * L + l]);
+            const float2 g0 = df_norm(DLY ? dg0[l] : G0[gx<L>(l, l)]);
+            const float2 g1 = df_norm(DLY ? dg1[l] : G1[gx<L>(l, l)]);
             const int sl = S.s[l];
             const float auf = (sl > 0) ? P.af_p : P.af_m;   // up:   sigma s_l = +s_l
             const float adf = (sl > 0) ? P.af_m : P.af_p;   // down: sigma s_l = -s_l
@@ -426,8 +452,8 @@ __device__ void df_chain(const QmcProblem& P, int c, unsigned char* base, int ti
                     // current column l and row l = stale values + pending products, in accept
                     // order; append u = f (G[:, l] - e_l), v = G[l, :]; update the diagonal
                     for (int i = tid; i < L; i += T) {
-                        float2 c0 = G0[i * L + l], c1 = G1[i * L + l];
-                        float2 r0 = G0[l * L + i], r1 = G1[l * L + i];
+                        float2 c0 = G0[gx<L>(i, l)], c1 = G1[gx<L>(i, l)];
+                        float2 r0 = G0[gx<L>(l, i)], r1 = G1[gx<L>(l, i)];
                         for (int q = 0; q < m; ++q) {
                             c0 = df_fma_lazy(Ut0[q * L + i], V0[q * L + l], c0);
                             c1 = df_fma_lazy(Ut1[q * L + i], V1[q * L + l], c1);
@@ -455,15 +481,15 @@ __device__ void df_chain(const QmcProblem& P, int c, unsigned char* base, int ti
                     }
                 } else {
                     for (int i = tid; i < L; i += T) {
-                        float2 x0 = G0[i * L + l], x1 = G1[i * L + l];
+                        float2 x0 = G0[gx<L>(i, l)], x1 = G1[gx<L>(i, l)];
                         if (i == l) {
                             x0 = df_add(x0, df_neg(one));
                             x1 = df_add(x1, df_neg(one));
                         }
                         cr[i] = df_mul(fu, x0);
                         cr[L + i] = df_mul(fd, x1);
-                        cr[2 * L + i] = G0[l * L + i];
-                        cr[3 * L + i] = G1[l * L + i];
+                        cr[2 * L + i] = G0[gx<L>(l, i)];
+                        cr[3 * L + i] = G1[gx<L>(l, i)];
                     }
                     team_sync<TW>();
                     df_rank1<L, TW>(G0, G1, cr, tid);
@@ -480,8 +506,9 @@ __device__ void df_chain(const QmcProblem& P, int c, unsigned char* base, int ti
         // diagonals of the last proposals until the barrier)
         team_sync<TW>();
         for (int e = tid; e < LL; e += T) {
-            G0[e] = df_norm(G0[e]);
-            G1[e] = df_norm(G1[e]);
+            const int i = e / L, j = e - (e / L) * L;
+            G0[gx<L>(i, j)] = df_norm(G0[gx<L>(i, j)]);
+            G1[gx<L>(i, j)] = df_norm(G1[gx<L>(i, j)]);
         }
         ++nsw;
         team_sync<TW>();
@@ -505,8 +532,9 @@ __device__ void df_chain(const QmcProblem& P, int c, unsigned char* base, int ti
     for (int q = tid; q < W; q += T)
         if (cur_bin < P.max_bins) bins_c[static_cast<size_t>(cur_bin) * W + q] = S.bacc[q];
     for (int e = tid; e < LL; e += T) {
-        Gp[e] = G0[e];
-        Gp[LL + e] = G1[e];
+        const int i = e / L, j = e - (e / L) * L;
+        Gp[e] = G0[gx<L>(i, j)];
+        Gp[LL + e] = G1[gx<L>(i, j)];
     }
     for (int l = tid; l < L; l += T) P.s[static_cast<size_t>(c) * L + l] = S.s[l];
     if (tid == 0) {

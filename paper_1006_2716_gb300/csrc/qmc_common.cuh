@@ -30,9 +30,11 @@ __device__ __forceinline__ void team_sync() {
     }
 }
 
-// Shared-memory footprint of one team (bytes), 16-byte granular.
+// Shared-memory footprint of one team (bytes), rounded up to 16 bytes so that every team of a
+// block starts 16-byte aligned.
 __host__ __device__ constexpr size_t team_bytes(int L) {
-    return static_cast<size_t>(2 * L * L + 7 * L + 11) * 8 + 16 + ((L + 15) / 16) * 16;
+    return (static_cast<size_t>(2 * L * L + 7 * L + 11) * 8 + 16 + ((L + 15) / 16) * 16 + 15) /
+           16 * 16;
 }
 
 template <int L>
