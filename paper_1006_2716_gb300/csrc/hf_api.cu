@@ -158,7 +158,7 @@ struct hf_ctx {
     double* gtau = nullptr;         // [nsite][2][L]
     double* G = nullptr;            // [nchain][2][L*L]
     float* Gf = nullptr;            // [nchain][2][L*L] (precision 1)
-    double* g0inv = nullptr;        // [nsite][2][L*L] (precision 1)
+    double* g0inv = nullptr;        // [nsite][2][L*L] inverse bath matrices
     bool g0inv_stale = true;        // the baths changed since g0inv was computed
     int8_t* s = nullptr;            // [nchain][L]
     uint32_t* nsw = nullptr;        // [nchain]
@@ -277,7 +277,7 @@ size_t layout(hf_ctx& c, void* base) {
     c.gtau = cv.take<double>(static_cast<size_t>(ns) * 2 * L);
     c.G = cv.take<double>(static_cast<size_t>(nc) * 2 * L * L);
     c.Gf = c.p.precision == 1 ? cv.take<float>(static_cast<size_t>(nc) * 2 * L * L) : nullptr;
-    c.g0inv = c.p.precision == 1 ? cv.take<double>(static_cast<size_t>(ns) * 2 * L * L) : nullptr;
+    c.g0inv = cv.take<double>(static_cast<size_t>(ns) * 2 * L * L);
     c.s = cv.take<int8_t>(static_cast<size_t>(nc) * L);
     c.nsw = cv.take<uint32_t>(nc);
     c.nmeas_d = cv.take<uint32_t>(nc);
@@ -373,17 +373,26 @@ hf_status check_status(hf_ctx* c) {
     return HF_OK;
 }
 
+// g0^{-1} of every site whenever the baths changed since it was last built (stream order).
+hf_status ensure_g0inv(hf_ctx* c, cudaStream_t st) {
+    if (!c->g0inv_stale) return HF_OK;
+    hfk::QmcBatch b{};
+    b.nprob = 1;
+    b.p[0] = make_problem(*c, 0, 0, 0);
+    const cudaError_t e = hfk::launch_g0_inverse(b, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "g0 inverse launch");
+    c->g0inv_stale = false;
+    return HF_OK;
+}
+
 // Mixed-precision sequence: FP32 sweep segments that end at the chains' next refresh point,
 // each followed by the FP64 refresh kernel, which also takes that sweep's measurement (the
 // measurement of a refresh sweep comes after the refresh, as in the FP64 path).
 hf_status launch_sweeps_f32(hf_ctx* c, int n_warmup, int n_measure, int refresh_first) {
     hfk::QmcProblem q = make_problem(*c, n_warmup, n_measure, refresh_first);
     cudaError_t e = cudaSuccess;
-    if (c->g0inv_stale) {
-        e = hfk::launch_g0_inverse(q, c->nsite, c->stream);
-        if (e != cudaSuccess) return cuda_fail(c, e, "g0 inverse launch");
-        c->g0inv_stale = false;
-    }
+    const hf_status sg = ensure_g0inv(c, c->stream);
+    if (sg != HF_OK) return sg;
     if (refresh_first) {
         q.refresh_measure = 0;
         e = hfk::launch_refresh_f64(q, c->stream);
@@ -419,6 +428,8 @@ hf_status launch_sweeps_f32(hf_ctx* c, int n_warmup, int n_measure, int refresh_
 
 hf_status launch_sweeps(hf_ctx* c, int n_warmup, int n_measure, int refresh_first) {
     if (c->p.precision == 1) return launch_sweeps_f32(c, n_warmup, n_measure, refresh_first);
+    const hf_status sg = ensure_g0inv(c, c->stream);
+    if (sg != HF_OK) return sg;
     hfk::QmcBatch b{};
     b.nprob = 1;
     b.p[0] = make_problem(*c, n_warmup, n_measure, refresh_first);
@@ -895,6 +906,14 @@ static hf_status bfail(hf_batch* b, hf_status st, const std::string& m) {
 
 // One fused launch of the sweeps of every context in the batch.
 static hf_status enqueue_batch_qmc(hf_batch* b, int n_warmup, int n_measure, int refresh_first) {
+    hfk::QmcBatch gb{};   // contexts whose baths changed: g0^{-1} first, in one launch
+    for (hf_ctx* c : b->ctx)
+        if (c->g0inv_stale) gb.p[gb.nprob++] = make_problem(*c, 0, 0, 0);
+    if (gb.nprob > 0) {
+        const cudaError_t eg = hfk::launch_g0_inverse(gb, b->stream);
+        if (eg != cudaSuccess) return bfail(b, HF_ECUDA, std::string("g0 inverse launch: ") + cudaGetErrorString(eg));
+        for (hf_ctx* c : b->ctx) c->g0inv_stale = false;
+    }
     hfk::QmcBatch qb{};
     qb.nprob = static_cast<int>(b->ctx.size());
     size_t smem = 0;
@@ -923,6 +942,7 @@ static hf_status enqueue_batch_iteration(hf_batch* b) {
         if (st != HF_OK) return bfail(b, st, c->err);
         const cudaError_t e = hfk::launch_weiss_tau(fourier_args(*c), b->stream);
         if (e != cudaSuccess) return bfail(b, HF_ECUDA, "Weiss-field launch");
+        c->g0inv_stale = true;
         cudaError_t e1 = cudaMemsetAsync(c->bins, 0, sizeof(double) * c->nchain * c->p.max_bins * (2 * c->L + 3), b->stream);
         cudaError_t e2 = cudaMemsetAsync(c->nmeas_d, 0, sizeof(uint32_t) * c->nchain, b->stream);
         if (e1 != cudaSuccess || e2 != cudaSuccess) return bfail(b, HF_ECUDA, "bin clear");

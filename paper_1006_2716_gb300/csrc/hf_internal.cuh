@@ -77,7 +77,7 @@ struct QmcProblem {
     int delay_k;          // FP32-pair sweeps: delayed-update depth (<= 1: rank-1 updates)
     int refresh_stagger;  // 1: chain (site, c) refreshes when nsw + site + c = 0 mod refresh_every
     const double* gtau;   // [nsite][2][L]  bath g~0(tau_m)
-    double* g0inv;        // [nsite][2][L*L] inverse bath matrices (FP32 path) or nullptr
+    double* g0inv;        // [nsite][2][L*L] inverse bath matrices (rebuilt with the bath)
     double* G;            // [nchain][2][L*L] (FP64 state, or FP64 scratch of the FP32 path)
     float* Gf;            // [nchain][2][L*L] FP32 state (precision 1) or nullptr
     int8_t* s;            // [nchain][L]
@@ -113,8 +113,10 @@ int qmc_f32_chains_per_block(int L);
 // p.Gf is set, its FP32 copy; measures afterwards when p.refresh_measure is set.
 size_t refresh_f64_smem_bytes(int L);
 cudaError_t launch_refresh_f64(const QmcProblem& p, cudaStream_t st);
-// g0^{-1} of every (site, spin) of p from p.gtau into p.g0inv (FP32 path, once per bath)
-cudaError_t launch_g0_inverse(const QmcProblem& p, int nsite, cudaStream_t st);
+// g0^{-1} of every (site, spin) of every problem of b, from p.gtau into p.g0inv (nchain / cps
+// sites each); the refreshes of all three sweep forms read it, so it is rebuilt whenever a bath
+// changes.
+cudaError_t launch_g0_inverse(const QmcBatch& b, cudaStream_t st);
 
 cudaError_t launch_init_fields(int8_t* s, int nchain, int cps, int L, uint32_t seed_lo,
                                uint32_t seed_hi, cudaStream_t st, int site0 = 0);

@@ -106,6 +106,7 @@ struct Launch {
 // Per-request device layout inside its arena block.
 struct Block {
     double* gtau;      // [2][L]
+    double* g0inv;     // [2][L*L] inverse bath matrices of the refreshes
     double* G;         // [cps][2][L*L]
     int8_t* s;         // [cps][L]
     uint32_t* nsw;     // [cps]
@@ -170,6 +171,7 @@ size_t job_bytes(const hf_srv_params& p, int nb, int L) {
     const size_t cps = static_cast<size_t>(p.chains_per_request);
     size_t n = 0;
     n += align256(sizeof(double) * 2 * L);
+    n += align256(sizeof(double) * 2 * L * L);
     n += align256(sizeof(double) * cps * 2 * L * L);
     n += align256(cps * L);
     n += align256(sizeof(uint32_t) * cps) * 2;
@@ -186,6 +188,7 @@ Block carve(char* base, const hf_srv_params& p, int nb, int L) {
     size_t o = 0;
     auto take = [&](size_t n) { char* q = base + o; o += align256(n); return q; };
     b.gtau = reinterpret_cast<double*>(take(sizeof(double) * 2 * L));
+    b.g0inv = reinterpret_cast<double*>(take(sizeof(double) * 2 * L * L));
     b.G = reinterpret_cast<double*>(take(sizeof(double) * cps * 2 * L * L));
     b.s = reinterpret_cast<int8_t*>(take(cps * L));
     b.nsw = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * cps));
@@ -283,6 +286,7 @@ hf_status start_launch(hf_srv* S, Launch& Lh) {
         q.delay_k = 1;
         if (L > 32 && q.team_warps == 1) q.team_warps = 2;
         q.gtau = b.gtau;
+        q.g0inv = b.g0inv;
         q.G = b.G;
         q.s = b.s;
         q.nsw = b.nsw;
@@ -296,6 +300,7 @@ hf_status start_launch(hf_srv* S, Launch& Lh) {
                                                : hfk::qmc_f64_smem_bytes(L, q.team_warps));
     }
     qb.nblocks = blocks;
+    if (e == cudaSuccess) e = hfk::launch_g0_inverse(qb, st);   // every request brings a new bath
     if (e == cudaSuccess)
         e = (p.precision == 2) ? hfk::launch_qmc_df64(qb, smem, st) : hfk::launch_qmc_f64(qb, smem, st);
     for (int k = 0; k < qb.nprob && e == cudaSuccess; ++k) {

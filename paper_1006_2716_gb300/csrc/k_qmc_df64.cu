@@ -95,24 +95,34 @@ __device__ __forceinline__ float2 df_recip(float2 R) {
     return df_add(r, df_mul(r, e));
 }
 
-// Dyson refresh of both spins in FP64 (as the FP64 kernel, on dense L x L matrices in the two
-// G buffers), each result parked in the chain's global slot, then split into double-floats in
-// the permuted placement.
+// Dyson refresh of both spins in FP64 (as the FP64 kernel: G_sigma = M_sigma^{-1} with
+// M_sigma = g0^{-1} e^{V_sigma} - (e^{V_sigma} - 1), dense in the two G buffers), both results
+// parked in the chain's global slot, then split into double-floats in the permuted placement.
 template <int L, int TW>
-__device__ void refresh_both_df(const QmcProblem& P, const TeamSmem<L>& S, const double* gt,
-                                double* Gg, int tid) {
+__device__ void refresh_both_df(const QmcProblem& P, const TeamSmem<L>& S, int site, double* Gg,
+                                int tid) {
     constexpr int T = 32 * TW;
     float2* X0 = reinterpret_cast<float2*>(S.G0);
     float2* X1 = reinterpret_cast<float2*>(S.G1);
-    build_dyson<L, TW>(P, gt, S.s, +1, S.G1, S.G0, tid);
-    team_sync<TW>();
-    bool ok = solve_dyson<L, TW>(S.G1, S.G0, S.cr, S.piv, tid);
-    for (int e = tid; e < L * L; e += T) Gg[e] = S.G0[e];            // park FP64 G_up
-    team_sync<TW>();
-    build_dyson<L, TW>(P, gt + L, S.s, -1, S.G0, S.G1, tid);
-    team_sync<TW>();
-    ok = solve_dyson<L, TW>(S.G0, S.G1, S.cr, S.piv, tid) && ok;
-    for (int e = tid; e < L * L; e += T) Gg[L * L + e] = S.G1[e];    // park FP64 G_dn
+    const GjTeamScratch<L> g(S);
+    bool ok = true;
+    if (P.ev_p == 0.0 && P.ev_m == 0.0) {   // U = 0: G = g0 exactly
+        const double* gt = P.gtau + static_cast<size_t>(site) * 2 * L;
+        build_bath_matrix<L, TW>(gt, S.G0, tid);
+        build_bath_matrix<L, TW>(gt + L, S.G1, tid);
+        team_sync<TW>();
+    } else {
+        const double* gi = P.g0inv + static_cast<size_t>(site) * 2 * L * L;
+        build_inverse_dyson<L, TW>(P, gi, S.s, +1, S.G0, tid);
+        build_inverse_dyson<L, TW>(P, gi + L * L, S.s, -1, S.G1, tid);
+        team_sync<TW>();
+        ok = gj_team<L, TW>(S.G0, g.fcol, g.pivrow, g.flag, g.pinv, tid);
+        ok = gj_team<L, TW>(S.G1, g.fcol, g.pivrow, g.flag, g.pinv, tid) && ok;
+    }
+    for (int e = tid; e < L * L; e += T) {
+        Gg[e] = S.G0[e];
+        Gg[L * L + e] = S.G1[e];
+    }
     team_sync<TW>();
     for (int e = tid; e < L * L; e += T) {
         const int i = e / L, j = e - (e / L) * L;
@@ -325,7 +335,6 @@ __device__ void df_chain(const QmcProblem& P, int c, unsigned char* base, int ti
     float2* cr = reinterpret_cast<float2*>(S.cr);
     const int site = c / P.cps;
     const int ch = c - site * P.cps;
-    const double* gt = P.gtau + static_cast<size_t>(site) * 2 * L;
     double* Gg = P.G + static_cast<size_t>(c) * 2 * LL;   // 8 bytes per element, pairs here
     float2* Gp = reinterpret_cast<float2*>(Gg);
     const uint2 key = make_uint2(P.seed_lo, P.seed_hi);
@@ -374,7 +383,7 @@ __device__ void df_chain(const QmcProblem& P, int c, unsigned char* base, int ti
         S.bacc[k] = (cur_bin < P.max_bins) ? bins_c[static_cast<size_t>(cur_bin) * W + k] : 0.0;
     team_sync<TW>();
     if (P.refresh_first) {
-        refresh_both_df<L, TW>(P, S, gt, Gg, tid);
+        refresh_both_df<L, TW>(P, S, site, Gg, tid);
     } else {
         for (int e = tid; e < LL; e += T) {
             const int i = e / L, j = e - (e / L) * L;
@@ -513,7 +522,7 @@ __device__ void df_chain(const QmcProblem& P, int c, unsigned char* base, int ti
         ++nsw;
         team_sync<TW>();
         if (P.refresh_every > 0 && ((nsw + rphase) % static_cast<uint32_t>(P.refresh_every)) == 0u)
-            refresh_both_df<L, TW>(P, S, gt, Gg, tid);
+            refresh_both_df<L, TW>(P, S, site, Gg, tid);
         if (k >= P.n_warmup) {
             measure_df<L, TW>(S, tid);
             ++nmeas;

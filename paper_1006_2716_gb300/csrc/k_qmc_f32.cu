@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(kT32) qmc_f32_kernel(const __grid_constant__ Q
 // --------------------------------------------------------------------------------------------
 // FP64 refresh (one block per chain, both spins) by way of the inverse Green function.
 // A G = g0 with A = 1 + (1 - g0) D, D = diag(e^V - 1), gives G^{-1} = g0^{-1} A =
-// g0^{-1} e^V - D.  With g0^{-1} computed once per bath (g0_inverse_kernel), a refresh is one
+// g0^{-1} e^V - D.  With g0^{-1} computed once per bath (launch_g0_inverse), a refresh is one
 // in-place Gauss-Jordan inversion of M = g0^{-1} e^V - D: L^3 FP64 multiply-adds, against the
 // (4/3) L^3 of factoring A and solving for the L columns of g0, and every elimination step is a
 // full-width rank-1 update that all threads share evenly.
@@ -333,36 +333,6 @@ __device__ bool gj_invert(const GjScratch& g, int tid) {
     return ok;
 }
 
-// g0^{-1} of every inequivalent site and spin: one block per (site, spin) builds the
-// antiperiodic bath matrix g0[l][l'] = g~0(tau_l - tau_l') from g~0(tau_m) and inverts it.
-template <int L>
-__device__ void g0_inverse_block(const QmcProblem& P, int blk, unsigned char* smem) {
-    const int tid = threadIdx.x;
-    const GjScratch g = gj_scratch<L>(smem);
-    const double* gt = P.gtau + static_cast<size_t>(blk) * L;
-    for (int e = tid; e < L * L; e += kT32) {
-        const int i = e / L, j = e - (e / L) * L;
-        const int d = i - j;
-        g.M[e] = (d >= 0) ? gt[d] : -gt[d + L];
-    }
-    __syncthreads();
-    const bool ok = gj_invert<L>(g, tid);
-    double* out = P.g0inv + static_cast<size_t>(blk) * L * L;
-    for (int e = tid; e < L * L; e += kT32) out[e] = g.M[e];
-    if (!ok && tid == 0) atomicExch(P.status, static_cast<int>(HF_ENUMERIC));
-}
-
-__global__ void __launch_bounds__(kT32) g0_inverse_kernel(const QmcProblem P) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    switch (P.L) {
-        case 16: g0_inverse_block<16>(P, blockIdx.x, smem); break;
-        case 32: g0_inverse_block<32>(P, blockIdx.x, smem); break;
-        case 64: g0_inverse_block<64>(P, blockIdx.x, smem); break;
-        case 128: g0_inverse_block<128>(P, blockIdx.x, smem); break;
-        default: break;
-    }
-}
-
 // G_sigma = M^{-1}, M = g0^{-1} e^{V_sigma} - (e^{V_sigma} - 1) (columns scaled by the fields)
 template <int L>
 __device__ bool refresh_chain(const QmcProblem& P, int c, unsigned char* smem) {
@@ -491,16 +461,6 @@ cudaError_t launch_qmc_f32(const QmcBatch& b, size_t smem, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     if (b.nblocks <= 0) return cudaSuccess;
     qmc_f32_kernel<<<b.nblocks, kT32, smem, st>>>(b);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_g0_inverse(const QmcProblem& p, int nsite, cudaStream_t st) {
-    const size_t smem = refresh_bytes(p.L);
-    cudaError_t e = cudaFuncSetAttribute(g0_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(refresh_bytes(128)));
-    if (e != cudaSuccess) return e;
-    if (nsite <= 0) return cudaSuccess;
-    g0_inverse_kernel<<<2 * nsite, kT32, smem, st>>>(p);
     return cudaGetLastError();
 }
 

@@ -15,6 +15,8 @@
 // GB300 has ~1 TFLOP/s of FP64 (DFMA and DMMA alike, 72x below FFMA), so this kernel is bound
 // by the FP64 pipe; it keeps the pipe busy with 12 chains per SM and issues no FP64 work that
 // the method does not need (the index arithmetic stays on the integer pipe).
+#include <algorithm>
+
 #include "qmc_common.cuh"
 
 namespace hfk {
@@ -23,23 +25,24 @@ namespace {
 using namespace qmc;
 
 
-// Dyson refresh of both spins.  A_up is built in G1's buffer and G_up solved in G0; G_up is
-// parked in the chain's global G slot while A_dn (in G0) and G_dn (in G1) are formed, then
-// brought back.  Every thread reads back exactly the elements it parked.
+// Dyson refresh of both spins: G_sigma = M_sigma^{-1}, M_sigma = g0^{-1} e^{V_sigma} -
+// (e^{V_sigma} - 1) built from the site's g0^{-1} and inverted in place in G_sigma's buffer.
 template <int L, int TW>
-__device__ void refresh_both(const QmcProblem& P, const TeamSmem<L>& S, const double* gt,
-                             double* Gg, int tid) {
-    constexpr int T = 32 * TW;
-    build_dyson<L, TW>(P, gt, S.s, +1, S.G1, S.G0, tid);
+__device__ void refresh_both(const QmcProblem& P, const TeamSmem<L>& S, int site, int tid) {
+    if (P.ev_p == 0.0 && P.ev_m == 0.0) {   // U = 0
+        const double* gt = P.gtau + static_cast<size_t>(site) * 2 * L;
+        build_bath_matrix<L, TW>(gt, S.G0, tid);
+        build_bath_matrix<L, TW>(gt + L, S.G1, tid);
+        team_sync<TW>();
+        return;
+    }
+    const GjTeamScratch<L> g(S);
+    const double* gi = P.g0inv + static_cast<size_t>(site) * 2 * L * L;
+    build_inverse_dyson<L, TW>(P, gi, S.s, +1, S.G0, tid);
+    build_inverse_dyson<L, TW>(P, gi + L * L, S.s, -1, S.G1, tid);
     team_sync<TW>();
-    bool ok = solve_dyson<L, TW>(S.G1, S.G0, S.cr, S.piv, tid);
-    for (int e = tid; e < L * L; e += T) Gg[e] = S.G0[e];
-    team_sync<TW>();
-    build_dyson<L, TW>(P, gt + L, S.s, -1, S.G0, S.G1, tid);
-    team_sync<TW>();
-    ok = solve_dyson<L, TW>(S.G0, S.G1, S.cr, S.piv, tid) && ok;
-    for (int e = tid; e < L * L; e += T) S.G0[e] = Gg[e];
-    team_sync<TW>();
+    bool ok = gj_team<L, TW>(S.G0, g.fcol, g.pivrow, g.flag, g.pinv, tid);
+    ok = gj_team<L, TW>(S.G1, g.fcol, g.pivrow, g.flag, g.pinv, tid) && ok;
     if (!ok && tid == 0) atomicExch(P.status, static_cast<int>(HF_ENUMERIC));
 }
 
@@ -185,7 +188,6 @@ __device__ void qmc_chain(const QmcProblem& P, int c, unsigned char* base, int t
     const TeamSmem<L> S(base);
     const int site = c / P.cps;
     const int ch = c - site * P.cps;
-    const double* gt = P.gtau + static_cast<size_t>(site) * 2 * L;
     double* Gg = P.G + static_cast<size_t>(c) * 2 * LL;
     const uint2 key = make_uint2(P.seed_lo, P.seed_hi);
 
@@ -207,7 +209,7 @@ __device__ void qmc_chain(const QmcProblem& P, int c, unsigned char* base, int t
         S.bacc[k] = (cur_bin < P.max_bins) ? bins_c[static_cast<size_t>(cur_bin) * W + k] : 0.0;
     team_sync<TW>();
     if (P.refresh_first) {
-        refresh_both<L, TW>(P, S, gt, Gg, tid);
+        refresh_both<L, TW>(P, S, site, tid);
     } else {
         for (int e = tid; e < LL; e += T) {
             S.G0[e] = Gg[e];
@@ -283,7 +285,7 @@ __device__ void qmc_chain(const QmcProblem& P, int c, unsigned char* base, int t
         ++nsw;
         team_sync<TW>();
         if (P.refresh_every > 0 && ((nsw + rphase) % static_cast<uint32_t>(P.refresh_every)) == 0u)
-            refresh_both<L, TW>(P, S, gt, Gg, tid);
+            refresh_both<L, TW>(P, S, site, tid);
         if (k >= P.n_warmup) {
             measure<L, TW>(S, tid);
             ++nmeas;
@@ -369,7 +371,79 @@ __global__ void init_fields_kernel(int8_t* s, int nchain, int cps, int L, uint32
     s[idx] = (x.x >> 31) ? static_cast<int8_t>(-1) : static_cast<int8_t>(1);
 }
 
+// g0^{-1} of every (site, spin) of every problem of a batch, for the refreshes: one block of
+// kBlock threads per (problem, site, spin) builds the antiperiodic bath matrix
+// g0[l][l'] = g~0(tau_l - tau_l') (g~0 negated for l < l') and inverts it by Gauss-Jordan.
+__host__ __device__ constexpr size_t g0inv_smem(int L) {
+    // M[L*L] + fcol[L] + pinv f64, flag[2] + pivrow[L] int
+    return static_cast<size_t>(L * L + L + 1) * 8 + static_cast<size_t>(L + 2) * 4;
+}
+
+template <int L>
+__device__ void g0inv_block(const QmcProblem& P, int b, unsigned char* smem) {
+    constexpr int TW = kBlock / 32;
+    double* M = reinterpret_cast<double*>(smem);
+    double* fcol = M + L * L;
+    double* pinv = fcol + L;
+    int* flag = reinterpret_cast<int*>(pinv + 1);
+    int* pivrow = flag + 2;
+    const int tid = threadIdx.x;
+    const double* gt = P.gtau + static_cast<size_t>(b) * L;
+    for (int e = tid; e < L * L; e += kBlock) {
+        const int i = e / L, j = e - (e / L) * L;
+        const int d = i - j;
+        M[e] = (d >= 0) ? gt[d] : -gt[d + L];
+    }
+    __syncthreads();
+    const bool ok = gj_team<L, TW>(M, fcol, pivrow, flag, pinv, tid);
+    double* out = P.g0inv + static_cast<size_t>(b) * L * L;
+    for (int e = tid; e < L * L; e += kBlock) out[e] = M[e];
+    if (!ok && tid == 0) atomicExch(P.status, static_cast<int>(HF_ENUMERIC));
+}
+
+__global__ void __launch_bounds__(kBlock) g0inv_kernel(const __grid_constant__ QmcBatch B) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    int pi = 0, base = 0;
+    while (pi < B.nprob) {
+        const int nb = 2 * (B.p[pi].nchain / B.p[pi].cps);
+        if (static_cast<int>(blockIdx.x) < base + nb) break;
+        base += nb;
+        ++pi;
+    }
+    if (pi >= B.nprob) return;
+    const QmcProblem& P = B.p[pi];
+    const int b = static_cast<int>(blockIdx.x) - base;
+    switch (P.L) {
+        case 8: g0inv_block<8>(P, b, smem); break;
+        case 12: g0inv_block<12>(P, b, smem); break;
+        case 16: g0inv_block<16>(P, b, smem); break;
+        case 20: g0inv_block<20>(P, b, smem); break;
+        case 24: g0inv_block<24>(P, b, smem); break;
+        case 32: g0inv_block<32>(P, b, smem); break;
+        case 40: g0inv_block<40>(P, b, smem); break;
+        case 48: g0inv_block<48>(P, b, smem); break;
+        case 64: g0inv_block<64>(P, b, smem); break;
+        case 128: g0inv_block<128>(P, b, smem); break;
+        default: break;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_g0_inverse(const QmcBatch& b, cudaStream_t st) {
+    int blocks = 0;
+    size_t smem = 0;
+    for (int i = 0; i < b.nprob; ++i) {
+        blocks += 2 * (b.p[i].nchain / b.p[i].cps);
+        smem = std::max(smem, g0inv_smem(b.p[i].L));
+    }
+    cudaError_t e = cudaFuncSetAttribute(g0inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(g0inv_smem(128)));
+    if (e != cudaSuccess) return e;
+    if (blocks <= 0) return cudaSuccess;
+    g0inv_kernel<<<blocks, kBlock, smem, st>>>(b);
+    return cudaGetLastError();
+}
 
 bool qmc_f64_supported(int L) {
     switch (L) {

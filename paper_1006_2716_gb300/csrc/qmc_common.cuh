@@ -193,5 +193,133 @@ __device__ bool solve_dyson(double* A, double* B, double* f, int* piv, int tid) 
 }
 
 
+// Dyson refresh by way of the inverse Green function.  A G = g0 with A = 1 + (1 - g0) D,
+// D = diag(e^{V_j} - 1), gives G^{-1} = g0^{-1} A = g0^{-1} e^V - D, so with g0^{-1} computed
+// once per bath a refresh is one inversion of M = g0^{-1} e^V - D: L^3 FP64 multiply-adds per
+// spin against the (4/3) L^3 of factoring A and solving for the L columns of g0.
+
+// The bath matrix itself, g0[l][l'] = g~0(tau_l - tau_l') (negated for l < l'): at U = 0 every
+// e^{V_j} is 1, A = 1 and the Dyson relation gives G = g0 exactly, with no inversion.
+template <int L, int TW>
+__device__ void build_bath_matrix(const double* gt, double* G, int tid) {
+    constexpr int T = 32 * TW;
+    for (int e = tid; e < L * L; e += T) {
+        const int i = e / L, j = e - (e / L) * L;
+        const int d = i - j;
+        G[e] = (d >= 0) ? gt[d] : -gt[d + L];
+    }
+}
+
+// M[i][j] = g0inv[i][j] e^{V_j} - delta_ij (e^{V_j} - 1), V_j = lambda sigma s_j (dense, row-major)
+template <int L, int TW>
+__device__ void build_inverse_dyson(const QmcProblem& P, const double* g0inv, const int8_t* s,
+                                    int sigma, double* M, int tid) {
+    constexpr int T = 32 * TW;
+    for (int e = tid; e < L * L; e += T) {
+        const int i = e / L, j = e - (e / L) * L;
+        const bool up = sigma * s[j] > 0;
+        const double ev = up ? P.ev_p : P.ev_m;
+        const double m = g0inv[e] * (1.0 + ev);
+        M[e] = (i == j) ? m - ev : m;
+    }
+}
+
+// In-place inverse of the dense row-major L x L matrix M by Gauss-Jordan elimination with partial
+// pivoting by rows, by a team of 32 TW threads: step k takes the largest |M[i][k]|, i >= k, as
+// pivot (the smallest i among equal magnitudes), swaps it into row k, scales row k by its
+// reciprocal, moves column k out and subtracts its multiples of row k from every other row; the
+// column order is restored at the end.  Scratch: fcol[L] doubles, pivrow[L] ints, flag[2] ints,
+// *pinv.  Returns false if a pivot column was exactly zero.
+template <int L, int TW>
+__device__ bool gj_team(double* M, double* fcol, int* pivrow, int* flag, double* pinv, int tid) {
+    constexpr int T = 32 * TW;
+    bool ok = true;
+    for (int k = 0; k < L; ++k) {
+        if (tid < 32) {
+            unsigned long long best = 0ull;
+            int bi = L;
+            for (int i = k + tid; i < L; i += 32) {
+                const unsigned long long key = mag_key(M[i * L + k]);
+                if (bi == L || key > best) {
+                    best = key;
+                    bi = i;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (oi != L && (bi == L || ob > best || (ob == best && oi < bi))) {
+                    best = ob;
+                    bi = oi;
+                }
+            }
+            if (tid == 0) {
+                pivrow[k] = bi;
+                flag[0] = bi;
+                flag[1] = (best == 0ull) ? 1 : 0;
+                *pinv = 1.0 / M[bi * L + k];
+            }
+        }
+        team_sync<TW>();
+        const int p = flag[0];
+        if (flag[1]) ok = false;
+        if (p != k) {
+            for (int j = tid; j < L; j += T) {
+                const double t = M[k * L + j];
+                M[k * L + j] = M[p * L + j];
+                M[p * L + j] = t;
+            }
+            team_sync<TW>();
+        }
+        const double pv = *pinv;
+        // disjoint elements: row k (scaled; its diagonal becomes the reciprocal) and the rest of
+        // column k (copied out and zeroed)
+        for (int j = tid; j < L; j += T) {
+            const double x = M[k * L + j];
+            M[k * L + j] = (j == k) ? pv : x * pv;
+        }
+        for (int i = tid; i < L; i += T) {
+            if (i != k) {
+                fcol[i] = M[i * L + k];
+                M[i * L + k] = 0.0;
+            } else {
+                fcol[i] = 0.0;
+            }
+        }
+        team_sync<TW>();
+        for (int e = tid; e < L * L; e += T) {
+            const int i = e / L, j = e - (e / L) * L;
+            if (i != k) M[e] = fma(-fcol[i], M[k * L + j], M[e]);
+        }
+        team_sync<TW>();
+    }
+    for (int k = L - 1; k >= 0; --k) {   // undo the row swaps as column swaps, last first
+        const int p = pivrow[k];
+        if (p != k) {
+            for (int i = tid; i < L; i += T) {
+                const double t = M[i * L + k];
+                M[i * L + k] = M[i * L + p];
+                M[i * L + p] = t;
+            }
+            team_sync<TW>();
+        }
+    }
+    team_sync<TW>();   // every thread has read pivrow before the scratch is reused
+    return ok;
+}
+
+// Scratch of gj_team inside a team's shared memory: fcol = cr[0..L), *pinv = cr[L], pivrow in
+// the ints from cr + L + 1 on (L ints fit in the remaining 3L - 1 doubles), flag = piv[0..1].
+template <int L>
+struct GjTeamScratch {
+    double* fcol;
+    double* pinv;
+    int* pivrow;
+    int* flag;
+    __device__ explicit GjTeamScratch(const TeamSmem<L>& S)
+        : fcol(S.cr), pinv(S.cr + L), pivrow(reinterpret_cast<int*>(S.cr + L + 1)), flag(S.piv) {}
+};
+
 }  // namespace qmc
 }  // namespace hfk

@@ -112,11 +112,14 @@ def test_sweeps_identical_decisions(hf, L, beta, precision, team_warps, stagger)
         x = np.concatenate(x)
         mean = x.mean(axis=0)
         err = x.std(axis=0, ddof=1) / np.sqrt(x.shape[0])
-        assert np.abs(gtau - mean[:2 * L]).max() < 1e-10
-        assert abs(n[0] - mean[2 * L]) < 1e-10 and abs(n[1] - mean[2 * L + 1]) < 1e-10
-        assert abs(d - mean[2 * L + 2]) < 1e-10
-        assert abs(m - (mean[2 * L] - mean[2 * L + 1])) < 1e-10
-        assert np.abs(errs[:2 * L + 3] - err).max() < 1e-9
+        # the bins average G over the sweeps between refreshes, where the FP32-pair form's
+        # 48-bit updates drift further from FP64 than at the refreshes checked above
+        tol = 1e-10 if precision == 0 else 5e-10
+        assert np.abs(gtau - mean[:2 * L]).max() < tol
+        assert abs(n[0] - mean[2 * L]) < tol and abs(n[1] - mean[2 * L + 1]) < tol
+        assert abs(d - mean[2 * L + 2]) < tol
+        assert abs(m - (mean[2 * L] - mean[2 * L + 1])) < tol
+        assert np.abs(errs[:2 * L + 3] - err).max() < 10 * tol
     ctx.close()
 
 
