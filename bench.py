@@ -200,7 +200,7 @@ DF_OPS_PER_FMA = 12          # FP32-pipe ops of one double-float multiply-add (l
 # DRAM bytes (read + write) of one full-size launch (2500 sweeps of all 1760 chains), from one
 # ncu capture of the kernel built from sources with this sha256 prefix (profiles/
 # qmc_df64_kernel_square20.md); a kernel whose sources changed since reports null.
-MEASURED_TRAFFIC = {"qmc_df64_kernel": (1.72e6 + 1.08e6, "79bb9b9d42a84886")}
+MEASURED_TRAFFIC = {"qmc_df64_kernel": (2.376e6 + 1.156e6, "2f46ee809d4da10f")}
 KERNEL_SOURCES = {"qmc_df64_kernel": ("k_qmc_df64.cu", "qmc_common.cuh", "hf_internal.cuh"),
                   "qmc_f64_kernel": ("k_qmc_f64.cu", "qmc_common.cuh", "hf_internal.cuh")}
 
@@ -241,9 +241,12 @@ def qmc_roofline(form, L, nchain, sweeps, accepts, n_measure, n_refresh, qmc_s, 
         src = ("mixed-pipe roof: refresh on FP64 (2 DFMA/clk/SM), pair arithmetic on FP32 "
                "(128 FFMA/clk/SM, %d ops per FP64-equivalent FMA), both at 2.07 GHz, overlapped"
                % DF_OPS_PER_FMA)
+    # the refreshes invert G^{-1} by Gauss-Jordan: 2 L^3 executed flops per spin against the
+    # 2 (8/3) L^3 of the algorithmic Dyson solve counted in f_ref
+    executed = (total - 0.25 * f_ref) / qmc_s / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": measured_traffic(kernel), "kernel": kernel,
-            "peak_source": src}
+            "executed_tflops": executed, "peak_source": src}
 
 
 def _time_iterations(hf, ctx, stream, flush, steps):

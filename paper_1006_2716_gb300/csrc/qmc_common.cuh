@@ -100,99 +100,6 @@ __device__ __forceinline__ double recip64(double R, float Rf) {
     return fma(r, e, r);
 }
 
-// Build A = 1 + (1 - g0) diag(e^{lambda sigma s_j} - 1) into A and g0 into B.
-template <int L, int TW>
-__device__ void build_dyson(const QmcProblem& P, const double* gt, const int8_t* s, int sigma,
-                            double* A, double* B, int tid) {
-    constexpr int T = 32 * TW;
-    for (int e = tid; e < L * L; e += T) {
-        const int i = e / L, j = e - (e / L) * L;
-        const int d = i - j;
-        const double g = (d >= 0) ? gt[d] : -gt[d + L];
-        const double ev = (sigma * s[j] > 0) ? P.ev_p : P.ev_m;
-        const double one = (i == j) ? 1.0 : 0.0;
-        A[e] = __dadd_rn(one, __dmul_rn(__dadd_rn(one, -g), ev));
-        B[e] = g;
-    }
-}
-
-// Solve A X = B in place (X overwrites B) by Gaussian elimination with partial pivoting.
-// Returns false if a pivot is exactly zero.
-template <int L, int TW>
-__device__ bool solve_dyson(double* A, double* B, double* f, int* piv, int tid) {
-    constexpr int T = 32 * TW;
-    bool ok = true;
-    for (int k = 0; k < L; ++k) {
-        if (tid < 32) {
-            unsigned long long best = 0ull;
-            int bi = L;  // sentinel: nothing found yet
-            for (int i = k + tid; i < L; i += 32) {
-                const unsigned long long key = mag_key(A[i * L + k]);
-                if (bi == L || key > best) {
-                    best = key;
-                    bi = i;
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                // larger magnitude wins; ties go to the smaller row (first maximum)
-                if (oi != L && (bi == L || ob > best || (ob == best && oi < bi))) {
-                    best = ob;
-                    bi = oi;
-                }
-            }
-            if (tid == 0) {
-                piv[0] = bi;
-                piv[1] = (best == 0ull) ? 1 : 0;
-            }
-        }
-        team_sync<TW>();
-        const int p = piv[0];
-        if (piv[1]) ok = false;
-        if (p != k) {
-            for (int j = tid; j < 2 * L; j += T) {
-                double* M = (j < L) ? A : B;
-                const int jj = (j < L) ? j : j - L;
-                const double t = M[k * L + jj];
-                M[k * L + jj] = M[p * L + jj];
-                M[p * L + jj] = t;
-            }
-        }
-        team_sync<TW>();
-        const double inv = 1.0 / A[k * L + k];
-        for (int i = k + 1 + tid; i < L; i += T) f[i] = A[i * L + k] * inv;
-        if (tid == 0) f[L + k] = inv;   // kept for the back substitution
-        team_sync<TW>();
-        // rows i > k of [A | B]: subtract f_i times row k (A columns j > k only)
-        const int rows = L - 1 - k;
-        for (int e = tid; e < rows * 2 * L; e += T) {
-            const int r = e / (2 * L);
-            const int j = e - r * (2 * L);
-            const int i = k + 1 + r;
-            if (j < L) {
-                if (j > k) A[i * L + j] = fma(-f[i], A[k * L + j], A[i * L + j]);
-            } else {
-                const int jj = j - L;
-                B[i * L + jj] = fma(-f[i], B[k * L + jj], B[i * L + jj]);
-            }
-        }
-        team_sync<TW>();
-    }
-    // back substitution, one column of B per thread (columns are independent)
-    for (int c = tid; c < L; c += T) {
-        for (int i = L - 1; i >= 0; --i) {
-            double acc = B[i * L + c];
-            for (int j = i + 1; j < L; ++j) acc = fma(-A[i * L + j], B[j * L + c], acc);
-            B[i * L + c] = acc * f[L + i];
-        }
-    }
-    team_sync<TW>();
-    return ok;
-}
-
-
 // Dyson refresh by way of the inverse Green function.  A G = g0 with A = 1 + (1 - g0) D,
 // D = diag(e^{V_j} - 1), gives G^{-1} = g0^{-1} A = g0^{-1} e^V - D, so with g0^{-1} computed
 // once per bath a refresh is one inversion of M = g0^{-1} e^V - D: L^3 FP64 multiply-adds per
