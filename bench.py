@@ -107,7 +107,7 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------------------------
-# CPU oracle leg (spawned process, one thread)
+# CPU oracle legs (spawned processes: one thread, and one worker per host core)
 # ---------------------------------------------------------------------------------------------
 def _oracle_sample(q, n_chains, n_freq):
     import numpy as np
@@ -140,6 +140,94 @@ def _oracle_sample(q, n_chains, n_freq):
                     refresh_stagger=cfg.get("refresh_stagger", 0))
     t_qmc = (time.perf_counter() - t0) * (1760.0 / n_chains)
     q.put((t_lat, t_qmc))
+
+
+# all host cores: the same sample split over a pool of spawned workers, one BLAS thread each
+_W = {}
+
+
+def _pool_init():
+    from oracle.rdmft import RDMFT
+
+    cfg = CFG
+    r = RDMFT(cfg["Lx"], cfg["Ly"], U=cfg["U"], V0=cfg["V0"], mu=cfg["mu"], beta=cfg["beta"], L=32,
+              nw=cfg["n_matsubara"], chains=1, seed=cfg["seed"], h_seed=cfg["h_seed"])
+    _W["H0"], _W["full"] = r.lat.H0, r.expand_sigma()
+
+
+def _pool_lattice(idx):
+    import numpy as np
+
+    from oracle.lattice import lattice_step
+
+    idx = np.asarray(idx)
+    for sp in range(2):
+        lattice_step(_W["H0"], CFG["mu"], CFG["beta"], _W["full"][sp][idx], n_index=idx)
+    return len(idx)
+
+
+def _pool_chains(chains):
+    import numpy as np
+
+    import oracle as o
+
+    cfg, L = CFG, 32
+    baths = wl.random_baths(2, max(chains) + 1, cfg["beta"], L)
+    _, lam = o.constants(cfg["beta"], cfg["U"], L)
+    for c in chains:
+        g0u, g0d = o.build_g0(baths[c, 0]), o.build_g0(baths[c, 1])
+        s = o.init_fields(cfg["seed"], c, 0, L)
+        Gu, _ = o.dyson(g0u, s, 1, lam)
+        Gd, _ = o.dyson(g0d, s, -1, lam)
+        bins = np.zeros((cfg["n_measure"] // cfg["bin_size"], 2 * L + 3))
+        o.run_chain(lam, g0u, g0d, cfg["seed"], c, 0, 0, cfg["n_warmup"], cfg["n_measure"],
+                    cfg["refresh_every"], cfg["bin_size"], s, Gu, Gd, bins,
+                    refresh_stagger=cfg.get("refresh_stagger", 0))
+    return len(chains)
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_oracle_all_cores(chains_per_core=20, freqs_per_core=2):
+    """Oracle time of one full iteration on every host core (seconds), from a bounded sample:
+    chains and lattice frequencies split over a spawned pool (one process and one BLAS thread
+    per core); returns (seconds, cores, sample)."""
+    cores = host_cores()
+    ctx = mp.get_context("spawn")
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        pool = ctx.Pool(cores, initializer=_pool_init)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    try:
+        pool.map(_pool_chains, [[w] for w in range(cores)], chunksize=1)   # warm: imports, builds
+        n_freq = min(500, cores * freqs_per_core)
+        idx = [int(k * (CFG["n_matsubara"] // n_freq)) for k in range(n_freq)]
+        t0 = time.perf_counter()
+        pool.map(_pool_lattice, [idx[w::cores] for w in range(cores) if idx[w::cores]], chunksize=1)
+        t_lat = (time.perf_counter() - t0) * (CFG["n_matsubara"] / n_freq)
+        n_chains = cores * chains_per_core
+        t0 = time.perf_counter()
+        pool.map(_pool_chains, [list(range(w, n_chains, cores)) for w in range(cores)], chunksize=1)
+        t_qmc = (time.perf_counter() - t0) * (1760.0 / n_chains)
+    finally:
+        pool.close()
+        pool.join()
+    sample = ("%d of 1760 chains x 2500 sweeps (L=32) + lattice step at %d of 500 frequencies x 2 "
+              "spins (dense inverse, N=400) over %d worker processes, each scaled to the full "
+              "iteration" % (n_chains, n_freq, cores))
+    return t_lat + t_qmc, cores, sample
 
 
 def cpu_oracle(n_chains=160, n_freq=20):
@@ -175,11 +263,11 @@ def run_reference(args):
         return 0
     proposals = 1760 * 2500 * 32
     times = []
-    sample = ""
+    sample, cores = "", 1
     for _ in range(args.warmup):
-        cpu_oracle(2, 4)
+        cpu_oracle_all_cores(chains_per_core=1, freqs_per_core=1)
     for _ in range(args.steps):
-        t, sample = cpu_oracle(64, 10)
+        t, cores, sample = cpu_oracle_all_cores(chains_per_core=8, freqs_per_core=1)
         times.append(t)
     sec = sum(times) / len(times)
     v = proposals / sec
@@ -187,7 +275,7 @@ def run_reference(args):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD},
-            "cpu_baseline": {"value": v, "unit": "proposals/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": "proposals/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": "proposals/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -284,8 +372,11 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         t_cpu, sample = cpu_oracle()
-        cpu = {"value": 1760 * 2500 * 32 / t_cpu, "unit": "proposals/s", "cores": 1,
-               "kind": "oracle", "sample": sample}
+        t_all, cores, sample_all = cpu_oracle_all_cores()
+        single = {"value": 1760 * 2500 * 32 / t_cpu, "unit": "proposals/s", "cores": 1,
+                  "sample": sample}
+        cpu = {"value": 1760 * 2500 * 32 / t_all, "unit": "proposals/s", "cores": cores,
+               "kind": "oracle", "sample": sample_all, "single_core": single}
     torch.cuda.set_device(local)
     from paper_1006_2716_gb300 import autotune, hf
 
