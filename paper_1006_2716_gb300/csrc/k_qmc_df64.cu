@@ -243,18 +243,21 @@ __device__ void df_flush(float2* G0, float2* G1, const float2* Ut0, const float2
 // v = cr[2L..3L) / cr[3L..4L).  Each thread takes its elements in groups of up to 8 rows: all
 // loads of a group, then the group's arithmetic, then its stores.  The compiler cannot prove
 // that the G stores miss the cr loads, so it would otherwise run one element's dependent pair
-// arithmetic after another.  Where the team's threads tile the matrix in column pairs, a thread
-// owns two adjacent columns: one 128-bit load and store per row and spin, and each u[i] serves
-// two elements.
+// arithmetic after another.  For even L a thread owns two adjacent columns: one 128-bit load and
+// store per row and spin, and each u[i] serves two elements.
 template <int L, int TW>
 __device__ __forceinline__ void df_rank1(float2* G0, float2* G1, const float2* cr, int tid) {
     constexpr int T = 32 * TW;
-    if constexpr ((2 * T) % L == 0) {
-        // column pair (j, j + 1), j = 2 (tid % (L/2)); rows i0, i0 + STEP, ...
+    if constexpr (L % 2 == 0 && T >= L / 2) {
+        // column pair (j, j + 1), j = 2 (tid % (L/2)); rows i0, i0 + STEP, ... below L.  STEP =
+        // T / (L/2) threads share a pair; the T - STEP L/2 spare threads (L not dividing 2T) sit
+        // out.
         constexpr int NCP = L / 2, STEP = T / NCP, NR = (L + STEP - 1) / STEP;
-        constexpr int GB = NR < 8 ? NR : 8;
+        constexpr int GB8 = NR < 8 ? NR : 8;
+        constexpr bool EXACT = (L % STEP == 0) && (NR % GB8 == 0);   // no row guard needed
+        constexpr int GB = EXACT ? GB8 : (NR < 4 ? NR : 4);          // guarded rows: fewer live
+        if (tid >= STEP * NCP) return;
         const int j = 2 * (tid % NCP), i0 = tid / NCP;
-        if (STEP > L && i0 >= L) return;
         const float4 r0 = *reinterpret_cast<const float4*>(cr + 2 * L + j);
         const float4 r1 = *reinterpret_cast<const float4*>(cr + 3 * L + j);
         for (int b = 0; b < NR; b += GB) {
@@ -263,10 +266,12 @@ __device__ __forceinline__ void df_rank1(float2* G0, float2* G1, const float2* c
 #pragma unroll
             for (int k = 0; k < GB; ++k) {
                 const int i = i0 + (b + k) * STEP;
-                a0[k] = *reinterpret_cast<const float4*>(G0 + gx<L>(i, j));
-                a1[k] = *reinterpret_cast<const float4*>(G1 + gx<L>(i, j));
-                c0[k] = cr[i];
-                c1[k] = cr[L + i];
+                if (EXACT || i < L) {
+                    a0[k] = *reinterpret_cast<const float4*>(G0 + gx<L>(i, j));
+                    a1[k] = *reinterpret_cast<const float4*>(G1 + gx<L>(i, j));
+                    c0[k] = cr[i];
+                    c1[k] = cr[L + i];
+                }
             }
 #pragma unroll
             for (int k = 0; k < GB; ++k) {
@@ -280,8 +285,10 @@ __device__ __forceinline__ void df_rank1(float2* G0, float2* G1, const float2* c
 #pragma unroll
             for (int k = 0; k < GB; ++k) {
                 const int i = i0 + (b + k) * STEP;
-                *reinterpret_cast<float4*>(G0 + gx<L>(i, j)) = a0[k];
-                *reinterpret_cast<float4*>(G1 + gx<L>(i, j)) = a1[k];
+                if (EXACT || i < L) {
+                    *reinterpret_cast<float4*>(G0 + gx<L>(i, j)) = a0[k];
+                    *reinterpret_cast<float4*>(G1 + gx<L>(i, j)) = a1[k];
+                }
             }
         }
     } else {
