@@ -133,11 +133,22 @@ __device__ void refresh_both_df(const QmcProblem& P, const TeamSmem<L>& S, int s
     if (!ok && tid == 0) atomicExch(P.status, static_cast<int>(HF_ENUMERIC));
 }
 
+// One measurement, accumulated in double-float on the FP32 pipe: the bin accumulator holds pair
+// sums of L G(tau_m) and of L n_up, L n_dn, L d (the per-measurement averages times L) in the
+// 8-byte slots of bacc; they become doubles, divided by L, only when a bin is written out.  On
+// this GPU FP64 instructions do not overlap the pair arithmetic, so the per-sweep path keeps
+// none.
+__device__ __forceinline__ float2 shfl_xor_df(float2 x, int o) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, x.x, o), __shfl_xor_sync(0xffffffffu, x.y, o));
+}
+
 template <int L, int TW>
 __device__ void measure_df(const TeamSmem<L>& S, int tid) {
     constexpr int T = 32 * TW;
     const float2* G0 = reinterpret_cast<const float2*>(S.G0);
     const float2* G1 = reinterpret_cast<const float2*>(S.G1);
+    float2* acc = reinterpret_cast<float2*>(S.bacc);
+    const float2 one = make_float2(1.0f, 0.0f);
     for (int m = tid; m < L; m += T) {
         float2 s0 = make_float2(0.0f, 0.0f), s1 = make_float2(0.0f, 0.0f);
         for (int q = 0; q < L; ++q) {
@@ -150,46 +161,47 @@ __device__ void measure_df(const TeamSmem<L>& S, int tid) {
             s0 = df_add(s0, wrap ? df_neg(x0) : x0);
             s1 = df_add(s1, wrap ? df_neg(x1) : x1);
         }
-        S.bacc[m] += df_to_d(s0) / L;
-        S.bacc[L + m] += df_to_d(s1) / L;
+        acc[m] = df_add(acc[m], s0);
+        acc[L + m] = df_add(acc[L + m], s1);
     }
-    double nu = 0.0, nd = 0.0, db = 0.0;
+    float2 nu = make_float2(0.0f, 0.0f), nd = nu, db = nu;
     for (int l = tid; l < L; l += T) {
-        const double a = 1.0 - df_to_d(G0[gx<L>(l, l)]);
-        const double b = 1.0 - df_to_d(G1[gx<L>(l, l)]);
-        nu += a;
-        nd += b;
-        db += a * b;
+        const float2 a = df_add(one, df_neg(df_norm(G0[gx<L>(l, l)])));
+        const float2 b = df_add(one, df_neg(df_norm(G1[gx<L>(l, l)])));
+        nu = df_add(nu, a);
+        nd = df_add(nd, b);
+        db = df_add(db, df_mul(a, b));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        nu += __shfl_xor_sync(0xffffffffu, nu, o);
-        nd += __shfl_xor_sync(0xffffffffu, nd, o);
-        db += __shfl_xor_sync(0xffffffffu, db, o);
+        nu = df_add(nu, shfl_xor_df(nu, o));
+        nd = df_add(nd, shfl_xor_df(nd, o));
+        db = df_add(db, shfl_xor_df(db, o));
     }
     if constexpr (TW > 1) {
+        float2* red = reinterpret_cast<float2*>(S.cr);   // [3][4] pairs
         const int w = tid >> 5;
         if ((tid & 31) == 0) {
-            S.red[w] = nu;
-            S.cr[w] = nd;
-            S.cr[4 + w] = db;
+            red[w] = nu;
+            red[4 + w] = nd;
+            red[8 + w] = db;
         }
         team_sync<TW>();
         if (tid == 0) {
-            nu = 0.0;
-            nd = 0.0;
-            db = 0.0;
-            for (int w2 = 0; w2 < TW; ++w2) {
-                nu += S.red[w2];
-                nd += S.cr[w2];
-                db += S.cr[4 + w2];
+            nu = red[0];
+            nd = red[4];
+            db = red[8];
+            for (int w2 = 1; w2 < TW; ++w2) {
+                nu = df_add(nu, red[w2]);
+                nd = df_add(nd, red[4 + w2]);
+                db = df_add(db, red[8 + w2]);
             }
         }
     }
     if (tid == 0) {
-        S.bacc[2 * L + 0] += nu / L;
-        S.bacc[2 * L + 1] += nd / L;
-        S.bacc[2 * L + 2] += db / L;
+        acc[2 * L + 0] = df_add(acc[2 * L + 0], nu);
+        acc[2 * L + 1] = df_add(acc[2 * L + 1], nd);
+        acc[2 * L + 2] = df_add(acc[2 * L + 2], db);
     }
     team_sync<TW>();
 }
@@ -387,7 +399,8 @@ __device__ void df_chain(const QmcProblem& P, int c, unsigned char* base, int ti
     int cur_bin = static_cast<int>(nmeas / P.bin_size);
     double* bins_c = P.bins + static_cast<size_t>(c) * P.max_bins * W;
     for (int k = tid; k < W; k += T)
-        S.bacc[k] = (cur_bin < P.max_bins) ? bins_c[static_cast<size_t>(cur_bin) * W + k] : 0.0;
+        reinterpret_cast<float2*>(S.bacc)[k] =
+            d_to_df((cur_bin < P.max_bins) ? bins_c[static_cast<size_t>(cur_bin) * W + k] * L : 0.0);
     team_sync<TW>();
     if (P.refresh_first) {
         refresh_both_df<L, TW>(P, S, site, Gg, tid);
@@ -536,8 +549,9 @@ __device__ void df_chain(const QmcProblem& P, int c, unsigned char* base, int ti
             if (nmeas % static_cast<uint32_t>(P.bin_size) == 0u) {
                 const int b = static_cast<int>(nmeas / P.bin_size) - 1;
                 for (int q = tid; q < W; q += T) {
-                    if (b < P.max_bins) bins_c[static_cast<size_t>(b) * W + q] = S.bacc[q];
-                    S.bacc[q] = 0.0;
+                    float2* acc = reinterpret_cast<float2*>(S.bacc);
+                    if (b < P.max_bins) bins_c[static_cast<size_t>(b) * W + q] = df_to_d(acc[q]) / L;
+                    acc[q] = make_float2(0.0f, 0.0f);
                 }
                 team_sync<TW>();
             }
@@ -546,7 +560,8 @@ __device__ void df_chain(const QmcProblem& P, int c, unsigned char* base, int ti
 
     cur_bin = static_cast<int>(nmeas / P.bin_size);
     for (int q = tid; q < W; q += T)
-        if (cur_bin < P.max_bins) bins_c[static_cast<size_t>(cur_bin) * W + q] = S.bacc[q];
+        if (cur_bin < P.max_bins)
+            bins_c[static_cast<size_t>(cur_bin) * W + q] = df_to_d(reinterpret_cast<float2*>(S.bacc)[q]) / L;
     for (int e = tid; e < LL; e += T) {
         const int i = e / L, j = e - (e / L) * L;
         Gp[e] = G0[gx<L>(i, j)];
