@@ -98,12 +98,14 @@ hf_status hf_get_orbits(const hf_ctx* ctx, int* rep, int* rep_of, int* flip);
 
 /* Set the Hartree-shifted bath g~0_sigma(tau_m), m = 0..L-1 (tau_0 = 0+), of one
  * inequivalent site and spin from a host array of L doubles.  The next hf_sweep with
- * refresh_first = 1 rebuilds every chain of that site from it (Dyson relation). */
+ * refresh_first = 1 rebuilds every chain of that site from it (Dyson relation); the inverse
+ * bath matrices the refreshes use are recomputed before that sweep.  Every site's bath must
+ * be set before sweeping (a zero bath matrix has no inverse: HF_ENUMERIC). */
 hf_status hf_set_g0(hf_ctx* ctx, int site, int spin, const double* g0_tau);
 
 /* Run n_warmup unmeasured then n_measure measured sweeps of every chain (asynchronous on
  * the context stream).  refresh_first = 1 first recomputes G = [1 + (1 - g0)(e^V - 1)]^{-1} g0
- * from the current bath and fields.  Per chain: sweep number w uses Philox counter
+ * from the current bath and fields (in FP64, as G = [g0^{-1} e^V - (e^V - 1)]^{-1}).  Per chain: sweep number w uses Philox counter
  * (w, l, chain, site); after the sweep the chain's counter advances and a Dyson refresh runs
  * when it is a multiple of refresh_every; measured sweeps then add to the current bin. */
 hf_status hf_sweep(hf_ctx* ctx, int n_warmup, int n_measure, int refresh_first);

@@ -6,11 +6,12 @@
 // fixed dtau, with the single-flip ratio, Metropolis acceptance and Sherman-Morrison update):
 //     R_sigma = 1 + (1 - G_sigma[l][l]) (e^{-2 lambda sigma s_l} - 1),  accept iff u < R_up R_dn,
 //     G_sigma += (a_sigma / R_sigma) (G_sigma[:, l] - e_l) G_sigma[l, :].
-// The bath matrix g0[l][l'] = g~0(tau_l - tau_l') (antiperiodic) is never stored: the Dyson
-// refresh G = [1 + (1 - g0)(e^V - 1)]^{-1} g0 builds it on the fly from g~0(tau_m), factors
-// the matrix by Gaussian elimination with partial pivoting in shared memory and runs after
-// every refresh_every-th sweep of the chain.  Measured sweeps accumulate G(tau_m), n_sigma and
-// the double occupancy into the chain's current bin.
+// The Dyson refresh G = [1 + (1 - g0)(e^V - 1)]^{-1} g0 runs after every refresh_every-th sweep
+// of the chain, as G = M^{-1} with M = g0^{-1} e^V - (e^V - 1) (the same relation multiplied
+// out): M is built from the site's g0^{-1} (computed once per bath by g0inv_kernel below, from
+// the antiperiodic bath matrix g0[l][l'] = g~0(tau_l - tau_l')) and inverted in place by
+// Gauss-Jordan elimination with partial pivoting in shared memory.  Measured sweeps accumulate
+// G(tau_m), n_sigma and the double occupancy into the chain's current bin.
 //
 // GB300 has ~1 TFLOP/s of FP64 (DFMA and DMMA alike, 72x below FFMA), so this kernel is bound
 // by the FP64 pipe; it keeps the pipe busy with 12 chains per SM and issues no FP64 work that

@@ -1,7 +1,7 @@
 // qmc_common.cuh -- device helpers shared by the FP64 and FP32-pair Hirsch-Fye sweep kernels:
 // team synchronisation, the per-chain shared-memory layout, integer-pipe FP32/FP64 views, the
-// Newton reciprocal and the FP64 Dyson refresh (bath matrix built on the fly, Gaussian
-// elimination with partial pivoting in shared memory).
+// Newton reciprocal and the FP64 Dyson refresh (G = M^{-1}, M = g0^{-1} e^V - (e^V - 1), by
+// in-place Gauss-Jordan elimination with partial pivoting in shared memory).
 #pragma once
 
 #include "hf_internal.cuh"
