@@ -288,7 +288,7 @@ DF_OPS_PER_FMA = 12          # FP32-pipe ops of one double-float multiply-add (l
 # DRAM bytes (read + write) of one full-size launch (2500 sweeps of all 1760 chains), from one
 # ncu capture of the kernel built from sources with this sha256 prefix (profiles/
 # qmc_df64_kernel_square20.md); a kernel whose sources changed since reports null.
-MEASURED_TRAFFIC = {"qmc_df64_kernel": (2.362e6 + 1.325e6, "ff89ee0ee424a4be")}
+MEASURED_TRAFFIC = {"qmc_df64_kernel": (2.362e6 + 1.325e6, "27a5cb76a243bebd")}
 KERNEL_SOURCES = {"qmc_df64_kernel": ("k_qmc_df64.cu", "qmc_common.cuh", "hf_internal.cuh"),
                   "qmc_f64_kernel": ("k_qmc_f64.cu", "qmc_common.cuh", "hf_internal.cuh")}
 
