@@ -477,7 +477,7 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "global_batch": nc * world, "seq_len": L,
+            "config": {"workload": WORKLOAD, "chains": nc * world, "time_slices": L,
                        "parallelism": "replicas%d" % world, "sweep_form": form,
                        "team_warps": tw if tw else "default", "delay_k": dk,
                        "refresh_stagger": args.refresh_stagger,
