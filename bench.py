@@ -591,11 +591,13 @@ def run_scan20(args):
         hf.hf_batch_rdmft_step(batch)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     ms = []
+    clocks = ClockSampler(local)
     for _ in range(args.steps):
         with torch.cuda.stream(stream):
             flush.zero_()
         torch.cuda.synchronize(dev)
         ms.append(hf.hf_batch_rdmft_step(batch))
+    clk = clocks.stop()
     proposals = sum(c.n_chains * 2500 * c.L for c in ctxs)
     ms_per = statistics.mean(ms)
     line = {"metric": METRIC, "value": proposals / (ms_per / 1e3), "unit": "proposals/s",
@@ -606,7 +608,7 @@ def run_scan20(args):
                                    "4 x 1760 chains in one fused graph-captured launch, "
                                    "500+2000 sweeps; one step = one batched RDMFT iteration",
                        "l2": "flushed (256 MB write) between timed steps"},
-            "autotune": {str(L): tune[L] for L in Ls}}
+            "clocks": clk, "autotune": {str(L): tune[L] for L in Ls}}
     print(json.dumps(line))
     hf.hf_batch_free(batch)
     for c in ctxs:
@@ -658,6 +660,7 @@ def run_disc40(args):
     alone = hf.hf_srv_wait(srv.handle, t, 600)["latency_s"]
     # capacity: every (run, site) solve at once (cold keys)
     keys = [(r, s) for s in range(nsite) for r in range(len(runs))]
+    clocks = ClockSampler(local)
     t0 = time.perf_counter()
     tickets = [hf.hf_srv_submit(srv.handle, req(r, s)) for r, s in keys]
     lat_cap = [hf.hf_srv_wait(srv.handle, tk, 600)["latency_s"] for tk in tickets]
@@ -686,6 +689,7 @@ def run_disc40(args):
                       "achieved_solves_per_s": n_req / wall, "p50_s": float(np.percentile(lat, 50)),
                       "p99_s": float(np.percentile(lat, 99)),
                       "warm_fraction": float(np.mean([x["warm"] for x in res]))})
+    clk = clocks.stop()
     st = hf.hf_srv_stats(srv.handle)
     srv.close()
     line = {"metric": "p50/p99 solve latency and solves/s (served)", "value": capacity,
@@ -700,7 +704,7 @@ def run_disc40(args):
             "capacity_solves_per_s": capacity,
             "capacity_latency_p50_s": float(np.percentile(lat_cap, 50)),
             "capacity_latency_p99_s": float(np.percentile(lat_cap, 99)),
-            "poisson": loads, "peak_inflight": st["peak_inflight"],
+            "poisson": loads, "clocks": clk, "peak_inflight": st["peak_inflight"],
             "peak_device_bytes": st["peak_bytes"]}
     print(json.dumps(line))
     return 0
