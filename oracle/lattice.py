@@ -136,3 +136,26 @@ def lattice_step(H0, mu, beta, sigma, n_index=None):
         M = (1j * w[q] + mu) * eye - H0 - np.diag(sigma[q])
         out[q] = np.diag(np.linalg.inv(M))
     return out
+
+
+def lattice_entries(H0, mu, beta, sigma_row, n, sites):
+    """eq. 2 at one frequency for large lattices: G_ii(i w_n) for the listed sites i only, each as
+    entry i of the column x = M^{-1} e_i of M = (i w_n + mu) 1 - H0 - diag(Sigma(i w_n)), from one
+    sparse LU factorisation of M (a library solve; M has at most five nonzeros per row).
+
+    sigma_row: [N] complex, the self-energy of every site at w_n.  Returns [len(sites)] complex.
+    """
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+
+    N = H0.shape[0]
+    w = (2.0 * n + 1.0) * np.pi / beta
+    M = sp.csc_matrix(((1j * w + mu) * sp.identity(N, dtype=np.complex128)
+                       - sp.csc_matrix(H0) - sp.diags(np.asarray(sigma_row))).astype(np.complex128))
+    lu = spla.splu(M)
+    out = np.zeros(len(sites), dtype=np.complex128)
+    for k, i in enumerate(sites):
+        e = np.zeros(N, dtype=np.complex128)
+        e[i] = 1.0
+        out[k] = lu.solve(e)[i]
+    return out

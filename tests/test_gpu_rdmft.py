@@ -8,7 +8,7 @@ relative (it divides by the measured Green function).
 import numpy as np
 import pytest
 
-from oracle.lattice import Lattice, lattice_step
+from oracle.lattice import Lattice, lattice_entries, lattice_step
 from oracle.rdmft import RDMFT
 from paper_1006_2716_gb300 import workloads as wl
 
@@ -139,4 +139,28 @@ def test_compute_baths_from_a_set_self_energy(hf, geom, Lx):
     want = ref.bath_tau(gw_t)[:, :, :L]
     assert np.abs(hf.hf_get_gloc(ctx.handle, ns, nw) - Gloc).max() < 1e-12 * np.abs(Gloc).max()
     assert np.abs(hf.hf_get_g0(ctx.handle, ns, L) - want).max() < 1e-12
+    ctx.close()
+
+
+def test_lattice_step_disc40_full_size_sampled(hf):
+    """The largest lattice in use (site-centred disc of radius 40: N = 5025, 663 inequivalent
+    sites) at the serving workload's parameters: the GPU band solver against one oracle column of
+    M^{-1} per sampled (frequency, spin, site), from the seeded self-energy."""
+    cfg = dict(wl.CONFIGS["square6"], Lx=40, Ly=40, geometry=1, U=8.0, V0=0.010, mu=4.0,
+               beta=8.0, dtau=0.25, n_matsubara=500, chains_per_site=1, n_warmup=1, n_measure=1,
+               bin_size=1, max_bins=1)
+    ctx = hf.Context(hf.make_params(cfg))
+    assert ctx.n_sites == 663
+    hf.hf_compute_baths(ctx.handle)
+    gloc = hf.hf_get_gloc(ctx.handle, ctx.n_sites, ctx.nw)
+    ref = _oracle_for(cfg)
+    assert ref.lat.N == 5025
+    full = ref.expand_sigma()
+    orbits = [0, 1, 331, 662]
+    sites = [int(ref.reps[o]) for o in orbits]
+    for n in (0, 1, 123, 499):
+        for sp in range(2):
+            want = lattice_entries(ref.lat.H0, cfg["mu"], cfg["beta"], full[sp][n], n, sites)
+            got = gloc[orbits, sp, n]
+            assert np.abs(got - want).max() < 1e-12 * np.abs(want).max(), (n, sp)
     ctx.close()

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 from oracle import fourier as F
-from oracle.lattice import Lattice, lattice_step, matsubara
+from oracle.lattice import Lattice, lattice_entries, lattice_step, matsubara
 
 
 @pytest.mark.parametrize("Lx,geom,expect", [(6, 0, 6), (20, 0, 55), (30, 0, 120), (8, 1, None)])
@@ -172,3 +172,26 @@ def test_density_from_lattice_step_and_tail():
         c4 = np.abs(np.linalg.matrix_power(lat.H0 - mu * np.eye(lat.N), 3)[i, i]) + 10
         assert abs(g[L] - nref[i]) < _trunc_bound(beta, nw, c4)
         assert abs(g[0] - (1 - nref[i])) < _trunc_bound(beta, nw, c4)
+
+
+@pytest.mark.parametrize("Lx,geom", [(6, 0), (6, 1)])
+def test_lattice_entries_match_the_inverse_and_eigh(Lx, geom):
+    """One column of M^{-1} per sampled site (sparse LU) equals the diagonal of the dense inverse
+    for an arbitrary causal self-energy, and the eigenvector sum for a static one."""
+    lat = Lattice(Lx, geometry=geom, V0=0.08)
+    beta, mu, N = 5.0, 1.3, lat.N
+    rng = np.random.default_rng(11 + geom)
+    sites = sorted(rng.choice(N, 5, replace=False))
+    for n in (0, 3, 40):
+        sig = 0.4 + rng.uniform(-0.5, 0.5, N) - 1j * rng.uniform(0.05, 0.6, N)
+        dense = lattice_step(lat.H0, mu, beta, sig[None, :], n_index=[n])[0]
+        got = lattice_entries(lat.H0, mu, beta, sig, n, sites)
+        assert np.abs(got - dense[sites]).max() < 1e-12 * np.abs(dense).max()
+    # static self-energy s: G_ii = sum_k |psi_k(i)|^2 / (i w_n + mu - s - e_k)
+    s0 = 0.7
+    e, psi = np.linalg.eigh(lat.H0)
+    for n in (0, 9):
+        w = (2 * n + 1) * np.pi / beta
+        want = (np.abs(psi[sites]) ** 2 / (1j * w + mu - s0 - e)[None, :]).sum(axis=1)
+        got = lattice_entries(lat.H0, mu, beta, np.full(N, s0, dtype=complex), n, sites)
+        assert np.abs(got - want).max() < 1e-12
