@@ -238,3 +238,29 @@ def test_resume_from_checkpoint_is_bitwise(hf):
         assert np.array_equal(hf.hf_get_green(a.handle, c, L), hf.hf_get_green(c2.handle, c, L))
     for ctx in (a, b, c2):
         ctx.close()
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+def test_zero_sweeps_is_a_pure_refresh(hf, precision):
+    """hf_sweep with no sweeps and refresh_first = 1 leaves fields and counters alone and makes
+    G the Dyson solution of the current fields (the empty launch)."""
+    L, beta = 24, 6.0
+    ctx, cfg = _ctx(hf, chains_per_site=2, beta=beta, dtau=0.25, U=5.0, precision=precision,
+                    seed=99)
+    baths = wl.random_baths(17, ctx.n_sites, beta, L)
+    for i in range(ctx.n_sites):
+        for sp in range(2):
+            hf.hf_set_g0(ctx.handle, i, sp, baths[i, sp])
+    f0, c0 = hf.hf_get_fields(ctx.handle, ctx.n_chains, L)
+    hf.hf_sweep(ctx.handle, 0, 0, 1)
+    f1, c1 = hf.hf_get_fields(ctx.handle, ctx.n_chains, L)
+    assert np.array_equal(f0, f1) and np.array_equal(c0, c1) and np.all(c1 == 0)
+    assert np.all(hf.hf_get_accepts(ctx.handle, ctx.n_chains) == 0)
+    _, lam = o.constants(beta, 5.0, L)
+    for c in range(ctx.n_chains):
+        site = c // 2
+        G = hf.hf_get_green(ctx.handle, c, L)
+        for sp, sg in ((0, 1), (1, -1)):
+            want, _ = o.dyson(o.build_g0(baths[site, sp]), f1[c], sg, lam)
+            assert _rel(G[sp], want) < 1e-12
+    ctx.close()
