@@ -320,12 +320,17 @@ def qmc_roofline(form, L, nchain, sweeps, accepts, n_measure, n_refresh, qmc_s, 
     f_ref = 2.0 * (8.0 / 3.0) * L ** 3 * nchain * n_refresh
     total = f_ratio + f_upd + f_meas + f_ref
     achieved = total / qmc_s / 1e12
+    extra = {}
     if form == 0:
         peak, src = FP64_PEAK_TFLOPS, "FP64 nominal: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz"
     else:
         t64 = f_ref / (FP64_PEAK_TFLOPS * 1e12)
         t32 = (f_ratio + f_upd + f_meas) / 2.0 * DF_OPS_PER_FMA / (FP32_PEAK_TFLOPS * 1e12 / 2.0)
         peak = total / max(t64, t32) / 1e12
+        # measured on this GPU: FP64 work does not overlap the pair arithmetic, so the roof of
+        # the two pipes one after the other is reported beside the overlapped one
+        extra = {"peak_serial": total / (t64 + t32) / 1e12,
+                 "frac_serial": achieved / (total / (t64 + t32) / 1e12)}
         src = ("mixed-pipe roof: refresh on FP64 (2 DFMA/clk/SM), pair arithmetic on FP32 "
                "(128 FFMA/clk/SM, %d ops per FP64-equivalent FMA), both at 2.07 GHz, overlapped"
                % DF_OPS_PER_FMA)
@@ -334,7 +339,7 @@ def qmc_roofline(form, L, nchain, sweeps, accepts, n_measure, n_refresh, qmc_s, 
     executed = (total - 0.25 * f_ref) / qmc_s / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": measured_traffic(kernel), "kernel": kernel,
-            "executed_tflops": executed, "peak_source": src}
+            "executed_tflops": executed, "peak_source": src, **extra}
 
 
 def _time_iterations(hf, ctx, stream, flush, steps):
