@@ -186,6 +186,57 @@ def _pool_chains(chains):
     return len(chains)
 
 
+def _pool_chains_sq30(job):
+    """Oracle (FP64 throughout) chains of the 30x30 workload: L = 128, refresh every sweep."""
+    import numpy as np
+
+    import oracle as o
+
+    chains, sweeps = job
+    cfg, L = wl.CONFIGS["square30"], 128
+    baths = wl.random_baths(3, max(chains) + 1, cfg["beta"], L)
+    _, lam = o.constants(cfg["beta"], cfg["U"], L)
+    for c in chains:
+        g0u, g0d = o.build_g0(baths[c, 0]), o.build_g0(baths[c, 1])
+        s = o.init_fields(cfg["seed"], c, 0, L)
+        Gu, _ = o.dyson(g0u, s, 1, lam)
+        Gd, _ = o.dyson(g0d, s, -1, lam)
+        bins = np.zeros((1, 2 * L + 3))
+        o.run_chain(lam, g0u, g0d, cfg["seed"], c, 0, 0, 0, sweeps, 1, sweeps, s, Gu, Gd, bins)
+    return len(chains)
+
+
+def cpu_oracle_square30(chains_per_core=2, sweeps=10):
+    """Proposals/s of the oracle on the 30x30 workload (L = 128, FP64 sweeps, refresh every
+    sweep) on every host core, from a bounded sample; returns (value, cores, sample)."""
+    cores = host_cores()
+    ctx = mp.get_context("spawn")
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        pool = ctx.Pool(cores)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    try:
+        pool.map(_pool_chains_sq30, [([w], 1) for w in range(cores)], chunksize=1)   # warm
+        n = cores * chains_per_core
+        t0 = time.perf_counter()
+        pool.map(_pool_chains_sq30, [(list(range(w, n, cores)), sweeps) for w in range(cores)],
+                 chunksize=1)
+        wall = time.perf_counter() - t0
+    finally:
+        pool.close()
+        pool.join()
+    sample = ("%d chains x %d sweeps (L=128, FP64, Dyson refresh every sweep) over %d worker "
+              "processes" % (n, sweeps, cores))
+    return n * sweeps * 128 / wall, cores, sample
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -513,6 +564,10 @@ def run_square30(args):
     rank, world, local = dist_env()
     if rank != 0:
         return 0
+    cpu = None
+    if not args.no_cpu:   # spawned before any CUDA work
+        v, cores, sample = cpu_oracle_square30()
+        cpu = {"value": v, "unit": "proposals/s", "cores": cores, "kind": "oracle", "sample": sample}
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(dev)
@@ -567,7 +622,7 @@ def run_square30(args):
             # per iteration: an FP32 sweep launch and an FP64 refresh launch per sweep, the first
             # refresh, lattice step, Weiss/tau, reduction, self-energy update
             "gpu_launches": (2 * sweeps + 5) * args.steps,
-            "clocks": clk}
+            "cpu_baseline": cpu, "clocks": clk}
     if args.sweeps:
         line["profile_case"] = "sweeps overridden to %d: not a benchmark value" % args.sweeps
     print(json.dumps(line))
