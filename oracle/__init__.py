@@ -16,6 +16,9 @@ Layout
 * ``fourier.py``   -- Matsubara grid, tau <-> i omega_n transforms with the
   high-frequency tail, natural cubic spline.
 * ``rdmft.py``     -- one self-consistency iteration in the paper's order.
+* ``ed.py``        -- exact diagonalisation of a small Anderson impurity with a
+  pole bath: the continuous-time (dtau -> 0) answer the Hirsch-Fye
+  discretisation approaches.
 """
 from .core import (  # noqa: F401
     lib, build, philox4x32_10, uniform, init_fields, constants, build_g0, dyson,
