@@ -630,6 +630,84 @@ def run_square30(args):
     return 0
 
 
+def run_dtau_scan(args):
+    """Trotter scan of one impurity (beta = 2, U = 2, 4-pole bath): dtau = beta / L for L = 16,
+    24, 32, 48, 64, 2048 chains each, 200 + 2000 sweeps, all five in one fused launch; one step
+    = one launch.  Reports proposals/s and the double occupancy extrapolated to dtau -> 0 (fit
+    a + b dtau^2 with the measured errors); tests/test_gpu_trotter.py compares that value with
+    the exact diagonalisation of the same impurity."""
+    import numpy as np
+    import torch
+
+    from paper_1006_2716_gb300 import hf
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    beta, U, seed = 2.0, 2.0, 3
+    e, w = wl.bath_poles(seed)
+    Ls = [16, 24, 32, 48, 64]
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    ctxs = []
+    for k, L in enumerate(Ls):
+        cfg = dict(wl.CONFIGS["square6"], Lx=1, Ly=1, beta=beta, dtau=beta / L, U=U, mu=0.0,
+                   V0=0.0, precision=2, chains_per_site=2048, n_matsubara=4, refresh_every=10,
+                   bin_size=100, max_bins=20, seed=900 + k)
+        ctx = hf.Context(hf.make_params(cfg), device=dev, stream=stream)
+        bath = wl.pole_bath_tau(beta, L, e, w)
+        hf.hf_set_g0(ctx.handle, 0, 0, bath)
+        hf.hf_set_g0(ctx.handle, 0, 1, bath)
+        ctxs.append(ctx)
+    b = hf.hf_batch_create([c.handle for c in ctxs], 0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def one_step():
+        for c in ctxs:
+            hf.hf_clear_measurements(c.handle)
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        torch.cuda.synchronize(dev)
+        hf.hf_batch_sweep(b, 200, 2000, 1)
+        return hf.hf_batch_elapsed(b)
+
+    for _ in range(args.warmup):
+        one_step()
+    clocks = ClockSampler(local)
+    ms = [one_step() for _ in range(args.steps)]
+    clk = clocks.stop()
+    d, sd = [], []
+    for c, L in zip(ctxs, Ls):
+        _, _, dd, _, errs = hf.hf_measure(c.handle, 0, L)
+        d.append(dd)
+        sd.append(errs[2 * L + 2])
+    hf.hf_batch_free(b)
+    for c in ctxs:
+        c.close()
+    d, sd = np.array(d), np.array(sd)
+    dt = beta / np.array(Ls, dtype=float)
+    A = np.stack([np.ones_like(dt), dt ** 2], axis=1) / sd[:, None]
+    coef, *_ = np.linalg.lstsq(A, d / sd, rcond=None)
+    sa = float(np.sqrt(np.linalg.inv(A.T @ A)[0, 0]))
+    proposals = sum(2048 * 2200 * L for L in Ls)
+    ms_per = statistics.mean(ms)
+    line = {"metric": METRIC, "value": proposals / (ms_per / 1e3), "unit": "proposals/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32x2+f64", "data": "synthetic",
+            "config": {"workload": "dtau_scan: one impurity, beta=2, U=2, 4-pole bath (seed 3), "
+                                   "L 16/24/32/48/64 x 2048 chains in one fused launch, 200+2000 "
+                                   "sweeps; one step = one launch",
+                       "l2": "flushed (256 MB write) between timed steps"},
+            "double_occupancy": {"per_L": dict(zip(map(str, Ls), d.tolist())),
+                                 "err_per_L": dict(zip(map(str, Ls), sd.tolist())),
+                                 "extrapolated": float(coef[0]), "extrapolated_err": sa},
+            "clocks": clk}
+    print(json.dumps(line))
+    return 0
+
+
 def run_scan20(args):
     """Batched uneven-L temperature scan: the 20x20 trap at beta = 5, 8, 10, 16 (L = 20, 32, 40,
     64), 1760 chains each, one fused graph-captured launch per iteration, sweep form and team
@@ -791,7 +869,7 @@ def main():
                     help="sweep arithmetic: 0 FP64, 2 FP32 pairs (both with FP64 refresh); "
                          "-1 (default): the autotuner picks form and team width")
     ap.add_argument("--workload", default="square20",
-                    choices=["square20", "scan20", "square30", "disc40"])
+                    choices=["square20", "scan20", "square30", "disc40", "dtau_scan"])
     ap.add_argument("--refresh-stagger", type=int, default=0, choices=[0, 1],
                     help="1: per-chain refresh phases; 0 (default): every chain refreshes on the "
                          "same sweeps")
@@ -810,6 +888,8 @@ def main():
         return run_disc40(args)
     if args.workload == "square30":
         return run_square30(args)
+    if args.workload == "dtau_scan":
+        return run_dtau_scan(args)
     return run_ours(args)
 
 
