@@ -51,8 +51,15 @@ typedef struct hf_ctx hf_ctx;
 /* Parameters of one trapped-lattice RDMFT problem (eq. 1 plus the QMC settings). */
 typedef struct hf_params {
     int Lx, Ly;          /* geometry 0: Lx x Ly square; geometry 1: disc of radius Lx       */
-    int geometry;        /* 0 square (centre ((Lx-1)/2, (Ly-1)/2)), 1 site-centred disc     */
-    int periodic;        /* 1: periodic boundaries (square only); 0: open                   */
+    int Lz;              /* geometries 2, 3: layers (ignored in two dimensions)              */
+    int geometry;        /* 0 square (centre ((Lx-1)/2, (Ly-1)/2)), 1 site-centred disc,     */
+                         /* 2 Lx x Ly x Lz box with a spherical trap about its centre,       */
+                         /* 3 slab of Lz layers with a cylindrical trap V0 (dx^2 + dy^2),    */
+                         /* periodic across the layers ("Efficient simulations for three     */
+                         /* dimensions").  Sites (x, y, z) are numbered (z Ly + y) Lx + x.   */
+    int periodic;        /* 1: periodic boundaries (square; box: all axes; slab: x and y),   */
+                         /* measured trap from the box centre; 0: open.  A periodic axis of  */
+                         /* the box or slab needs an even length >= 4                       */
     double t, U, V0, mu; /* eq. 1: hopping, interaction, trap strength, chemical potential  */
     double beta, dtau;   /* inverse temperature, Trotter step; L = round(beta / dtau)       */
     int n_matsubara;     /* Matsubara frequencies kept explicitly (paper: 500)              */
@@ -81,6 +88,14 @@ typedef struct hf_params {
 
 /* Bytes of device workspace hf_init needs for *p (*bytes set on HF_OK). */
 hf_status hf_workspace_size(const hf_params* p, size_t* bytes);
+
+/* Host only, no device work: the lattice *p describes (after the same validation as hf_init).
+ * Writes the number of sites, of inequivalent sites and the band half-width of H0 that the
+ * lattice step factors; rep [n_sites], rep_of [N] and flip [N] (as in hf_get_orbits) when not
+ * NULL -- call once with them NULL to learn the sizes.  HF_EINVAL for invalid parameters or a
+ * band wider than the lattice step supports. */
+hf_status hf_lattice_info(const hf_params* p, int* N, int* n_sites, int* band, int* rep, int* rep_of,
+                          int* flip);
 
 /* Validate *p, build the lattice (eq. 1) and its C4v orbits, lay the state out in the
  * caller's device workspace d_ws (ws_bytes >= hf_workspace_size), draw the initial Ising

@@ -1,4 +1,4 @@
-"""Lattice side of the oracle: geometry, trap, C4v orbits and the RDMFT lattice step.
+"""Lattice side of the oracle: geometry, trap, point-group orbits and the RDMFT lattice step.
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
@@ -19,52 +19,67 @@ class Lattice:
 
     geometry 0: Lx x Ly square, site (x, y) has index y * Lx + x, centre ((Lx-1)/2, (Ly-1)/2).
     geometry 1: site-centred disc x^2 + y^2 <= R^2 (R = Lx), sites ordered by (y, x).
+    geometry 2: Lx x Ly x Lz box, site (x, y, z) has index (z * Ly + y) * Lx + x, spherical trap
+                V0 (dx^2 + dy^2 + dz^2) about the box centre; periodic wraps all three axes.
+    geometry 3: slab of Lz layers, same numbering, cylindrical trap V0 (dx^2 + dy^2); always
+                periodic across the layers, periodic also wraps x and y.
+    The two three-dimensional cases follow "Efficient simulations for three dimensions": periodic
+    boundaries for the trapped box, and a slab periodic perpendicular to its layers with the
+    perpendicular part of the trap left out.
     """
 
-    def __init__(self, Lx, Ly=None, geometry=0, periodic=False, t=1.0, V0=0.0):
+    def __init__(self, Lx, Ly=None, geometry=0, periodic=False, t=1.0, V0=0.0, Lz=1):
         self.geometry = geometry
         self.t = float(t)
         self.V0 = float(V0)
-        if geometry == 0:
-            Ly = Lx if Ly is None else Ly
-            xs, ys = [], []
-            for y in range(Ly):
-                for x in range(Lx):
-                    xs.append(x)
-                    ys.append(y)
-            self.x = np.array(xs)
-            self.y = np.array(ys)
-            self.cx, self.cy = (Lx - 1) / 2.0, (Ly - 1) / 2.0
-            self.dx = self.x - self.cx
-            self.dy = self.y - self.cy
+        Ly = Lx if Ly is None else Ly
+        three_d = geometry in (2, 3)
+        Lz = Lz if three_d else 1
+        self.Lx, self.Ly, self.Lz = Lx, Ly, Lz
+        xs, ys, zs = [], [], []
+        if geometry in (0, 2, 3):
+            for z in range(Lz):
+                for y in range(Ly):
+                    for x in range(Lx):
+                        xs.append(x)
+                        ys.append(y)
+                        zs.append(z)
+            self.cx, self.cy, self.cz = (Lx - 1) / 2.0, (Ly - 1) / 2.0, (Lz - 1) / 2.0
         elif geometry == 1:
             R = Lx
-            xs, ys = [], []
             for y in range(-R, R + 1):
                 for x in range(-R, R + 1):
                     if x * x + y * y <= R * R:
                         xs.append(x)
                         ys.append(y)
-            self.x = np.array(xs)
-            self.y = np.array(ys)
-            self.cx, self.cy = 0.0, 0.0
-            self.dx = self.x.astype(float)
-            self.dy = self.y.astype(float)
+                        zs.append(0)
+            self.cx, self.cy, self.cz = 0.0, 0.0, 0.0
         else:
             raise ValueError("geometry")
+        self.x, self.y, self.zc = np.array(xs), np.array(ys), np.array(zs)
+        self.dx = self.x - self.cx
+        self.dy = self.y - self.cy
+        self.dz = (self.zc - self.cz) if three_d else np.zeros(len(xs))
         self.N = len(self.x)
-        self.r2 = self.dx ** 2 + self.dy ** 2
+        self.r2 = self.dx ** 2 + self.dy ** 2 + (self.dz ** 2 if geometry == 2 else 0.0)
         self.V = self.V0 * self.r2
-        self.parity = np.where((self.x + self.y) % 2 == 0, 1, -1)
-        index = {(int(a), int(b)): i for i, (a, b) in enumerate(zip(self.x, self.y))}
+        self.parity = np.where((self.x + self.y + self.zc) % 2 == 0, 1, -1)
+        index = {(int(a), int(b), int(c)): i for i, (a, b, c) in enumerate(zip(self.x, self.y, self.zc))}
+        wrap_xy = periodic and geometry in (0, 2, 3)
+        wrap_z = geometry == 3 or (geometry == 2 and periodic)
+        steps = [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0)]
+        if three_d:
+            steps += [(0, 0, 1), (0, 0, -1)]
         A = np.zeros((self.N, self.N))
         for i in range(self.N):
-            for (ddx, ddy) in ((1, 0), (-1, 0), (0, 1), (0, -1)):
-                xn, yn = int(self.x[i]) + ddx, int(self.y[i]) + ddy
-                if periodic and geometry == 0:
+            for (ddx, ddy, ddz) in steps:
+                xn, yn, zn = int(self.x[i]) + ddx, int(self.y[i]) + ddy, int(self.zc[i]) + ddz
+                if wrap_xy:
                     xn %= Lx
                     yn %= Ly
-                j = index.get((xn, yn))
+                if wrap_z:
+                    zn %= Lz
+                j = index.get((xn, yn, zn))
                 if j is not None and j != i:
                     A[i, j] = 1.0
         self.adjacency = A
@@ -72,48 +87,76 @@ class Lattice:
         self.H0 = -self.t * A + np.diag(self.V)
         self._index = index
 
-    # --- C4v orbits -------------------------------------------------------
+    # --- point-group orbits ------------------------------------------------
+    def _operations(self):
+        """Candidate maps of the integer coordinates: signed axis permutations about the trap
+        centre (the 8 planar ones in two dimensions, all 48 for the box), and for the slab the 8
+        planar ones combined with z -> +-z + c (mod Lz).  Each returns (x, y, z) or None when
+        the image is not a lattice point."""
+        planar = [(0, 1, 2), (1, 0, 2)]
+        if self.geometry == 2:
+            perms = [(0, 1, 2), (1, 0, 2), (0, 2, 1), (2, 1, 0), (1, 2, 0), (2, 0, 1)]
+        else:
+            perms = planar
+        zsigns = (1, -1) if self.geometry in (2, 3) else (1,)
+        shifts = range(self.Lz) if self.geometry == 3 else (0,)
+        centre = (self.cx, self.cy, self.cz)
+        ops = []
+        for perm in perms:
+            for sx in (1, -1):
+                for sy in (1, -1):
+                    for sz in zsigns:
+                        for c in shifts:
+                            ops.append((perm, (sx, sy, sz), c))
+
+        def apply(op, i):
+            perm, sg, c = op
+            d = (self.dx[i], self.dy[i], self.dz[i])
+            out = []
+            for a in range(2):
+                v = sg[a] * d[perm[a]] + centre[a]
+                if abs(v - round(v)) > 1e-9:
+                    return None
+                out.append(int(round(v)))
+            if self.geometry == 3:
+                out.append((sg[2] * int(self.zc[i]) + c) % self.Lz)
+            else:
+                v = sg[2] * d[perm[2]] + centre[2]
+                if abs(v - round(v)) > 1e-9:
+                    return None
+                out.append(int(round(v)))
+            return tuple(out)
+
+        return ops, apply
+
     def orbits(self):
         """Inequivalent sites under the point group of the trap and the lattice.
 
-        The 8 operations (dx, dy) -> (+-dx, +-dy), (+-dy, +-dx) about the trap centre are kept if
-        they map the site set onto itself.  Returns (reps, rep_of, flip): reps = sorted site
-        indices of the orbit representatives; rep_of[i] = position in reps of the orbit of site i;
-        flip[i] = 1 if site i and its representative lie on different sublattices.  An
-        antiferromagnetic state then satisfies G_{i,sigma} = G_{rep, sigma xor flip}.
+        The operations of _operations() are kept if they map the site set onto itself.  Returns
+        (reps, rep_of, flip): reps = sorted site indices of the orbit representatives; rep_of[i]
+        = position in reps of the orbit of site i; flip[i] = 1 if site i and its representative
+        lie on different sublattices.  An antiferromagnetic state then satisfies
+        G_{i,sigma} = G_{rep, sigma xor flip}.
         """
-        ops = []
-        for swap in (False, True):
-            for sx in (1, -1):
-                for sy in (1, -1):
-                    ops.append((swap, sx, sy))
+        ops, apply = self._operations()
         images = []
-        for (swap, sx, sy) in ops:
-            a = np.where(swap, self.dy, self.dx) * sx
-            b = np.where(swap, self.dx, self.dy) * sy
+        for op in ops:
             img = []
-            ok = True
             for i in range(self.N):
-                key = self._coord_to_index(a[i], b[i])
-                if key is None:
-                    ok = False
+                c = apply(op, i)
+                j = None if c is None else self._index.get(c)
+                if j is None:
                     break
-                img.append(key)
-            if ok:
+                img.append(j)
+            if len(img) == self.N:
                 images.append(np.array(img))
         rep_site = np.array([min(int(im[i]) for im in images) for i in range(self.N)])
         reps = np.array(sorted(set(rep_site.tolist())))
         pos = {int(r): k for k, r in enumerate(reps)}
         rep_of = np.array([pos[int(r)] for r in rep_site])
         flip = (self.parity != self.parity[rep_site]).astype(np.int64)
+        self._images = images
         return reps, rep_of, flip
-
-    def _coord_to_index(self, ddx, ddy):
-        x, y = ddx + self.cx, ddy + self.cy
-        xi, yi = int(round(x)), int(round(y))
-        if abs(x - xi) > 1e-9 or abs(y - yi) > 1e-9:
-            return None
-        return self._index.get((xi, yi))
 
 
 def matsubara(beta, nw):

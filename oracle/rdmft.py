@@ -22,8 +22,9 @@ from .lattice import Lattice, lattice_step
 class RDMFT:
     def __init__(self, Lx, Ly=None, geometry=0, periodic=False, t=1.0, U=4.0, V0=0.1, mu=2.0,
                  beta=4.0, L=16, nw=500, chains=1, seed=1, h_seed=0.1, mix=0.5,
-                 n_warmup=500, n_measure=2000, refresh_every=10, bin_size=100, refresh_stagger=0):
-        self.lat = Lattice(Lx, Ly, geometry=geometry, periodic=periodic, t=t, V0=V0)
+                 n_warmup=500, n_measure=2000, refresh_every=10, bin_size=100, refresh_stagger=0,
+                 Lz=1):
+        self.lat = Lattice(Lx, Ly, geometry=geometry, periodic=periodic, t=t, V0=V0, Lz=Lz)
         self.reps, self.rep_of, self.flip = self.lat.orbits()
         self.U, self.mu, self.beta, self.L, self.nw = U, mu, beta, L, nw
         self.t = t

@@ -14,6 +14,7 @@
 #include <vector>
 #include <algorithm>
 #include <chrono>
+#include <tuple>
 
 #include "hf_internal.cuh"
 #include "k_lattice.cuh"
@@ -24,60 +25,99 @@ thread_local std::string g_init_error;
 
 // ---------------------------------------------------------------------------------------
 // Lattice of eq. 1: sites, trap potential V_i = V0 r_i^2, nearest-neighbour hopping t.
-// Square: site (x, y) -> y * Lx + x, centre ((Lx-1)/2, (Ly-1)/2).  Disc: sites with
-// x^2 + y^2 <= R^2 in row order (y, then x), centre at the origin.  Orbits: the operations
-// (dx, dy) -> (+-dx, +-dy), (+-dy, +-dx) that map the site set onto itself; the representative
-// of an orbit is its smallest site index, inequivalent sites are numbered by increasing
-// representative; a site whose sublattice parity differs from its representative's carries
-// the spin exchange of an antiferromagnetic state.
+//   geometry 0: Lx x Ly square, site (x, y) -> y Lx + x, centre ((Lx-1)/2, (Ly-1)/2).
+//   geometry 1: site-centred disc x^2 + y^2 <= R^2 (R = Lx) in row order (y, then x).
+//   geometry 2: Lx x Ly x Lz box, site (x, y, z) -> (z Ly + y) Lx + x, spherical trap
+//               V0 (dx^2 + dy^2 + dz^2) about the box centre; periodic = 1 wraps all three axes.
+//   geometry 3: slab of Lz layers, same numbering, cylindrical trap V0 (dx^2 + dy^2) (the
+//               component perpendicular to the slab dropped), always periodic across the layers;
+//               periodic = 1 also wraps x and y.  ("Efficient simulations for three dimensions".)
+// With periodic boundaries the trap is measured from the box centre, so a wrapped bond joins two
+// sites of equal potential.
+// Orbits: the point operations about the trap centre that map the site set onto itself --
+// (dx, dy) -> (+-dx, +-dy), (+-dy, +-dx) in two dimensions, the 48 signed axis permutations for
+// the box, and for the slab the 8 in-plane ones combined with z -> +-z + c (mod Lz), the layers
+// being equivalent.  The representative of an orbit is its smallest site index, inequivalent
+// sites are numbered by increasing representative; a site whose sublattice parity differs from
+// its representative's carries the spin exchange of an antiferromagnetic state.
+// Band order: the lattice step factors H0 as a band matrix, so sites are placed along the band
+// (order / pos) with every periodic axis folded (0, n-1, 1, n-2, ...): a wrapped bond then spans
+// at most two positions along its axis instead of n - 1.  The slab's layers come innermost.
 // ---------------------------------------------------------------------------------------
 struct HostLattice {
     int N = 0;
-    int b = 0;                      // band half-width of H0 in this numbering
-    std::vector<int> x, y;
-    std::vector<double> dx, dy, V;
-    std::vector<int> parity, z;
+    int b = 0;                      // band half-width of H0 in the band order
+    std::vector<int> x, y, zc;      // integer coordinates (zc = 0 in two dimensions)
+    std::vector<double> dx, dy, dz, V;
+    std::vector<int> parity, z;     // sublattice parity (+-1), number of neighbours
     std::vector<std::vector<int>> nbr;
     std::vector<int> rep, rep_of, flip, site_rep;
+    std::vector<int> order, pos;    // band position -> site, site -> band position
 };
 
+// Position of coordinate c (0 <= c < n) along a folded periodic axis: 0, n-1, 1, n-2, ...
+int fold(int c, int n) { return 2 * c < n ? 2 * c : 2 * (n - 1 - c) + 1; }
+
 bool build_lattice(const hf_params& p, HostLattice& lat, std::string& err) {
-    std::map<std::pair<int, int>, int> index;
-    double cx = 0.0, cy = 0.0;
-    if (p.geometry == 0) {
-        if (p.Lx < 1 || p.Ly < 1) { err = "Lx, Ly must be >= 1"; return false; }
-        for (int yy = 0; yy < p.Ly; ++yy)
-            for (int xx = 0; xx < p.Lx; ++xx) { lat.x.push_back(xx); lat.y.push_back(yy); }
+    std::map<std::tuple<int, int, int>, int> index;
+    const int g = p.geometry;
+    const bool three_d = (g == 2 || g == 3);
+    const int Lz = three_d ? p.Lz : 1;
+    double cx = 0.0, cy = 0.0, cz = 0.0;
+    if (g == 0 || three_d) {
+        if (p.Lx < 1 || p.Ly < 1 || Lz < 1) { err = "Lx, Ly (and Lz) must be >= 1"; return false; }
+        const bool wrap_xy = p.periodic != 0 && three_d;
+        const bool wrap_z = (g == 3) || (g == 2 && p.periodic != 0);
+        if ((wrap_xy && (p.Lx % 2 || p.Lx < 4 || p.Ly % 2 || p.Ly < 4)) ||
+            (wrap_z && (Lz % 2 || Lz < 4))) {
+            err = "a periodic axis of the box or slab needs an even length >= 4";
+            return false;
+        }
+        for (int zz = 0; zz < Lz; ++zz)
+            for (int yy = 0; yy < p.Ly; ++yy)
+                for (int xx = 0; xx < p.Lx; ++xx) {
+                    lat.x.push_back(xx); lat.y.push_back(yy); lat.zc.push_back(zz);
+                }
         cx = (p.Lx - 1) / 2.0;
         cy = (p.Ly - 1) / 2.0;
-    } else if (p.geometry == 1) {
+        cz = (Lz - 1) / 2.0;
+    } else if (g == 1) {
         const int R = p.Lx;
         if (R < 0) { err = "disc radius must be >= 0"; return false; }
         for (int yy = -R; yy <= R; ++yy)
             for (int xx = -R; xx <= R; ++xx)
-                if (xx * xx + yy * yy <= R * R) { lat.x.push_back(xx); lat.y.push_back(yy); }
+                if (xx * xx + yy * yy <= R * R) {
+                    lat.x.push_back(xx); lat.y.push_back(yy); lat.zc.push_back(0);
+                }
     } else {
-        err = "geometry must be 0 (square) or 1 (disc)";
+        err = "geometry must be 0 (square), 1 (disc), 2 (box) or 3 (slab)";
         return false;
     }
     lat.N = static_cast<int>(lat.x.size());
     const int N = lat.N;
-    for (int i = 0; i < N; ++i) index[{lat.x[i], lat.y[i]}] = i;
-    lat.dx.resize(N); lat.dy.resize(N); lat.V.resize(N); lat.parity.resize(N); lat.z.resize(N);
+    for (int i = 0; i < N; ++i) index[{lat.x[i], lat.y[i], lat.zc[i]}] = i;
+    lat.dx.resize(N); lat.dy.resize(N); lat.dz.resize(N); lat.V.resize(N);
+    lat.parity.resize(N); lat.z.resize(N);
     lat.nbr.assign(N, {});
+    const bool wx = p.periodic != 0 && (g == 0 || three_d);   // wrapped axes
+    const bool wz = (g == 3) || (g == 2 && p.periodic != 0);
+    const int n_off = three_d ? 6 : 4;
+    const int off[6][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
     for (int i = 0; i < N; ++i) {
         lat.dx[i] = lat.x[i] - cx;
         lat.dy[i] = lat.y[i] - cy;
-        lat.V[i] = p.V0 * (lat.dx[i] * lat.dx[i] + lat.dy[i] * lat.dy[i]);
-        lat.parity[i] = (((lat.x[i] + lat.y[i]) % 2) + 2) % 2 == 0 ? 1 : -1;
-        const int off[4][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1}};
-        for (auto& o : off) {
-            int xn = lat.x[i] + o[0], yn = lat.y[i] + o[1];
-            if (p.periodic && p.geometry == 0) {
+        lat.dz[i] = three_d ? lat.zc[i] - cz : 0.0;
+        const double r2z = (g == 2) ? lat.dz[i] * lat.dz[i] : 0.0;
+        lat.V[i] = p.V0 * (lat.dx[i] * lat.dx[i] + lat.dy[i] * lat.dy[i] + r2z);
+        lat.parity[i] = (((lat.x[i] + lat.y[i] + lat.zc[i]) % 2) + 2) % 2 == 0 ? 1 : -1;
+        for (int o = 0; o < n_off; ++o) {
+            int xn = lat.x[i] + off[o][0], yn = lat.y[i] + off[o][1], zn = lat.zc[i] + off[o][2];
+            if (wx) {
                 xn = ((xn % p.Lx) + p.Lx) % p.Lx;
                 yn = ((yn % p.Ly) + p.Ly) % p.Ly;
             }
-            auto it = index.find({xn, yn});
+            if (wz) zn = ((zn % Lz) + Lz) % Lz;
+            auto it = index.find({xn, yn, zn});
             if (it != index.end() && it->second != i) {
                 bool dup = false;
                 for (int j : lat.nbr[i]) dup |= (j == it->second);
@@ -85,27 +125,64 @@ bool build_lattice(const hf_params& p, HostLattice& lat, std::string& err) {
             }
         }
         lat.z[i] = static_cast<int>(lat.nbr[i].size());
-        for (int j : lat.nbr[i]) lat.b = std::max(lat.b, std::abs(j - i));
     }
-    // orbits
-    std::vector<std::vector<int>> images;
-    for (int swap = 0; swap < 2; ++swap)
+    // band order
+    lat.pos.resize(N);
+    lat.order.resize(N);
+    for (int i = 0; i < N; ++i) {
+        const int px = wx ? fold(lat.x[i], p.Lx) : lat.x[i];
+        const int py = wx ? fold(lat.y[i], p.Ly) : lat.y[i];
+        int k = i;                                               // disc: row order
+        if (g == 0) k = py * p.Lx + px;
+        if (g == 2) k = ((wz ? fold(lat.zc[i], Lz) : lat.zc[i]) * p.Ly + py) * p.Lx + px;
+        if (g == 3) k = (py * p.Lx + px) * Lz + fold(lat.zc[i], Lz);
+        lat.pos[i] = k;
+        lat.order[k] = i;
+    }
+    for (int i = 0; i < N; ++i)
+        for (int j : lat.nbr[i]) lat.b = std::max(lat.b, std::abs(lat.pos[j] - lat.pos[i]));
+    // orbits: operations d -> (sgn_a d[perm_a]) about the centre; for the slab the layer index
+    // maps as z -> (sgn_z z + shift) mod Lz instead
+    struct Op { int perm[3]; int sgn[3]; int shift; };
+    std::vector<Op> ops;
+    const int perms[6][3] = {{0, 1, 2}, {1, 0, 2}, {0, 2, 1}, {2, 1, 0}, {1, 2, 0}, {2, 0, 1}};
+    const int n_perm = (g == 2) ? 6 : 2;
+    const int n_shift = (g == 3) ? Lz : 1;
+    for (int pi = 0; pi < n_perm; ++pi)
         for (int sx = 1; sx >= -1; sx -= 2)
-            for (int sy = 1; sy >= -1; sy -= 2) {
-                std::vector<int> img(N);
-                bool ok = true;
-                for (int i = 0; i < N && ok; ++i) {
-                    const double a = (swap ? lat.dy[i] : lat.dx[i]) * sx;
-                    const double c = (swap ? lat.dx[i] : lat.dy[i]) * sy;
-                    const double xf = a + cx, yf = c + cy;
-                    const long xi = std::lround(xf), yi = std::lround(yf);
-                    if (std::fabs(xf - xi) > 1e-9 || std::fabs(yf - yi) > 1e-9) { ok = false; break; }
-                    auto it = index.find({static_cast<int>(xi), static_cast<int>(yi)});
-                    if (it == index.end()) { ok = false; break; }
-                    img[i] = it->second;
-                }
-                if (ok) images.push_back(img);
+            for (int sy = 1; sy >= -1; sy -= 2)
+                for (int sz = 1; sz >= (three_d ? -1 : 1); sz -= 2)
+                    for (int c = 0; c < n_shift; ++c) {
+                        Op op{};
+                        for (int a = 0; a < 3; ++a) op.perm[a] = perms[pi][a];
+                        op.sgn[0] = sx; op.sgn[1] = sy; op.sgn[2] = sz;
+                        op.shift = c;
+                        ops.push_back(op);
+                    }
+    std::vector<std::vector<int>> images;
+    for (const Op& op : ops) {
+        std::vector<int> img(N);
+        bool ok = true;
+        for (int i = 0; i < N && ok; ++i) {
+            const double d[3] = {lat.dx[i], lat.dy[i], lat.dz[i]};
+            const double xf = op.sgn[0] * d[op.perm[0]] + cx;
+            const double yf = op.sgn[1] * d[op.perm[1]] + cy;
+            const long xi = std::lround(xf), yi = std::lround(yf);
+            long zi = 0;
+            if (g == 3) {
+                zi = ((op.sgn[2] * lat.zc[i] + op.shift) % Lz + Lz) % Lz;
+            } else {
+                const double zf = op.sgn[2] * d[op.perm[2]] + cz;
+                zi = std::lround(zf);
+                if (std::fabs(zf - zi) > 1e-9) { ok = false; break; }
             }
+            if (std::fabs(xf - xi) > 1e-9 || std::fabs(yf - yi) > 1e-9) { ok = false; break; }
+            auto it = index.find({static_cast<int>(xi), static_cast<int>(yi), static_cast<int>(zi)});
+            if (it == index.end()) { ok = false; break; }
+            img[i] = it->second;
+        }
+        if (ok) images.push_back(img);
+    }
     std::vector<int> rep_site(N);
     for (int i = 0; i < N; ++i) {
         int m = i;
@@ -309,6 +386,11 @@ hf_status setup_sizes(hf_ctx& c, const hf_params* p) {
     if (st != HF_OK) return fail(nullptr, st, err);
     c.p = *p;
     if (!build_lattice(*p, c.lat, err)) return fail(nullptr, HF_EINVAL, err);
+    if (!hfk::lattice_band_supported(c.lat.b))
+        return fail(nullptr, HF_EINVAL,
+                    "the lattice's band half-width " + std::to_string(c.lat.b) +
+                        " exceeds the lattice step's shared-memory window (largest: " +
+                        std::to_string(hfk::lattice_max_band()) + ")");
     c.L = static_cast<int>(std::lround(p->beta / p->dtau));
     c.nsite = static_cast<int>(c.lat.rep.size());
     c.nchain = c.nsite * p->chains_per_site;
@@ -506,6 +588,21 @@ hf_status hf_workspace_size(const hf_params* p, size_t* bytes) {
     return HF_OK;
 }
 
+hf_status hf_lattice_info(const hf_params* p, int* N, int* n_sites, int* band, int* rep, int* rep_of,
+                          int* flip) {
+    hf_ctx c;
+    hf_status st = setup_sizes(c, p);
+    if (st != HF_OK) return st;
+    const HostLattice& lat = c.lat;
+    if (N) *N = lat.N;
+    if (n_sites) *n_sites = static_cast<int>(lat.rep.size());
+    if (band) *band = lat.b;
+    if (rep) std::memcpy(rep, lat.rep.data(), sizeof(int) * lat.rep.size());
+    if (rep_of) std::memcpy(rep_of, lat.rep_of.data(), sizeof(int) * lat.N);
+    if (flip) std::memcpy(flip, lat.flip.data(), sizeof(int) * lat.N);
+    return HF_OK;
+}
+
 hf_status hf_init(const hf_params* p, void* d_ws, size_t ws_bytes, hf_ctx** out) {
     if (!out) return fail(nullptr, HF_EINVAL, "null output handle");
     *out = nullptr;
@@ -535,11 +632,18 @@ hf_status hf_init(const hf_params* p, void* d_ws, size_t ws_bytes, hf_ctx** out)
     c->ev_m = std::exp(-c->lambda) - 1.0;
 
     const int N = c->lat.N, bw = c->lat.b + 1, ns = c->nsite, nw = c->nw;
+    // H0 and the orbit tables in band order (band position k holds site order[k])
+    const HostLattice& lat = c->lat;
     std::vector<double> h0(static_cast<size_t>(N) * bw, 0.0);
+    std::vector<int> rep_of_k(N), flip_k(N), site_rep_k(N);
     for (int k = 0; k < N; ++k) {
-        h0[static_cast<size_t>(k) * bw] = c->lat.V[k];
-        for (int j : c->lat.nbr[k])
-            if (j > k) h0[static_cast<size_t>(k) * bw + (j - k)] += -p->t;
+        const int i = lat.order[k];
+        h0[static_cast<size_t>(k) * bw] = lat.V[i];
+        for (int j : lat.nbr[i])
+            if (lat.pos[j] > k) h0[static_cast<size_t>(k) * bw + (lat.pos[j] - k)] += -p->t;
+        rep_of_k[k] = lat.rep_of[i];
+        flip_k[k] = lat.flip[i];
+        site_rep_k[k] = lat.site_rep[i];
     }
     std::vector<double> c23(static_cast<size_t>(ns) * 2);
     std::vector<double2> sig(static_cast<size_t>(ns) * 2 * nw);
@@ -559,9 +663,9 @@ hf_status hf_init(const hf_params* p, void* d_ws, size_t ws_bytes, hf_ctx** out)
         return cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, st0);
     };
     cudaError_t e = up(c->h0band, h0.data(), h0.size() * sizeof(double));
-    if (e == cudaSuccess) e = up(c->rep_of, c->lat.rep_of.data(), N * sizeof(int));
-    if (e == cudaSuccess) e = up(c->flip, c->lat.flip.data(), N * sizeof(int));
-    if (e == cudaSuccess) e = up(c->site_rep, c->lat.site_rep.data(), N * sizeof(int));
+    if (e == cudaSuccess) e = up(c->rep_of, rep_of_k.data(), N * sizeof(int));
+    if (e == cudaSuccess) e = up(c->flip, flip_k.data(), N * sizeof(int));
+    if (e == cudaSuccess) e = up(c->site_rep, site_rep_k.data(), N * sizeof(int));
     if (e == cudaSuccess) e = up(c->c23, c23.data(), c23.size() * sizeof(double));
     if (e == cudaSuccess) e = up(c->sigma, sig.data(), sig.size() * sizeof(double2));
     if (e == cudaSuccess) e = cudaMemsetAsync(c->gtau, 0, sizeof(double) * ns * 2 * c->L, st0);

@@ -149,6 +149,16 @@ size_t lattice_smem_per_warp(int b) {
     return static_cast<size_t>(b * b + 2 * (b + 1)) * sizeof(double2);
 }
 
+bool lattice_band_supported(int b) {
+    return b >= 0 && lattice_smem_per_warp(b) <= static_cast<size_t>(227) * 1024;
+}
+
+int lattice_max_band() {
+    int b = 0;
+    while (lattice_band_supported(b + 1)) ++b;
+    return b;
+}
+
 int lattice_warps_per_block(int b) {
     const size_t per = lattice_smem_per_warp(b);
     int w = 4;

@@ -19,6 +19,8 @@ struct LatticeArgs {
 };
 
 size_t lattice_smem_per_warp(int b);
+bool lattice_band_supported(int b);
+int lattice_max_band();
 int lattice_warps_per_block(int b);
 size_t lattice_scratch_per_matrix(int N, int b);
 cudaError_t launch_lattice(const LatticeArgs& a, int q0, int nq, cudaStream_t st);

@@ -26,7 +26,7 @@ class HFError(RuntimeError):
 
 class hf_params(C.Structure):
     _fields_ = [
-        ("Lx", C.c_int), ("Ly", C.c_int), ("geometry", C.c_int), ("periodic", C.c_int),
+        ("Lx", C.c_int), ("Ly", C.c_int), ("Lz", C.c_int), ("geometry", C.c_int), ("periodic", C.c_int),
         ("t", C.c_double), ("U", C.c_double), ("V0", C.c_double), ("mu", C.c_double),
         ("beta", C.c_double), ("dtau", C.c_double),
         ("n_matsubara", C.c_int), ("chains_per_site", C.c_int), ("precision", C.c_int),
@@ -79,6 +79,7 @@ _lib = None
 _VP, _DP, _IP = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)
 SIGNATURES = [
     ("hf_workspace_size", C.c_int, [C.POINTER(hf_params), C.POINTER(C.c_size_t)]),
+    ("hf_lattice_info", C.c_int, [C.POINTER(hf_params), _IP, _IP, _IP, _IP, _IP, _IP]),
     ("hf_init", C.c_int, [C.POINTER(hf_params), _VP, C.c_size_t, C.POINTER(_VP)]),
     ("hf_get_sizes", C.c_int, [_VP, _IP, _IP, _IP, _IP]),
     ("hf_get_orbits", C.c_int, [_VP, _IP, _IP, _IP]),
@@ -145,6 +146,18 @@ def _check(st, ctx=None):
 
 
 # --- one wrapper per entry point, same names as the C ABI -----------------------------------
+
+def hf_lattice_info(p: hf_params):
+    """Host-only lattice description: (N, n_sites, band, rep, rep_of, flip) as numpy arrays."""
+    N, ns, b = C.c_int(), C.c_int(), C.c_int()
+    _check(lib().hf_lattice_info(C.byref(p), C.byref(N), C.byref(ns), C.byref(b), None, None, None))
+    rep = np.zeros(ns.value, dtype=np.int32)
+    rep_of = np.zeros(N.value, dtype=np.int32)
+    flip = np.zeros(N.value, dtype=np.int32)
+    _check(lib().hf_lattice_info(C.byref(p), None, None, None, rep.ctypes.data_as(_IP),
+                               rep_of.ctypes.data_as(_IP), flip.ctypes.data_as(_IP)))
+    return N.value, ns.value, b.value, rep, rep_of, flip
+
 
 def hf_workspace_size(p: hf_params) -> int:
     n = C.c_size_t()
@@ -434,6 +447,7 @@ def make_params(cfg: dict, stream=None, **over) -> hf_params:
     p = hf_params()
     p.Lx = int(d.get("Lx", 6))
     p.Ly = int(d.get("Ly", p.Lx))
+    p.Lz = int(d.get("Lz", 1))
     p.geometry = int(d.get("geometry", 0))
     p.periodic = int(d.get("periodic", 0))
     p.t = float(d.get("t", 1.0))

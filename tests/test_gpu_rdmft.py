@@ -37,7 +37,7 @@ def _oracle_for(cfg):
                  chains=cfg["chains_per_site"], seed=cfg["seed"], h_seed=cfg["h_seed"],
                  mix=cfg["mix"], n_warmup=cfg["n_warmup"], n_measure=cfg["n_measure"],
                  refresh_every=cfg["refresh_every"], bin_size=cfg["bin_size"],
-                 refresh_stagger=cfg.get("refresh_stagger", 0))
+                 refresh_stagger=cfg.get("refresh_stagger", 0), Lz=cfg.get("Lz", 1))
 
 
 @pytest.mark.parametrize("Lx,geom", [(6, 0), (20, 0), (30, 0), (40, 1), (7, 1)])

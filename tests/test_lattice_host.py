@@ -1,0 +1,60 @@
+"""Host side of the library's lattices (no GPU): the orbit tables that hf_lattice_info reports
+equal the oracle's, bit for bit, for every geometry, and the band half-width of the folded band
+order is the one its construction gives."""
+import numpy as np
+import pytest
+
+from oracle.lattice import Lattice
+from paper_1006_2716_gb300 import build as B
+from paper_1006_2716_gb300 import hf
+from paper_1006_2716_gb300 import workloads as wl
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return hf.lib()
+
+
+CASES = [
+    # geometry, Lx, Ly, Lz, periodic, band half-width of the folded order
+    (0, 6, 6, 1, 0, 6),
+    (0, 7, 5, 1, 1, 14),
+    (0, 20, 20, 1, 1, 40),
+    (1, 7, 7, 1, 0, None),
+    (2, 4, 4, 4, 1, 32),
+    (2, 5, 5, 5, 0, 25),
+    (2, 4, 4, 6, 0, 16),
+    (2, 6, 6, 6, 1, 72),
+    (3, 6, 6, 4, 0, 24),
+    (3, 8, 6, 4, 1, 64),
+    (3, 24, 24, 4, 0, 96),
+]
+
+
+@pytest.mark.parametrize("geom,Lx,Ly,Lz,per,band", CASES)
+def test_orbit_tables_match_the_oracle(lib, geom, Lx, Ly, Lz, per, band):
+    p = hf.make_params(wl.CONFIGS["square6"], geometry=geom, Lx=Lx, Ly=Ly, Lz=Lz, periodic=per,
+                       n_matsubara=4, chains_per_site=1)
+    N, ns, b, rep, rep_of, flip = hf.hf_lattice_info(p)
+    lat = Lattice(Lx, Ly, geometry=geom, periodic=bool(per), V0=0.1, Lz=Lz)
+    r2, ro2, f2 = lat.orbits()
+    assert N == lat.N and ns == len(r2)
+    assert np.array_equal(rep, r2) and np.array_equal(rep_of, ro2) and np.array_equal(flip, f2)
+    if band is not None:
+        assert b == band
+
+
+@pytest.mark.parametrize("over,frag", [
+    (dict(geometry=2, Lx=5, Ly=5, Lz=5, periodic=1), "even length"),
+    (dict(geometry=3, Lx=6, Ly=6, Lz=3), "even length"),
+    (dict(geometry=3, Lx=6, Ly=6, Lz=2), "even length"),
+    (dict(geometry=2, Lx=4, Ly=4, Lz=0), ">= 1"),
+    (dict(geometry=3, Lx=40, Ly=40, Lz=4), "band half-width"),
+])
+def test_invalid_three_dimensional_lattices(lib, over, frag):
+    p = hf.make_params(wl.CONFIGS["square6"], **over)
+    with pytest.raises(hf.HFError) as e:
+        hf.hf_lattice_info(p)
+    assert e.value.status == hf.HF_EINVAL
+    assert frag in str(e.value)
