@@ -526,8 +526,7 @@ def run_ours(args):
                                               "qmc_f64_kernel")}
         c0.close()
 
-    per_matrix = ctx.N * (20 + 1) * 16
-    launches_per_step = -(-2 * nw // max(1, min(2 * nw, (1 << 30) // per_matrix))) + 4
+    launches_per_step = lattice_launches(hf, cfg) + 5
     dtype = "f64" if form == 0 else "f32x2+f64"
     line = {"metric": METRIC, "value": value, "unit": "proposals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -550,6 +549,188 @@ def run_ours(args):
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
+    return 0
+
+
+def lattice_launches(hf, cfg):
+    """Lattice-step launches of one iteration: the nspin x nw matrices in chunks of as many band
+    buffers as fit in 1 GiB (at most 2 nw)."""
+    N, _, b, nspin, _, _, _ = hf.hf_lattice_info(hf.make_params(cfg))
+    nw = cfg["n_matsubara"]
+    batch = max(1, min(2 * nw, (1 << 30) // (N * (b + 1) * 16)))
+    return -(-nspin * nw // batch)
+
+
+def lattice_flops(N, b, nspin, nw):
+    """Algorithmic FP64 flops of one lattice step: per matrix, the band LDL^T trailing updates
+    (dmax (dmax + 1) / 2 complex multiply-adds at step k, dmax = min(b, N - 1 - k)) and the
+    selected-inversion products (dmax^2 + dmax), 8 real flops per complex multiply-add."""
+    cfma = 0
+    for k in range(N):
+        d = min(b, N - 1 - k)
+        cfma += d * (d + 1) // 2 + d * d + d
+    return 8.0 * cfma * nspin * nw
+
+
+_W3 = {}
+
+
+def _pool3_lattice(job):
+    import numpy as np
+
+    from oracle.lattice import lattice_step
+    from oracle.rdmft import RDMFT
+
+    name, idx = job
+    cfg = wl.CONFIGS[name]
+    if _W3.get("name") != name:
+        r = RDMFT(cfg["Lx"], cfg["Ly"], geometry=cfg["geometry"], periodic=bool(cfg["periodic"]),
+                  U=cfg["U"], V0=cfg["V0"], mu=cfg["mu"], beta=cfg["beta"], L=8,
+                  nw=cfg["n_matsubara"], chains=1, seed=cfg["seed"], h_seed=cfg["h_seed"],
+                  Lz=cfg["Lz"])
+        _W3.update(name=name, H0=r.lat.H0, full=r.expand_sigma())
+    idx = np.asarray(idx)
+    for sp in range(2):
+        lattice_step(_W3["H0"], cfg["mu"], cfg["beta"], _W3["full"][sp][idx], n_index=idx)
+    return len(idx)
+
+
+def _pool3_chains(job):
+    import numpy as np
+
+    import oracle as o
+
+    name, chains = job
+    cfg = wl.CONFIGS[name]
+    L = int(round(cfg["beta"] / cfg["dtau"]))
+    baths = wl.random_baths(cfg["seed"], max(chains) + 1, cfg["beta"], L)
+    _, lam = o.constants(cfg["beta"], cfg["U"], L)
+    for c in chains:
+        g0u, g0d = o.build_g0(baths[c, 0]), o.build_g0(baths[c, 1])
+        s = o.init_fields(cfg["seed"], c, 0, L)
+        Gu, _ = o.dyson(g0u, s, 1, lam)
+        Gd, _ = o.dyson(g0d, s, -1, lam)
+        bins = np.zeros((cfg["n_measure"] // cfg["bin_size"], 2 * L + 3))
+        o.run_chain(lam, g0u, g0d, cfg["seed"], c, 0, 0, cfg["n_warmup"], cfg["n_measure"],
+                    cfg["refresh_every"], cfg["bin_size"], s, Gu, Gd, bins)
+    return len(chains)
+
+
+def cpu_oracle_3d(name, n_chains_total, chains_per_core=8, freqs_per_core=1):
+    """Oracle seconds of one iteration of a three-dimensional workload on every host core, from a
+    bounded sample (chains and lattice frequencies over a spawned pool, one BLAS thread each);
+    returns (seconds, cores, sample)."""
+    cfg = wl.CONFIGS[name]
+    cores = host_cores()
+    ctx = mp.get_context("spawn")
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        pool = ctx.Pool(cores)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    try:
+        nw = cfg["n_matsubara"]
+        pool.map(_pool3_lattice, [(name, [0])] * cores, chunksize=1)      # warm: lattice, imports
+        n_freq = min(nw, cores * freqs_per_core)
+        idx = [int(k * (nw // n_freq)) for k in range(n_freq)]
+        t0 = time.perf_counter()
+        pool.map(_pool3_lattice, [(name, idx[w::cores]) for w in range(cores) if idx[w::cores]],
+                 chunksize=1)
+        t_lat = (time.perf_counter() - t0) * (nw / n_freq)
+        n = cores * chains_per_core
+        t0 = time.perf_counter()
+        pool.map(_pool3_chains, [(name, list(range(w, n, cores))) for w in range(cores)], chunksize=1)
+        t_qmc = (time.perf_counter() - t0) * (n_chains_total / n)
+    finally:
+        pool.close()
+        pool.join()
+    L = int(round(cfg["beta"] / cfg["dtau"]))
+    sample = ("%d of %d chains x 2500 sweeps (L=%d) + lattice step at %d of %d frequencies x 2 "
+              "spins (dense inverse) over %d worker processes, each scaled to the full iteration"
+              % (n, n_chains_total, L, n_freq, nw, cores))
+    return t_lat + t_qmc, cores, sample
+
+
+def run_lattice3d(args):
+    """Three-dimensional workloads (slab16, box12): whole RDMFT iterations with the FP32-pair
+    sweeps, reported with the rooflines of both the impurity sweeps and the lattice step, which
+    in three dimensions is no longer small."""
+    import torch
+
+    from paper_1006_2716_gb300 import hf
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    name = args.workload
+    cfg = dict(wl.CONFIGS[name])
+    N, ns, b, nspin, _, _, _ = hf.hf_lattice_info(hf.make_params(cfg))
+    nc = ns * cfg["chains_per_site"]
+    cpu = None
+    if not args.no_cpu:   # spawned before any CUDA work
+        secs, cores, sample = cpu_oracle_3d(name, nc)
+        L0 = int(round(cfg["beta"] / cfg["dtau"]))
+        cpu = {"value": nc * (cfg["n_warmup"] + cfg["n_measure"]) * L0 / secs,
+               "unit": "proposals/s", "cores": cores, "kind": "oracle", "sample": sample}
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    ctx = hf.Context(hf.make_params(cfg), device=dev, stream=stream)
+    L, nw = ctx.L, ctx.nw
+    sweeps = cfg["n_warmup"] + cfg["n_measure"]
+    proposals = nc * sweeps * L
+    n_refresh = sweeps // cfg["refresh_every"] + 1
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        hf.hf_rdmft_step(ctx.handle)
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    acc0 = hf.hf_get_accepts(ctx.handle, nc).sum()
+    ms_steps, qmc_ms, phase = _time_iterations(hf, ctx, stream, flush, args.steps)
+    clk = clocks.stop()
+    accepts = int(hf.hf_get_accepts(ctx.handle, nc).sum() - acc0) / args.steps
+    ms_per = statistics.mean(ms_steps)
+    phase = phase / args.steps
+    qroof = qmc_roofline(2, L, nc, sweeps, accepts, cfg["n_measure"], n_refresh,
+                         statistics.mean(qmc_ms) / 1e3, "qmc_df64_kernel")
+    qroof["acceptance"] = accepts / proposals
+    fl = lattice_flops(N, b, nspin, nw)
+    lat_s = phase[0] / 1e3
+    lroof = {"bound": "alu", "achieved": fl / lat_s / 1e12, "peak": FP64_PEAK_TFLOPS,
+             "unit": "TFLOP/s", "frac": fl / lat_s / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
+             "kernel": "lattice_kernel", "matrices": nspin * nw, "N": N, "band": b,
+             "peak_source": "FP64 nominal: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz"}
+    dominant = lroof if phase[0] > phase[2] else qroof
+    geo = ("%dx%d slab of %d layers, periodic in all directions, cylindrical trap" % (cfg["Lx"], cfg["Ly"], cfg["Lz"])
+           if cfg["geometry"] == 3 else
+           "%dx%dx%d %s box, spherical trap" % (cfg["Lx"], cfg["Ly"], cfg["Lz"],
+                                                 "periodic" if cfg["periodic"] else "open"))
+    line = {"metric": METRIC, "value": proposals / (ms_per / 1e3), "unit": "proposals/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32x2+f64", "data": "synthetic",
+            "config": {"workload": "%s: %s (%d sites, %d inequivalent, band half-width %d), U=%g, "
+                                   "V0=%g, mu=%g, beta=%g, dtau=%g (L=%d), %d chains per site, "
+                                   "500+2000 sweeps, 500 Matsubara frequencies; one step = one "
+                                   "RDMFT iteration" % (name, geo, N, ns, b, cfg["U"], cfg["V0"],
+                                                        cfg["mu"], cfg["beta"], cfg["dtau"], L,
+                                                        cfg["chains_per_site"]),
+                       "chains": nc, "time_slices": L,
+                       "l2": "flushed (256 MB write) between timed steps"},
+            "rdmft_iteration_ms": ms_per,
+            "phase_ms": dict(zip(["lattice", "weiss_tau", "qmc", "reduce", "sigma"],
+                                 [float(x) for x in phase])),
+            "roofline": dominant, "qmc_roofline": qroof, "lattice_roofline": lroof,
+            "gpu_launches": (lattice_launches(hf, cfg) + 5) * args.steps,
+            "cpu_baseline": cpu, "clocks": clk}
+    print(json.dumps(line))
+    ctx.close()
     return 0
 
 
@@ -869,7 +1050,8 @@ def main():
                     help="sweep arithmetic: 0 FP64, 2 FP32 pairs (both with FP64 refresh); "
                          "-1 (default): the autotuner picks form and team width")
     ap.add_argument("--workload", default="square20",
-                    choices=["square20", "scan20", "square30", "disc40", "dtau_scan"])
+                    choices=["square20", "scan20", "square30", "disc40", "dtau_scan", "slab16",
+                             "box12"])
     ap.add_argument("--refresh-stagger", type=int, default=0, choices=[0, 1],
                     help="1: per-chain refresh phases; 0 (default): every chain refreshes on the "
                          "same sweeps")
@@ -888,6 +1070,8 @@ def main():
         return run_disc40(args)
     if args.workload == "square30":
         return run_square30(args)
+    if args.workload in ("slab16", "box12"):
+        return run_lattice3d(args)
     if args.workload == "dtau_scan":
         return run_dtau_scan(args)
     return run_ours(args)

@@ -90,12 +90,14 @@ typedef struct hf_params {
 hf_status hf_workspace_size(const hf_params* p, size_t* bytes);
 
 /* Host only, no device work: the lattice *p describes (after the same validation as hf_init).
- * Writes the number of sites, of inequivalent sites and the band half-width of H0 that the
- * lattice step factors; rep [n_sites], rep_of [N] and flip [N] (as in hf_get_orbits) when not
- * NULL -- call once with them NULL to learn the sizes.  HF_EINVAL for invalid parameters or a
- * band wider than the lattice step supports. */
-hf_status hf_lattice_info(const hf_params* p, int* N, int* n_sites, int* band, int* rep, int* rep_of,
-                          int* flip);
+ * Writes the number of sites, of inequivalent sites, the band half-width of H0 that the lattice
+ * step factors, and the matrices it inverts per Matsubara frequency (2; or 1 when a symmetry of
+ * the lattice exchanges the two sublattices, so that the spin-down G_ii are spin-up ones at
+ * permuted sites); rep [n_sites], rep_of [N] and flip [N] (as in hf_get_orbits) when not NULL --
+ * call once with them NULL to learn the sizes.  HF_EINVAL for invalid parameters or a band wider
+ * than the lattice step supports. */
+hf_status hf_lattice_info(const hf_params* p, int* N, int* n_sites, int* band, int* spins, int* rep,
+                          int* rep_of, int* flip);
 
 /* Validate *p, build the lattice (eq. 1) and its C4v orbits, lay the state out in the
  * caller's device workspace d_ws (ws_bytes >= hf_workspace_size), draw the initial Ising

@@ -53,6 +53,8 @@ struct HostLattice {
     std::vector<std::vector<int>> nbr;
     std::vector<int> rep, rep_of, flip, site_rep;
     std::vector<int> order, pos;    // band position -> site, site -> band position
+    std::vector<int> gdn;           // image of each site under an operation that exchanges the
+                                    // sublattices (empty if the group has none)
 };
 
 // Position of coordinate c (0 <= c < n) along a folded periodic axis: 0, n-1, 1, n-2, ...
@@ -183,6 +185,14 @@ bool build_lattice(const hf_params& p, HostLattice& lat, std::string& err) {
         }
         if (ok) images.push_back(img);
     }
+    // an operation that maps every site onto the other sublattice: with it the spin-down lattice
+    // Green function is the spin-up one at permuted sites (the lattice step inverts half the
+    // matrices)
+    for (const auto& im : images) {
+        bool all = true;
+        for (int i = 0; i < N && all; ++i) all = lat.parity[im[i]] != lat.parity[i];
+        if (all) { lat.gdn = im; break; }
+    }
     std::vector<int> rep_site(N);
     for (int i = 0; i < N; ++i) {
         int m = i;
@@ -256,6 +266,7 @@ struct hf_ctx {
     int* rep_of = nullptr;          // [N]
     int* flip = nullptr;            // [N]
     int* site_rep = nullptr;        // [N]
+    int* site_dn = nullptr;         // [N]
     double2* lat_scratch = nullptr; // [lat_batch][N][b+1]
     // phase timing: events on the context stream (see hf_get_timings)
     cudaEvent_t ev[9] = {};
@@ -375,6 +386,7 @@ size_t layout(hf_ctx& c, void* base) {
     c.rep_of = cv.take<int>(N);
     c.flip = cv.take<int>(N);
     c.site_rep = cv.take<int>(N);
+    c.site_dn = cv.take<int>(N);
     c.lat_scratch = cv.take<double2>(static_cast<size_t>(c.lat_batch) * N * bw);
     return cv.off + 256;
 }
@@ -538,6 +550,8 @@ hfk::LatticeArgs lattice_args(const hf_ctx& c) {
     la.rep_of = c.rep_of;
     la.flip = c.flip;
     la.site_rep = c.site_rep;
+    la.site_dn = c.lat.gdn.empty() ? nullptr : c.site_dn;
+    la.nspin = c.lat.gdn.empty() ? 2 : 1;
     la.sigma = c.sigma;
     la.gloc = c.gloc;
     la.scratch = c.lat_scratch;
@@ -547,7 +561,7 @@ hfk::LatticeArgs lattice_args(const hf_ctx& c) {
 
 hf_status enqueue_lattice(hf_ctx* c) {
     const hfk::LatticeArgs la = lattice_args(*c);
-    const int nq = 2 * c->nw;
+    const int nq = la.nspin * c->nw;
     for (int q0 = 0; q0 < nq; q0 += c->lat_batch) {
         cudaError_t e = hfk::launch_lattice(la, q0, std::min(c->lat_batch, nq - q0), c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "lattice step launch");
@@ -588,8 +602,8 @@ hf_status hf_workspace_size(const hf_params* p, size_t* bytes) {
     return HF_OK;
 }
 
-hf_status hf_lattice_info(const hf_params* p, int* N, int* n_sites, int* band, int* rep, int* rep_of,
-                          int* flip) {
+hf_status hf_lattice_info(const hf_params* p, int* N, int* n_sites, int* band, int* spins, int* rep,
+                          int* rep_of, int* flip) {
     hf_ctx c;
     hf_status st = setup_sizes(c, p);
     if (st != HF_OK) return st;
@@ -597,6 +611,7 @@ hf_status hf_lattice_info(const hf_params* p, int* N, int* n_sites, int* band, i
     if (N) *N = lat.N;
     if (n_sites) *n_sites = static_cast<int>(lat.rep.size());
     if (band) *band = lat.b;
+    if (spins) *spins = lat.gdn.empty() ? 2 : 1;
     if (rep) std::memcpy(rep, lat.rep.data(), sizeof(int) * lat.rep.size());
     if (rep_of) std::memcpy(rep_of, lat.rep_of.data(), sizeof(int) * lat.N);
     if (flip) std::memcpy(flip, lat.flip.data(), sizeof(int) * lat.N);
@@ -635,7 +650,7 @@ hf_status hf_init(const hf_params* p, void* d_ws, size_t ws_bytes, hf_ctx** out)
     // H0 and the orbit tables in band order (band position k holds site order[k])
     const HostLattice& lat = c->lat;
     std::vector<double> h0(static_cast<size_t>(N) * bw, 0.0);
-    std::vector<int> rep_of_k(N), flip_k(N), site_rep_k(N);
+    std::vector<int> rep_of_k(N), flip_k(N), site_rep_k(N), site_dn_k(N, -1);
     for (int k = 0; k < N; ++k) {
         const int i = lat.order[k];
         h0[static_cast<size_t>(k) * bw] = lat.V[i];
@@ -645,6 +660,8 @@ hf_status hf_init(const hf_params* p, void* d_ws, size_t ws_bytes, hf_ctx** out)
         flip_k[k] = lat.flip[i];
         site_rep_k[k] = lat.site_rep[i];
     }
+    if (!lat.gdn.empty())
+        for (int r = 0; r < ns; ++r) site_dn_k[lat.pos[lat.gdn[lat.rep[r]]]] = r;
     std::vector<double> c23(static_cast<size_t>(ns) * 2);
     std::vector<double2> sig(static_cast<size_t>(ns) * 2 * nw);
     for (int i = 0; i < ns; ++i) {
@@ -666,6 +683,7 @@ hf_status hf_init(const hf_params* p, void* d_ws, size_t ws_bytes, hf_ctx** out)
     if (e == cudaSuccess) e = up(c->rep_of, rep_of_k.data(), N * sizeof(int));
     if (e == cudaSuccess) e = up(c->flip, flip_k.data(), N * sizeof(int));
     if (e == cudaSuccess) e = up(c->site_rep, site_rep_k.data(), N * sizeof(int));
+    if (e == cudaSuccess) e = up(c->site_dn, site_dn_k.data(), N * sizeof(int));
     if (e == cudaSuccess) e = up(c->c23, c23.data(), c23.size() * sizeof(double));
     if (e == cudaSuccess) e = up(c->sigma, sig.data(), sig.size() * sizeof(double2));
     if (e == cudaSuccess) e = cudaMemsetAsync(c->gtau, 0, sizeof(double) * ns * 2 * c->L, st0);
@@ -974,6 +992,8 @@ hf_status hf_lattice_step_noalloc(hf_ctx* c, const double* d_sigma, double* d_gl
     la.rep_of = c->rep_of;
     la.flip = c->flip;
     la.site_rep = c->site_rep;
+    la.site_dn = c->lat.gdn.empty() ? nullptr : c->site_dn;
+    la.nspin = c->lat.gdn.empty() ? 2 : 1;
     la.sigma = reinterpret_cast<const double2*>(d_sigma);
     la.gloc = reinterpret_cast<double2*>(d_gloc);
     la.scratch = nullptr;

@@ -12,20 +12,21 @@ struct LatticeArgs {
     const int* rep_of;        // [N] inequivalent index of each site
     const int* flip;          // [N] 1: spins exchanged relative to the representative
     const int* site_rep;      // [N] inequivalent index if the site is a representative, else -1
+    const int* site_dn;       // [N] or nullptr: inequivalent index r whose spin-down G_rr equals
+                              //     the spin-up G at this position, else -1 (nspin = 1)
+    int nspin;                // 2: a matrix per (w_n, sigma); 1: spin-up matrices only
     const double2* sigma;     // [nsite][2][nw]
     double2* gloc;            // [nsite][2][nw] output G_ii of the representatives
-    double2* scratch;         // [nq][N][b+1] band factors of the matrices in flight
+    double2* scratch;         // [nq][N][b+1] band factors of the matrices in flight (q = sigma nw + n)
     int* status;
 };
 
-size_t lattice_smem_per_warp(int b);
 bool lattice_band_supported(int b);
 int lattice_max_band();
-int lattice_warps_per_block(int b);
 size_t lattice_scratch_per_matrix(int N, int b);
 cudaError_t launch_lattice(const LatticeArgs& a, int q0, int nq, cudaStream_t st);
 
-// Lattice step over all 2 * nw matrices with the band buffers in a fixed 16 MiB device array
+// Lattice step over all nspin * nw matrices with the band buffers in a fixed 16 MiB device array
 // (a.scratch is ignored); rejects a lattice whose single band does not fit.
 size_t lattice_static_scratch_bytes();
 cudaError_t launch_lattice_static(const LatticeArgs& a, cudaStream_t st);

@@ -79,7 +79,7 @@ _lib = None
 _VP, _DP, _IP = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)
 SIGNATURES = [
     ("hf_workspace_size", C.c_int, [C.POINTER(hf_params), C.POINTER(C.c_size_t)]),
-    ("hf_lattice_info", C.c_int, [C.POINTER(hf_params), _IP, _IP, _IP, _IP, _IP, _IP]),
+    ("hf_lattice_info", C.c_int, [C.POINTER(hf_params), _IP, _IP, _IP, _IP, _IP, _IP, _IP]),
     ("hf_init", C.c_int, [C.POINTER(hf_params), _VP, C.c_size_t, C.POINTER(_VP)]),
     ("hf_get_sizes", C.c_int, [_VP, _IP, _IP, _IP, _IP]),
     ("hf_get_orbits", C.c_int, [_VP, _IP, _IP, _IP]),
@@ -148,15 +148,16 @@ def _check(st, ctx=None):
 # --- one wrapper per entry point, same names as the C ABI -----------------------------------
 
 def hf_lattice_info(p: hf_params):
-    """Host-only lattice description: (N, n_sites, band, rep, rep_of, flip) as numpy arrays."""
-    N, ns, b = C.c_int(), C.c_int(), C.c_int()
-    _check(lib().hf_lattice_info(C.byref(p), C.byref(N), C.byref(ns), C.byref(b), None, None, None))
+    """Host-only lattice description: (N, n_sites, band, spins, rep, rep_of, flip)."""
+    N, ns, b, nsp = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    _check(lib().hf_lattice_info(C.byref(p), C.byref(N), C.byref(ns), C.byref(b), C.byref(nsp),
+                                 None, None, None))
     rep = np.zeros(ns.value, dtype=np.int32)
     rep_of = np.zeros(N.value, dtype=np.int32)
     flip = np.zeros(N.value, dtype=np.int32)
-    _check(lib().hf_lattice_info(C.byref(p), None, None, None, rep.ctypes.data_as(_IP),
-                               rep_of.ctypes.data_as(_IP), flip.ctypes.data_as(_IP)))
-    return N.value, ns.value, b.value, rep, rep_of, flip
+    _check(lib().hf_lattice_info(C.byref(p), None, None, None, None, rep.ctypes.data_as(_IP),
+                                 rep_of.ctypes.data_as(_IP), flip.ctypes.data_as(_IP)))
+    return N.value, ns.value, b.value, nsp.value, rep, rep_of, flip
 
 
 def hf_workspace_size(p: hf_params) -> int:

@@ -15,6 +15,12 @@ Configurations (the trapped 2D Hubbard model of eq. 1 with V_i = V0 r_i^2, t = 1
   site (120 sites), single-precision sweeps with a double-precision refresh every sweep.
 * ``disc40``    -- site-centred disc of radius 40 (5025 sites, 663 inequivalent), U=8; impurity
   solve requests at L in {32, 40, 64}.
+* ``slab16``    -- three dimensions, the reduced system of "Efficient simulations for three
+  dimensions": a 16x16 slab of 4 layers, periodic in all three directions, cylindrical trap
+  V0=0.05, U=8, mu=4 (half filling at the axis), T = 0.41 (beta=2.4), dtau=0.1 (L=24), 32 chains
+  per inequivalent site (36 sites).
+* ``box12``     -- a 12x12x12 open box with a spherical trap V0=0.08, otherwise as slab16
+  (56 inequivalent sites).
 """
 from __future__ import annotations
 
@@ -37,6 +43,14 @@ CONFIGS = {
                      n_warmup=500,
                      n_measure=2000, refresh_every=1, bin_size=100, seed=4, h_seed=0.1,
                      mix=0.5),
+    "slab16": dict(Lx=16, Ly=16, Lz=4, geometry=3, periodic=1, t=1.0, U=8.0, V0=0.05, mu=4.0,
+                   beta=2.4, dtau=0.1, precision=2, team_warps=1, n_matsubara=500,
+                   chains_per_site=32, n_warmup=500, n_measure=2000, refresh_every=10,
+                   bin_size=100, seed=5, h_seed=0.1, mix=0.5),
+    "box12": dict(Lx=12, Ly=12, Lz=12, geometry=2, periodic=0, t=1.0, U=8.0, V0=0.08, mu=4.0,
+                  beta=2.4, dtau=0.1, precision=2, team_warps=1, n_matsubara=500,
+                  chains_per_site=32, n_warmup=500, n_measure=2000, refresh_every=10,
+                  bin_size=100, seed=6, h_seed=0.1, mix=0.5),
 }
 SCAN20_BETAS = (5.0, 8.0, 10.0, 16.0)
 

@@ -36,13 +36,16 @@ CASES = [
 def test_orbit_tables_match_the_oracle(lib, geom, Lx, Ly, Lz, per, band):
     p = hf.make_params(wl.CONFIGS["square6"], geometry=geom, Lx=Lx, Ly=Ly, Lz=Lz, periodic=per,
                        n_matsubara=4, chains_per_site=1)
-    N, ns, b, rep, rep_of, flip = hf.hf_lattice_info(p)
+    N, ns, b, nsp, rep, rep_of, flip = hf.hf_lattice_info(p)
     lat = Lattice(Lx, Ly, geometry=geom, periodic=bool(per), V0=0.1, Lz=Lz)
     r2, ro2, f2 = lat.orbits()
     assert N == lat.N and ns == len(r2)
     assert np.array_equal(rep, r2) and np.array_equal(rep_of, ro2) and np.array_equal(flip, f2)
     if band is not None:
         assert b == band
+    # one matrix per frequency exactly when some operation exchanges the sublattices
+    has_flip = any(np.all(lat.parity[im] != lat.parity) for im in lat._images)
+    assert nsp == (1 if has_flip else 2)
 
 
 @pytest.mark.parametrize("over,frag", [
@@ -50,7 +53,7 @@ def test_orbit_tables_match_the_oracle(lib, geom, Lx, Ly, Lz, per, band):
     (dict(geometry=3, Lx=6, Ly=6, Lz=3), "even length"),
     (dict(geometry=3, Lx=6, Ly=6, Lz=2), "even length"),
     (dict(geometry=2, Lx=4, Ly=4, Lz=0), ">= 1"),
-    (dict(geometry=3, Lx=40, Ly=40, Lz=4), "band half-width"),
+    (dict(geometry=3, Lx=48, Ly=48, Lz=4), "band half-width"),     # b = 192 > 166
 ])
 def test_invalid_three_dimensional_lattices(lib, over, frag):
     p = hf.make_params(wl.CONFIGS["square6"], **over)
