@@ -26,8 +26,8 @@
 // A single packed symmetric window of b + 1 slots in shared memory (index i in slot i mod (b+1))
 // holds the active trailing block of the factorisation and then the window of Z; L and D go to
 // global memory once and are read back once.  A narrow band (b <= kNarrowBand) takes one warp per
-// matrix; a wide one a block of kWideThreads, so that the four schedulers of an SM all issue FP64
-// work (this GPU executes 2 FP64 FMA lanes per clock per SM).
+// matrix; a wide one a block with a thread per window row (at least two warps), so that several
+// schedulers of an SM issue FP64 work (this GPU executes 2 FP64 FMA lanes per clock per SM).
 #include <algorithm>
 
 #include "hf_internal.cuh"
@@ -37,8 +37,6 @@ namespace hfk {
 namespace {
 
 constexpr int kNarrowBand = 32;
-constexpr int kWideThreads = 128;
-constexpr int kWideWarps = kWideThreads / 32;
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
     return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
@@ -93,32 +91,43 @@ __device__ __forceinline__ double2 m_entry(const LatticeArgs& A, int i, int j, i
     return make_double2(-A.h0band[static_cast<size_t>(j) * (A.b + 1) + (i - j)], 0.0);
 }
 
-template <int WPM>
+template <bool kBlock>
 __device__ __forceinline__ void mat_sync() {
-    if constexpr (WPM == 1) __syncwarp(); else __syncthreads();
+    if constexpr (kBlock) __syncthreads(); else __syncwarp();
 }
 
-// One matrix per WPM warps (WPM = 1: several matrices per block, one per warp; WPM = 4: one per
-// block).  WPM = 4 spreads rows over the warps and columns over the lanes; WPM = 1 gives each
-// lane whole rows, so that no reductions are needed on the short rows of a narrow band.
-template <int WPM>
-__global__ void __launch_bounds__(128) lattice_kernel(const LatticeArgs A, int q0, int nq) {
+// Slot of index k + d given the slot sk of k (0 <= d < S).
+__device__ __forceinline__ int slot(int sk, int d, int S) {
+    const int v = sk + d;
+    return v >= S ? v - S : v;
+}
+
+// One matrix per warp (kBlock = false; several warps, i.e. matrices, per block) or per block
+// (kBlock = true; blockDim.x threads).  Every thread owns whole rows of the selected-inversion
+// products (no cross-lane sums on the FP64 pipe); the trailing update of the factorisation walks
+// the triangle d2 <= d1 in one flat order shared evenly by the threads; the global loads of the
+// next step (the entering row of M, the next column of L) are issued before the arithmetic of the
+// current one.
+template <bool kBlock>
+__global__ void __launch_bounds__(256) lattice_kernel(const LatticeArgs A, int q0, int nq) {
     extern __shared__ __align__(16) unsigned char smem[];
-    constexpr int T = 32 * WPM;
-    const int tid = threadIdx.x % T;
+    const int T = kBlock ? static_cast<int>(blockDim.x) : 32;
+    const int tid = kBlock ? static_cast<int>(threadIdx.x) : static_cast<int>(threadIdx.x & 31);
+    const int lane = threadIdx.x & 31;
     const int warp = tid >> 5;
-    const int lane = tid & 31;
-    const int mi = threadIdx.x / T;
-    const int qi = blockIdx.x * (blockDim.x / T) + mi;
-    if (qi >= nq) return;      // WPM = 1 only (one matrix per block otherwise)
+    const int mi = kBlock ? 0 : static_cast<int>(threadIdx.x >> 5);
+    const int qi = kBlock ? static_cast<int>(blockIdx.x)
+                          : static_cast<int>(blockIdx.x * (blockDim.x >> 5)) + mi;
+    if (qi >= nq) return;      // one warp of a multi-matrix block; no block barriers follow
     int sp, n;
     item_of(A, q0 + qi, sp, n);
     const int N = A.N, b = A.b, S = A.b + 1;
     const double wn = (2.0 * n + 1.0) * M_PI / A.beta;
     double2* Lg = A.scratch + static_cast<size_t>(qi) * N * S;    // Lg[k*S] = D_k, [k*S+d] = L_{k+d,k}
-    double2* W = reinterpret_cast<double2*>(smem) + static_cast<size_t>(mi) * (S * (S + 1) / 2 + 2 * S);
-    double2* lv = W + S * (S + 1) / 2;                              // [S]
-    double2* vv = lv + S;                                           // [S]
+    double2* W = reinterpret_cast<double2*>(smem) + static_cast<size_t>(mi) * (S * (S + 1) / 2 + 3 * S);
+    double2* lvb = W + S * (S + 1) / 2;   // two columns of L, [S] each (buffer p at lvb + p S)
+    double2* vv = lvb + 2 * S;            // [S]
+    double2* lv = lvb;
     bool bad = false;
 
     // 1. the window starts as the leading (b+1) x (b+1) block of M (slot = index)
@@ -129,7 +138,7 @@ __global__ void __launch_bounds__(128) lattice_kernel(const LatticeArgs A, int q
         while ((i + 1) * (i + 2) / 2 <= t) ++i;
         W[t] = m_entry(A, i, t - i * (i + 1) / 2, sp, n, wn);
     }
-    mat_sync<WPM>();
+    mat_sync<kBlock>();
 
     // 2. band LDL^T, right-looking, on the window
     for (int k = 0; k < N; ++k) {
@@ -138,7 +147,7 @@ __global__ void __launch_bounds__(128) lattice_kernel(const LatticeArgs A, int q
         const double2 Dk = W[wtri(sk, sk)];
         const double2 inv = crecip(Dk);
         for (int d = 1 + tid; d <= dmax; d += T) {
-            const double2 v = W[wtri((k + d) % S, sk)];
+            const double2 v = W[wtri(slot(sk, d, S), sk)];
             const double2 l = cmul(v, inv);
             vv[d] = v;
             lv[d] = l;
@@ -148,68 +157,62 @@ __global__ void __launch_bounds__(128) lattice_kernel(const LatticeArgs A, int q
             Lg[static_cast<size_t>(k) * S] = Dk;
             if (!(fabs(Dk.x) + fabs(Dk.y) > 0.0) || !isfinite(Dk.x) || !isfinite(Dk.y)) bad = true;
         }
-        mat_sync<WPM>();
-        // trailing update M[k+d1][k+d2] -= L_{k+d1,k} v_d2 (1 <= d2 <= d1 <= dmax)
-        if constexpr (WPM == 1) {
-            for (int d1 = 1 + lane; d1 <= dmax; d1 += 32) {
-                const int s1 = (k + d1) % S;
-                const double2 l1 = lv[d1];
-                for (int d2 = 1; d2 <= d1; ++d2) {
-                    double2* t = W + wtri(s1, (k + d2) % S);
-                    *t = cfms(*t, l1, vv[d2]);
-                }
-            }
-        } else {
-            for (int d1 = 1 + warp; d1 <= dmax; d1 += WPM) {
-                const int s1 = (k + d1) % S;
-                const double2 l1 = lv[d1];
-                for (int d2 = 1 + lane; d2 <= d1; d2 += 32) {
-                    double2* t = W + wtri(s1, (k + d2) % S);
-                    *t = cfms(*t, l1, vv[d2]);
-                }
+        mat_sync<kBlock>();
+        // index k + b + 1 enters the slot of k (the load is issued before the update)
+        const int inew = k + S;
+        const int j0 = k + 1 + tid;
+        const bool has_new = inew < N && j0 <= inew;
+        const double2 newv = has_new ? m_entry(A, inew, j0, sp, n, wn) : make_double2(0.0, 0.0);
+        // trailing update M[k+d1][k+d2] -= L_{k+d1,k} v_d2 over the flat triangle
+        // f = d1 (d1 - 1) / 2 + d2 - 1 (1 <= d2 <= d1 <= dmax)
+        const int E = dmax * (dmax + 1) / 2;
+        if (tid < E) {
+            int d1 = static_cast<int>((sqrtf(8.0f * tid + 1.0f) + 1.0f) * 0.5f);
+            while (d1 * (d1 - 1) / 2 > tid) --d1;
+            while (d1 * (d1 + 1) / 2 <= tid) ++d1;
+            int d2 = tid - d1 * (d1 - 1) / 2 + 1;
+            for (int f = tid; f < E; f += T) {
+                double2* t = W + wtri(slot(sk, d1, S), slot(sk, d2, S));
+                *t = cfms(*t, lv[d1], vv[d2]);
+                d2 += T;
+                while (d2 > d1) { d2 -= d1; ++d1; }
             }
         }
-        // index k + b + 1 enters the slot of k: its row of the unfactored matrix
-        const int inew = k + S;
-        if (inew < N)
-            for (int j = k + 1 + tid; j <= inew; j += T) W[wtri(sk, j % S)] = m_entry(A, inew, j, sp, n, wn);
-        mat_sync<WPM>();
+        if (has_new) W[wtri(sk, j0 % S)] = newv;
+        for (int j = j0 + T; j <= inew && inew < N; j += T) W[wtri(sk, j % S)] = m_entry(A, inew, j, sp, n, wn);
+        mat_sync<kBlock>();
     }
 
-    // 3. selected inversion, k = N-1 .. 0; the window now holds Z for the indices in (k, k+b]
+    // 3. selected inversion, k = N-1 .. 0; the window now holds Z for the indices in (k, k+b].
+    // buffer k & 1 holds column k of L (entry 0: D_k), the other one receives column k - 1.
+    if (tid == 0) lvb[((N - 1) & 1) * S] = Lg[static_cast<size_t>(N - 1) * S];
+    mat_sync<kBlock>();
     for (int k = N - 1; k >= 0; --k) {
         const int dmax = min(b, N - 1 - k);
         const int sk = k % S;
-        for (int e = 1 + tid; e <= dmax; e += T) lv[e] = Lg[static_cast<size_t>(k) * S + e];
-        mat_sync<WPM>();
-        // Z_{k+d,k} = -sum_e Z_{k+d,k+e} L_{k+e,k}
-        if constexpr (WPM == 1) {
-            for (int d = 1 + lane; d <= dmax; d += 32) {
-                const int s1 = (k + d) % S;
-                double2 acc = make_double2(0.0, 0.0);
-                for (int e = 1; e <= dmax; ++e) acc = cfms(acc, W[wtri(s1, (k + e) % S)], lv[e]);
-                vv[d] = acc;
+        const double2* cur = lvb + (k & 1) * S;
+        double2* nxt = lvb + ((k + 1) & 1) * S;
+        const int dprev = min(b, N - k);           // dmax of step k - 1
+        const bool has_pre = k > 0 && tid <= dprev;
+        const double2 pre = has_pre ? Lg[static_cast<size_t>(k - 1) * S + tid] : make_double2(0.0, 0.0);
+        // Z_{k+d,k} = -sum_e Z_{k+d,k+e} L_{k+e,k}, one row per thread
+        for (int d = 1 + tid; d <= dmax; d += T) {
+            const int s1 = slot(sk, d, S);
+            double2 a0 = make_double2(0.0, 0.0), a1 = make_double2(0.0, 0.0);
+            int e = 1;
+            for (; e + 1 <= dmax; e += 2) {
+                a0 = cfms(a0, W[wtri(s1, slot(sk, e, S))], cur[e]);
+                a1 = cfms(a1, W[wtri(s1, slot(sk, e + 1, S))], cur[e + 1]);
             }
-        } else {
-            for (int d = 1 + warp; d <= dmax; d += WPM) {
-                const int s1 = (k + d) % S;
-                double2 acc = make_double2(0.0, 0.0);
-                for (int e = 1 + lane; e <= dmax; e += 32) acc = cfms(acc, W[wtri(s1, (k + e) % S)], lv[e]);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const double2 t = shfl_xor_c(acc, o);
-                    acc.x += t.x;
-                    acc.y += t.y;
-                }
-                if (lane == 0) vv[d] = acc;
-            }
+            if (e <= dmax) a0 = cfms(a0, W[wtri(s1, slot(sk, e, S))], cur[e]);
+            vv[d] = make_double2(a0.x + a1.x, a0.y + a1.y);
         }
-        mat_sync<WPM>();
+        mat_sync<kBlock>();
         // row/column k into the slot of k (which held k + b + 1, outside every later window)
-        for (int d = 1 + tid; d <= dmax; d += T) W[wtri(sk, (k + d) % S)] = vv[d];
+        for (int d = 1 + tid; d <= dmax; d += T) W[wtri(sk, slot(sk, d, S))] = vv[d];
         if (warp == 0) {
             double2 part = make_double2(0.0, 0.0);
-            for (int d = 1 + lane; d <= dmax; d += 32) part = cfms(part, lv[d], vv[d]);
+            for (int d = 1 + lane; d <= dmax; d += 32) part = cfms(part, cur[d], vv[d]);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 const double2 t = shfl_xor_c(part, o);
@@ -217,21 +220,28 @@ __global__ void __launch_bounds__(128) lattice_kernel(const LatticeArgs A, int q
                 part.y += t.y;
             }
             if (lane == 0) {
-                const double2 ri = crecip(Lg[static_cast<size_t>(k) * S]);
+                const double2 ri = crecip(cur[0]);
                 const double2 zkk = make_double2(ri.x + part.x, ri.y + part.y);
                 W[wtri(sk, sk)] = zkk;
                 store_diag(A, k, sp, n, zkk);
                 if (!isfinite(zkk.x) || !isfinite(zkk.y)) bad = true;
             }
         }
-        mat_sync<WPM>();
+        if (has_pre) nxt[tid] = pre;
+        if (k > 0)
+            for (int e = tid + T; e <= dprev; e += T) nxt[e] = Lg[static_cast<size_t>(k - 1) * S + e];
+        mat_sync<kBlock>();
     }
     if (bad) atomicExch(A.status, static_cast<int>(HF_ENUMERIC));
 }
 
-size_t window_bytes(int b) {     // one matrix: packed window and two vectors
+size_t window_bytes(int b) {     // one matrix: packed window and three vectors
     const size_t S = static_cast<size_t>(b) + 1;
-    return (S * (S + 1) / 2 + 2 * S) * sizeof(double2);
+    return (S * (S + 1) / 2 + 3 * S) * sizeof(double2);
+}
+
+int block_threads(int b) {       // one thread per row of the window, at least two warps
+    return std::min(256, std::max(64, 32 * ((b + 31) / 32)));
 }
 
 }  // namespace
@@ -255,17 +265,17 @@ cudaError_t launch_lattice(const LatticeArgs& a, int q0, int nq, cudaStream_t st
     if (!lattice_band_supported(a.b)) return cudaErrorInvalidValue;
     const size_t smem = window_bytes(a.b);
     if (a.b > kNarrowBand) {
-        cudaError_t e = cudaFuncSetAttribute(lattice_kernel<kWideWarps>,
+        cudaError_t e = cudaFuncSetAttribute(lattice_kernel<true>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(smem));
         if (e != cudaSuccess) return e;
-        lattice_kernel<kWideWarps><<<nq, kWideThreads, smem, st>>>(a, q0, nq);
+        lattice_kernel<true><<<nq, block_threads(a.b), smem, st>>>(a, q0, nq);
         return cudaGetLastError();
     }
-    cudaError_t e = cudaFuncSetAttribute(lattice_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(lattice_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    lattice_kernel<1><<<nq, 32, smem, st>>>(a, q0, nq);
+    lattice_kernel<false><<<nq, 32, smem, st>>>(a, q0, nq);
     return cudaGetLastError();
 }
 
