@@ -26,8 +26,8 @@
 // A single packed symmetric window of b + 1 slots in shared memory (index i in slot i mod (b+1))
 // holds the active trailing block of the factorisation and then the window of Z; L and D go to
 // global memory once and are read back once.  A narrow band (b <= kNarrowBand) takes one warp per
-// matrix; a wide one a block with a thread per window row (at least two warps), so that several
-// schedulers of an SM issue FP64 work (this GPU executes 2 FP64 FMA lanes per clock per SM).
+// matrix; a wide one a block with two threads per window row, so that every scheduler of the SM
+// has two warps issuing FP64 work (this GPU executes 2 FP64 FMA lanes per clock per SM).
 #include <algorithm>
 
 #include "hf_internal.cuh"
@@ -103,13 +103,14 @@ __device__ __forceinline__ int slot(int sk, int d, int S) {
 }
 
 // One matrix per warp (kBlock = false; several warps, i.e. matrices, per block) or per block
-// (kBlock = true; blockDim.x threads).  Every thread owns whole rows of the selected-inversion
-// products (no cross-lane sums on the FP64 pipe); the trailing update of the factorisation walks
-// the triangle d2 <= d1 in one flat order shared evenly by the threads; the global loads of the
-// next step (the entering row of M, the next column of L) are issued before the arithmetic of the
-// current one.
+// (kBlock = true; blockDim.x threads).  The selected-inversion products go a row per thread (warp
+// form) or per pair of adjacent lanes (block form: two threads per window row, so two warps per
+// scheduler), with no cross-lane sums on the FP64 pipe beyond one per row; the trailing update of
+// the factorisation walks the triangle d2 <= d1 in one flat order shared evenly by the threads;
+// the global loads of the next step (the entering row of M, the next column of L) are issued
+// before the arithmetic of the current one.
 template <bool kBlock>
-__global__ void __launch_bounds__(256) lattice_kernel(const LatticeArgs A, int q0, int nq) {
+__global__ void __launch_bounds__(384, 1) lattice_kernel(const LatticeArgs A, int q0, int nq) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int T = kBlock ? static_cast<int>(blockDim.x) : 32;
     const int tid = kBlock ? static_cast<int>(threadIdx.x) : static_cast<int>(threadIdx.x & 31);
@@ -195,17 +196,40 @@ __global__ void __launch_bounds__(256) lattice_kernel(const LatticeArgs A, int q
         const int dprev = min(b, N - k);           // dmax of step k - 1
         const bool has_pre = k > 0 && tid <= dprev;
         const double2 pre = has_pre ? Lg[static_cast<size_t>(k - 1) * S + tid] : make_double2(0.0, 0.0);
-        // Z_{k+d,k} = -sum_e Z_{k+d,k+e} L_{k+e,k}, one row per thread
-        for (int d = 1 + tid; d <= dmax; d += T) {
-            const int s1 = slot(sk, d, S);
-            double2 a0 = make_double2(0.0, 0.0), a1 = make_double2(0.0, 0.0);
-            int e = 1;
-            for (; e + 1 <= dmax; e += 2) {
-                a0 = cfms(a0, W[wtri(s1, slot(sk, e, S))], cur[e]);
-                a1 = cfms(a1, W[wtri(s1, slot(sk, e + 1, S))], cur[e + 1]);
+        // Z_{k+d,k} = -sum_e Z_{k+d,k+e} L_{k+e,k}: a row per thread (warp form) or per pair of
+        // adjacent lanes, each summing alternate e (block form: two warps per scheduler)
+        if constexpr (kBlock) {
+            // rows r0 + lane / 2 of this warp; the loop bound is uniform over the warp, so every
+            // lane reaches the pair shuffle (lanes past dmax contribute nothing)
+            const int h = lane & 1;
+            for (int r0 = (tid - lane) >> 1; r0 < dmax; r0 += (T >> 1)) {
+                const int d = r0 + (lane >> 1) + 1;
+                double2 a0 = make_double2(0.0, 0.0), a1 = a0;
+                if (d <= dmax) {
+                    const int s1 = slot(sk, d, S);
+                    int e = 1 + h;
+                    for (; e + 2 <= dmax; e += 4) {
+                        a0 = cfms(a0, W[wtri(s1, slot(sk, e, S))], cur[e]);
+                        a1 = cfms(a1, W[wtri(s1, slot(sk, e + 2, S))], cur[e + 2]);
+                    }
+                    if (e <= dmax) a0 = cfms(a0, W[wtri(s1, slot(sk, e, S))], cur[e]);
+                }
+                const double2 a = make_double2(a0.x + a1.x, a0.y + a1.y);
+                const double2 o = shfl_xor_c(a, 1);
+                if (h == 0 && d <= dmax) vv[d] = make_double2(a.x + o.x, a.y + o.y);
             }
-            if (e <= dmax) a0 = cfms(a0, W[wtri(s1, slot(sk, e, S))], cur[e]);
-            vv[d] = make_double2(a0.x + a1.x, a0.y + a1.y);
+        } else {
+            for (int d = 1 + tid; d <= dmax; d += T) {
+                const int s1 = slot(sk, d, S);
+                double2 a0 = make_double2(0.0, 0.0), a1 = a0;
+                int e = 1;
+                for (; e + 1 <= dmax; e += 2) {
+                    a0 = cfms(a0, W[wtri(s1, slot(sk, e, S))], cur[e]);
+                    a1 = cfms(a1, W[wtri(s1, slot(sk, e + 1, S))], cur[e + 1]);
+                }
+                if (e <= dmax) a0 = cfms(a0, W[wtri(s1, slot(sk, e, S))], cur[e]);
+                vv[d] = make_double2(a0.x + a1.x, a0.y + a1.y);
+            }
         }
         mat_sync<kBlock>();
         // row/column k into the slot of k (which held k + b + 1, outside every later window)
@@ -240,8 +264,8 @@ size_t window_bytes(int b) {     // one matrix: packed window and three vectors
     return (S * (S + 1) / 2 + 3 * S) * sizeof(double2);
 }
 
-int block_threads(int b) {       // one thread per row of the window, at least two warps
-    return std::min(256, std::max(64, 32 * ((b + 31) / 32)));
+int block_threads(int b) {       // two threads per row of the window
+    return 64 * ((b + 31) / 32);
 }
 
 }  // namespace
