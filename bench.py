@@ -740,6 +740,66 @@ def run_lattice3d(args):
     return 0
 
 
+def run_entropy6(args):
+    """Entropy from dS/dmu = dN/dT on the 6x6 trap at U = 4, T = 0.5 (beta = 2, L = 8): RDMFT runs
+    at T -+ 0.05 on 41 chemical potentials from -10 (empty trap) to 2 (half filling at the centre),
+    6 iterations each, in fused batches of 8 runs; one step = the whole scan.  Timed on the host
+    clock (context set-up included, as a user of the scan sees it)."""
+    import numpy as np
+    import torch
+
+    from paper_1006_2716_gb300 import hf, thermo
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    cfg = dict(wl.CONFIGS["square6"], U=4.0, precision=2, chains_per_site=8, n_warmup=200,
+               n_measure=800, bin_size=100)
+    T, dT, L, iters = 0.5, 0.05, 8, 6
+    mus = np.linspace(-10.0, 2.0, 41)
+    _, ns, _, _, rep, _, _ = hf.hf_lattice_info(hf.make_params(cfg))
+    sweeps = cfg["n_warmup"] + cfg["n_measure"]
+    proposals = 2 * len(mus) * iters * ns * cfg["chains_per_site"] * sweeps * L
+    # launches of one scan: per batch of nb runs and iteration, nb x (lattice, Weiss/tau, g0^-1,
+    # reduction, self-energy) and one fused sweep launch; one field initialisation per run
+    runs = 2 * len(mus)
+    sizes = [min(8, runs - b) for b in range(0, runs, 8)]
+    launches = sum(iters * ((lattice_launches(hf, cfg) + 4) * nb + 1) + nb for nb in sizes)
+    # centre of the bond-centred square: the orbit closest to the trap centre
+    c = (cfg["Lx"] - 1) / 2.0
+    centre = int(np.argmin([(r % cfg["Lx"] - c) ** 2 + (r // cfg["Lx"] - c) ** 2 for r in rep]))
+    for _ in range(max(0, args.warmup)):
+        thermo.entropy_scan(cfg, T, dT, mus[:3], L, 1, device=dev)
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    times, res = [], None
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        res = thermo.entropy_scan(cfg, T, dT, mus, L, iters, device=dev)
+        torch.cuda.synchronize(dev)
+        times.append(time.perf_counter() - t0)
+    clk = clocks.stop()
+    wall = statistics.mean(times)
+    line = {"metric": METRIC, "value": proposals / wall, "unit": "proposals/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32x2+f64", "data": "synthetic",
+            "config": {"workload": "entropy6: 6x6 trap, U=4, V0=0.1, T=0.5 -+ 0.05 (beta ~2, L=8), "
+                                   "41 mu in [-10, 2], 6 RDMFT iterations per point, 8 chains per "
+                                   "site, 200+800 sweeps; one step = the whole scan (82 runs)",
+                       "timing": "host clock around the scan, context set-up included"},
+            "scan_points_per_s": 2 * len(mus) / wall,
+            "entropy": {"mu": float(res["mu"][-1]), "S": float(res["S"][-1]),
+                        "N": float(res["N"][-1]), "S_per_particle": float(res["S"][-1] / res["N"][-1]),
+                        "centre_site_entropy": float(res["s_site"][centre, -1]),
+                        "centre_site_density": float(res["n_site"][-1, centre])},
+            "gpu_launches": launches * args.steps, "cpu_baseline": None, "clocks": clk}
+    print(json.dumps(line))
+    return 0
+
+
 def run_square30(args):
     """Mixed precision on the 30x30 trap (120 inequivalent sites x 16 chains, L = 128): FP32
     sweeps with FP32 accumulation, an FP64 Dyson refresh (and the measurement) after every
@@ -1057,7 +1117,7 @@ def main():
                          "-1 (default): the autotuner picks form and team width")
     ap.add_argument("--workload", default="square20",
                     choices=["square20", "scan20", "square30", "disc40", "dtau_scan", "slab16",
-                             "box12"])
+                             "box12", "entropy6"])
     ap.add_argument("--refresh-stagger", type=int, default=0, choices=[0, 1],
                     help="1: per-chain refresh phases; 0 (default): every chain refreshes on the "
                          "same sweeps")
@@ -1076,6 +1136,8 @@ def main():
         return run_disc40(args)
     if args.workload == "square30":
         return run_square30(args)
+    if args.workload == "entropy6":
+        return run_entropy6(args)
     if args.workload in ("slab16", "box12"):
         return run_lattice3d(args)
     if args.workload == "dtau_scan":
