@@ -800,6 +800,82 @@ def run_entropy6(args):
     return 0
 
 
+def run_fig1(args):
+    """Physics cross-check with the parameters of the paper's Fig. 1 (square lattice, V0 = 0.25,
+    U = 10, dtau = 0.1): a site-centred 17x17 trap half filled at its centre (mu = U/2), converged
+    RDMFT (mixing 0.5 from the staggered seed field) at T = 0.156, 0.25 and 0.5 (L = 64, 40, 20).
+    Reports the radial profiles of density, double occupancy and staggered moment, and the
+    paper's statements: a core polarised up to 90% at low T, no order above T_N ~ 0.32, a double
+    occupancy near 0.02 at the centre at high T that the AF core enhances by up to 50%, and a
+    density that hardly changes with T.  One step = all three runs."""
+    import numpy as np
+    import torch
+
+    from paper_1006_2716_gb300 import hf
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    base = dict(wl.CONFIGS["square20"], Lx=17, Ly=17, U=10.0, V0=0.25, mu=5.0, dtau=0.1,
+                chains_per_site=16, precision=2, h_seed=0.1, mix=0.5)
+    runs = ((0.15625, 64), (0.25, 40), (0.5, 20))
+    iters = args.iterations
+    _, ns, _, _, rep, _, _ = hf.hf_lattice_info(hf.make_params(dict(base, beta=6.4)))
+    c = 8.0
+    r = np.sqrt([(q % 17 - c) ** 2 + (q // 17 - c) ** 2 for q in rep])
+    parity = np.array([1 if ((q % 17) + (q // 17)) % 2 == 0 else -1 for q in rep])
+    order = np.argsort(r, kind="stable")
+    clocks = ClockSampler(local)
+    t0 = time.perf_counter()
+    prof, proposals = {}, 0
+    for T, L in runs:
+        cfg = dict(base, beta=1.0 / T)
+        ctx = hf.Context(hf.make_params(cfg), device=dev, stream=stream)
+        for _ in range(iters):
+            hf.hf_rdmft_step(ctx.handle)
+        mean, err = hf.hf_get_observables(ctx.handle, ns, L)
+        n = mean[:, 2 * L] + mean[:, 2 * L + 1]
+        d, m = mean[:, 2 * L + 2], mean[:, 2 * L + 3]
+        prof[T] = {"n": n, "d": d, "d_err": err[:, 2 * L + 2], "m_stag": m * parity}
+        proposals += ctx.n_chains * (cfg["n_warmup"] + cfg["n_measure"]) * L * iters
+        ctx.close()
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    lo, mid, hi = (prof[T] for T, _ in runs)
+    ctr = int(order[0])
+    core = r <= 3.0
+    checks = {
+        "centre_polarisation_T0.156": float(abs(lo["m_stag"][ctr]) / lo["n"][ctr]),
+        "centre_polarisation_T0.5": float(abs(hi["m_stag"][ctr]) / hi["n"][ctr]),
+        "max_abs_m_stag_T0.5": float(np.abs(hi["m_stag"]).max()),
+        "centre_double_occupancy_T0.5": float(hi["d"][ctr]),
+        "max_double_occupancy_T0.5": float(hi["d"].max()),
+        "core_double_occupancy_enhancement_T0.156_vs_T0.5": float(lo["d"][core].mean() / hi["d"][core].mean()),
+        "max_density_change_T0.156_vs_T0.5": float(np.abs(lo["n"] - hi["n"]).max()),
+    }
+    line = {"metric": METRIC, "value": proposals / wall, "unit": "proposals/s", "n_gpus": 1,
+            "steps": 1, "warmup": 0, "ms_per_step": wall * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32x2+f64", "data": "synthetic",
+            "config": {"workload": "fig1: site-centred 17x17 square trap, U=10, V0=0.25, mu=5, "
+                                   "dtau=0.1, T = 0.156/0.25/0.5 (L = 64/40/20), 45 inequivalent "
+                                   "sites x 16 chains, %d RDMFT iterations per temperature, "
+                                   "500+2000 sweeps" % iters,
+                       "timing": "host clock around the three runs"},
+            "checks": checks,
+            "profiles": {str(T): {"r": [float(x) for x in r[order]],
+                                  "n": [float(x) for x in prof[T]["n"][order]],
+                                  "d": [float(x) for x in prof[T]["d"][order]],
+                                  "m_stag": [float(x) for x in prof[T]["m_stag"][order]]}
+                         for T, _ in runs},
+            "gpu_launches": None, "cpu_baseline": None, "clocks": clk}
+    print(json.dumps(line))
+    return 0
+
+
 def run_square30(args):
     """Mixed precision on the 30x30 trap (120 inequivalent sites x 16 chains, L = 128): FP32
     sweeps with FP32 accumulation, an FP64 Dyson refresh (and the measurement) after every
@@ -1117,7 +1193,7 @@ def main():
                          "-1 (default): the autotuner picks form and team width")
     ap.add_argument("--workload", default="square20",
                     choices=["square20", "scan20", "square30", "disc40", "dtau_scan", "slab16",
-                             "box12", "entropy6"])
+                             "box12", "entropy6", "fig1"])
     ap.add_argument("--refresh-stagger", type=int, default=0, choices=[0, 1],
                     help="1: per-chain refresh phases; 0 (default): every chain refreshes on the "
                          "same sweeps")
@@ -1125,6 +1201,8 @@ def main():
                     help="disc40: requests per Poisson load level")
     ap.add_argument("--no-fp64-form", action="store_true",
                     help="skip the plain FP64 form measured beside the chosen form")
+    ap.add_argument("--iterations", type=int, default=20,
+                    help="fig1: RDMFT iterations per temperature")
     ap.add_argument("--sweeps", type=int, default=0,
                     help="profiling only: override sweeps per iteration (result is not a bench value)")
     args = ap.parse_args()
@@ -1136,6 +1214,8 @@ def main():
         return run_disc40(args)
     if args.workload == "square30":
         return run_square30(args)
+    if args.workload == "fig1":
+        return run_fig1(args)
     if args.workload == "entropy6":
         return run_entropy6(args)
     if args.workload in ("slab16", "box12"):
