@@ -458,12 +458,16 @@ __device__ void df_chain(const QmcProblem& P, int c, unsigned char* base, int ti
             }
             if (accept) {
                 // f_sigma = a_sigma / R_sigma in double-float
-                const float2 au2 = (sl > 0) ? a_p : a_m;
-                const float2 ad2 = (sl > 0) ? a_m : a_p;
-                const float2 Ru = df_add(one, df_mul(df_add(one, df_neg(g0)), au2));
-                const float2 Rd = df_add(one, df_mul(df_add(one, df_neg(g1)), ad2));
-                const float2 fu = df_mul(au2, df_recip(Ru));
-                const float2 fd = df_mul(ad2, df_recip(Rd));
+                // lanes 0-15 take spin up, lanes 16-31 spin down (the same arithmetic for both,
+                // half the instructions), then every lane reads both from the warp
+                const bool dn = (tid & 16) != 0;
+                const float2 as = (sl > 0) != dn ? a_p : a_m;
+                const float2 Rs = df_add(one, df_mul(df_add(one, df_neg(dn ? g1 : g0)), as));
+                const float2 fs = df_mul(as, df_recip(Rs));
+                const float2 fu = make_float2(__shfl_sync(0xffffffffu, fs.x, 0),
+                                              __shfl_sync(0xffffffffu, fs.y, 0));
+                const float2 fd = make_float2(__shfl_sync(0xffffffffu, fs.x, 16),
+                                              __shfl_sync(0xffffffffu, fs.y, 16));
                 if constexpr (DLY) {
 #ifdef HF_DEBUG_SMEM
                     if (m < 0 || m >= K) {   // self-check: append slot inside the buffers
