@@ -339,9 +339,12 @@ DF_OPS_PER_FMA = 12          # FP32-pipe ops of one double-float multiply-add (l
 # DRAM bytes (read + write) of one full-size launch (2500 sweeps of all 1760 chains), from one
 # ncu capture of the kernel built from sources with this sha256 prefix (profiles/
 # qmc_df64_kernel_square20.md); a kernel whose sources changed since reports null.
-MEASURED_TRAFFIC = {"qmc_df64_kernel": (2.362e6 + 1.325e6, "27a5cb76a243bebd")}
+MEASURED_TRAFFIC = {"qmc_df64_kernel": (2.628e6 + 1.452e6, "f0ade2fccbd67061"),
+                    # the lattice step of the slab16 workload (N = 1024, b = 128, 500 matrices)
+                    "lattice_kernel:slab16": (652.3e6 + 947.5e6, "bce118bbe49681e3")}
 KERNEL_SOURCES = {"qmc_df64_kernel": ("k_qmc_df64.cu", "qmc_common.cuh", "hf_internal.cuh"),
-                  "qmc_f64_kernel": ("k_qmc_f64.cu", "qmc_common.cuh", "hf_internal.cuh")}
+                  "qmc_f64_kernel": ("k_qmc_f64.cu", "qmc_common.cuh", "hf_internal.cuh"),
+                  "lattice_kernel:slab16": ("k_lattice.cu", "k_lattice.cuh", "hf_internal.cuh")}
 
 
 def measured_traffic(kernel):
@@ -707,7 +710,8 @@ def run_lattice3d(args):
     fl = lattice_flops(N, b, nspin, nw)
     lat_s = phase[0] / 1e3
     lroof = {"bound": "alu", "achieved": fl / lat_s / 1e12, "peak": FP64_PEAK_TFLOPS,
-             "unit": "TFLOP/s", "frac": fl / lat_s / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
+             "unit": "TFLOP/s", "frac": fl / lat_s / 1e12 / FP64_PEAK_TFLOPS,
+             "traffic": measured_traffic("lattice_kernel:" + name),
              "kernel": "lattice_kernel", "matrices": nspin * nw, "N": N, "band": b,
              "peak_source": "FP64 nominal: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz"}
     dominant = lroof if phase[0] > phase[2] else qroof
