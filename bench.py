@@ -834,7 +834,7 @@ def run_fig1(args):
     order = np.argsort(r, kind="stable")
     clocks = ClockSampler(local)
     t0 = time.perf_counter()
-    prof, proposals = {}, 0
+    prof, proposals, launches = {}, 0, 0
     for T, L in runs:
         cfg = dict(base, beta=1.0 / T)
         ctx = hf.Context(hf.make_params(cfg), device=dev, stream=stream)
@@ -845,6 +845,9 @@ def run_fig1(args):
         d, m = mean[:, 2 * L + 2], mean[:, 2 * L + 3]
         prof[T] = {"n": n, "d": d, "d_err": err[:, 2 * L + 2], "m_stag": m * parity}
         proposals += ctx.n_chains * (cfg["n_warmup"] + cfg["n_measure"]) * L * iters
+        # per iteration: lattice step, Weiss/tau, g0^-1, sweeps, reduction, self-energy; one
+        # field initialisation per run
+        launches += iters * (lattice_launches(hf, cfg) + 5) + 1
         ctx.close()
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - t0
@@ -875,7 +878,7 @@ def run_fig1(args):
                                   "d": [float(x) for x in prof[T]["d"][order]],
                                   "m_stag": [float(x) for x in prof[T]["m_stag"][order]]}
                          for T, _ in runs},
-            "gpu_launches": None, "cpu_baseline": None, "clocks": clk}
+            "gpu_launches": launches, "cpu_baseline": None, "clocks": clk}
     print(json.dumps(line))
     return 0
 

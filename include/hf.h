@@ -99,10 +99,14 @@ hf_status hf_workspace_size(const hf_params* p, size_t* bytes);
 hf_status hf_lattice_info(const hf_params* p, int* N, int* n_sites, int* band, int* spins, int* rep,
                           int* rep_of, int* flip);
 
-/* Validate *p, build the lattice (eq. 1) and its C4v orbits, lay the state out in the
- * caller's device workspace d_ws (ws_bytes >= hf_workspace_size), draw the initial Ising
- * fields of every chain and seed Sigma_{i,sigma}(i w_n) = U/2 - sigma h_seed eps_i.
- * *out receives a host handle released by hf_free. */
+/* Validate *p, build the lattice (eq. 1) and its point-group orbits (C4v in two dimensions,
+ * the cubic group for the box, the planar group with the layer translations for the slab), lay
+ * the state out in the caller's device workspace d_ws (ws_bytes >= hf_workspace_size), draw the
+ * initial Ising fields of every chain and seed Sigma_{i,sigma}(i w_n) = U/2 - sigma h_seed
+ * eps_i.  *out receives a host handle released by hf_free.  HF_EINVAL for invalid parameters,
+ * including a lattice whose band half-width in the lattice step's band order (periodic axes
+ * folded) exceeds 165, the largest window the step keeps in shared memory; HF_ENOMEM for a
+ * workspace smaller than hf_workspace_size. */
 hf_status hf_init(const hf_params* p, void* d_ws, size_t ws_bytes, hf_ctx** out);
 
 /* Number of inequivalent sites, chains, L, lattice sites N (any pointer may be NULL). */

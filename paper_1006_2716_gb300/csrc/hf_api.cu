@@ -1,9 +1,10 @@
 // hf_api.cu -- C ABI of the Hirsch-Fye QMC / RDMFT library (declared in include/hf.h).
 //
-// Host side of one context: validates parameters, builds the trapped lattice of eq. 1 and its
-// C4v orbits, lays the device state out inside the caller's workspace and sequences the
-// kernels of one RDMFT iteration ("Model and Methods": lattice step per Matsubara frequency,
-// one impurity problem per inequivalent site, many Markov chains per impurity).
+// Host side of one context: validates parameters, builds the trapped lattice of eq. 1 (square,
+// disc, box or slab) and its point-group orbits, lays the device state out inside the caller's
+// workspace and sequences the kernels of one RDMFT iteration ("Model and Methods": lattice step
+// per Matsubara frequency, one impurity problem per inequivalent site, many Markov chains per
+// impurity).
 #include <cmath>
 #include <cstdio>
 #include <cstring>
