@@ -29,6 +29,8 @@ CASES = [
     (3, 6, 6, 4, 0, 24),
     (3, 8, 6, 4, 1, 64),
     (3, 24, 24, 4, 0, 96),
+    (2, 12, 12, 12, 0, 144),
+    (3, 20, 20, 4, 1, 160),
 ]
 
 
@@ -61,3 +63,21 @@ def test_invalid_three_dimensional_lattices(lib, over, frag):
         hf.hf_lattice_info(p)
     assert e.value.status == hf.HF_EINVAL
     assert frag in str(e.value)
+
+
+def test_bench_lattice_bookkeeping(lib):
+    """bench.py's launch count and algorithmic flop count of the lattice step: one launch per
+    iteration while the band buffers of all matrices fit in 1 GiB; for a dense band (b >= N - 1)
+    the count is the textbook one, N^3/6 multiply-adds for LDL^T plus N^3/3 for the selected
+    inversion to leading order (exactly sum_d [d(d+1)/2 + d^2 + d], d = 0..N-1)."""
+    import bench
+
+    assert bench.lattice_launches(hf, wl.CONFIGS["square20"]) == 1
+    assert bench.lattice_launches(hf, wl.CONFIGS["slab16"]) == 1
+    # 12^3 box: 500 matrices of 1728 x 145 x 16 bytes = 2.0 GB -> two launches
+    assert bench.lattice_launches(hf, wl.CONFIGS["box12"]) == 2
+    N = 40
+    exact = 8.0 * sum(d * (d + 1) // 2 + d * d + d for d in range(N))
+    assert bench.lattice_flops(N, N - 1, 1, 1) == exact
+    assert bench.lattice_flops(N, 100, 2, 3) == 6 * exact
+    assert abs(bench.lattice_flops(400, 399, 1, 1) / (8 * 400 ** 3 / 2) - 1) < 0.01
