@@ -72,6 +72,9 @@ typedef struct hf_params {
                          /* Philox counter words), so the FP64 refreshes of chains that run  */
                          /* side by side fall on different sweeps; needs precision 0 or 2    */
                          /* unless refresh_every is 1                                       */
+    int check_drift;     /* 1: at every refresh within a sweep launch, measure how far the    */
+                         /* updated G has drifted from the Dyson solution that replaces it   */
+                         /* (hf_get_drift); 0: off.  The chains' arithmetic is unchanged     */
     int delay_k;         /* delayed-update depth: 0/1 rank-1 Sherman-Morrison; 4, 8, 16, 32  */
                          /* (precision 2, one warp per chain): accepted flips gathered as    */
                          /* rank-k corrections                                              */
@@ -131,7 +134,8 @@ hf_status hf_set_g0(hf_ctx* ctx, int site, int spin, const double* g0_tau);
  * when it is a multiple of refresh_every; measured sweeps then add to the current bin. */
 hf_status hf_sweep(hf_ctx* ctx, int n_warmup, int n_measure, int refresh_first);
 
-/* Zero all measurement bins and counters (the next measured sweep starts bin 0). */
+/* Zero all measurement bins and counters (the next measured sweep starts bin 0) and the drift
+ * monitor. */
 hf_status hf_clear_measurements(hf_ctx* ctx);
 
 /* Reduce the completed bins of every chain of one inequivalent site (synchronises):
@@ -179,6 +183,14 @@ hf_status hf_set_fields(hf_ctx* ctx, const signed char* fields, const uint32_t* 
  * [n_chains]. */
 hf_status hf_get_green(hf_ctx* ctx, int chain, double* G);
 hf_status hf_get_accepts(hf_ctx* ctx, unsigned long long* accepts);
+
+/* Numerical-drift monitor (hf_params.check_drift = 1): the largest max_ij |G_SM - G_Dyson| over
+ * every chain, spin and refresh inside the sweep launches since the last
+ * hf_clear_measurements, where G_SM is the state the Sherman-Morrison updates reached and G_Dyson
+ * the FP64 Dyson solution that replaces it (both as stored: FP64, FP32 pairs or FP32), and the
+ * number of chain refreshes checked.  The refresh at the start of a launch is not checked (the
+ * bath may have changed).  Either pointer may be NULL.  Synchronises. */
+hf_status hf_get_drift(hf_ctx* ctx, double* max_drift, unsigned long long* refreshes);
 
 /* Waits for the context stream and reports any failure the device recorded (numerical, or a
  * self-check of a checking build).  */

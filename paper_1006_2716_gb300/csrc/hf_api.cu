@@ -253,7 +253,7 @@ struct hf_ctx {
     uint32_t* nmeas_d = nullptr;    // [nchain]
     unsigned long long* acc = nullptr;  // [nchain]
     double* bins = nullptr;         // [nchain][max_bins][2L+3]
-    int* status = nullptr;          // [4]
+    int* status = nullptr;          // [8]: [0..3] errors and counters, [4..5] drift monitor
     double* obs_mean = nullptr;     // [nsite][2L+4]
     double* obs_err = nullptr;      // [nsite][2L+4]
     double2* sigma = nullptr;       // [nsite][2][nw]
@@ -343,6 +343,7 @@ hf_status validate(const hf_params& p, std::string& err) {
         err = "FP32 sweeps need a periodic FP64 refresh (refresh_every >= 1)";
         return HF_EINVAL;
     }
+    if (!(p.check_drift == 0 || p.check_drift == 1)) { err = "check_drift must be 0 or 1"; return HF_EINVAL; }
     if (!(p.refresh_stagger == 0 || p.refresh_stagger == 1) ||
         (p.refresh_stagger == 1 && p.precision == 1 && p.refresh_every > 1)) {
         err = "refresh_stagger must be 0 or 1; staggered phases need fused refreshes (precision 0 "
@@ -372,7 +373,7 @@ size_t layout(hf_ctx& c, void* base) {
     c.nmeas_d = cv.take<uint32_t>(nc);
     c.acc = cv.take<unsigned long long>(nc);
     c.bins = cv.take<double>(static_cast<size_t>(nc) * c.p.max_bins * (2 * L + 3));
-    c.status = cv.take<int>(4);
+    c.status = cv.take<int>(8);
     c.obs_mean = cv.take<double>(static_cast<size_t>(ns) * (2 * L + 4));
     c.obs_err = cv.take<double>(static_cast<size_t>(ns) * (2 * L + 4));
     const size_t nsw2 = static_cast<size_t>(ns) * 2 * nw;
@@ -450,6 +451,7 @@ hfk::QmcProblem make_problem(const hf_ctx& c, int n_warmup, int n_measure, int r
     q.acc = c.acc;
     q.bins = c.bins;
     q.status = c.status;
+    q.drift = c.p.check_drift ? reinterpret_cast<unsigned int*>(c.status + 4) : nullptr;
     return q;
 }
 
@@ -489,8 +491,10 @@ hf_status launch_sweeps_f32(hf_ctx* c, int n_warmup, int n_measure, int refresh_
     const hf_status sg = ensure_g0inv(c, c->stream);
     if (sg != HF_OK) return sg;
     if (refresh_first) {
-        q.refresh_measure = 0;
-        e = hfk::launch_refresh_f64(q, c->stream);
+        hfk::QmcProblem q0 = q;
+        q0.refresh_measure = 0;
+        q0.drift = nullptr;          // the first refresh follows a possible bath change
+        e = hfk::launch_refresh_f64(q0, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "FP64 refresh launch");
     }
     const int total = n_warmup + n_measure;
@@ -693,7 +697,7 @@ hf_status hf_init(const hf_params* p, void* d_ws, size_t ws_bytes, hf_ctx** out)
     if (e == cudaSuccess) e = cudaMemsetAsync(c->acc, 0, sizeof(unsigned long long) * c->nchain, st0);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(c->bins, 0, sizeof(double) * c->nchain * p->max_bins * (2 * c->L + 3), st0);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int) * 4, st0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int) * 8, st0);
     if (e == cudaSuccess)
         e = hfk::launch_init_fields(c->s, c->nchain, p->chains_per_site, c->L,
                                     static_cast<uint32_t>(p->seed & 0xFFFFFFFFull),
@@ -769,6 +773,7 @@ hf_status hf_clear_measurements(hf_ctx* c) {
     HF_CUDA(c, cudaMemsetAsync(c->bins, 0, sizeof(double) * c->nchain * c->p.max_bins * (2 * c->L + 3),
                                c->stream));
     HF_CUDA(c, cudaMemsetAsync(c->nmeas_d, 0, sizeof(uint32_t) * c->nchain, c->stream));
+    HF_CUDA(c, cudaMemsetAsync(c->status + 4, 0, sizeof(int) * 2, c->stream));
     c->nmeas = 0;
     return HF_OK;
 }
@@ -956,6 +961,18 @@ hf_status hf_get_accepts(hf_ctx* c, unsigned long long* accepts) {
 hf_status hf_sync(hf_ctx* c) {
     if (!c) return fail(nullptr, HF_EINVAL, "null context");
     return check_status(c);
+}
+
+hf_status hf_get_drift(hf_ctx* c, double* max_drift, unsigned long long* refreshes) {
+    if (!c) return fail(nullptr, HF_EINVAL, "null context");
+    unsigned int w[2] = {0u, 0u};
+    HF_CUDA(c, cudaMemcpyAsync(w, c->status + 4, sizeof(w), cudaMemcpyDeviceToHost, c->stream));
+    HF_CUDA(c, cudaStreamSynchronize(c->stream));
+    float m = 0.0f;
+    std::memcpy(&m, &w[0], sizeof(m));
+    if (max_drift) *max_drift = m;
+    if (refreshes) *refreshes = w[1];
+    return HF_OK;
 }
 
 hf_status hf_get_timings(hf_ctx* c, double* ms) {

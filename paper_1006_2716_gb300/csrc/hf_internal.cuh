@@ -86,6 +86,8 @@ struct QmcProblem {
     unsigned long long* acc;  // [nchain] accepted flips
     double* bins;         // [nchain][max_bins][2L+3]
     int* status;          // [0]: error code (HF_ENUMERIC...), [1]: non-positive ratios seen
+    unsigned int* drift;  // nullptr, or [0] largest |G_SM - G_Dyson| met at an in-launch refresh
+                          // (float bits) and [1] refreshes checked
 };
 
 struct QmcBatch {
@@ -93,6 +95,17 @@ struct QmcBatch {
     int nblocks;
     QmcProblem p[kMaxProblems];
 };
+
+// Drift monitor: folds the largest |G_SM - G_Dyson| v >= 0 a warp has seen into the context's
+// words -- [0] the maximum as float bits (non-negative floats order like their bit patterns, so an
+// integer maximum keeps the float maximum), [1] one count per chain refresh (count = true on one
+// thread of the team).  Every lane of the warp takes part.
+__device__ __forceinline__ void drift_fold(unsigned int* drift, float v, bool count) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(drift, __float_as_uint(v));
+    if (count) atomicAdd(drift + 1, 1u);
+}
 
 // FP64 and FP32-pair sweeps: blocks of kBlock threads hold 4 / team_warps chains.
 size_t qmc_f64_smem_bytes(int L, int team_warps);

@@ -98,14 +98,24 @@ __device__ __forceinline__ float2 df_recip(float2 R) {
 // Dyson refresh of both spins in FP64 (as the FP64 kernel: G_sigma = M_sigma^{-1} with
 // M_sigma = g0^{-1} e^{V_sigma} - (e^{V_sigma} - 1), dense in the two G buffers), both results
 // parked in the chain's global slot, then split into double-floats in the permuted placement.
+// check (drift monitor): the outgoing pair state is parked in the global slot first and
+// compared with the Dyson solution as that is parked (each thread its own elements).
 template <int L, int TW>
 __device__ void refresh_both_df(const QmcProblem& P, const TeamSmem<L>& S, int site, double* Gg,
-                                int tid) {
+                                int tid, bool check) {
     constexpr int T = 32 * TW;
     float2* X0 = reinterpret_cast<float2*>(S.G0);
     float2* X1 = reinterpret_cast<float2*>(S.G1);
     const GjTeamScratch<L> g(S);
     bool ok = true;
+    if (check) {
+        for (int e = tid; e < L * L; e += T) {
+            const int i = e / L, j = e - (e / L) * L;
+            Gg[e] = df_to_d(X0[gx<L>(i, j)]);
+            Gg[L * L + e] = df_to_d(X1[gx<L>(i, j)]);
+        }
+        team_sync<TW>();
+    }
     if (P.ev_p == 0.0 && P.ev_m == 0.0) {   // U = 0: G = g0 exactly
         const double* gt = P.gtau + static_cast<size_t>(site) * 2 * L;
         build_bath_matrix<L, TW>(gt, S.G0, tid);
@@ -119,10 +129,16 @@ __device__ void refresh_both_df(const QmcProblem& P, const TeamSmem<L>& S, int s
         ok = gj_team<L, TW>(S.G0, g.fcol, g.pivrow, g.flag, g.pinv, tid);
         ok = gj_team<L, TW>(S.G1, g.fcol, g.pivrow, g.flag, g.pinv, tid) && ok;
     }
+    float v = 0.0f;
     for (int e = tid; e < L * L; e += T) {
+        if (check) {
+            v = fmaxf(v, static_cast<float>(fabs(S.G0[e] - Gg[e])));
+            v = fmaxf(v, static_cast<float>(fabs(S.G1[e] - Gg[L * L + e])));
+        }
         Gg[e] = S.G0[e];
         Gg[L * L + e] = S.G1[e];
     }
+    if (check) drift_fold(P.drift, v, tid == 0);
     team_sync<TW>();
     for (int e = tid; e < L * L; e += T) {
         const int i = e / L, j = e - (e / L) * L;
@@ -403,7 +419,7 @@ __device__ void df_chain(const QmcProblem& P, int c, unsigned char* base, int ti
             d_to_df((cur_bin < P.max_bins) ? bins_c[static_cast<size_t>(cur_bin) * W + k] * L : 0.0);
     team_sync<TW>();
     if (P.refresh_first) {
-        refresh_both_df<L, TW>(P, S, site, Gg, tid);
+        refresh_both_df<L, TW>(P, S, site, Gg, tid, false);   // the bath may have changed
     } else {
         for (int e = tid; e < LL; e += T) {
             const int i = e / L, j = e - (e / L) * L;
@@ -546,7 +562,7 @@ __device__ void df_chain(const QmcProblem& P, int c, unsigned char* base, int ti
         ++nsw;
         team_sync<TW>();
         if (P.refresh_every > 0 && ((nsw + rphase) % static_cast<uint32_t>(P.refresh_every)) == 0u)
-            refresh_both_df<L, TW>(P, S, site, Gg, tid);
+            refresh_both_df<L, TW>(P, S, site, Gg, tid, P.drift != nullptr);
         if (k >= P.n_warmup) {
             measure_df<L, TW>(S, tid);
             ++nmeas;

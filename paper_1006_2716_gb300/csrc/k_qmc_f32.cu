@@ -345,6 +345,7 @@ __device__ bool refresh_chain(const QmcProblem& P, int c, unsigned char* smem) {
     float* Gf = P.Gf ? P.Gf + static_cast<size_t>(c) * 2 * LL : nullptr;
     const double ex_p = 1.0 + P.ev_p, ex_m = 1.0 + P.ev_m;
     bool ok = true;
+    float dv = 0.0f;
     for (int sp = 0; sp < 2; ++sp) {
         const int sigma = sp == 0 ? 1 : -1;
         const double* gi = P.g0inv + (static_cast<size_t>(site) * 2 + sp) * LL;
@@ -359,10 +360,15 @@ __device__ bool refresh_chain(const QmcProblem& P, int c, unsigned char* smem) {
         for (int e = tid; e < LL; e += kT32) {
             const double x = g.M[e];
             Gout[static_cast<size_t>(sp) * LL + e] = x;
-            if (Gf) Gf[static_cast<size_t>(sp) * LL + e] = static_cast<float>(x);
+            if (Gf) {
+                // drift monitor: the FP32 state the sweeps reached against the Dyson solution
+                if (P.drift) dv = fmaxf(dv, static_cast<float>(fabs(x - Gf[static_cast<size_t>(sp) * LL + e])));
+                Gf[static_cast<size_t>(sp) * LL + e] = static_cast<float>(x);
+            }
         }
         __syncthreads();
     }
+    if (P.drift) drift_fold(P.drift, dv, tid == 0);
     return ok;
 }
 

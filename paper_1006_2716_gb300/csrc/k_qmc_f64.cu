@@ -285,8 +285,24 @@ __device__ void qmc_chain(const QmcProblem& P, int c, unsigned char* base, int t
         }
         ++nsw;
         team_sync<TW>();
-        if (P.refresh_every > 0 && ((nsw + rphase) % static_cast<uint32_t>(P.refresh_every)) == 0u)
+        if (P.refresh_every > 0 && ((nsw + rphase) % static_cast<uint32_t>(P.refresh_every)) == 0u) {
+            if (P.drift) {   // drift monitor: park the updated state in the chain's global slot
+                for (int e = tid; e < LL; e += T) {
+                    Gg[e] = S.G0[e];
+                    Gg[LL + e] = S.G1[e];
+                }
+                team_sync<TW>();
+            }
             refresh_both<L, TW>(P, S, site, tid);
+            if (P.drift) {   // ... and compare it with the Dyson solution (each thread its own e)
+                float v = 0.0f;
+                for (int e = tid; e < LL; e += T) {
+                    v = fmaxf(v, static_cast<float>(fabs(S.G0[e] - Gg[e])));
+                    v = fmaxf(v, static_cast<float>(fabs(S.G1[e] - Gg[LL + e])));
+                }
+                drift_fold(P.drift, v, tid == 0);
+            }
+        }
         if (k >= P.n_warmup) {
             measure<L, TW>(S, tid);
             ++nmeas;

@@ -30,7 +30,8 @@ class hf_params(C.Structure):
         ("t", C.c_double), ("U", C.c_double), ("V0", C.c_double), ("mu", C.c_double),
         ("beta", C.c_double), ("dtau", C.c_double),
         ("n_matsubara", C.c_int), ("chains_per_site", C.c_int), ("precision", C.c_int),
-        ("refresh_every", C.c_int), ("refresh_stagger", C.c_int), ("delay_k", C.c_int),
+        ("refresh_every", C.c_int), ("refresh_stagger", C.c_int), ("check_drift", C.c_int),
+        ("delay_k", C.c_int),
         ("team_warps", C.c_int),
         ("bin_size", C.c_int),
         ("max_bins", C.c_int), ("n_warmup", C.c_int), ("n_measure", C.c_int),
@@ -100,6 +101,7 @@ SIGNATURES = [
     ("hf_get_accepts", C.c_int, [_VP, C.POINTER(C.c_ulonglong)]),
     ("hf_get_timings", C.c_int, [_VP, _DP]),
     ("hf_sync", C.c_int, [_VP]),
+    ("hf_get_drift", C.c_int, [_VP, _DP, C.POINTER(C.c_ulonglong)]),
     ("hf_lattice_step_noalloc", C.c_int, [_VP, _VP, _VP]),
     ("hf_batch_create", C.c_int, [C.POINTER(_VP), C.c_int, C.c_int, C.POINTER(_VP)]),
     ("hf_batch_sweep", C.c_int, [_VP, C.c_int, C.c_int, C.c_int]),
@@ -284,6 +286,14 @@ def hf_sync(ctx):
     _check(lib().hf_sync(ctx), ctx)
 
 
+def hf_get_drift(ctx):
+    """(largest |G_SM - G_Dyson| at the checked refreshes, number of chain refreshes checked)."""
+    m = C.c_double()
+    n = C.c_ulonglong()
+    _check(lib().hf_get_drift(ctx, C.byref(m), C.byref(n)), ctx)
+    return m.value, n.value
+
+
 def hf_get_timings(ctx):
     ms = np.zeros(6)
     _check(lib().hf_get_timings(ctx, _dp(ms)), ctx)
@@ -462,6 +472,7 @@ def make_params(cfg: dict, stream=None, **over) -> hf_params:
     p.precision = int(d.get("precision", 0))
     p.refresh_every = int(d.get("refresh_every", 10))
     p.refresh_stagger = int(d.get("refresh_stagger", 0))
+    p.check_drift = int(d.get("check_drift", 0))
     p.delay_k = int(d.get("delay_k", 1))
     p.team_warps = int(d.get("team_warps", 0))
     p.bin_size = int(d.get("bin_size", 100))

@@ -62,6 +62,7 @@ def test_workspace_size_and_orbit_counts(lib):
     (dict(precision=1, beta=4.0, dtau=0.25, refresh_every=0), "refresh"),
     (dict(precision=1, beta=4.0, dtau=0.25, refresh_every=5, refresh_stagger=1), "stagger"),
     (dict(refresh_stagger=2), "stagger"),
+    (dict(check_drift=2), "check_drift"),
     (dict(team_warps=3), "team_warps"),
     (dict(beta=16.0, dtau=0.25, team_warps=1), "team_warps"),
     (dict(precision=3), "precision"),
