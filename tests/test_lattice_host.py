@@ -22,6 +22,7 @@ CASES = [
     (0, 7, 5, 1, 1, 14),
     (0, 20, 20, 1, 1, 40),
     (1, 7, 7, 1, 0, None),
+    (1, 40, 40, 1, 0, 80),          # serving disc, 663 orbits: (40 - x) + (x + 39) + 1
     (2, 4, 4, 4, 1, 32),
     (2, 5, 5, 5, 0, 25),
     (2, 4, 4, 6, 0, 16),
