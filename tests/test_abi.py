@@ -84,3 +84,29 @@ def test_init_rejects_small_workspace_without_touching_gpu(lib):
     with pytest.raises(hf.HFError) as e:
         hf.hf_init(p, 256, 1024)
     assert e.value.status == hf.HF_ENOMEM
+
+
+def _c_struct_fields(name):
+    """Field names, in order, of `typedef struct name {...} name;` in include/hf.h."""
+    txt = open(os.path.join(ROOT, "include", "hf.h")).read()
+    body = txt[txt.index("typedef struct %s {" % name):txt.index("} %s;" % name)]
+    body = re.sub(r"/\*.*?\*/", " ", body, flags=re.S)
+    names = []
+    for line in body.splitlines()[1:]:
+        line = line.strip().rstrip(";")
+        parts = line.split(None, 1)
+        if len(parts) < 2:
+            continue
+        for n in parts[1].split(","):
+            names.append(re.sub(r"\[.*", "", n.strip().lstrip("*")))
+    return names
+
+
+@pytest.mark.parametrize("cname,pyname", [("hf_params", "hf_params"), ("hf_srv_params", "hf_srv_params"),
+                                          ("hf_request", "hf_request"), ("hf_result", "hf_result"),
+                                          ("hf_srv_stats_t", "hf_srv_stats_t")])
+def test_binding_structs_mirror_the_header(cname, pyname):
+    """The ctypes mirrors list the C structs' fields in the same order (a mismatch would shift
+    every later field silently)."""
+    py = [f[0] for f in getattr(hf, pyname)._fields_]
+    assert _c_struct_fields(cname) == py
