@@ -82,3 +82,14 @@ def test_bench_lattice_bookkeeping(lib):
     assert bench.lattice_flops(N, N - 1, 1, 1) == exact
     assert bench.lattice_flops(N, 100, 2, 3) == 6 * exact
     assert abs(bench.lattice_flops(400, 399, 1, 1) / (8 * 400 ** 3 / 2) - 1) < 0.01
+
+
+def test_largest_band_is_165(lib):
+    """The lattice step keeps a (b+1)(b+2)/2-entry window in shared memory: b = 165 is the
+    largest half-width it accepts (an 11x15x3 open box has b = Lx Ly = 165; 2x83x2 has 166)."""
+    p = hf.make_params(wl.CONFIGS["square6"], geometry=2, Lx=11, Ly=15, Lz=3, periodic=0)
+    assert hf.hf_lattice_info(p)[2] == 165
+    p = hf.make_params(wl.CONFIGS["square6"], geometry=2, Lx=2, Ly=83, Lz=2, periodic=0)
+    with pytest.raises(hf.HFError) as e:
+        hf.hf_lattice_info(p)
+    assert e.value.status == hf.HF_EINVAL and "largest: 165" in str(e.value)
