@@ -110,3 +110,40 @@ def test_binding_structs_mirror_the_header(cname, pyname):
     every later field silently)."""
     py = [f[0] for f in getattr(hf, pyname)._fields_]
     assert _c_struct_fields(cname) == py
+
+
+def _srv_params(**over):
+    p = hf.hf_srv_params()
+    d = dict(chains_per_request=8, n_warmup=10, n_measure=40, refresh_every=10, bin_size=10,
+             precision=2, team_warps=0, max_L=64, max_inflight=64, max_keys=256, n_streams=4,
+             requests_per_launch=16)
+    d.update(over)
+    for k, v in d.items():
+        setattr(p, k, v)
+    return p
+
+
+def test_server_pool_size_grows_with_its_limits(lib):
+    n = hf.hf_srv_workspace_size(_srv_params())
+    assert n > 0
+    assert hf.hf_srv_workspace_size(_srv_params(max_inflight=128)) > n
+    assert hf.hf_srv_workspace_size(_srv_params(max_keys=512)) > n
+    assert hf.hf_srv_workspace_size(_srv_params(max_L=32)) < n
+
+
+@pytest.mark.parametrize("over,frag", [
+    (dict(chains_per_request=0), "chains_per_request"),
+    (dict(n_measure=0), "n_measure"),
+    (dict(n_measure=45), "multiple of bin_size"),
+    (dict(refresh_every=-1), "refresh_every"),
+    (dict(refresh_stagger=3), "refresh_stagger"),
+    (dict(precision=1), "precision"),
+    (dict(max_L=128), "max_L"),
+    (dict(n_streams=0), "n_streams"),
+    (dict(max_inflight=0), "max_inflight"),
+    (dict(team_warps=3), "team_warps"),
+])
+def test_server_rejects_invalid_params(lib, over, frag):
+    with pytest.raises(hf.HFError) as e:
+        hf.hf_srv_workspace_size(_srv_params(**over))
+    assert e.value.status == hf.HF_EINVAL and frag in str(e.value)
