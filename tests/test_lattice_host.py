@@ -18,6 +18,9 @@ def lib():
 
 CASES = [
     # geometry, Lx, Ly, Lz, periodic, band half-width of the folded order
+    (0, 1, 1, 1, 0, 0),             # a single site: N = 1, no band
+    (1, 0, 0, 1, 0, 0),             # the disc of radius 0
+    (3, 1, 1, 4, 0, 2),             # a column of 4 layers: one orbit, folded ring
     (0, 6, 6, 1, 0, 6),
     (0, 7, 5, 1, 1, 14),
     (0, 20, 20, 1, 1, 40),
