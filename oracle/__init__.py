@@ -22,5 +22,5 @@ Layout
 """
 from .core import (  # noqa: F401
     lib, build, philox4x32_10, uniform, init_fields, constants, build_g0, dyson,
-    ratio, sweep, measure, run_chain, brute_force,
+    ratio, sweep, measure, run_chain, brute_force, tie_watch, tie_count,
 )

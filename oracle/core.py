@@ -65,6 +65,10 @@ def lib():
                                         C.c_uint32, u32p, C.c_int, C.c_int, C.c_int, C.c_int,
                                         C.c_int, i8p, dp, dp, dp]
             L.hfo_run_chain.restype = C.c_long
+            L.hfo_tie_watch.argtypes = [C.c_double]
+            L.hfo_tie_watch.restype = None
+            L.hfo_tie_count.argtypes = []
+            L.hfo_tie_count.restype = C.c_long
             L.hfo_brute_force.argtypes = [C.c_int, C.c_double, dp, dp, dp]
             L.hfo_brute_force.restype = C.c_int
             _lib = L
@@ -166,6 +170,15 @@ def run_chain(lam, g0up, g0dn, seed, site, chain, nsw, n_warmup, n_measure,
     if acc < 0:
         raise FloatingPointError("singular Dyson refresh")
     return int(acc), int(n.value)
+
+
+def tie_watch(rel):
+    """Count, from now on, the sweep proposals with |u - R_up R_dn| < rel |R_up R_dn| (0: off)."""
+    lib().hfo_tie_watch(float(rel))
+
+
+def tie_count():
+    return int(lib().hfo_tie_count())
 
 
 def brute_force(lam, g0up, g0dn):

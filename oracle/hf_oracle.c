@@ -172,6 +172,20 @@ double hfo_ratio(int L, double lambda, const int8_t* s, int l, const double* Gup
     return R[0] * R[1];
 }
 
+/* Near-tie watch (instrumentation only, no effect on any result): proposals whose uniform lies
+ * within tie_rel * |R_up R_dn| of the Metropolis threshold, where two implementations that
+ * round differently could decide differently. */
+static double tie_rel = 0.0;
+static long tie_count = 0;
+
+void hfo_tie_watch(double rel)
+{
+    tie_rel = rel;
+    tie_count = 0;
+}
+
+long hfo_tie_count(void) { return tie_count; }
+
 int hfo_sweep(int L, double lambda, uint64_t seed, uint32_t site, uint32_t chain,
               uint32_t sweep, int8_t* s, double* Gup, double* Gdn)
 {
@@ -183,6 +197,7 @@ int hfo_sweep(int L, double lambda, uint64_t seed, uint32_t site, uint32_t chain
         double a[2], R[2];
         double p = hfo_ratio(L, lambda, s, l, Gup, Gdn, a, R);
         double a_up = a[0], a_dn = a[1], R_up = R[0], R_dn = R[1];
+        if (tie_rel > 0.0 && fabs(u - p) < tie_rel * fabs(p)) ++tie_count;
         if (u < p) {
             rank1_update(L, l, a_up, R_up, Gup, col, row);
             rank1_update(L, l, a_dn, R_dn, Gdn, col, row);

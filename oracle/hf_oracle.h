@@ -66,6 +66,12 @@ double hfo_ratio(int L, double lambda, const int8_t* s, int l, const double* Gup
 int hfo_sweep(int L, double lambda, uint64_t seed, uint32_t site, uint32_t chain,
               uint32_t sweep, int8_t* s, double* Gup, double* Gdn);
 
+/* Near-tie watch: from now on count the proposals of hfo_sweep whose uniform u lies within
+ * rel * |R_up R_dn| of R_up R_dn (rel = 0 switches it off); hfo_tie_count returns the count.
+ * Process-wide state, not thread safe; it changes no result. */
+void hfo_tie_watch(double rel);
+long hfo_tie_count(void);
+
 /* Accumulate one measurement of G into acc: layout acc[0..L-1] = G_up(tau_m),
  * acc[L..2L-1] = G_dn(tau_m), acc[2L] = n_up, acc[2L+1] = n_dn, acc[2L+2] = double
  * occupancy.  G_sigma(tau_m) = (1/L) sum_l sgn G[(l+m) mod L][l], sgn = -1 on wrap. */

@@ -250,3 +250,30 @@ def test_run_chain_refresh_and_bins(stagger, refresh_at):
     # a measurement is an average of L diagonals: density = 1 - G(0+)
     m = o.measure(Hu, Hd)
     assert abs(m[2 * L] - (1 - m[0])) < 1e-14
+
+
+def test_tie_watch_counts_without_changing_results():
+    # the near-tie watch is instrumentation: with it on, every decision and every G entry are
+    # those of an unwatched run; a huge window counts every proposal, a zero window none
+    L, beta, U = 16, 4.0, 4.0
+    b = wl.random_baths(11, 1, beta, L)[0]
+    _, lam = o.constants(beta, U, L)
+    g0u, g0d = o.build_g0(b[0]), o.build_g0(b[1])
+
+    def run(rel):
+        o.tie_watch(rel)
+        s = o.init_fields(5, 0, 0, L)
+        Gu, _ = o.dyson(g0u, s, 1, lam)
+        Gd, _ = o.dyson(g0d, s, -1, lam)
+        acc = sum(o.sweep(lam, 5, 0, 0, k, s, Gu, Gd) for k in range(6))
+        n = o.tie_count()
+        o.tie_watch(0.0)
+        return acc, s, Gu, Gd, n
+
+    a0, s0, u0, d0, n0 = run(0.0)
+    a1, s1, u1, d1, n1 = run(1e300)
+    assert n0 == 0 and n1 == 6 * L
+    assert a0 == a1 and np.array_equal(s0, s1)
+    assert np.array_equal(u0, u1) and np.array_equal(d0, d1)
+    _, _, _, _, n2 = run(1e-3)
+    assert 0 <= n2 <= 6 * L
