@@ -203,7 +203,7 @@ hf_status hf_sync(hf_ctx* ctx);
 hf_status hf_get_timings(hf_ctx* ctx, double* ms);
 
 /* ---- Batches: uneven-L problems in one fused launch, graph-captured iterations -------------
- * A batch groups 1..8 contexts that share one stream, one sweep form (precision 0 or 2, not 1)
+ * A batch groups 1..16 contexts that share one stream, one sweep form (precision 0 or 2, not 1)
  * and the same n_warmup / n_measure -- e.g. one RDMFT run per temperature of a scan, each with its
  * own L.  The impurity sweeps of all of them run as a single launch of the fused sweep kernel
  * (problems ordered by L, largest first, so the longest chains start first); every other phase
@@ -239,8 +239,9 @@ const char* hf_batch_last_error(const hf_batch* b);
  * and launches on different streams overlap on the GPU, so requests that arrive while others run
  * start without waiting for them.  The Ising fields and sweep counters of each (run, site) key
  * stay on the device between its requests (warm start; a key's next request waits for its
- * previous one); with more keys than max_keys the least recently used idle key is dropped and
- * its next request starts cold.  Chains are keyed by (seed, site, chain) and computed exactly as
+ * previous one); a request whose L differs from the L of the key's kept fields starts cold, and
+ * its fields then replace the kept ones; with more keys than max_keys the least recently used
+ * idle key is dropped and its next request starts cold.  Chains are keyed by (seed, site, chain) and computed exactly as
  * in a context of their own, so a result does not depend on which requests shared its launch.
  * No device code waits or polls: all waiting is on the host, with timeouts. */
 typedef struct hf_srv hf_srv;
@@ -323,6 +324,16 @@ const char* hf_srv_last_error(const hf_srv* s);
  * first call on a device looks the array's device address up (cudaGetSymbolAddress) with that
  * device current; make that first call before any stream capture. */
 hf_status hf_lattice_step_noalloc(hf_ctx* ctx, const double* d_sigma, double* d_gloc);
+
+/* Raw blocks of the device random-number generator every sweep draws from: Philox4x32-10
+ * (Salmon, Moraes, Dror and Shaw, SC'11), the counter-based generator the sweeps key by (sweep,
+ * slice, chain, site).  For k < n, writes the four 32-bit words of the block at counter
+ * d_ctr[4k .. 4k+3] under key (key_lo, key_hi) to d_out[4k .. 4k+3].  d_ctr and d_out are device
+ * buffers of 4n uint32 each (the caller's, 16-byte aligned); the work is queued on cuda_stream (a cudaStream_t,
+ * NULL = the legacy default stream) and the call does not synchronise.  HF_EINVAL for n < 0, or
+ * for a null or unaligned buffer with n > 0; HF_ECUDA if the launch fails. */
+hf_status hf_philox_blocks(uint32_t key_lo, uint32_t key_hi, const uint32_t* d_ctr, int n,
+                           uint32_t* d_out, void* cuda_stream);
 
 /* Release the host handle (the device workspace stays the caller's). */
 void hf_free(hf_ctx* ctx);

@@ -238,6 +238,7 @@ struct hf_ctx {
     double dtau = 0.0, lambda = 0.0;
     double a_p = 0.0, a_m = 0.0, ev_p = 0.0, ev_m = 0.0;
     cudaStream_t stream = nullptr;
+    int device = 0;                 // device current at hf_init (the workspace's device)
     int lat_batch = 0;              // matrices per lattice-step launch
     uint32_t nmeas = 0;             // measured sweeps since the last clear (all chains)
     uint32_t nsw_host = 0;          // sweep counter shared by all chains (FP32 path)
@@ -574,6 +575,13 @@ hf_status enqueue_lattice(hf_ctx* c) {
     return HF_OK;
 }
 
+// Raw generator blocks for hf_philox_blocks: one thread per counter.
+__global__ void philox_blocks_kernel(uint2 key, const uint4* __restrict__ ctr, int n,
+                                     uint4* __restrict__ out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) out[k] = hfk::philox4x32_10(ctr[k], key);
+}
+
 hfk::FourierArgs fourier_args(const hf_ctx& c) {
     hfk::FourierArgs fa{};
     fa.nsite = c.nsite;
@@ -643,6 +651,11 @@ hf_status hf_init(const hf_params* p, void* d_ws, size_t ws_bytes, hf_ctx** out)
     }
     layout(*c, d_ws);
     c->stream = static_cast<cudaStream_t>(p->cuda_stream);
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete c;
+        return fail(nullptr, HF_ECUDA, "hf_init: no current CUDA device");
+    }
     // a1: Trotter step and Hubbard-Stratonovich coupling (host libm)
     c->dtau = p->beta / c->L;
     c->lambda = std::acosh(std::exp(c->dtau * p->U / 2.0));
@@ -1000,25 +1013,36 @@ hf_status hf_lattice_step_noalloc(hf_ctx* c, const double* d_sigma, double* d_gl
                         " bytes of scratch, more than the " +
                         std::to_string(hfk::lattice_static_scratch_bytes()) +
                         "-byte static array holds; use hf_rdmft_step with a workspace instead");
-    hfk::LatticeArgs la{};
-    la.N = c->lat.N;
-    la.b = c->lat.b;
-    la.nw = c->nw;
-    la.beta = c->p.beta;
-    la.mu = c->p.mu;
-    la.h0band = c->h0band;
-    la.rep_of = c->rep_of;
-    la.flip = c->flip;
-    la.site_rep = c->site_rep;
-    la.site_dn = c->lat.gdn.empty() ? nullptr : c->site_dn;
-    la.nspin = c->lat.gdn.empty() ? 2 : 1;
+    int dev = -1;
+    HF_CUDA(c, cudaGetDevice(&dev));
+    if (dev != c->device)
+        return fail(c, HF_EINVAL,
+                    "hf_lattice_step_noalloc: the context's device (" + std::to_string(c->device) +
+                        ") must be the current device (" + std::to_string(dev) + ")");
+    // the same arguments as the lattice phase of hf_rdmft_step, with the caller's buffers and
+    // the library's static band array instead of the workspace
+    hfk::LatticeArgs la = lattice_args(*c);
     la.sigma = reinterpret_cast<const double2*>(d_sigma);
     la.gloc = reinterpret_cast<double2*>(d_gloc);
     la.scratch = nullptr;
-    la.status = c->status;
     cudaError_t e = hfk::launch_lattice_static(la, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "hf_lattice_step_noalloc launch");
     return check_status(c);
+}
+
+hf_status hf_philox_blocks(uint32_t key_lo, uint32_t key_hi, const uint32_t* d_ctr, int n,
+                           uint32_t* d_out, void* cuda_stream) {
+    if (n < 0 || (n > 0 && (!d_ctr || !d_out)))
+        return fail(nullptr, HF_EINVAL, "hf_philox_blocks: n < 0 or null buffer");
+    if (n == 0) return HF_OK;
+    if ((reinterpret_cast<uintptr_t>(d_ctr) & 15u) != 0 || (reinterpret_cast<uintptr_t>(d_out) & 15u) != 0)
+        return fail(nullptr, HF_EINVAL, "hf_philox_blocks: buffers must be 16-byte aligned");
+    philox_blocks_kernel<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(cuda_stream)>>>(
+        make_uint2(key_lo, key_hi), reinterpret_cast<const uint4*>(d_ctr), n,
+        reinterpret_cast<uint4*>(d_out));
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "hf_philox_blocks launch");
+    return HF_OK;
 }
 
 // ----------------------------------------------------------------------------------------------

@@ -103,6 +103,7 @@ SIGNATURES = [
     ("hf_sync", C.c_int, [_VP]),
     ("hf_get_drift", C.c_int, [_VP, _DP, C.POINTER(C.c_ulonglong)]),
     ("hf_lattice_step_noalloc", C.c_int, [_VP, _VP, _VP]),
+    ("hf_philox_blocks", C.c_int, [C.c_uint32, C.c_uint32, _VP, C.c_int, _VP, _VP]),
     ("hf_batch_create", C.c_int, [C.POINTER(_VP), C.c_int, C.c_int, C.POINTER(_VP)]),
     ("hf_batch_sweep", C.c_int, [_VP, C.c_int, C.c_int, C.c_int]),
     ("hf_batch_rdmft_step", C.c_int, [_VP, _DP]),
@@ -303,6 +304,10 @@ def hf_get_timings(ctx):
 def hf_lattice_step_noalloc(ctx, d_sigma: int, d_gloc: int):
     """d_sigma, d_gloc: device addresses of [n_sites][2][nw] complex128 buffers."""
     _check(lib().hf_lattice_step_noalloc(ctx, C.c_void_p(d_sigma), C.c_void_p(d_gloc)), ctx)
+
+
+def hf_philox_blocks(key_lo, key_hi, d_ctr: int, n: int, d_out: int, stream=None):
+    _check(lib().hf_philox_blocks(key_lo, key_hi, d_ctr, n, d_out, stream))
 
 
 def _bcheck(st, b=None):
