@@ -140,6 +140,7 @@ struct hf_srv {
     std::map<std::pair<int, int>, int> key_of;
     std::vector<int> key_busy;       // 1 while a request of the key is admitted
     std::vector<int> key_valid;      // 1 once the key holds fields
+    std::vector<int> key_L;          // L of the fields the key holds (its last request's L)
     std::vector<uint64_t> key_used;  // LRU clock
     uint64_t lru_clock = 0;
     // queues and results
@@ -367,6 +368,7 @@ void progress(hf_srv* S) {
                 S->arena.release(j.off, j.bytes);
                 S->key_busy[j.key] = 0;
                 S->key_valid[j.key] = (res[k].status == HF_OK) ? 1 : 0;
+                S->key_L[j.key] = j.req.L;
                 S->done[j.ticket] = res[k];
                 ++S->n_completed;
             }
@@ -401,7 +403,9 @@ void progress(hf_srv* S) {
                 int key;
                 if (kit != S->key_of.end()) {
                     key = kit->second;
-                    j.warm = S->key_valid[key] != 0;
+                    // fields kept at another L are not a state of this request's chains:
+                    // such a request starts cold (and its fields then replace the record's)
+                    j.warm = S->key_valid[key] != 0 && S->key_L[key] == j.req.L;
                 } else {
                     // new key: a free record, else the least recently used idle one
                     key = -1;
@@ -515,6 +519,7 @@ hf_status hf_srv_create(const hf_srv_params* p, void* d_pool, size_t pool_bytes,
     S->arena.reset(pool_bytes - wb);
     S->key_busy.assign(p->max_keys, 0);
     S->key_valid.assign(p->max_keys, 0);
+    S->key_L.assign(p->max_keys, 0);
     S->key_used.assign(p->max_keys, 0);
     cudaError_t ce = cudaGetDevice(&S->device);
     const int ns = p->n_streams;

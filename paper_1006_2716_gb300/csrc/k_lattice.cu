@@ -29,8 +29,10 @@
 // matrix; a wide one a block with two threads per window row, so that every scheduler of the SM
 // has two warps issuing FP64 work (this GPU executes 2 FP64 FMA lanes per clock per SM).
 #include <algorithm>
+#include <atomic>
 
 #include "hf_internal.cuh"
+
 #include "k_lattice.cuh"
 
 namespace hfk {
@@ -317,21 +319,25 @@ static __device__ __align__(256) double2
 size_t lattice_static_scratch_bytes() { return kStaticLatticeScratchBytes; }
 
 // Device address of g_lattice_scratch on the current device, looked up once per device (the
-// host-side symbol is only a stand-in and must never reach a kernel).
+// host-side symbol is only a stand-in and must never reach a kernel).  The per-device entries
+// are atomics: host threads that make their first call on a device at the same time each look
+// the address up and store the same value.
 static cudaError_t static_scratch_address(double2** out) {
     constexpr int kMaxDevices = 64;
-    static double2* addr[kMaxDevices] = {};
+    static std::atomic<double2*> addr[kMaxDevices] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    if (addr[dev] == nullptr) {
+    double2* a = addr[dev].load(std::memory_order_acquire);
+    if (a == nullptr) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_lattice_scratch);
         if (e != cudaSuccess) return e;
-        addr[dev] = static_cast<double2*>(p);
+        a = static_cast<double2*>(p);
+        addr[dev].store(a, std::memory_order_release);
     }
-    *out = addr[dev];
+    *out = a;
     return cudaSuccess;
 }
 

@@ -128,3 +128,25 @@ def test_invalid_requests_rejected(hf):
     with pytest.raises(hf.HFError):
         hf.hf_srv_poll(srv.handle, 12345)
     srv.close()
+
+
+def test_key_with_a_new_L_starts_cold(hf):
+    # fields kept for a key at one L are not a state of chains at another L: a request of the
+    # same (run, site) with a different L starts cold, and its own fields become the kept ones
+    srv = hf.Server(_params(hf, precision=0))
+    r16, _ = _req(hf, 3, 5, 16)
+    r32, _ = _req(hf, 3, 5, 32)
+    first = hf.hf_srv_wait(srv.handle, hf.hf_srv_submit(srv.handle, r16))
+    assert first["status"] == hf.HF_OK and first["warm"] == 0
+    again16 = hf.hf_srv_wait(srv.handle, hf.hf_srv_submit(srv.handle, r16))
+    assert again16["warm"] == 1
+    switched = hf.hf_srv_wait(srv.handle, hf.hf_srv_submit(srv.handle, r32))
+    assert switched["status"] == hf.HF_OK and switched["warm"] == 0
+    # a cold L = 32 solve of this key is the solve of a fresh service
+    fresh = hf.Server(_params(hf, precision=0))
+    ref = hf.hf_srv_wait(fresh.handle, hf.hf_srv_submit(fresh.handle, r32))
+    fresh.close()
+    assert np.array_equal(switched["gtau"], ref["gtau"]) and switched["d"] == ref["d"]
+    again32 = hf.hf_srv_wait(srv.handle, hf.hf_srv_submit(srv.handle, r32))
+    assert again32["warm"] == 1
+    srv.close()

@@ -45,7 +45,14 @@ def test_noalloc_matches_workspace_lattice_step_twice(hf):
         d_sigma.copy_(torch.from_numpy(sigma))
         d_gloc.fill_(float("nan"))
         torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         hf.hf_lattice_step_noalloc(ctx.handle, d_sigma.data_ptr(), d_gloc.data_ptr())
+        free_after = torch.cuda.mem_get_info()[0]
+        if call > 0:
+            # the first call may load the module and look up the static array; from then on a
+            # call must leave the device's free memory exactly as it found it (a cudaMalloc inside
+            # the library would not show in torch's allocator statistics, but shows here)
+            assert free_after == free_before, (free_before, free_after)
         got = d_gloc.cpu().numpy()
         assert np.all(np.isfinite(got)), "call %d left outputs unwritten" % call
         assert np.abs(got - want).max() < 1e-12 * np.abs(want).max(), "call %d" % call
