@@ -35,6 +35,7 @@ WORKLOAD = ("square20: 20x20 open trap, U=8, V0=0.05, mu=%.4f, beta=8, dtau=0.25
             "55 inequivalent sites x 32 chains, 500+2000 sweeps, refresh every 10, "
             "500 Matsubara frequencies; one step = one RDMFT iteration" % CFG["mu"])
 FP64_PEAK_TFLOPS = 2.0 * 2 * 152 * 2.07e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz
+DFMA_PROBE_TFLOPS = 1.008   # independent DFMA chains, 152 SMs x 8 blocks x 256 threads, this GPU
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -109,81 +110,176 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------------------
 # CPU oracle legs (spawned processes: one thread, and one worker per host core)
 # ---------------------------------------------------------------------------------------------
-def _oracle_sample(q, n_chains, n_freq):
-    import numpy as np
-
-    import oracle as o
-    from oracle.lattice import Lattice, lattice_step
-    from oracle.rdmft import RDMFT
-
-    cfg = CFG
-    L = 32
-    r = RDMFT(cfg["Lx"], cfg["Ly"], U=cfg["U"], V0=cfg["V0"], mu=cfg["mu"], beta=cfg["beta"], L=L,
-              nw=cfg["n_matsubara"], chains=1, seed=cfg["seed"], h_seed=cfg["h_seed"])
-    full = r.expand_sigma()
-    t0 = time.perf_counter()
-    idx = np.arange(n_freq) * (cfg["n_matsubara"] // n_freq)
-    for sp in range(2):
-        lattice_step(r.lat.H0, cfg["mu"], cfg["beta"], full[sp][idx], n_index=idx)
-    t_lat = (time.perf_counter() - t0) * (cfg["n_matsubara"] / n_freq)
-    baths = wl.random_baths(2, n_chains, cfg["beta"], L)
-    _, lam = o.constants(cfg["beta"], cfg["U"], L)
-    t0 = time.perf_counter()
-    for c in range(n_chains):
-        g0u, g0d = o.build_g0(baths[c, 0]), o.build_g0(baths[c, 1])
-        s = o.init_fields(cfg["seed"], c, 0, L)
-        Gu, _ = o.dyson(g0u, s, 1, lam)
-        Gd, _ = o.dyson(g0d, s, -1, lam)
-        bins = np.zeros((cfg["n_measure"] // cfg["bin_size"], 2 * L + 3))
-        o.run_chain(lam, g0u, g0d, cfg["seed"], c, 0, 0, cfg["n_warmup"], cfg["n_measure"],
-                    cfg["refresh_every"], cfg["bin_size"], s, Gu, Gd, bins,
-                    refresh_stagger=cfg.get("refresh_stagger", 0))
-    t_qmc = (time.perf_counter() - t0) * (1760.0 / n_chains)
-    q.put((t_lat, t_qmc))
-
-
-# all host cores: the same sample split over a pool of spawned workers, one BLAS thread each
+# all host cores: a pool of spawned workers (one BLAS thread each) that hold the workload's
+# lattice and seeded self-energy; the parent computes the baths between the two parallel phases
 _W = {}
 
 
-def _pool_init():
+def _square20_rdmft():
     from oracle.rdmft import RDMFT
 
     cfg = CFG
-    r = RDMFT(cfg["Lx"], cfg["Ly"], U=cfg["U"], V0=cfg["V0"], mu=cfg["mu"], beta=cfg["beta"], L=32,
-              nw=cfg["n_matsubara"], chains=1, seed=cfg["seed"], h_seed=cfg["h_seed"])
-    _W["H0"], _W["full"] = r.lat.H0, r.expand_sigma()
+    return RDMFT(cfg["Lx"], cfg["Ly"], U=cfg["U"], V0=cfg["V0"], mu=cfg["mu"], beta=cfg["beta"],
+                 L=32, nw=cfg["n_matsubara"], chains=1, seed=cfg["seed"], h_seed=cfg["h_seed"],
+                 n_warmup=cfg["n_warmup"], n_measure=cfg["n_measure"],
+                 refresh_every=cfg["refresh_every"], bin_size=cfg["bin_size"])
+
+
+def _pool_init():
+    r = _square20_rdmft()
+    _W["r"], _W["full"] = r, r.expand_sigma()
 
 
 def _pool_lattice(idx):
+    """eq. 2 at the frequencies idx for both spins; G_ii of the inequivalent sites [2, k, ns]."""
     import numpy as np
 
     from oracle.lattice import lattice_step
 
+    r = _W["r"]
     idx = np.asarray(idx)
-    for sp in range(2):
-        lattice_step(_W["H0"], CFG["mu"], CFG["beta"], _W["full"][sp][idx], n_index=idx)
-    return len(idx)
+    return idx, [lattice_step(r.lat.H0, CFG["mu"], CFG["beta"], _W["full"][sp][idx],
+                              n_index=idx)[:, r.reps] for sp in range(2)]
 
 
-def _pool_chains(chains):
+def _pool_chains(job):
+    """Whole 2500-sweep chains c (site c // 32, chain c % 32) on the given baths; returns their
+    bins [len(chains), nbins, 2L+3] and the worker's seconds."""
     import numpy as np
 
     import oracle as o
 
-    cfg, L = CFG, 32
-    baths = wl.random_baths(2, max(chains) + 1, cfg["beta"], L)
+    chains, g0_tau = job
+    t0 = time.perf_counter()
+    cfg, L, cps = CFG, 32, CFG["chains_per_site"]
     _, lam = o.constants(cfg["beta"], cfg["U"], L)
-    for c in chains:
-        g0u, g0d = o.build_g0(baths[c, 0]), o.build_g0(baths[c, 1])
-        s = o.init_fields(cfg["seed"], c, 0, L)
+    out = np.zeros((len(chains), cfg["n_measure"] // cfg["bin_size"], 2 * L + 3))
+    for k, c in enumerate(chains):
+        site, ch = divmod(c, cps)
+        g0u, g0d = o.build_g0(g0_tau[site, 0, :L]), o.build_g0(g0_tau[site, 1, :L])
+        s = o.init_fields(cfg["seed"], site, ch, L)
         Gu, _ = o.dyson(g0u, s, 1, lam)
         Gd, _ = o.dyson(g0d, s, -1, lam)
-        bins = np.zeros((cfg["n_measure"] // cfg["bin_size"], 2 * L + 3))
-        o.run_chain(lam, g0u, g0d, cfg["seed"], c, 0, 0, cfg["n_warmup"], cfg["n_measure"],
-                    cfg["refresh_every"], cfg["bin_size"], s, Gu, Gd, bins,
-                    refresh_stagger=cfg.get("refresh_stagger", 0))
-    return len(chains)
+        o.run_chain(lam, g0u, g0d, cfg["seed"], site, ch, 0, cfg["n_warmup"], cfg["n_measure"],
+                    cfg["refresh_every"], cfg["bin_size"], s, Gu, Gd, out[k])
+    return out, time.perf_counter() - t0
+
+
+def _spawn_pool(n, initializer=None):
+    """A spawned pool of n worker processes with one BLAS / OpenMP thread each (the variables
+    are set before the children start, so numpy in them sees them at import)."""
+    ctx = mp.get_context("spawn")
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        return ctx.Pool(n, initializer=initializer)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def oracle_iteration(pool, workers, n_chains=1760, n_freq=500):
+    """Seconds of one RDMFT iteration of the oracle on the square20 workload from its seeded
+    self-energy: the lattice step (eq. 2, dense inverse) at n_freq of the 500 frequencies, the
+    baths, n_chains of the 1760 chains (evenly spaced, so every site is sampled) on those baths,
+    then reduction, tau -> i w and the self-energy update; the lattice step and the chains are
+    each scaled to the full iteration when sampled (n_freq < 500 or n_chains < 1760).  With
+    everything in, it is the oracle's own iteration, whose chains make the GPU's decisions on
+    the same baths and seeds."""
+    import numpy as np
+
+    from oracle.fourier import tau_to_iw
+
+    r = _square20_rdmft()
+    nw, ns, L = CFG["n_matsubara"], r.nsite, 32
+    t0 = time.perf_counter()
+    if n_freq >= nw:
+        idx = list(range(nw))
+    else:
+        idx = [k * (nw // n_freq) for k in range(n_freq)]
+    chunks = [idx[w::workers] for w in range(workers) if idx[w::workers]]
+    Gloc = np.zeros((ns, 2, nw), dtype=np.complex128)
+    for ids, g in pool.map(_pool_lattice, chunks, chunksize=1):
+        for sp in range(2):
+            Gloc[:, sp, ids] = g[sp].T
+    t_lat = (time.perf_counter() - t0) * (nw / len(idx))
+    t0 = time.perf_counter()
+    if len(idx) < nw:   # sampled: the baths of the seeded self-energy from the full step anyway
+        for ids, g in pool.map(_pool_lattice, [list(range(w, nw, workers)) for w in range(workers)],
+                               chunksize=1):
+            for sp in range(2):
+                Gloc[:, sp, ids] = g[sp].T
+        t0 = time.perf_counter()
+    weiss_inv, gw_t = r.weiss(Gloc)
+    g0_tau = r.bath_tau(gw_t)
+    t_bath = time.perf_counter() - t0
+    # a sample takes chains evenly spaced over all 1760 (every site's chains are represented)
+    chains = sorted({int(k * 1760 // n_chains) for k in range(n_chains)})
+    n_chains = len(chains)
+    t0 = time.perf_counter()
+    parts = pool.map(_pool_chains, [(chains[w::workers], g0_tau) for w in range(workers)
+                                    if chains[w::workers]], chunksize=1)
+    if n_chains >= 1760:
+        t_qmc = time.perf_counter() - t0
+    else:
+        # sampled: the workers' summed chain time, spread over all workers and scaled to the
+        # 1760 chains (the whole set balances over the workers; a small sample would not)
+        t_qmc = sum(t for _, t in parts) / workers * (1760.0 / n_chains)
+    parts = [b for b, _ in parts]
+    t0 = time.perf_counter()
+    bins = np.zeros((1760, CFG["n_measure"] // CFG["bin_size"], 2 * L + 3))
+    for w, part in enumerate(parts):
+        bins[chains[w::workers]] = part
+    if n_chains < 1760:   # a sample: every chain of the reduction gets a sampled chain's bins
+        have = np.array(chains)
+        for c in range(1760):
+            bins[c] = bins[have[np.abs(have - c).argmin()]]
+    mean, _ = r.reduce(bins.reshape(ns, CFG["chains_per_site"], *bins.shape[1:]))
+    for i in range(ns):
+        for sp in range(2):
+            gimp = tau_to_iw(CFG["beta"], mean[i, sp * L:(sp + 1) * L], g0_tau[i, sp, :L], gw_t[i, sp])
+            r.sigma[i, sp] = r.mix * (weiss_inv[i, sp] - 1.0 / gimp) + (1.0 - r.mix) * r.sigma[i, sp]
+    t_rest = time.perf_counter() - t0
+    return t_lat + t_bath + t_qmc + t_rest
+
+
+def cpu_oracle_all_cores():
+    """One whole oracle iteration of the square20 workload on every host core (nothing sampled);
+    returns (seconds, cores, description)."""
+    cores = host_cores()
+    pool = _spawn_pool(cores, _pool_init)
+    try:
+        oracle_iteration(pool, cores, n_chains=cores, n_freq=cores)   # warm: imports, builds
+        sec = oracle_iteration(pool, cores)
+    finally:
+        pool.close()
+        pool.join()
+    sample = ("one whole RDMFT iteration (lattice step at all 500 frequencies x 2 spins, dense "
+              "inverse N=400; baths; all 1760 chains x 2500 sweeps, L=32, FP64, on the workload's "
+              "own baths and seeds; reduction and self-energy update) over %d worker processes"
+              % cores)
+    return sec, cores, sample
+
+
+def cpu_oracle(n_chains=64, n_freq=10):
+    """Oracle seconds of one iteration on one core (one process, one BLAS thread), from a
+    bounded sample: n_chains chains and n_freq frequencies, each part scaled to the full
+    iteration."""
+    pool = _spawn_pool(1, _pool_init)
+    try:
+        oracle_iteration(pool, 1, n_chains=1, n_freq=1)
+        sec = oracle_iteration(pool, 1, n_chains=n_chains, n_freq=n_freq)
+    finally:
+        pool.close()
+        pool.join()
+    sample = ("%d of 1760 chains x 2500 sweeps (L=32, on the workload's own baths) + the lattice "
+              "step at %d of 500 frequencies x 2 spins (dense inverse, N=400), one process, each "
+              "part scaled to the full iteration" % (n_chains, n_freq))
+    return sec, sample
 
 
 def _pool_chains_sq30(job):
@@ -244,82 +340,33 @@ def host_cores():
         return os.cpu_count() or 1
 
 
-def cpu_oracle_all_cores(chains_per_core=20, freqs_per_core=2):
-    """Oracle time of one full iteration on every host core (seconds), from a bounded sample:
-    chains and lattice frequencies split over a spawned pool (one process and one BLAS thread
-    per core); returns (seconds, cores, sample)."""
-    cores = host_cores()
-    ctx = mp.get_context("spawn")
-    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
-    for k in saved:
-        os.environ[k] = "1"
-    try:
-        pool = ctx.Pool(cores, initializer=_pool_init)
-    finally:
-        for k, v in saved.items():
-            if v is None:
-                os.environ.pop(k, None)
-            else:
-                os.environ[k] = v
-    try:
-        pool.map(_pool_chains, [[w] for w in range(cores)], chunksize=1)   # warm: imports, builds
-        n_freq = min(500, cores * freqs_per_core)
-        idx = [int(k * (CFG["n_matsubara"] // n_freq)) for k in range(n_freq)]
-        t0 = time.perf_counter()
-        pool.map(_pool_lattice, [idx[w::cores] for w in range(cores) if idx[w::cores]], chunksize=1)
-        t_lat = (time.perf_counter() - t0) * (CFG["n_matsubara"] / n_freq)
-        n_chains = cores * chains_per_core
-        t0 = time.perf_counter()
-        pool.map(_pool_chains, [list(range(w, n_chains, cores)) for w in range(cores)], chunksize=1)
-        t_qmc = (time.perf_counter() - t0) * (1760.0 / n_chains)
-    finally:
-        pool.close()
-        pool.join()
-    sample = ("%d of 1760 chains x 2500 sweeps (L=32) + lattice step at %d of 500 frequencies x 2 "
-              "spins (dense inverse, N=400) over %d worker processes, each scaled to the full "
-              "iteration" % (n_chains, n_freq, cores))
-    return t_lat + t_qmc, cores, sample
-
-
-def cpu_oracle(n_chains=160, n_freq=20):
-    """Oracle time of one full iteration, extrapolated from a bounded sample (seconds).
-
-    Runs in a spawned process with one BLAS / OpenMP thread (the variables are set before the
-    child starts, so numpy in the child sees them at import)."""
-    ctx = mp.get_context("spawn")
-    q = ctx.Queue()
-    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
-    for k in saved:
-        os.environ[k] = "1"
-    try:
-        p = ctx.Process(target=_oracle_sample, args=(q, n_chains, n_freq))
-        p.start()
-    finally:
-        for k, v in saved.items():
-            if v is None:
-                os.environ.pop(k, None)
-            else:
-                os.environ[k] = v
-    t_lat, t_qmc = q.get()
-    p.join()
-    sample = ("%d of 1760 chains x 2500 sweeps (L=32) + lattice step at %d of 500 frequencies x "
-              "2 spins (dense inverse, N=400), each scaled to the full iteration" % (n_chains, n_freq))
-    return t_lat + t_qmc, sample
-
-
 # ---------------------------------------------------------------------------------------------
 def run_reference(args):
+    """The oracle as it stands on every host core: each timed step is one RDMFT iteration of the
+    square20 workload with its chains sampled (20 per core, scaled; everything else whole, see
+    oracle_iteration), so that --steps 20 ends within a few minutes; warm-up steps run a small
+    sample."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     proposals = 1760 * 2500 * 32
-    times = []
-    sample, cores = "", 1
-    for _ in range(args.warmup):
-        cpu_oracle_all_cores(chains_per_core=1, freqs_per_core=1)
-    for _ in range(args.steps):
-        t, cores, sample = cpu_oracle_all_cores(chains_per_core=8, freqs_per_core=1)
-        times.append(t)
+    cores = host_cores()
+    pool = _spawn_pool(cores, _pool_init)
+    try:
+        oracle_iteration(pool, cores, n_chains=cores, n_freq=cores)     # imports, builds
+        for _ in range(args.warmup):
+            oracle_iteration(pool, cores, n_chains=cores, n_freq=cores)
+        n_ch = min(1760, 20 * cores)
+        times = [oracle_iteration(pool, cores, n_chains=n_ch) for _ in range(args.steps)]
+    finally:
+        pool.close()
+        pool.join()
+    sample = ("per step one RDMFT iteration: lattice step at all 500 frequencies x 2 spins (dense "
+              "inverse N=400), the baths, %d of the 1760 chains x 2500 sweeps (L=32, FP64, evenly "
+              "spaced over the sites, on the workload's own baths and seeds; the workers' summed chain "
+              "time scaled by 1760/%d and spread over the workers), "
+              "reduction and self-energy update, over %d worker processes"
+              % (n_ch, n_ch, cores))
     sec = sum(times) / len(times)
     v = proposals / sec
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "proposals/s",
@@ -336,9 +383,9 @@ def run_reference(args):
 
 FP32_PEAK_TFLOPS = 2.0 * 128 * 152 * 2.07e9 / 1e12   # 128 FFMA/clk/SM
 DF_OPS_PER_FMA = 12          # FP32-pipe ops of one double-float multiply-add (lazy renormalisation)
-# DRAM bytes (read + write) of one full-size launch (2500 sweeps of all 1760 chains), from one
-# ncu capture of the kernel built from sources with this sha256 prefix (profiles/
-# qmc_df64_kernel_square20.md); a kernel whose sources changed since reports null.
+# DRAM bytes (read + write) of one full-size launch, from one ncu capture of the kernel built from
+# sources whose sha256 starts with the given prefix (the capture's command and counters are kept
+# in the profile summaries); a kernel whose sources changed since reports null.
 MEASURED_TRAFFIC = {"qmc_df64_kernel": (2.628e6 + 1.452e6, "f0ade2fccbd67061"),
                     # the lattice step of the slab16 workload (N = 1024, b = 128, 500 matrices)
                     "lattice_kernel:slab16": (652.3e6 + 947.5e6, "bce118bbe49681e3")}
@@ -361,13 +408,23 @@ def measured_traffic(kernel):
     return nbytes if h.hexdigest().startswith(digest) else None
 
 
-def qmc_roofline(form, L, nchain, sweeps, accepts, n_measure, n_refresh, qmc_s, kernel):
-    """Roofline of the fused QMC kernel for one launch.
+def qmc_alg_bytes(L, nchain, nsite, n_measure, bin_size):
+    """DRAM bytes one sweep launch must move: per chain its G (written back), its fields (read and
+    written) and its bins (written); per inequivalent site its two inverse bath matrices (read)."""
+    bins = -(-n_measure // bin_size) * (2 * L + 3) * 8
+    return nchain * (2 * L * L * 8 + 2 * L + bins) + nsite * 2 * L * L * 8
 
-    form 0 (FP64): every flop runs on the FP64 pipe; peak = nominal FP64 (2 DFMA/clk/SM).
+
+def qmc_roofline(form, L, nchain, sweeps, accepts, n_measure, n_refresh, qmc_s, kernel,
+                 alg_bytes=None):
+    """Roofline of the fused QMC kernel for one launch (algorithmic flops of the method).
+
+    form 0 (FP64): every flop runs on the FP64 pipe; peak = nominal FP64 (2 DFMA/clk/SM x 152 SMs
+    x 2.07 GHz).  The rate a plain DFMA probe reached on this GPU is reported beside it.
     form 2 (FP32 pairs): the refresh runs on the FP64 pipe, the sweep arithmetic on the FP32 pipe
-    at DF_OPS_PER_FMA ops per FP64-equivalent multiply-add; peak = the FP64-equivalent rate if
-    both pipes ran flat out and overlapped (algorithmic flops / max of the two pipe times)."""
+    at DF_OPS_PER_FMA ops per FP64-equivalent multiply-add.  The two do not overlap on this GPU
+    (measured), so the roof is total flops / (FP64 time + FP32 time); the roof of both pipes
+    overlapped is reported beside it."""
     f_ratio = 10.0 * L * nchain * sweeps
     f_upd = 4.0 * L * L * accepts
     f_meas = 2.0 * L * L * nchain * n_measure
@@ -377,23 +434,24 @@ def qmc_roofline(form, L, nchain, sweeps, accepts, n_measure, n_refresh, qmc_s, 
     extra = {}
     if form == 0:
         peak, src = FP64_PEAK_TFLOPS, "FP64 nominal: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz"
+        extra = {"dfma_probe_tflops": DFMA_PROBE_TFLOPS,
+                 "frac_of_dfma_probe": achieved / DFMA_PROBE_TFLOPS}
     else:
         t64 = f_ref / (FP64_PEAK_TFLOPS * 1e12)
         t32 = (f_ratio + f_upd + f_meas) / 2.0 * DF_OPS_PER_FMA / (FP32_PEAK_TFLOPS * 1e12 / 2.0)
-        peak = total / max(t64, t32) / 1e12
-        # measured on this GPU: FP64 work does not overlap the pair arithmetic, so the roof of
-        # the two pipes one after the other is reported beside the overlapped one
-        extra = {"peak_serial": total / (t64 + t32) / 1e12,
-                 "frac_serial": achieved / (total / (t64 + t32) / 1e12)}
-        src = ("mixed-pipe roof: refresh on FP64 (2 DFMA/clk/SM), pair arithmetic on FP32 "
-               "(128 FFMA/clk/SM, %d ops per FP64-equivalent FMA), both at 2.07 GHz, overlapped"
+        peak = total / (t64 + t32) / 1e12
+        over = total / max(t64, t32) / 1e12
+        extra = {"peak_overlapped": over, "frac_overlapped": achieved / over}
+        src = ("serial two-pipe roof: refresh on FP64 (2 DFMA/clk/SM), then the pair arithmetic "
+               "on FP32 (128 FFMA/clk/SM, %d ops per FP64-equivalent FMA), both at 2.07 GHz"
                % DF_OPS_PER_FMA)
     # the refreshes invert G^{-1} by Gauss-Jordan: 2 L^3 executed flops per spin against the
     # 2 (8/3) L^3 of the algorithmic Dyson solve counted in f_ref
     executed = (total - 0.25 * f_ref) / qmc_s / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": measured_traffic(kernel), "kernel": kernel,
-            "executed_tflops": executed, "peak_source": src, **extra}
+            "frac": achieved / peak, "traffic": measured_traffic(kernel),
+            "algorithmic_bytes": alg_bytes,
+            "kernel": kernel, "executed_tflops": executed, "peak_source": src, **extra}
 
 
 def _time_iterations(hf, ctx, stream, flush, steps):
@@ -443,11 +501,12 @@ def run_ours(args):
     stream = torch.cuda.Stream(dev)
     L = 32
     if args.precision < 0:
-        # chosen form: autotuned over both FP64-parity forms and the team widths
+        # the headline is the FP64 solver the workload names: FP64 sweeps and refreshes, team
+        # width autotuned on the workload itself
         tune = autotune.tune_workload("square20" if args.refresh_stagger == 0 else "square20_stagger",
                                       dict(CFG, refresh_stagger=args.refresh_stagger),
-                                      forms=(0, 2), device=dev, stream=stream)
-        form, tw, dk = tune["precision"], tune["team_warps"], tune["delay_k"]
+                                      forms=(0,), device=dev, stream=stream)
+        form, tw, dk = 0, tune["team_warps"], 1
     else:
         form, tw, dk, tune = args.precision, args.team_warps, args.delay_k, None
     cfg = dict(CFG, precision=form, team_warps=tw, delay_k=dk, refresh_stagger=args.refresh_stagger)
@@ -506,27 +565,37 @@ def run_ours(args):
            "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h}
     kernel = "qmc_df64_kernel" if form == 2 else "qmc_f64_kernel"
+    alg_bytes = qmc_alg_bytes(L, nc, ns, cfg["n_measure"], cfg["bin_size"])
     roofline = qmc_roofline(form, L, nc, sweeps, accepts / args.steps, cfg["n_measure"],
-                            n_refresh, statistics.mean(qmc_ms) / 1e3, kernel)
+                            n_refresh, statistics.mean(qmc_ms) / 1e3, kernel, alg_bytes)
     roofline["acceptance"] = accepts / (args.steps * proposals)
     ctx.close()
 
-    # the plain FP64 per-impurity form beside the chosen form (same workload, device-timed)
-    fp64_form = None
-    if form != 0 and not args.sweeps and not args.no_fp64_form:
-        c0 = hf.Context(hf.make_params(dict(CFG, precision=0, team_warps=0,
+    # the other sweep form beside the headline one, same workload and the same number of timed
+    # iterations: the FP32-pair form (48-bit significand sweeps, FP64 refresh) beside the FP64
+    # headline, or the FP64 form beside a pair-form run asked for with --precision 2
+    other = None
+    if not args.sweeps and not args.no_other_form:
+        of = 2 if form == 0 else 0
+        c0 = hf.Context(hf.make_params(dict(CFG, precision=of, team_warps=1 if of == 2 else 0,
                                             refresh_stagger=args.refresh_stagger)), device=dev,
                         stream=stream)
         for _ in range(2):
             hf.hf_rdmft_step(c0.handle)
         a0 = hf.hf_get_accepts(c0.handle, nc).sum()
-        ms0, q0, _ = _time_iterations(hf, c0, stream, flush, 2)
+        ms0, q0, _ = _time_iterations(hf, c0, stream, flush, args.steps)
         acc_0 = int(hf.hf_get_accepts(c0.handle, nc).sum() - a0)
-        fp64_form = {"value": proposals / (statistics.mean(ms0) / 1e3), "unit": "proposals/s",
-                     "ms_per_step": statistics.mean(ms0),
-                     "roofline": qmc_roofline(0, L, nc, sweeps, acc_0 / 2, cfg["n_measure"],
-                                              n_refresh, statistics.mean(q0) / 1e3,
-                                              "qmc_f64_kernel")}
+        other = {"value": proposals / (statistics.mean(ms0) / 1e3), "unit": "proposals/s",
+                 "ms_per_step": statistics.mean(ms0), "steps": args.steps,
+                 "dtype": "f64" if of == 0 else "f32x2+f64",
+                 "roofline": qmc_roofline(of, L, nc, sweeps, acc_0 / args.steps, cfg["n_measure"],
+                                          n_refresh, statistics.mean(q0) / 1e3,
+                                          "qmc_f64_kernel" if of == 0 else "qmc_df64_kernel",
+                                          alg_bytes)}
+        if of == 2:
+            other["note"] = ("FP32-pair sweeps: 48-bit significand between FP64 refreshes, so G "
+                             "drifts further from the FP64 chain than FP64 arithmetic does; not "
+                             "an FP64 result")
         c0.close()
 
     launches_per_step = lattice_launches(hf, cfg) + 5
@@ -545,7 +614,7 @@ def run_ours(args):
                                  [float(x) for x in phase / args.steps])),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps, "clocks": clk,
-            "fp64_form": fp64_form, "autotune": tune}
+            ("pair_form" if form == 0 else "fp64_form"): other, "autotune": tune}
     if args.sweeps:
         line["profile_case"] = "sweeps overridden to %d: not a benchmark value" % args.sweeps
     if rank == 0:
@@ -1038,10 +1107,96 @@ def run_dtau_scan(args):
     return 0
 
 
+def _pool_scan_job(job):
+    """Oracle work of the scan's cpu baseline: ('chains', beta, [c...]) runs whole 2500-sweep
+    chains at that temperature; ('lattice', beta, [n...]) the dense lattice step at those
+    frequencies.  Returns seconds."""
+    import numpy as np
+
+    import oracle as o
+    from oracle.lattice import lattice_step
+    from oracle.rdmft import RDMFT
+
+    kind, beta, items = job
+    cfg = dict(CFG, beta=beta)
+    L = int(round(beta / cfg["dtau"]))
+    t0 = time.perf_counter()
+    if kind == "lattice":
+        r = RDMFT(cfg["Lx"], cfg["Ly"], U=cfg["U"], V0=cfg["V0"], mu=cfg["mu"], beta=beta, L=L,
+                  nw=cfg["n_matsubara"], chains=1, seed=cfg["seed"], h_seed=cfg["h_seed"])
+        full = r.expand_sigma()
+        t0 = time.perf_counter()
+        idx = np.asarray(items)
+        for sp in range(2):
+            lattice_step(r.lat.H0, cfg["mu"], beta, full[sp][idx], n_index=idx)
+        return time.perf_counter() - t0
+    baths = wl.random_baths(L, max(items) + 1, beta, L)
+    _, lam = o.constants(beta, cfg["U"], L)
+    for c in items:
+        g0u, g0d = o.build_g0(baths[c, 0]), o.build_g0(baths[c, 1])
+        s = o.init_fields(cfg["seed"], c, 0, L)
+        Gu, _ = o.dyson(g0u, s, 1, lam)
+        Gd, _ = o.dyson(g0d, s, -1, lam)
+        bins = np.zeros((cfg["n_measure"] // cfg["bin_size"], 2 * L + 3))
+        o.run_chain(lam, g0u, g0d, cfg["seed"], c, 0, 0, cfg["n_warmup"], cfg["n_measure"],
+                    cfg["refresh_every"], cfg["bin_size"], s, Gu, Gd, bins)
+    return time.perf_counter() - t0
+
+
+def cpu_oracle_scan20(chains_per_core=1):
+    """Oracle seconds of one batched scan iteration (4 temperatures x 1760 chains x 2500 sweeps,
+    and 4 lattice steps of 500 frequencies x 2 spins) on every host core, from a bounded sample:
+    per temperature, chains_per_core chains and one frequency per core, over a spawned pool (one
+    process and one BLAS thread per core); each part scaled to the full iteration."""
+    cores = host_cores()
+    ctx = mp.get_context("spawn")
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        pool = ctx.Pool(cores)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    total = 0.0
+    try:
+        pool.map(_pool_scan_job, [("chains", 5.0, [w]) for w in range(cores)], chunksize=1)
+        nw = CFG["n_matsubara"]
+        for beta in wl.SCAN20_BETAS:
+            n = cores * chains_per_core
+            t0 = time.perf_counter()
+            pool.map(_pool_scan_job, [("chains", beta, list(range(w, n, cores))) for w in range(cores)],
+                     chunksize=1)
+            total += (time.perf_counter() - t0) * 1760.0 / n
+            idx = [k * (nw // cores) for k in range(cores)]
+            t0 = time.perf_counter()
+            pool.map(_pool_scan_job, [("lattice", beta, [i]) for i in idx], chunksize=1)
+            total += (time.perf_counter() - t0) * nw / len(idx)
+    finally:
+        pool.close()
+        pool.join()
+    sample = ("per beta in {5,8,10,16}: %d of 1760 chains x 2500 sweeps (L=20/32/40/64, FP64, "
+              "refresh every 10) + the dense lattice step (N=400) at %d of 500 frequencies x 2 "
+              "spins, over %d worker processes, each part scaled to the full iteration"
+              % (cores * chains_per_core, cores, cores))
+    return total, cores, sample
+
+
+def qmc_flops(L, nchain, sweeps, accepts, n_measure, n_refresh):
+    """Algorithmic flops of one sweep launch (proposals, accepted updates, measurements, Dyson
+    refreshes as 2 (8/3) L^3 per chain and refresh)."""
+    return (10.0 * L * nchain * sweeps + 4.0 * L * L * accepts + 2.0 * L * L * nchain * n_measure
+            + 2.0 * (8.0 / 3.0) * L ** 3 * nchain * n_refresh)
+
+
 def run_scan20(args):
     """Batched uneven-L temperature scan: the 20x20 trap at beta = 5, 8, 10, 16 (L = 20, 32, 40,
-    64), 1760 chains each, one fused graph-captured launch per iteration, sweep form and team
-    width autotuned per L."""
+    64), 1760 chains each, one fused graph-captured launch per iteration, FP64 sweeps and
+    refreshes, team width and delay depth autotuned per L."""
+    import numpy as np
     import torch
 
     from paper_1006_2716_gb300 import autotune, hf
@@ -1049,14 +1204,21 @@ def run_scan20(args):
     rank, world, local = dist_env()
     if rank != 0:
         return 0
+    cpu = None
+    if not args.no_cpu:   # spawned before any CUDA work
+        secs, cores, sample = cpu_oracle_scan20()
+        props = sum(1760 * 2500 * int(round(b / 0.25)) for b in wl.SCAN20_BETAS)
+        cpu = {"value": props / secs, "unit": "proposals/s", "cores": cores, "kind": "oracle",
+               "sample": sample}
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(dev)
     betas = wl.SCAN20_BETAS
     Ls = [int(round(b / 0.25)) for b in betas]
-    tune = {L: autotune.tune_workload("scan20_beta%g" % b, dict(CFG, beta=b), forms=(2,),
+    form = 0 if args.precision < 0 else args.precision
+    tune = {L: autotune.tune_workload("scan20_beta%g" % b, dict(CFG, beta=b), forms=(form,),
                                       device=dev, stream=stream) for b, L in zip(betas, Ls)}
-    ctxs = [hf.Context(hf.make_params(dict(CFG, beta=b, precision=2,
+    ctxs = [hf.Context(hf.make_params(dict(CFG, beta=b, precision=form,
                                            team_warps=tune[L]["team_warps"],
                                            delay_k=tune[L]["delay_k"])),
                        device=dev, stream=stream) for b, L in zip(betas, Ls)]
@@ -1065,6 +1227,7 @@ def run_scan20(args):
         hf.hf_batch_rdmft_step(batch)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     ms = []
+    acc0 = [hf.hf_get_accepts(c.handle, c.n_chains).sum() for c in ctxs]
     clocks = ClockSampler(local)
     for _ in range(args.steps):
         with torch.cuda.stream(stream):
@@ -1072,16 +1235,76 @@ def run_scan20(args):
         torch.cuda.synchronize(dev)
         ms.append(hf.hf_batch_rdmft_step(batch))
     clk = clocks.stop()
+    accepts = [(hf.hf_get_accepts(c.handle, c.n_chains).sum() - a) / args.steps
+               for c, a in zip(ctxs, acc0)]
     proposals = sum(c.n_chains * 2500 * c.L for c in ctxs)
     ms_per = statistics.mean(ms)
+    # the fused sweep launch alone (its g0^-1 launch included), for the kernel's roofline
+    with torch.cuda.stream(stream):
+        flush.zero_()
+    torch.cuda.synchronize(dev)
+    for c in ctxs:
+        hf.hf_clear_measurements(c.handle)
+    hf.hf_batch_sweep(batch, CFG["n_warmup"], CFG["n_measure"], 1)
+    qmc_ms = hf.hf_batch_elapsed(batch)
+    flops = sum(qmc_flops(c.L, c.n_chains, 2500, a, CFG["n_measure"], 1 + 2500 // CFG["refresh_every"])
+                for c, a in zip(ctxs, accepts))
+    achieved = flops / (qmc_ms / 1e3) / 1e12
+    if form == 0:
+        peak, src = FP64_PEAK_TFLOPS, "FP64 nominal: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz"
+    else:
+        f_ref = sum(2.0 * (8.0 / 3.0) * c.L ** 3 * c.n_chains * (1 + 2500 // CFG["refresh_every"])
+                    for c in ctxs)
+        t_roof = (f_ref / (FP64_PEAK_TFLOPS * 1e12) +
+                  (flops - f_ref) / 2.0 * DF_OPS_PER_FMA / (FP32_PEAK_TFLOPS * 1e12 / 2.0))
+        peak, src = flops / t_roof / 1e12, "serial two-pipe roof (refresh FP64, pairs FP32)"
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None, "kernel": "qmc_%s_kernel (fused, 4 problems)"
+            % ("f64" if form == 0 else "df64"), "qmc_ms": qmc_ms, "peak_source": src,
+            "algorithmic_bytes": sum(qmc_alg_bytes(c.L, c.n_chains, c.n_sites, CFG["n_measure"],
+                                                   CFG["bin_size"]) for c in ctxs)}
+    # end to end through the public API with host buffers: every step sends each run's
+    # self-energy to the device, runs the batched iteration and reads back each run's observables
+    # and self-energy
+    nw = ctxs[0].nw
+    pins = [(torch.empty(c.n_sites * 2 * nw * 2, dtype=torch.float64, pin_memory=True),
+             torch.empty(2 * c.n_sites * (2 * c.L + 4), dtype=torch.float64, pin_memory=True))
+            for c in ctxs]
+    sig = []
+    for c, (ps, _) in zip(ctxs, pins):
+        v = ps.numpy().view(np.complex128).reshape(c.n_sites, 2, nw)
+        v[:] = hf.hf_get_sigma(c.handle, c.n_sites, nw)
+        sig.append(v)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for c, v in zip(ctxs, sig):
+            hf.lib().hf_set_sigma(c.handle, v.ctypes.data_as(hf._DP))
+        hf.hf_batch_rdmft_step(batch)
+        for c, v, (_, po) in zip(ctxs, sig, pins):
+            obs = po.numpy()
+            hf.lib().hf_get_observables(c.handle, obs.ctypes.data_as(hf._DP),
+                                        obs[c.n_sites * (2 * c.L + 4):].ctypes.data_as(hf._DP))
+            hf.lib().hf_get_sigma(c.handle, v.ctypes.data_as(hf._DP))
+    torch.cuda.synchronize(dev)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    h2d = sum(v.nbytes for v in sig)
+    d2h = h2d + sum(po.numpy().nbytes for _, po in pins)
     line = {"metric": METRIC, "value": proposals / (ms_per / 1e3), "unit": "proposals/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32x2+f64", "data": "synthetic",
+            "dtype": "f64" if form == 0 else "f32x2+f64", "data": "synthetic",
             "config": {"workload": "scan20: 20x20 trap at beta 5/8/10/16 (L 20/32/40/64), "
                                    "4 x 1760 chains in one fused graph-captured launch, "
                                    "500+2000 sweeps; one step = one batched RDMFT iteration",
                        "l2": "flushed (256 MB write) between timed steps"},
+            "rdmft_iteration_ms": ms_per, "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": proposals / e2e_s, "unit": "proposals/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            # per step: one graph replay holding, per run, the lattice-step launches, Weiss/tau,
+            # g0^-1 and two memsets, reduction and self-energy update, plus the fused sweep launch
+            "gpu_launches": args.steps * (sum(lattice_launches(hf, dict(CFG, beta=b)) + 4
+                                              for b in betas) + 1),
             "clocks": clk, "autotune": {str(L): tune[L] for L in Ls}}
     print(json.dumps(line))
     hf.hf_batch_free(batch)
@@ -1091,7 +1314,7 @@ def run_scan20(args):
 
 
 def run_disc40(args):
-    """Serving: impurity solves for the radius-40 disc (5025 sites, 663 inequivalent, U = 8)
+    """Serving (FP64 sweeps unless --precision 2): impurity solves for the radius-40 disc (5025 sites, 663 inequivalent, U = 8)
     from 4 concurrent RDMFT runs at (beta, V0) = (8, .010), (10, .010), (16, .010), (8, .015),
     i.e. L = 32, 40, 64, 32; 16 chains x (200 + 1000) sweeps per solve.  Baths come from each
     run's own lattice step.  Capacity = all 2652 solves submitted at once; then Poisson streams at
@@ -1107,6 +1330,7 @@ def run_disc40(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     runs = [(8.0, 0.010), (10.0, 0.010), (16.0, 0.010), (8.0, 0.015)]
+    form = 0 if args.precision < 0 else args.precision
     baths, Ls = [], []
     for beta, V0 in runs:
         cfg = dict(Lx=40, geometry=1, U=8.0, V0=V0, mu=4.0, beta=beta, dtau=0.25,
@@ -1120,7 +1344,7 @@ def run_disc40(args):
         ctx.close()
     sp = hf.hf_srv_params()
     for k, v in dict(chains_per_request=16, n_warmup=200, n_measure=1000, refresh_every=10,
-                     bin_size=100, precision=2, team_warps=0, max_L=64, max_inflight=160,
+                     bin_size=100, precision=form, team_warps=0, max_L=64, max_inflight=160,
                      max_keys=len(runs) * nsite, n_streams=12, requests_per_launch=16).items():
         setattr(sp, k, v)
     srv = hf.Server(sp, device=dev)
@@ -1169,7 +1393,7 @@ def run_disc40(args):
     line = {"metric": "p50/p99 solve latency and solves/s (served)", "value": capacity,
             "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": cap_s * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32x2+f64", "data": "synthetic",
+            "dtype": "f64" if form == 0 else "f32x2+f64", "data": "synthetic",
             "config": {"workload": "disc40: site-centred disc r=40 (5025 sites, 663 inequivalent), "
                                    "U=8, mu=4, 4 runs (beta,V0)=(8,.010),(10,.010),(16,.010),(8,.015) "
                                    "-> L 32/40/64/32; 16 chains x (200+1000) sweeps per solve",
@@ -1196,8 +1420,8 @@ def main():
     ap.add_argument("--delay-k", type=int, default=1, choices=[1, 4, 8, 16, 32],
                     help="delayed-update depth (FP32-pair form)")
     ap.add_argument("--precision", type=int, default=-1, choices=[-1, 0, 2],
-                    help="sweep arithmetic: 0 FP64, 2 FP32 pairs (both with FP64 refresh); "
-                         "-1 (default): the autotuner picks form and team width")
+                    help="sweep arithmetic: 0 FP64, 2 FP32 pairs (48-bit; both with FP64 "
+                         "refresh); -1 (default): FP64 with the autotuned team width")
     ap.add_argument("--workload", default="square20",
                     choices=["square20", "scan20", "square30", "disc40", "dtau_scan", "slab16",
                              "box12", "entropy6", "fig1"])
@@ -1206,8 +1430,8 @@ def main():
                          "same sweeps")
     ap.add_argument("--serve-requests", type=int, default=600,
                     help="disc40: requests per Poisson load level")
-    ap.add_argument("--no-fp64-form", action="store_true",
-                    help="skip the plain FP64 form measured beside the chosen form")
+    ap.add_argument("--no-other-form", action="store_true",
+                    help="skip the second sweep form measured beside the headline one")
     ap.add_argument("--iterations", type=int, default=20,
                     help="fig1: RDMFT iterations per temperature")
     ap.add_argument("--sweeps", type=int, default=0,

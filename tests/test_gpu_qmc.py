@@ -1,8 +1,11 @@
 """Parity of the FP64-class CUDA Hirsch-Fye paths with the CPU oracle, through the C ABI.
 
-precision 0 = FP64 sweeps, precision 2 = FP32-pair sweeps with FP64 refresh.  Bar for both:
-identical accept decisions under the same Philox stream (fields compared after every sweep), G
-within 1e-10 of the oracle relative to max|G|, measurement bins within 1e-10.
+precision 0 = FP64 sweeps (the FP64 solver), precision 2 = FP32-pair sweeps (a 48-bit
+significand between FP64 refreshes; not FP64 arithmetic).  Bar: identical accept decisions under
+the same Philox stream (fields compared after every sweep) and G within 1e-10 of the oracle
+relative to max|G| for both; measurement bins within 1e-10 for the FP64 form.  The pair form's
+bins average G over the sweeps between refreshes, where its 48-bit updates drift further from
+FP64 than FP64 itself does; they are held to 5e-10, its own bar, which is not an FP64 claim.
 """
 import numpy as np
 import pytest
@@ -112,8 +115,7 @@ def test_sweeps_identical_decisions(hf, L, beta, precision, team_warps, stagger)
         x = np.concatenate(x)
         mean = x.mean(axis=0)
         err = x.std(axis=0, ddof=1) / np.sqrt(x.shape[0])
-        # the bins average G over the sweeps between refreshes, where the FP32-pair form's
-        # 48-bit updates drift further from FP64 than at the refreshes checked above
+        # FP64 form: the FP64 bar; the 48-bit pair form: its own, looser bar (module docstring)
         tol = 1e-10 if precision == 0 else 5e-10
         assert np.abs(gtau - mean[:2 * L]).max() < tol
         assert abs(n[0] - mean[2 * L]) < tol and abs(n[1] - mean[2 * L + 1]) < tol
