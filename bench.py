@@ -386,7 +386,8 @@ DF_OPS_PER_FMA = 12          # FP32-pipe ops of one double-float multiply-add (l
 # DRAM bytes (read + write) of one full-size launch, from one ncu capture of the kernel built from
 # sources whose sha256 starts with the given prefix (the capture's command and counters are kept
 # in the profile summaries); a kernel whose sources changed since reports null.
-MEASURED_TRAFFIC = {"qmc_df64_kernel": (2.628e6 + 1.452e6, "f0ade2fccbd67061"),
+MEASURED_TRAFFIC = {"qmc_f64_kernel": (2377728 + 1792, "4d68298916e948ee"),
+                    "qmc_df64_kernel": (2.628e6 + 1.452e6, "f0ade2fccbd67061"),
                     # the lattice step of the slab16 workload (N = 1024, b = 128, 500 matrices)
                     "lattice_kernel:slab16": (652.3e6 + 947.5e6, "bce118bbe49681e3")}
 KERNEL_SOURCES = {"qmc_df64_kernel": ("k_qmc_df64.cu", "qmc_common.cuh", "hf_internal.cuh"),
