@@ -36,6 +36,18 @@ WORKLOAD = ("square20: 20x20 open trap, U=8, V0=0.05, mu=%.4f, beta=8, dtau=0.25
             "500 Matsubara frequencies; one step = one RDMFT iteration" % CFG["mu"])
 FP64_PEAK_TFLOPS = 2.0 * 2 * 152 * 2.07e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz
 DFMA_PROBE_TFLOPS = 1.008   # independent DFMA chains, 152 SMs x 8 blocks x 256 threads, this GPU
+
+
+def _measured_peak(key, fallback):
+    """A measured peak of this GPU pool (MEASURED_PEAKS.json), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)[key])
+    except (OSError, ValueError, KeyError):
+        return fallback
+
+
+MEASURED_BF16_SUSTAINED = _measured_peak("bf16_tflops_sustained", 1700.0)
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -971,7 +983,7 @@ def run_square30(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(dev)
-    cfg = dict(wl.CONFIGS["square30"])
+    cfg = dict(wl.CONFIGS["square30"], refresh_gj=args.refresh_gj)
     if args.sweeps:
         # short QMC launch for profiling captures only (not a benchmark value)
         nm = args.sweeps - args.sweeps // 5
@@ -991,13 +1003,45 @@ def run_square30(args):
     accepts = int(hf.hf_get_accepts(ctx.handle, nc).sum() - acc0) / args.steps
     ms_per = statistics.mean(ms_steps)
     qmc_s = statistics.mean(qmc_ms) / 1e3
-    # FP64 refresh (a separate kernel after every sweep) and FP32 sweeps run one after the
-    # other: roof time = FP64-pipe time of the refresh flops + FP32-pipe time of the rest
+    # the sweeps alone, timed live on a twin context that never refreshes within the launch: the
+    # refresh kernels' share of the QMC phase is the difference
+    twin = hf.Context(hf.make_params(dict(cfg, refresh_every=100000)), device=dev, stream=stream)
+    hf.hf_compute_baths(twin.handle)
+    hf.hf_sweep(twin.handle, 2, 0, 1)
+    n_tw = min(sweeps, 200)
+    hf.hf_sweep(twin.handle, n_tw, 0, 0)
+    sweep_s = hf.hf_get_timings(twin.handle)[5] / 1e3 * sweeps / n_tw
+    twin.close()
+    refresh_s = max(qmc_s - sweep_s, 1e-9)
     f_ref = 2.0 * (8.0 / 3.0) * L ** 3 * nc * sweeps
     f_sweep = 10.0 * L * nc * sweeps + 4.0 * L * L * accepts + 2.0 * L * L * nc * cfg["n_measure"]
-    t_roof = f_ref / (FP64_PEAK_TFLOPS * 1e12) + f_sweep / (FP32_PEAK_TFLOPS * 1e12)
-    achieved = (f_ref + f_sweep) / qmc_s / 1e12
-    peak = (f_ref + f_sweep) / t_roof / 1e12
+    tc = not cfg.get("refresh_gj", 0)
+    # FP32 sweeps with delayed rank-8 updates: each G element is read and written once per 8
+    # multiply-adds, so the FP32 pipe (128 FFMA/clk/SM), not shared memory, is the roof
+    sweep_roof = {"bound": "alu", "kernel": "qmc_f32_kernel", "achieved": f_sweep / sweep_s / 1e12,
+                  "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                  "frac": f_sweep / sweep_s / 1e12 / FP32_PEAK_TFLOPS, "traffic": None,
+                  "seconds": sweep_s,
+                  "peak_source": "FP32 nominal: 128 FFMA/clk/SM x 152 SMs x 2.07 GHz"}
+    if tc:
+        # executed tensor-core work: the digit products the Newton steps ran in the last timed
+        # iteration (the library counts them), 2 x 128^3 bf16 flops each
+        n_tc, n_fb, n_prod = hf.hf_get_refresh_stats(ctx.handle)
+        tflop = n_prod * 2.0 * L ** 3
+        ref_roof = {"bound": "tensor", "kernel": "refresh_tc_kernel", "achieved": tflop / refresh_s / 1e12,
+                    "peak": MEASURED_BF16_SUSTAINED, "unit": "TFLOP/s",
+                    "frac": tflop / refresh_s / 1e12 / MEASURED_BF16_SUSTAINED, "traffic": None,
+                    "seconds": refresh_s, "algorithmic_fp64_tflops": f_ref / refresh_s / 1e12,
+                    "peak_source": "measured dense bf16 (cuBLAS, sustained) of this GPU",
+                    "work": "bf16 flops of the exact digit products the refreshes ran",
+                    "tensor_refreshes": n_tc, "gauss_jordan_fallbacks": n_fb,
+                    "digit_products_per_refresh": n_prod / max(n_tc + n_fb, 1)}
+    else:
+        ref_roof = {"bound": "alu", "kernel": "refresh_f64_kernel", "achieved": f_ref / refresh_s / 1e12,
+                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": f_ref / refresh_s / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
+                    "seconds": refresh_s, "peak_source": "FP64 nominal: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz"}
+    dominant = ref_roof if refresh_s > sweep_s else sweep_roof
     line = {"metric": METRIC, "value": proposals / (ms_per / 1e3), "unit": "proposals/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -1010,18 +1054,14 @@ def run_square30(args):
             "rdmft_iteration_ms": ms_per,
             "phase_ms": dict(zip(["lattice", "weiss_tau", "qmc", "reduce", "sigma"],
                                  [float(x) for x in phase / args.steps])),
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
-                         # the refresh inverts G^{-1} by Gauss-Jordan: 2 L^3 executed flops per
-                         # spin against the 2 (8/3) L^3 of the algorithmic Dyson solve counted above
-                         "executed_tflops": (0.75 * f_ref + f_sweep) / qmc_s / 1e12,
-                         "kernel": "refresh_f64_kernel + qmc_f32_kernel",
-                         "peak_source": "FP64 refresh flops at nominal FP64 (2 DFMA/clk/SM) plus "
-                                        "sweep flops at FP32 (128 FFMA/clk/SM), not overlapped",
-                         "acceptance": accepts / proposals},
-            # per iteration: an FP32 sweep launch and an FP64 refresh launch per sweep, the first
-            # refresh, lattice step, Weiss/tau, reduction, self-energy update
-            "gpu_launches": (2 * sweeps + 5) * args.steps,
+            "roofline": dominant, "sweep_roofline": sweep_roof, "refresh_roofline": ref_roof,
+            "refresh": "tensor-core Newton steps" if tc else "FP64 Gauss-Jordan",
+            "acceptance": accepts / proposals,
+            # per iteration: an FP32 sweep launch and the refresh launches per sweep (tensor-core
+            # Newton steps and the Gauss-Jordan pass over the chains they flag, or Gauss-Jordan
+            # alone), the first refresh, g0^-1 (and its digits), lattice step, Weiss/tau,
+            # reduction, self-energy update
+            "gpu_launches": (((3 if tc else 2) * sweeps) + (7 if tc else 6)) * args.steps,
             "cpu_baseline": cpu, "clocks": clk}
     if args.sweeps:
         line["profile_case"] = "sweeps overridden to %d: not a benchmark value" % args.sweeps
@@ -1429,6 +1469,9 @@ def main():
     ap.add_argument("--refresh-stagger", type=int, default=0, choices=[0, 1],
                     help="1: per-chain refresh phases; 0 (default): every chain refreshes on the "
                          "same sweeps")
+    ap.add_argument("--refresh-gj", type=int, default=0, choices=[0, 1],
+                    help="square30: 1 refreshes by FP64 Gauss-Jordan instead of the tensor-core "
+                         "Newton steps")
     ap.add_argument("--serve-requests", type=int, default=600,
                     help="disc40: requests per Poisson load level")
     ap.add_argument("--no-other-form", action="store_true",

@@ -75,6 +75,10 @@ typedef struct hf_params {
     int check_drift;     /* 1: at every refresh within a sweep launch, measure how far the    */
                          /* updated G has drifted from the Dyson solution that replaces it   */
                          /* (hf_get_drift); 0: off.  The chains' arithmetic is unchanged     */
+    int refresh_gj;      /* precision 1 at L = 128: 0 (default) refreshes after each sweep by */
+                         /* two Newton steps on the tensor cores (products formed exactly     */
+                         /* from bf16 digits), falling back to Gauss-Jordan for a chain whose */
+                         /* residual does not converge; 1 always uses FP64 Gauss-Jordan       */
     int delay_k;         /* delayed-update depth: 0/1 rank-1 Sherman-Morrison; 4, 8, 16, 32  */
                          /* (precision 2, one warp per chain): accepted flips gathered as    */
                          /* rank-k corrections                                              */
@@ -134,8 +138,8 @@ hf_status hf_set_g0(hf_ctx* ctx, int site, int spin, const double* g0_tau);
  * when it is a multiple of refresh_every; measured sweeps then add to the current bin. */
 hf_status hf_sweep(hf_ctx* ctx, int n_warmup, int n_measure, int refresh_first);
 
-/* Zero all measurement bins and counters (the next measured sweep starts bin 0) and the drift
- * monitor. */
+/* Zero all measurement bins and counters (the next measured sweep starts bin 0), the drift
+ * monitor and the refresh counters of hf_get_refresh_stats. */
 hf_status hf_clear_measurements(hf_ctx* ctx);
 
 /* Reduce the completed bins of every chain of one inequivalent site (synchronises):
@@ -191,6 +195,14 @@ hf_status hf_get_accepts(hf_ctx* ctx, unsigned long long* accepts);
  * number of chain refreshes checked.  The refresh at the start of a launch is not checked (the
  * bath may have changed).  Either pointer may be NULL.  Synchronises. */
 hf_status hf_get_drift(hf_ctx* ctx, double* max_drift, unsigned long long* refreshes);
+
+/* Refreshes of the mixed-precision form at L = 128 since the last hf_clear_measurements: chains
+ * refreshed by the Newton steps on the tensor cores; chains those steps handed to the FP64
+ * Gauss-Jordan refresh (a residual that did not converge, or a G too badly conditioned for the
+ * residual's fixed-point accuracy); and the 128 x 128 x 128 digit products the steps ran on the
+ * tensor cores (2 * 128^3 bf16 flops each).  Any pointer may be NULL.  Synchronises. */
+hf_status hf_get_refresh_stats(hf_ctx* ctx, unsigned long long* tensor_refreshes,
+                               unsigned long long* fallbacks, unsigned long long* digit_products);
 
 /* Waits for the context stream and reports any failure the device recorded (numerical, or a
  * self-check of a checking build).  */
@@ -334,6 +346,20 @@ hf_status hf_lattice_step_noalloc(hf_ctx* ctx, const double* d_sigma, double* d_
  * for a null or unaligned buffer with n > 0; HF_ECUDA if the launch fails. */
 hf_status hf_philox_blocks(uint32_t key_lo, uint32_t key_hi, const uint32_t* d_ctr, int n,
                            uint32_t* d_out, void* cuda_stream);
+
+/* FP64-accurate products of 128 x 128 matrices on the tensor cores, the building block of the
+ * L = 128 refresh: C_b = A_b B_b for b < n, row-major FP64 matrices of 128 x 128 doubles at
+ * d_A + 16384 b, d_B + 16384 b, d_C + 16384 b (device buffers, the caller's, 16-byte aligned).
+ * Every row of A and column of B is scaled by a power of two and cut into `digits` (1, 3, 5, 7 or
+ * 8) balanced base-256 digits, exact in bf16; the digit products of the levels s + t <= digits + 1
+ * are summed exactly in FP32 tensor-core accumulators and combined in 64-bit integers.  The error
+ * of C_ij is below about 2^(9 - 8 digits) of 2^(TA_i + TB_j), the operands' row and column scales
+ * (|A_ik| <= 2^(TA_i - 1), |B_kj| <= 2^(TB_j - 1)); 8 digits hold the operands' 62-bit fixed-point
+ * forms exactly.  d_status (device int, may be NULL)
+ * receives HF_ETIMEOUT if a bounded wait for the tensor cores ran out.  Asynchronous on
+ * cuda_stream.  HF_EINVAL for n < 0, an unsupported digit count or a null or unaligned buffer. */
+hf_status hf_tc_dgemm128(const double* d_A, const double* d_B, double* d_C, int n, int digits,
+                         int* d_status, void* cuda_stream);
 
 /* Release the host handle (the device workspace stays the caller's). */
 void hf_free(hf_ctx* ctx);

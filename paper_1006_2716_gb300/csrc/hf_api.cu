@@ -19,6 +19,7 @@
 
 #include "hf_internal.cuh"
 #include "k_lattice.cuh"
+#include "k_refresh_tc.cuh"
 
 namespace {
 
@@ -270,6 +271,9 @@ struct hf_ctx {
     int* site_rep = nullptr;        // [N]
     int* site_dn = nullptr;         // [N]
     double2* lat_scratch = nullptr; // [lat_batch][N][b+1]
+    // tensor-core refresh of the mixed-precision form (precision 1, L = 128, refresh_gj = 0)
+    bool tc_on = false;
+    hfk::TcRefreshArgs tc{};
     // phase timing: events on the context stream (see hf_get_timings)
     cudaEvent_t ev[9] = {};
     bool ev_rdmft = false, ev_sweep = false;
@@ -391,6 +395,14 @@ size_t layout(hf_ctx& c, void* base) {
     c.site_rep = cv.take<int>(N);
     c.site_dn = cv.take<int>(N);
     c.lat_scratch = cv.take<double2>(static_cast<size_t>(c.lat_batch) * N * bw);
+    c.tc_on = c.p.precision == 1 && L == hfk::kTcL && c.p.refresh_gj == 0;
+    if (c.tc_on) {
+        c.tc.g0inv_digits = cv.take<uint16_t>(hfk::tc_digits_bytes(ns) / 2);
+        c.tc.g0inv_rowT = cv.take<int>(static_cast<size_t>(ns) * 2 * L);
+        c.tc.scratch = cv.take<double>(static_cast<size_t>(nc) * L * L);
+        c.tc.fail = cv.take<int>(nc);
+        c.tc.products = cv.take<unsigned long long>(1);
+    }
     return cv.off + 256;
 }
 
@@ -477,8 +489,12 @@ hf_status ensure_g0inv(hf_ctx* c, cudaStream_t st) {
     hfk::QmcBatch b{};
     b.nprob = 1;
     b.p[0] = make_problem(*c, 0, 0, 0);
-    const cudaError_t e = hfk::launch_g0_inverse(b, st);
+    cudaError_t e = hfk::launch_g0_inverse(b, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "g0 inverse launch");
+    if (c->tc_on) {   // the digits of g0^{-1} that the tensor-core refresh multiplies by
+        e = hfk::launch_g0inv_digits(b.p[0], c->tc, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "g0 inverse digits launch");
+    }
     c->g0inv_stale = false;
     return HF_OK;
 }
@@ -516,7 +532,14 @@ hf_status launch_sweeps_f32(hf_ctx* c, int n_warmup, int n_measure, int refresh_
         if (e != cudaSuccess) return cuda_fail(c, e, "FP32 sweep launch");
         if (lands) {
             q.refresh_measure = (k + n - 1 >= n_warmup) ? 1 : 0;
-            e = hfk::launch_refresh_f64(q, c->stream);
+            if (c->tc_on) {
+                // Newton steps on the tensor cores from the sweep's FP32 state; a chain whose
+                // residual does not converge is refreshed by Gauss-Jordan right after
+                e = hfk::launch_refresh_tc(q, c->tc, c->stream);
+                if (e == cudaSuccess) e = hfk::launch_refresh_f64_only(q, c->tc.fail, c->stream);
+            } else {
+                e = hfk::launch_refresh_f64(q, c->stream);
+            }
             if (e != cudaSuccess) return cuda_fail(c, e, "FP64 refresh launch");
         }
         k += n;
@@ -711,6 +734,7 @@ hf_status hf_init(const hf_params* p, void* d_ws, size_t ws_bytes, hf_ctx** out)
     if (e == cudaSuccess)
         e = cudaMemsetAsync(c->bins, 0, sizeof(double) * c->nchain * p->max_bins * (2 * c->L + 3), st0);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int) * 8, st0);
+    if (e == cudaSuccess && c->tc_on) e = cudaMemsetAsync(c->tc.products, 0, sizeof(unsigned long long), st0);
     if (e == cudaSuccess)
         e = hfk::launch_init_fields(c->s, c->nchain, p->chains_per_site, c->L,
                                     static_cast<uint32_t>(p->seed & 0xFFFFFFFFull),
@@ -786,7 +810,8 @@ hf_status hf_clear_measurements(hf_ctx* c) {
     HF_CUDA(c, cudaMemsetAsync(c->bins, 0, sizeof(double) * c->nchain * c->p.max_bins * (2 * c->L + 3),
                                c->stream));
     HF_CUDA(c, cudaMemsetAsync(c->nmeas_d, 0, sizeof(uint32_t) * c->nchain, c->stream));
-    HF_CUDA(c, cudaMemsetAsync(c->status + 4, 0, sizeof(int) * 2, c->stream));
+    HF_CUDA(c, cudaMemsetAsync(c->status + 4, 0, sizeof(int) * 4, c->stream));
+    if (c->tc_on) HF_CUDA(c, cudaMemsetAsync(c->tc.products, 0, sizeof(unsigned long long), c->stream));
     c->nmeas = 0;
     return HF_OK;
 }
@@ -988,6 +1013,21 @@ hf_status hf_get_drift(hf_ctx* c, double* max_drift, unsigned long long* refresh
     return HF_OK;
 }
 
+hf_status hf_get_refresh_stats(hf_ctx* c, unsigned long long* tensor_refreshes,
+                               unsigned long long* fallbacks, unsigned long long* digit_products) {
+    if (!c) return fail(nullptr, HF_EINVAL, "null context");
+    unsigned int w[2] = {0u, 0u};
+    unsigned long long np = 0ull;
+    HF_CUDA(c, cudaMemcpyAsync(w, c->status + 6, sizeof(w), cudaMemcpyDeviceToHost, c->stream));
+    if (c->tc_on)
+        HF_CUDA(c, cudaMemcpyAsync(&np, c->tc.products, sizeof(np), cudaMemcpyDeviceToHost, c->stream));
+    HF_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (tensor_refreshes) *tensor_refreshes = w[0];
+    if (fallbacks) *fallbacks = w[1];
+    if (digit_products) *digit_products = np;
+    return HF_OK;
+}
+
 hf_status hf_get_timings(hf_ctx* c, double* ms) {
     if (!c || !ms) return fail(c, HF_EINVAL, "hf_get_timings: null argument");
     const int pairs[6][2] = {{0, 1}, {1, 2}, {3, 4}, {4, 5}, {5, 6}, {7, 8}};
@@ -1042,6 +1082,21 @@ hf_status hf_philox_blocks(uint32_t key_lo, uint32_t key_hi, const uint32_t* d_c
         reinterpret_cast<uint4*>(d_out));
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "hf_philox_blocks launch");
+    return HF_OK;
+}
+
+hf_status hf_tc_dgemm128(const double* d_A, const double* d_B, double* d_C, int n, int digits,
+                         int* d_status, void* cuda_stream) {
+    if (n < 0) return fail(nullptr, HF_EINVAL, "hf_tc_dgemm128: n < 0");
+    if (digits != 1 && digits != 3 && digits != 5 && digits != 7 && digits != 8)
+        return fail(nullptr, HF_EINVAL, "hf_tc_dgemm128: digits must be 1, 3, 5, 7 or 8");
+    if (n == 0) return HF_OK;
+    if (!d_A || !d_B || !d_C || ((reinterpret_cast<uintptr_t>(d_A) | reinterpret_cast<uintptr_t>(d_B) |
+                                   reinterpret_cast<uintptr_t>(d_C)) & 15u) != 0)
+        return fail(nullptr, HF_EINVAL, "hf_tc_dgemm128: null or unaligned buffer");
+    const cudaError_t e = hfk::launch_tc_dgemm128(d_A, d_B, d_C, n, digits, d_status,
+                                                  static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "hf_tc_dgemm128 launch");
     return HF_OK;
 }
 

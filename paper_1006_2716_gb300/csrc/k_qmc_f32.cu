@@ -2,7 +2,8 @@
 //
 // Sweeps (single-flip ratio, Metropolis test and Sherman-Morrison update of the Hirsch-Fye
 // algorithm named in "Model and Methods") run in FP32 with FP32 accumulation, so that G_up and
-// G_dn of a chain with L = 128 (2 x 64 KiB) stay in shared memory.  The refresh
+// G_dn of a chain with L = 128 (2 x 64 KiB) stay in shared memory; accepted flips are applied as
+// delayed rank-8 updates.  The refresh
 // G = [1 + (1 - g0)(e^V - 1)]^{-1} g0 runs in FP64 in its own kernel, as the in-place
 // Gauss-Jordan inversion of G^{-1} = g0^{-1} e^V - (e^V - 1) (L x L FP64, 128 KiB at L = 128,
 // in shared memory), with g0^{-1} computed once per bath.  The refresh writes the FP64 G (used
@@ -11,6 +12,8 @@
 #include <algorithm>
 
 #include "hf_internal.cuh"
+#include "k_refresh_tc.cuh"
+#include "refresh_measure.cuh"
 
 namespace hfk {
 namespace {
@@ -18,16 +21,29 @@ namespace {
 constexpr int kT32 = 256;   // threads per block
 
 // --------------------------------------------------------------------------------------------
-// FP32 sweep kernel
+// FP32 sweep kernel with delayed updates
+//
+// G_up and G_dn stay in shared memory (rows padded to L + 1 floats, so that a column read hits
+// 32 different banks).  An accepted flip is not applied to G at once: its Sherman-Morrison factors
+// u = (a / R)(G[:, l] - e_l) and w = G[l, :] (of the current G, pending updates included) are
+// appended as column p of U and row p of W, and every kDK accepted flips (and at the end of the
+// sweep) G += U W in one pass, kDK multiply-adds per element for one read and one write of it.
+// The diagonal element a proposal needs, and the column and row an accepted flip needs, are G's
+// plus the pending updates' contribution (O(kDK) per element).  The arithmetic is that of the
+// rank-1 form reassociated, all in FP32 with FP32 accumulation.
 // --------------------------------------------------------------------------------------------
+constexpr int kDK = 8;   // pending rank-1 updates per spin
+
 __host__ __device__ constexpr size_t sweep32_bytes(int L) {
-    // Gf[2][L*L] f32, cr[4L] f32, u[L] f32, bacc[2L+3] f64, red[32] f64, s[L] i8
-    return static_cast<size_t>(2 * L * L + 5 * L) * 4 + static_cast<size_t>(2 * L + 3 + 32) * 8 +
-           ((L + 15) / 16) * 16 + 16;
+    // G[2][L][L+1] f32, U[2][L][kDK] f32, W[2][kDK][L] f32, u[L] f32 (even count), bacc[2L+3] f64,
+    // red[32] f64, s[L] i8
+    return static_cast<size_t>(2 * L * (L + 1) + 4 * L * kDK + L + (L & 1)) * 4 +
+           static_cast<size_t>(2 * L + 3 + 32) * 8 + ((L + 15) / 16) * 16 + 16;
 }
 
 template <int L>
 __device__ void measure32(const float* G0, const float* G1, double* bacc, double* red, int tid) {
+    constexpr int LP = L + 1;
     for (int m = tid; m < L; m += kT32) {
         double s0 = 0.0, s1 = 0.0;
         for (int q = 0; q < L; ++q) {
@@ -36,7 +52,7 @@ __device__ void measure32(const float* G0, const float* G1, double* bacc, double
             int r = l + m;
             const bool wrap = r >= L;
             if (wrap) r -= L;
-            const double x0 = G0[r * L + l], x1 = G1[r * L + l];
+            const double x0 = G0[r * LP + l], x1 = G1[r * LP + l];
             s0 = wrap ? s0 - x0 : s0 + x0;
             s1 = wrap ? s1 - x1 : s1 + x1;
         }
@@ -45,8 +61,8 @@ __device__ void measure32(const float* G0, const float* G1, double* bacc, double
     }
     double nu = 0.0, nd = 0.0, db = 0.0;
     for (int l = tid; l < L; l += kT32) {
-        const double a = 1.0 - static_cast<double>(G0[l * L + l]);
-        const double b = 1.0 - static_cast<double>(G1[l * L + l]);
+        const double a = 1.0 - static_cast<double>(G0[l * LP + l]);
+        const double b = 1.0 - static_cast<double>(G1[l * LP + l]);
         nu += a;
         nd += b;
         db += a * b;
@@ -78,17 +94,63 @@ __device__ void measure32(const float* G0, const float* G1, double* bacc, double
     __syncthreads();
 }
 
+// G += U W for the first m pending updates of both spins.  Thread t owns column t % L and rows
+// t / L, t / L + kT32 / L, ...; W's column is kept in registers, each U row is read as two 16-byte
+// broadcasts.
+template <int L>
+__device__ __forceinline__ void flush32(float* G0, float* G1, const float* U0, const float* U1,
+                                        const float* W0, const float* W1, int m, int tid) {
+    constexpr int LP = L + 1, STEP = kT32 / L;
+    const int j = tid % L, i0 = tid / L;
+    float w0[kDK], w1[kDK];
+#pragma unroll
+    for (int p = 0; p < kDK; ++p) {
+        w0[p] = p < m ? W0[p * L + j] : 0.0f;
+        w1[p] = p < m ? W1[p * L + j] : 0.0f;
+    }
+#pragma unroll 4
+    for (int i = i0; i < L; i += STEP) {
+        const float4 a0 = *reinterpret_cast<const float4*>(U0 + i * kDK);
+        const float4 a1 = *reinterpret_cast<const float4*>(U0 + i * kDK + 4);
+        const float4 b0 = *reinterpret_cast<const float4*>(U1 + i * kDK);
+        const float4 b1 = *reinterpret_cast<const float4*>(U1 + i * kDK + 4);
+        float g = G0[i * LP + j], h = G1[i * LP + j];
+        g = fmaf(a0.x, w0[0], g);
+        g = fmaf(a0.y, w0[1], g);
+        g = fmaf(a0.z, w0[2], g);
+        g = fmaf(a0.w, w0[3], g);
+        g = fmaf(a1.x, w0[4], g);
+        g = fmaf(a1.y, w0[5], g);
+        g = fmaf(a1.z, w0[6], g);
+        g = fmaf(a1.w, w0[7], g);
+        h = fmaf(b0.x, w1[0], h);
+        h = fmaf(b0.y, w1[1], h);
+        h = fmaf(b0.z, w1[2], h);
+        h = fmaf(b0.w, w1[3], h);
+        h = fmaf(b1.x, w1[4], h);
+        h = fmaf(b1.y, w1[5], h);
+        h = fmaf(b1.z, w1[6], h);
+        h = fmaf(b1.w, w1[7], h);
+        G0[i * LP + j] = g;
+        G1[i * LP + j] = h;
+    }
+}
+
 template <int L>
 __device__ void sweep32_chain(const QmcProblem& P, int c, unsigned char* base) {
     constexpr int LL = L * L;
+    constexpr int LP = L + 1;
     constexpr int W = 2 * L + 3;
-    static_assert(kT32 % L == 0, "one column per thread");
+    static_assert(kT32 % L == 0 && L <= 128 && kDK == 8, "thread layout");
     const int tid = threadIdx.x;
     float* G0 = reinterpret_cast<float*>(base);
-    float* G1 = G0 + LL;
-    float* cr = G1 + LL;
-    float* u = cr + 4 * L;
-    double* bacc = reinterpret_cast<double*>(u + L + ((L & 1) ? 1 : 0));
+    float* G1 = G0 + L * LP;
+    float* U0 = G1 + L * LP;                  // [L][kDK]
+    float* U1 = U0 + L * kDK;
+    float* W0 = U1 + L * kDK;                 // [kDK][L]
+    float* W1 = W0 + kDK * L;
+    float* u = W1 + kDK * L;
+    double* bacc = reinterpret_cast<double*>(u + L + (L & 1));
     double* red = bacc + W;
     int8_t* s = reinterpret_cast<int8_t*>(red + 32);
 
@@ -97,9 +159,11 @@ __device__ void sweep32_chain(const QmcProblem& P, int c, unsigned char* base) {
     const uint2 key = make_uint2(P.seed_lo, P.seed_hi);
     const float* Gg = P.Gf + static_cast<size_t>(c) * 2 * LL;
     for (int e = tid; e < LL; e += kT32) {
-        G0[e] = Gg[e];
-        G1[e] = Gg[LL + e];
+        const int i = e / L, j = e - (e / L) * L;
+        G0[i * LP + j] = Gg[e];
+        G1[i * LP + j] = Gg[LL + e];
     }
+    for (int e = tid; e < 4 * L * kDK; e += kT32) U0[e] = 0.0f;   // U and W: no stale patterns
     for (int l = tid; l < L; l += kT32) s[l] = P.s[static_cast<size_t>(c) * L + l];
     uint32_t nsw = P.nsw[c];
     uint32_t nmeas = P.nmeas[c];
@@ -110,44 +174,60 @@ __device__ void sweep32_chain(const QmcProblem& P, int c, unsigned char* base) {
         bacc[k] = (cur_bin < P.max_bins) ? bins_c[static_cast<size_t>(cur_bin) * W + k] : 0.0;
     __syncthreads();
 
-    const int j = tid % L;
-    const int i0 = tid / L;
     for (int k = 0; k < P.nsweeps; ++k) {
         for (int l = tid; l < L; l += kT32)
             u[l] = uniform24(philox4x32_10(make_uint4(nsw, static_cast<uint32_t>(l),
                                                       static_cast<uint32_t>(ch),
                                                       static_cast<uint32_t>(P.site0 + site)), key));
         __syncthreads();
+        int m = 0;   // pending updates (block-uniform)
         for (int l = 0; l < L; ++l) {
-            const float g0 = G0[l * L + l], g1 = G1[l * L + l];
+            // the current diagonal: G_ll plus the pending updates' part
+            float g0 = G0[l * LP + l], g1 = G1[l * LP + l];
+            for (int p = 0; p < m; ++p) {
+                g0 = fmaf(U0[l * kDK + p], W0[p * L + l], g0);
+                g1 = fmaf(U1[l * kDK + p], W1[p * L + l], g1);
+            }
             const int sl = s[l];
             const float au = (sl > 0) ? P.af_p : P.af_m;
             const float ad = (sl > 0) ? P.af_m : P.af_p;
             const float Ru = 1.0f + (1.0f - g0) * au;
             const float Rd = 1.0f + (1.0f - g1) * ad;
-            const float p = Ru * Rd;
-            if (!(p > 0.0f) && tid == 0) atomicAdd(P.status + 1, 1);
-            if (u[l] < p) {
+            const float pr = Ru * Rd;
+            if (!(pr > 0.0f) && tid == 0) atomicAdd(P.status + 1, 1);
+            if (u[l] < pr) {
                 const float fu = au / Ru, fd = ad / Rd;
-                for (int i = tid; i < L; i += kT32) {
+                if (tid < L) {                     // column l of the current G -> U[:, m]
+                    const int i = tid;
+                    float c0 = G0[i * LP + l], c1 = G1[i * LP + l];
+                    for (int p = 0; p < m; ++p) {
+                        c0 = fmaf(U0[i * kDK + p], W0[p * L + l], c0);
+                        c1 = fmaf(U1[i * kDK + p], W1[p * L + l], c1);
+                    }
                     const float one = (i == l) ? 1.0f : 0.0f;
-                    cr[i] = fu * (G0[i * L + l] - one);
-                    cr[L + i] = fd * (G1[i * L + l] - one);
-                    cr[2 * L + i] = G0[l * L + i];
-                    cr[3 * L + i] = G1[l * L + i];
-                }
-                __syncthreads();
-                const float r0 = cr[2 * L + j], r1 = cr[3 * L + j];
-#pragma unroll 8
-                for (int i = i0; i < L; i += kT32 / L) {
-                    G0[i * L + j] = fmaf(cr[i], r0, G0[i * L + j]);
-                    G1[i * L + j] = fmaf(cr[L + i], r1, G1[i * L + j]);
+                    U0[i * kDK + m] = fu * (c0 - one);
+                    U1[i * kDK + m] = fd * (c1 - one);
+                } else if (tid >= 128 && tid < 128 + L) {   // row l -> W[m, :]
+                    const int j = tid - 128;
+                    float r0 = G0[l * LP + j], r1 = G1[l * LP + j];
+                    for (int p = 0; p < m; ++p) {
+                        r0 = fmaf(U0[l * kDK + p], W0[p * L + j], r0);
+                        r1 = fmaf(U1[l * kDK + p], W1[p * L + j], r1);
+                    }
+                    W0[m * L + j] = r0;
+                    W1[m * L + j] = r1;
                 }
                 __syncthreads();
                 if (tid == 0) s[l] = static_cast<int8_t>(-sl);
                 ++acc;
+                if (++m == kDK) {
+                    flush32<L>(G0, G1, U0, U1, W0, W1, m, tid);
+                    m = 0;
+                    __syncthreads();
+                }
             }
         }
+        if (m > 0) flush32<L>(G0, G1, U0, U1, W0, W1, m, tid);
         ++nsw;
         __syncthreads();
         if (k >= P.meas_from && k < P.meas_to) {
@@ -168,8 +248,9 @@ __device__ void sweep32_chain(const QmcProblem& P, int c, unsigned char* base) {
         if (cur_bin < P.max_bins) bins_c[static_cast<size_t>(cur_bin) * W + q] = bacc[q];
     float* Gw = P.Gf + static_cast<size_t>(c) * 2 * LL;
     for (int e = tid; e < LL; e += kT32) {
-        Gw[e] = G0[e];
-        Gw[LL + e] = G1[e];
+        const int i = e / L, j = e - (e / L) * L;
+        Gw[e] = G0[i * LP + j];
+        Gw[LL + e] = G1[i * LP + j];
     }
     for (int l = tid; l < L; l += kT32) P.s[static_cast<size_t>(c) * L + l] = s[l];
     if (tid == 0) {
@@ -372,11 +453,12 @@ __device__ bool refresh_chain(const QmcProblem& P, int c, unsigned char* smem) {
     return ok;
 }
 
-__global__ void __launch_bounds__(kT32) refresh_f64_kernel(const QmcProblem P) {
+__global__ void __launch_bounds__(kT32) refresh_f64_kernel(const QmcProblem P, const int* only) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int L = P.L;
     const int c = blockIdx.x;
     if (c >= P.nchain) return;
+    if (only && only[c] == 0) return;   // the tensor-core refresh already handled this chain
     const int tid = threadIdx.x;
     const int LL = L * L;
     bool ok = true;
@@ -388,70 +470,12 @@ __global__ void __launch_bounds__(kT32) refresh_f64_kernel(const QmcProblem P) {
         default: break;
     }
     double* red = reinterpret_cast<double*>(smem) + LL + L;
-    double* Gout = P.G + static_cast<size_t>(c) * 2 * LL;
     if (!ok && tid == 0) atomicExch(P.status, static_cast<int>(HF_ENUMERIC));
     if (!P.refresh_measure) return;
     // measurement from the FP64 G just written (this block wrote it; block-wide visibility)
     __threadfence_block();
     __syncthreads();
-    const int W = 2 * L + 3;
-    uint32_t nmeas = P.nmeas[c];
-    const int b = static_cast<int>(nmeas / P.bin_size);
-    double* bin = P.bins + (static_cast<size_t>(c) * P.max_bins + b) * W;
-    const double* G0 = Gout;
-    const double* G1 = Gout + LL;
-    for (int m = tid; m < L; m += kT32) {
-        double s0 = 0.0, s1 = 0.0;
-        for (int q = 0; q < L; ++q) {
-            int l = q + m;
-            if (l >= L) l -= L;
-            int r = l + m;
-            const bool wrap = r >= L;
-            if (wrap) r -= L;
-            const double x0 = G0[r * L + l], x1 = G1[r * L + l];
-            s0 = wrap ? s0 - x0 : s0 + x0;
-            s1 = wrap ? s1 - x1 : s1 + x1;
-        }
-        if (b < P.max_bins) {
-            bin[m] += s0 / L;
-            bin[L + m] += s1 / L;
-        }
-    }
-    double nu = 0.0, nd = 0.0, db = 0.0;
-    for (int l = tid; l < L; l += kT32) {
-        const double a = 1.0 - G0[l * L + l];
-        const double bb = 1.0 - G1[l * L + l];
-        nu += a;
-        nd += bb;
-        db += a * bb;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        nu += __shfl_xor_sync(0xffffffffu, nu, o);
-        nd += __shfl_xor_sync(0xffffffffu, nd, o);
-        db += __shfl_xor_sync(0xffffffffu, db, o);
-    }
-    const int w = tid >> 5;
-    if ((tid & 31) == 0) {
-        red[w] = nu;
-        red[8 + w] = nd;
-        red[16 + w] = db;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        double a = 0.0, bb = 0.0, cc = 0.0;
-        for (int k = 0; k < kT32 / 32; ++k) {
-            a += red[k];
-            bb += red[8 + k];
-            cc += red[16 + k];
-        }
-        if (b < P.max_bins) {
-            bin[2 * L + 0] += a / L;
-            bin[2 * L + 1] += bb / L;
-            bin[2 * L + 2] += cc / L;
-        }
-        P.nmeas[c] = nmeas + 1;
-    }
+    measure_refreshed<kT32>(P, c, red);
 }
 
 }  // namespace
@@ -476,7 +500,17 @@ cudaError_t launch_refresh_f64(const QmcProblem& p, cudaStream_t st) {
                                          static_cast<int>(refresh_bytes(128)));
     if (e != cudaSuccess) return e;
     if (p.nchain <= 0) return cudaSuccess;
-    refresh_f64_kernel<<<p.nchain, kT32, smem, st>>>(p);
+    refresh_f64_kernel<<<p.nchain, kT32, smem, st>>>(p, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refresh_f64_only(const QmcProblem& p, const int* only, cudaStream_t st) {
+    const size_t smem = refresh_bytes(p.L);
+    cudaError_t e = cudaFuncSetAttribute(refresh_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(refresh_bytes(128)));
+    if (e != cudaSuccess) return e;
+    if (p.nchain <= 0) return cudaSuccess;
+    refresh_f64_kernel<<<p.nchain, kT32, smem, st>>>(p, only);
     return cudaGetLastError();
 }
 

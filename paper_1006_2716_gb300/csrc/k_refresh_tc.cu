@@ -1,0 +1,661 @@
+// k_refresh_tc.cu -- FP64 Dyson refresh of the mixed-precision form on the tensor cores (L = 128).
+//
+// The refresh G = [1 + (1 - g0)(e^V - 1)]^{-1} g0 is the inverse of M = g0^{-1} e^V - (e^V - 1)
+// (the Dyson relation multiplied out by g0^{-1}, which is kept per bath).  After an FP32 sweep the
+// chain's G is an approximate inverse X0 of M, good to a few parts in 10^5, so two Newton steps
+//     R = 1 - M X,   X <- X + X R
+// take it to FP64 accuracy: each step squares the relative error, and the products themselves
+// must be accurate only to what the step needs.  Step 0 forms the residual from 7-digit operands
+// (levels s + t <= 8) and the correction from 5-digit ones (<= 6), which leaves an error small
+// enough that one full step (8 digits, levels <= 9; correction as before) converges; a second
+// full step runs when it has not.  Every product is formed
+// exactly on the tensor cores from base-256 digits (tc_ozaki.cuh), so the FP64 pipe, which GB300
+// has cut to 2 multiply-adds per clock per SM, does one addition per element per step instead of
+// the L^3 multiply-adds of an elimination.  M X is evaluated as g0^{-1} (E X) - D X with E =
+// diag(e^V), D = diag(e^V - 1): the digits of g0^{-1} are cut once per bath, E X is cut per
+// refresh on the integer pipe (the significands of e and x multiplied exactly), and D X enters the
+// residual in fixed point.
+//
+// One 256-thread CTA per chain (one per SM: 173 KB of shared memory, all 512 TMEM columns).  A
+// product runs in two passes of 64 output columns; per pass, K = 128 in four chunks of 32, double
+// buffered: while the tensor cores work on one chunk, all threads cut the digits of the next.
+// Thread 0 issues the MMAs (M = 128, N = 64, K = 16; one accumulator per level n = s + t), commits
+// them to an mbarrier, and after the last chunk every thread reads its row of each level back
+// from TMEM and combines the levels in 64-bit integers.
+//
+// If the Newton residual does not fall below 2^-24 within two full steps (an FP32 state too far
+// from the inverse), or the operands' scales are too large for the residual's accuracy (a badly
+// conditioned G) or leave the fixed-point range, the chain is flagged and refreshed by the Gauss-Jordan
+// kernel instead (launch_refresh_f64_only); its outputs here are not written.
+#include <algorithm>
+
+#include "k_refresh_tc.cuh"
+#include "refresh_measure.cuh"
+#include "tc_ozaki.cuh"
+
+namespace hfk {
+namespace {
+
+using namespace tc;
+
+constexpr int L = kTcL, LL = L * L;
+constexpr int kThreads = 256;
+constexpr int KC = 32;              // K per chunk
+constexpr int NCH = L / KC;         // chunks
+constexpr int NPW = 64;             // output columns per pass
+constexpr int SMAX = kTcDigits;
+constexpr int A_SL = L * KC * 2;    // bytes of one digit of an A chunk (128 rows x 32 K, bf16)
+constexpr int B_SL = NPW * KC * 2;  // bytes of one digit of a B chunk (64 columns x 32 K)
+constexpr int BUFB = SMAX * (A_SL + B_SL);
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kIdesc = idesc_bf16_f32(128, NPW);
+constexpr int kConvergedExp = -24;  // Newton residual bound 2^-24: the step's remaining error,
+                                    // its square, is below the products' own accuracy
+constexpr int kFarExp = -4;         // a first residual above 2^-4: no approximate inverse
+// Accuracy limit of the residual: its error is about 2^(-55 + Ta_i + Tb_j) (the operands' 62-bit
+// fixed point and the dropped levels), i.e. relative to G about 2^(-55 + max Ta + max Tb) times
+// a modest factor.  Chains whose scales exceed this bound -- G with entries in the hundreds, a
+// badly conditioned Dyson matrix -- are left to the Gauss-Jordan refresh, so that the tensor-core
+// result stays within about 1e-12 of the exact G relative to its largest entry.
+constexpr int kMaxScaleSum = 12;
+
+struct Smem {
+    unsigned char buf[2][BUFB];     // double-buffered digit chunks: A digits, then B digits
+    int rowT[L], colT[L];           // power-of-two scales of the current operands
+    int tmpT[kThreads];
+    unsigned long long red[kThreads / 32];
+    int8_t s[L];                    // the chain's fields
+    uint64_t mbar[2];
+    uint32_t tmem;
+    int flag;                       // fallback requested
+    int timeout;
+};
+
+__device__ __forceinline__ unsigned char* bufA(Smem& S, int b, int s) { return S.buf[b] + s * A_SL; }
+__device__ __forceinline__ unsigned char* bufB(Smem& S, int b, int t) {
+    return S.buf[b] + SMAX * A_SL + t * B_SL;
+}
+
+// significand (with the implicit bit) and exponent of a normal double: x = m 2^(E - 52)
+__device__ __forceinline__ void split_double(double x, unsigned long long& m, int& E) {
+    const long long b = __double_as_longlong(x);
+    m = (static_cast<unsigned long long>(b) & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+    E = static_cast<int>((b >> 52) & 0x7FF) - 1023;
+}
+
+// D 2^(54 - 8 n) as an integer (levels above 6 lose their lowest bits, rounded)
+__device__ __forceinline__ long long level_shift(long long D, int n) {
+    const int sh = 54 - 8 * n;
+    return sh >= 0 ? (D << sh) : ((D + (1ll << (-sh - 1))) >> (-sh));
+}
+
+// max of x over the block (non-negative integers), every thread gets it
+__device__ __forceinline__ unsigned long long block_max(Smem& S, unsigned long long x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, o);
+        x = y > x ? y : x;
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) S.red[threadIdx.x >> 5] = x;
+    __syncthreads();
+    unsigned long long m = 0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) m = S.red[w] > m ? S.red[w] : m;
+    return m;
+}
+
+// ------------------------------------------------------------------------------------------
+// operand fills: one K-chunk of every digit, laid out as K-major core matrices
+// (core (group, kc) at (group * 4 + kc) * 128 bytes, row r of the core at r * 16)
+// ------------------------------------------------------------------------------------------
+
+// A from precomputed digit chunks (each an 8 KB block in exactly this layout)
+template <int SA>
+__device__ void fill_A_digits(Smem& S, int b, int c, const uint16_t* digits) {
+#pragma unroll
+    for (int s = 0; s < SA; ++s) {
+        const uint4* src = reinterpret_cast<const uint4*>(digits + (static_cast<size_t>(s) * NCH + c) * (A_SL / 2));
+        uint4* dst = reinterpret_cast<uint4*>(bufA(S, b, s));
+        for (int u = threadIdx.x; u < A_SL / 16; u += kThreads) dst[u] = src[u];
+    }
+}
+
+// 8 fixed-point values -> SD digit rows of 16 bytes at dst[d] + off
+template <int SD>
+__device__ __forceinline__ void store_digits(long long (&F)[8], unsigned char* base, int stride,
+                                             int off) {
+#pragma unroll
+    for (int s = 1; s <= SD; ++s) {
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int d0 = next_digit(F[2 * q], s);
+            const int d1 = next_digit(F[2 * q + 1], s);
+            w[q] = pack_bf16x2(bf16_of_int(d0), bf16_of_int(d1));
+        }
+        *reinterpret_cast<uint4*>(base + (s - 1) * stride + off) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// A from the rows of a row-major FP64 matrix X with row scales S.rowT
+template <int SA>
+__device__ void fill_A_rows(Smem& S, int b, int c, const double* X) {
+    for (int u = threadIdx.x; u < L * (KC / 8); u += kThreads) {
+        const int i = u & (L - 1), kg = u >> 7;
+        const double* src = X + static_cast<size_t>(i) * L + c * KC + kg * 8;
+        const int T = S.rowT[i];
+        long long F[8];
+#pragma unroll
+        for (int q = 0; q < 8; q += 2) {
+            const double2 v = *reinterpret_cast<const double2*>(src + q);
+            F[q] = to_fixed(v.x, T);
+            F[q + 1] = to_fixed(v.y, T);
+        }
+        store_digits<SA>(F, bufA(S, b, 0), A_SL, ((i >> 3) * 4 + kg) * 128 + (i & 7) * 16);
+    }
+}
+
+// B from the columns p*64 .. p*64+63 of a row-major FP64 matrix X with column scales S.colT;
+// with E, row k is multiplied by e_k (significand me[k], exponent Ee[k]) exactly on the way
+template <int SB, bool E>
+__device__ void fill_B_cols(Smem& S, int b, int c, int p, const double* X,
+                            const unsigned long long* me, const int* Ee) {
+    const int t = threadIdx.x;
+    const int jl = t & (NPW - 1), kg = t >> 6;
+    const int j = p * NPW + jl;
+    const int T = S.colT[j];
+    long long F[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int k = c * KC + kg * 8 + q;
+        const double x = X[static_cast<size_t>(k) * L + j];
+        if constexpr (E) {
+            const int up = S.s[k] > 0 ? 1 : 0;   // caller stores sigma s_k in S.s
+            F[q] = to_fixed_scaled(x, me[up], Ee[up], T);
+        } else {
+            F[q] = to_fixed(x, T);
+        }
+    }
+    store_digits<SB>(F, bufB(S, b, 0), B_SL, ((jl >> 3) * 4 + kg) * 128 + (jl & 7) * 16);
+}
+
+// ------------------------------------------------------------------------------------------
+// one product pass: fills, MMAs, readout
+// ------------------------------------------------------------------------------------------
+template <int SA, int SB, int NL>
+__device__ void issue_chunk(Smem& S, int b, int c) {
+    tc_fence_after_sync();
+    const uint32_t a0 = smem_addr(bufA(S, b, 0)), b0 = smem_addr(bufB(S, b, 0));
+#pragma unroll
+    for (int n = 2; n <= NL; ++n) {
+        const int smin = n - SB > 1 ? n - SB : 1;
+        const int smax = n - 1 < SA ? n - 1 : SA;
+        for (int s = smin; s <= smax; ++s) {
+            const int t = n - s;
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk) {
+                const uint64_t ad = smem_desc(a0 + (s - 1) * A_SL + kk * 256, 128, 512);
+                const uint64_t bd = smem_desc(b0 + (t - 1) * B_SL + kk * 256, 128, 512);
+                mma_bf16(S.tmem + (n - 2) * NPW, ad, bd, kIdesc, !(c == 0 && kk == 0 && s == smin));
+            }
+        }
+    }
+    mma_commit(&S.mbar[b]);
+}
+
+// Runs one pass (output columns p*64 ...) of C = A B with the given operand fills and hands every
+// element's level sum Q (C_ij = Q 2^(rowT_i + colT_j - 54)) to epi(i, j, Q).  ph[] tracks the
+// two mbarriers' phases.  Returns false if a wait ran out (the CTA then stops using TMEM).
+template <int SA, int SB, int NL, class FA, class FB, class EPI>
+__device__ bool product_pass(Smem& S, int p, uint32_t (&ph)[2], FA fillA, FB fillB, EPI epi) {
+    static_assert(NL - 1 <= 8 && (NL - 1) * NPW <= static_cast<int>(kTmemCols), "levels fit TMEM");
+    const int tid = threadIdx.x;
+    bool ok = true;
+    for (int c = 0; c < NCH; ++c) {
+        const int b = c & 1;
+        if (c >= 2) {   // the MMAs that read this buffer two chunks ago must be done
+            ok = mbar_wait(&S.mbar[b], ph[b]) && ok;
+            ph[b] ^= 1u;
+        }
+        fillA(b, c);
+        fillB(b, c);
+        fence_async_shared();
+        tc_fence_before_sync();
+        __syncthreads();
+        if (tid == 0) issue_chunk<SA, SB, NL>(S, b, c);
+    }
+    ok = mbar_wait(&S.mbar[0], ph[0]) && ok;
+    ph[0] ^= 1u;
+    ok = mbar_wait(&S.mbar[1], ph[1]) && ok;
+    ph[1] ^= 1u;
+    if (!ok) return false;
+    tc_fence_after_sync();
+    const int w = tid >> 5, lane = tid & 31;
+    const int i = 32 * (w & 3) + lane;
+    const int cg = w >> 2;
+    const uint32_t trow = S.tmem + (static_cast<uint32_t>(32 * (w & 3)) << 16);
+#pragma unroll 1
+    for (int g = 0; g < 2; ++g) {
+        long long Q[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) Q[k] = 0;
+#pragma unroll
+        for (int n = 2; n <= NL; ++n) {
+            float v[16];
+            tmem_ld16(trow + (n - 2) * NPW + 32 * cg + 16 * g, v);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) Q[k] += level_shift(static_cast<long long>(__float2int_rz(v[k])), n);
+        }
+#pragma unroll 4
+        for (int k = 0; k < 16; ++k) epi(i, p * NPW + 32 * cg + 16 * g + k, Q[k]);
+    }
+    tc_fence_before_sync();
+    __syncthreads();
+    return true;
+}
+
+// number of digit products (s, t) with s + t <= NL of two S-digit operands
+__host__ __device__ constexpr int n_products(int S, int NL) {
+    int n = 0;
+    for (int s = 1; s <= S; ++s)
+        for (int t = 1; t <= S; ++t)
+            if (s + t <= NL) ++n;
+    return n;
+}
+
+// ------------------------------------------------------------------------------------------
+// operand scales
+// ------------------------------------------------------------------------------------------
+// colT[j] = max_k (exp(X_kj) + add_k) + 2 (+1 for the e scaling): |e_k X_kj| <= 2^(colT_j - 1)
+__device__ void col_scales(Smem& S, const double* X, const int* Ee) {
+    const int t = threadIdx.x, j = t & (L - 1), h = t >> 7;
+    int m = kNoExp;
+    for (int k = h * (L / 2); k < (h + 1) * (L / 2); ++k) {
+        int e = exp_of(X[static_cast<size_t>(k) * L + j]);
+        if (Ee && e != kNoExp) e += Ee[S.s[k] > 0 ? 1 : 0] + 1;
+        m = e > m ? e : m;
+    }
+    S.tmpT[t] = m;
+    __syncthreads();
+    if (t < L) {
+        const int a = S.tmpT[t], b2 = S.tmpT[t + L];
+        S.colT[t] = (a > b2 ? a : b2) + 2;
+    }
+    __syncthreads();
+}
+
+// rowT[i] = max_k exp(X_ik) + 2, one warp per row at a time (coalesced)
+__device__ void row_scales(Smem& S, const double* X) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = w; i < L; i += kThreads / 32) {
+        int m = kNoExp;
+#pragma unroll
+        for (int q = 0; q < L / 32; ++q) {
+            const int e = exp_of(X[static_cast<size_t>(i) * L + lane + 32 * q]);
+            m = e > m ? e : m;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const int y = __shfl_xor_sync(0xffffffffu, m, o);
+            m = y > m ? y : m;
+        }
+        if (lane == 0) S.rowT[i] = m + 2;
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------------------------------
+// the refresh of one spin: X (FP32 state in Gf, FP64 iterate in Xa / Xb) -> G in Xa
+// ------------------------------------------------------------------------------------------
+struct SpinArgs {
+    double* Xa;               // the chain's FP64 G of this spin (input: unused; output: G)
+    double* Xb;               // scratch
+    const float* Gf;          // FP32 state of this spin
+    const uint16_t* digits;   // g0^{-1} digits of (site, spin)
+    const int* rowTg;         // and its row scales
+    unsigned long long me[2]; // significands of e^V: [0] sigma s = -1, [1] sigma s = +1
+    int Ee[2];
+    unsigned long long mev[2];// significands of |e^V - 1|
+    int Eev[2];
+    bool evneg[2];            // e^V - 1 < 0
+};
+
+// R = 1 - g0^{-1} (E X) + D X for X in Xsrc, written to Rdst; returns max |R| (bit pattern key)
+template <int S_, int NL>
+__device__ bool residual(Smem& S, uint32_t (&ph)[2], const SpinArgs& a, const double* Xsrc,
+                         double* Rdst, unsigned long long& rmax) {
+    for (int i = threadIdx.x; i < L; i += kThreads) S.rowT[i] = a.rowTg[i];
+    col_scales(S, Xsrc, a.Ee);
+    if (threadIdx.x < 32) {   // largest row scale + largest column scale
+        int mr = kNoExp, mc = kNoExp;
+        for (int i = threadIdx.x; i < L; i += 32) {
+            mr = S.rowT[i] > mr ? S.rowT[i] : mr;
+            mc = S.colT[i] > mc ? S.colT[i] : mc;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mr = max(mr, __shfl_xor_sync(0xffffffffu, mr, o));
+            mc = max(mc, __shfl_xor_sync(0xffffffffu, mc, o));
+        }
+        if (threadIdx.x == 0 && mr + mc > kMaxScaleSum) S.flag = 1;
+    }
+    unsigned long long mx = 0;
+    for (int p = 0; p < L / NPW; ++p) {
+        const bool ok = product_pass<S_, S_, NL>(
+            S, p, ph, [&](int b, int c) { fill_A_digits<S_>(S, b, c, a.digits); },
+            [&](int b, int c) { fill_B_cols<S_, true>(S, b, c, p, Xsrc, a.me, a.Ee); },
+            [&](int i, int j, long long Q) {
+                const int EQ = S.rowT[i] + S.colT[j] - 54;
+                long long q = -Q;
+                if (i == j) {
+                    const int sh = -EQ;
+                    if (sh < 0 || sh > 61) S.flag = 1;
+                    else q += 1ll << sh;
+                }
+                const int up = S.s[i] > 0 ? 1 : 0;
+                const int T = 62 + EQ;
+                // |ev X| must lie below 2^(T - 1) for the fixed-point form; it does whenever the
+                // scales are sane, otherwise the chain falls back
+                const double x = Xsrc[static_cast<size_t>(i) * L + j];
+                const int ex = exp_of(x);
+                if (ex != kNoExp && ex + a.Eev[up] + 2 > T - 1) S.flag = 1;
+                long long v = to_fixed_scaled(x, a.mev[up], a.Eev[up], T);
+                q += a.evneg[up] ? -v : v;
+                const double r = fixed_to_double(q, EQ);
+                Rdst[static_cast<size_t>(i) * L + j] = r;
+                const unsigned long long key =
+                    static_cast<unsigned long long>(__double_as_longlong(r)) & 0x7FFFFFFFFFFFFFFFull;
+                mx = key > mx ? key : mx;
+            });
+        if (!ok) return false;
+    }
+    rmax = block_max(S, mx);
+    return true;
+}
+
+// X_new = X + X R (X in Xsrc, R in Rsrc), written over Rsrc (each pass writes only the columns
+// it has finished reading)
+template <int S_, int NL>
+__device__ bool correct(Smem& S, uint32_t (&ph)[2], const double* Xsrc, double* Rsrc) {
+    row_scales(S, Xsrc);
+    col_scales(S, Rsrc, nullptr);
+    for (int p = 0; p < L / NPW; ++p) {
+        const bool ok = product_pass<S_, S_, NL>(
+            S, p, ph, [&](int b, int c) { fill_A_rows<S_>(S, b, c, Xsrc); },
+            [&](int b, int c) { fill_B_cols<S_, false>(S, b, c, p, Rsrc, nullptr, nullptr); },
+            [&](int i, int j, long long Q) {
+                const size_t e = static_cast<size_t>(i) * L + j;
+                Rsrc[e] = Xsrc[e] + fixed_to_double(Q, S.rowT[i] + S.colT[j] - 54);
+            });
+        if (!ok) return false;
+    }
+    return true;
+}
+
+__device__ bool refresh_spin(Smem& S, uint32_t (&ph)[2], const SpinArgs& a, int& products) {
+    // X0 = the FP32 state
+    for (int e = threadIdx.x; e < LL; e += kThreads) a.Xa[e] = static_cast<double>(a.Gf[e]);
+    __syncthreads();
+    unsigned long long r = 0;
+    // step 0: residual to about 2^-35 of the operand scales, enough that one full step then
+    // converges from an FP32 state; correction to what that needs
+    if (!residual<7, 8>(S, ph, a, a.Xa, a.Xb, r)) return false;
+    products += n_products(7, 8);
+    if (S.flag) return true;                                        // scales out of range
+    if (exp_of(__longlong_as_double(static_cast<long long>(r))) >= kFarExp) {
+        if (threadIdx.x == 0) S.flag = 1;                         // no approximate inverse
+        __syncthreads();
+        return true;
+    }
+    if (!correct<5, 6>(S, ph, a.Xa, a.Xb)) return false;          // X1 in Xb
+    products += n_products(5, 6);
+    // full-accuracy steps until the residual is below 2^-24 (its square is then far below the
+    // products' own error), at most two
+    double* X = a.Xb;
+    double* R = a.Xa;
+    bool done = false;
+    for (int it = 0; it < 2 && !done; ++it) {
+        if (!residual<8, 9>(S, ph, a, X, R, r)) return false;
+        products += n_products(8, 9);
+        if (S.flag) return true;
+        if (!correct<5, 6>(S, ph, X, R)) return false;            // X + X R over R
+        products += n_products(5, 6);
+        double* t = X;
+        X = R;
+        R = t;
+        done = exp_of(__longlong_as_double(static_cast<long long>(r))) < kConvergedExp;
+    }
+    if (!done) {
+        if (threadIdx.x == 0) S.flag = 1;
+        __syncthreads();
+        return true;
+    }
+    if (X != a.Xa) {   // the result belongs in the chain's G
+        for (int e = threadIdx.x; e < LL; e += kThreads) a.Xa[e] = X[e];
+        __syncthreads();
+    }
+    return true;
+}
+
+__device__ void split_e(double e, unsigned long long& m, int& E) { split_double(e, m, E); }
+
+__global__ void __launch_bounds__(kThreads, 1)
+refresh_tc_kernel(const QmcProblem P, const TcRefreshArgs A) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+    const int c = blockIdx.x;
+    if (c >= P.nchain) return;
+    const int tid = threadIdx.x;
+    const int site = c / P.cps;
+    // after a timeout anywhere in this context, leave every chain to the Gauss-Jordan refresh
+    if (*reinterpret_cast<volatile const int*>(P.status) == static_cast<int>(HF_ETIMEOUT)) {
+        if (tid == 0) A.fail[c] = 1;
+        return;
+    }
+    if (tid == 0) {
+        S.flag = 0;
+        S.timeout = 0;
+        mbar_init(&S.mbar[0], 1);
+        mbar_init(&S.mbar[1], 1);
+        mbar_init_fence();
+    }
+    if (tid < 32) tmem_alloc(&S.tmem, kTmemCols);
+    tc_fence_before_sync();
+    __syncthreads();
+    tc_fence_after_sync();
+    uint32_t ph[2] = {0u, 0u};
+    const double e_p = 1.0 + P.ev_p, e_m = 1.0 + P.ev_m;
+    bool ok = true;
+    int products = 0;
+    for (int sp = 0; sp < 2 && ok; ++sp) {
+        const int sigma = sp == 0 ? 1 : -1;
+        for (int l = tid; l < L; l += kThreads)
+            S.s[l] = static_cast<int8_t>(sigma * P.s[static_cast<size_t>(c) * L + l]);
+        SpinArgs a;
+        a.Xa = P.G + (static_cast<size_t>(c) * 2 + sp) * LL;
+        a.Xb = A.scratch + static_cast<size_t>(c) * LL;
+        a.Gf = P.Gf + (static_cast<size_t>(c) * 2 + sp) * LL;
+        a.digits = A.g0inv_digits + (static_cast<size_t>(site) * 2 + sp) * SMAX * LL;
+        a.rowTg = A.g0inv_rowT + (static_cast<size_t>(site) * 2 + sp) * L;
+        split_e(e_m, a.me[0], a.Ee[0]);
+        split_e(e_p, a.me[1], a.Ee[1]);
+        split_e(fabs(P.ev_m), a.mev[0], a.Eev[0]);
+        split_e(fabs(P.ev_p), a.mev[1], a.Eev[1]);
+        a.evneg[0] = P.ev_m < 0.0;
+        a.evneg[1] = P.ev_p < 0.0;
+        __syncthreads();
+        ok = refresh_spin(S, ph, a, products);
+        if (!ok) {
+            if (tid == 0) S.timeout = 1;
+            break;
+        }
+        if (S.flag) break;
+    }
+    __syncthreads();
+    tc_fence_after_sync();
+    if (tid < 32) tmem_dealloc(S.tmem, kTmemCols);
+    if (tid == 0 && A.products) atomicAdd(A.products, static_cast<unsigned long long>(products));
+    if (S.timeout) {
+        if (tid == 0) {
+            atomicExch(P.status, static_cast<int>(HF_ETIMEOUT));
+            A.fail[c] = 1;
+        }
+        return;
+    }
+    if (S.flag) {
+        if (tid == 0) {
+            A.fail[c] = 1;
+            atomicAdd(reinterpret_cast<unsigned int*>(P.status + 7), 1u);
+        }
+        return;
+    }
+    if (tid == 0) {
+        A.fail[c] = 0;
+        atomicAdd(reinterpret_cast<unsigned int*>(P.status + 6), 1u);
+    }
+    // the FP32 copy (sweep state) and the drift of the state the sweeps reached
+    float dv = 0.0f;
+    for (int e = tid; e < 2 * LL; e += kThreads) {
+        const double x = P.G[static_cast<size_t>(c) * 2 * LL + e];
+        float* gf = P.Gf + static_cast<size_t>(c) * 2 * LL + e;
+        if (P.drift) dv = fmaxf(dv, static_cast<float>(fabs(x - static_cast<double>(*gf))));
+        *gf = static_cast<float>(x);
+    }
+    if (P.drift) drift_fold(P.drift, dv, tid == 0);
+    if (P.refresh_measure) {
+        __syncthreads();
+        measure_refreshed<kThreads>(P, c, reinterpret_cast<double*>(S.tmpT));
+    }
+}
+
+// digits and row scales of g0^{-1}, one CTA per (site, spin)
+__global__ void __launch_bounds__(kThreads) g0inv_digits_kernel(const QmcProblem P, TcRefreshArgs A) {
+    const int b = blockIdx.x;   // site * 2 + spin
+    const double* G = P.g0inv + static_cast<size_t>(b) * LL;
+    uint16_t* out = A.g0inv_digits + static_cast<size_t>(b) * SMAX * LL;
+    int* rT = A.g0inv_rowT + static_cast<size_t>(b) * L;
+    __shared__ int T[L];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = w; i < L; i += kThreads / 32) {
+        int m = kNoExp;
+        for (int q = 0; q < L / 32; ++q) {
+            const int e = exp_of(G[static_cast<size_t>(i) * L + lane + 32 * q]);
+            m = e > m ? e : m;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const int y = __shfl_xor_sync(0xffffffffu, m, o);
+            m = y > m ? y : m;
+        }
+        if (lane == 0) {
+            T[i] = m + 2;
+            rT[i] = m + 2;
+        }
+    }
+    __syncthreads();
+    // unit (i, kg): 8 consecutive K of row i; chunk c = kg / 4 holds its core column kg % 4
+    for (int u = threadIdx.x; u < L * (L / 8); u += kThreads) {
+        const int i = u & (L - 1), kg = u >> 7;
+        const int c = kg >> 2, kgl = kg & 3;
+        long long F[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) F[q] = to_fixed(G[static_cast<size_t>(i) * L + kg * 8 + q], T[i]);
+        unsigned char* base = reinterpret_cast<unsigned char*>(out) + static_cast<size_t>(c) * A_SL;
+        store_digits<SMAX>(F, base, NCH * A_SL, ((i >> 3) * 4 + kgl) * 128 + (i & 7) * 16);
+    }
+}
+
+// C = A B for independent 128 x 128 pairs (one CTA each), both operands with `SD` digits
+template <int SD>
+__global__ void __launch_bounds__(kThreads, 1)
+tc_dgemm_kernel(const double* Am, const double* Bm, double* Cm, int n, int* status) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+    const int m = blockIdx.x;
+    if (m >= n) return;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&S.mbar[0], 1);
+        mbar_init(&S.mbar[1], 1);
+        mbar_init_fence();
+    }
+    if (tid < 32) tmem_alloc(&S.tmem, kTmemCols);
+    tc_fence_before_sync();
+    __syncthreads();
+    tc_fence_after_sync();
+    uint32_t ph[2] = {0u, 0u};
+    const double* Ab = Am + static_cast<size_t>(m) * LL;
+    const double* Bb = Bm + static_cast<size_t>(m) * LL;
+    double* Cb = Cm + static_cast<size_t>(m) * LL;
+    row_scales(S, Ab);
+    col_scales(S, Bb, nullptr);
+    bool ok = true;
+    for (int p = 0; p < L / NPW && ok; ++p)
+        ok = product_pass<SD, SD, SD + 1>(
+            S, p, ph, [&](int b, int c) { fill_A_rows<SD>(S, b, c, Ab); },
+            [&](int b, int c) { fill_B_cols<SD, false>(S, b, c, p, Bb, nullptr, nullptr); },
+            [&](int i, int j, long long Q) {
+                Cb[static_cast<size_t>(i) * L + j] = fixed_to_double(Q, S.rowT[i] + S.colT[j] - 54);
+            });
+    __syncthreads();
+    tc_fence_after_sync();
+    if (tid < 32) tmem_dealloc(S.tmem, kTmemCols);
+    if (!ok && tid == 0 && status) atomicExch(status, static_cast<int>(HF_ETIMEOUT));
+}
+
+}  // namespace
+
+size_t tc_digits_bytes(int nsite) { return static_cast<size_t>(nsite) * 2 * SMAX * LL * 2; }
+size_t tc_refresh_smem_bytes() { return sizeof(Smem); }
+
+cudaError_t launch_g0inv_digits(const QmcProblem& p, const TcRefreshArgs& a, cudaStream_t st) {
+    const int nb = 2 * (p.nchain / p.cps);
+    if (nb <= 0) return cudaSuccess;
+    g0inv_digits_kernel<<<nb, kThreads, 0, st>>>(p, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refresh_tc(const QmcProblem& p, const TcRefreshArgs& a, cudaStream_t st) {
+    if (p.L != kTcL) return cudaErrorInvalidValue;
+    const int smem = static_cast<int>(sizeof(Smem));
+    cudaError_t e = cudaFuncSetAttribute(refresh_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    if (p.nchain <= 0) return cudaSuccess;
+    refresh_tc_kernel<<<p.nchain, kThreads, smem, st>>>(p, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_dgemm128(const double* A, const double* B, double* C, int n, int digits,
+                               int* status, cudaStream_t st) {
+    const int smem = static_cast<int>(sizeof(Smem));
+    cudaError_t e = cudaSuccess;
+    switch (digits) {
+        case 1:
+            e = cudaFuncSetAttribute(tc_dgemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e == cudaSuccess && n > 0) tc_dgemm_kernel<1><<<n, kThreads, smem, st>>>(A, B, C, n, status);
+            break;
+        case 3:
+            e = cudaFuncSetAttribute(tc_dgemm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e == cudaSuccess && n > 0) tc_dgemm_kernel<3><<<n, kThreads, smem, st>>>(A, B, C, n, status);
+            break;
+        case 5:
+            e = cudaFuncSetAttribute(tc_dgemm_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e == cudaSuccess && n > 0) tc_dgemm_kernel<5><<<n, kThreads, smem, st>>>(A, B, C, n, status);
+            break;
+        case 7:
+            e = cudaFuncSetAttribute(tc_dgemm_kernel<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e == cudaSuccess && n > 0) tc_dgemm_kernel<7><<<n, kThreads, smem, st>>>(A, B, C, n, status);
+            break;
+        case 8:
+            e = cudaFuncSetAttribute(tc_dgemm_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e == cudaSuccess && n > 0) tc_dgemm_kernel<8><<<n, kThreads, smem, st>>>(A, B, C, n, status);
+            break;
+        default:
+            return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+}  // namespace hfk

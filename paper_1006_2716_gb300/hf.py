@@ -31,6 +31,7 @@ class hf_params(C.Structure):
         ("beta", C.c_double), ("dtau", C.c_double),
         ("n_matsubara", C.c_int), ("chains_per_site", C.c_int), ("precision", C.c_int),
         ("refresh_every", C.c_int), ("refresh_stagger", C.c_int), ("check_drift", C.c_int),
+        ("refresh_gj", C.c_int),
         ("delay_k", C.c_int),
         ("team_warps", C.c_int),
         ("bin_size", C.c_int),
@@ -102,8 +103,11 @@ SIGNATURES = [
     ("hf_get_timings", C.c_int, [_VP, _DP]),
     ("hf_sync", C.c_int, [_VP]),
     ("hf_get_drift", C.c_int, [_VP, _DP, C.POINTER(C.c_ulonglong)]),
+    ("hf_get_refresh_stats", C.c_int, [_VP, C.POINTER(C.c_ulonglong), C.POINTER(C.c_ulonglong),
+                                        C.POINTER(C.c_ulonglong)]),
     ("hf_lattice_step_noalloc", C.c_int, [_VP, _VP, _VP]),
     ("hf_philox_blocks", C.c_int, [C.c_uint32, C.c_uint32, _VP, C.c_int, _VP, _VP]),
+    ("hf_tc_dgemm128", C.c_int, [_VP, _VP, _VP, C.c_int, C.c_int, _VP, _VP]),
     ("hf_batch_create", C.c_int, [C.POINTER(_VP), C.c_int, C.c_int, C.POINTER(_VP)]),
     ("hf_batch_sweep", C.c_int, [_VP, C.c_int, C.c_int, C.c_int]),
     ("hf_batch_rdmft_step", C.c_int, [_VP, _DP]),
@@ -295,6 +299,13 @@ def hf_get_drift(ctx):
     return m.value, n.value
 
 
+def hf_get_refresh_stats(ctx):
+    """(tensor-core refreshes, fallbacks to Gauss-Jordan, digit products) since the last clear."""
+    a, b, n = C.c_ulonglong(), C.c_ulonglong(), C.c_ulonglong()
+    _check(lib().hf_get_refresh_stats(ctx, C.byref(a), C.byref(b), C.byref(n)), ctx)
+    return a.value, b.value, n.value
+
+
 def hf_get_timings(ctx):
     ms = np.zeros(6)
     _check(lib().hf_get_timings(ctx, _dp(ms)), ctx)
@@ -308,6 +319,10 @@ def hf_lattice_step_noalloc(ctx, d_sigma: int, d_gloc: int):
 
 def hf_philox_blocks(key_lo, key_hi, d_ctr: int, n: int, d_out: int, stream=None):
     _check(lib().hf_philox_blocks(key_lo, key_hi, d_ctr, n, d_out, stream))
+
+
+def hf_tc_dgemm128(d_A: int, d_B: int, d_C: int, n: int, digits: int, d_status=None, stream=None):
+    _check(lib().hf_tc_dgemm128(d_A, d_B, d_C, n, digits, d_status, stream))
 
 
 def _bcheck(st, b=None):
@@ -478,6 +493,7 @@ def make_params(cfg: dict, stream=None, **over) -> hf_params:
     p.refresh_every = int(d.get("refresh_every", 10))
     p.refresh_stagger = int(d.get("refresh_stagger", 0))
     p.check_drift = int(d.get("check_drift", 0))
+    p.refresh_gj = int(d.get("refresh_gj", 0))
     p.delay_k = int(d.get("delay_k", 1))
     p.team_warps = int(d.get("team_warps", 0))
     p.bin_size = int(d.get("bin_size", 100))
