@@ -42,13 +42,12 @@ constexpr int L = kTcL, LL = L * L;
 constexpr int kThreads = 256;
 constexpr int KC = 32;              // K per chunk
 constexpr int NCH = L / KC;         // chunks
-constexpr int NPW = 64;             // output columns per pass
 constexpr int SMAX = kTcDigits;
 constexpr int A_SL = L * KC * 2;    // bytes of one digit of an A chunk (128 rows x 32 K, bf16)
-constexpr int B_SL = NPW * KC * 2;  // bytes of one digit of a B chunk (64 columns x 32 K)
-constexpr int BUFB = SMAX * (A_SL + B_SL);
+// a B chunk of NP output columns: NP * KC * 2 bytes per digit; the buffer holds SMAX digits of
+// A and SMAX digits of 64 columns, or SMAX / 2 digits of all 128
+constexpr int BUFB = SMAX * (A_SL + 64 * KC * 2);
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kIdesc = idesc_bf16_f32(128, NPW);
 constexpr int kConvergedExp = -24;  // Newton residual bound 2^-24: the step's remaining error,
                                     // its square, is below the products' own accuracy
 constexpr int kFarExp = -4;         // a first residual above 2^-4: no approximate inverse
@@ -65,15 +64,17 @@ struct Smem {
     int tmpT[kThreads];
     unsigned long long red[kThreads / 32];
     int8_t s[L];                    // the chain's fields
-    uint64_t mbar[2];
+    uint64_t mbar[2];               // MMAs of the chunk in buffer b complete
+    uint64_t tbar[2];               // bulk copies into buffer b complete
     uint32_t tmem;
     int flag;                       // fallback requested
     int timeout;
 };
 
 __device__ __forceinline__ unsigned char* bufA(Smem& S, int b, int s) { return S.buf[b] + s * A_SL; }
+template <int NP>
 __device__ __forceinline__ unsigned char* bufB(Smem& S, int b, int t) {
-    return S.buf[b] + SMAX * A_SL + t * B_SL;
+    return S.buf[b] + SMAX * A_SL + t * (NP * KC * 2);
 }
 
 // significand (with the implicit bit) and exponent of a normal double: x = m 2^(E - 52)
@@ -110,14 +111,16 @@ __device__ __forceinline__ unsigned long long block_max(Smem& S, unsigned long l
 // (core (group, kc) at (group * 4 + kc) * 128 bytes, row r of the core at r * 16)
 // ------------------------------------------------------------------------------------------
 
-// A from precomputed digit chunks (each an 8 KB block in exactly this layout)
+// A from precomputed digit chunks (each an 8 KB block in exactly this layout): SA bulk copies by
+// thread 0, landing on tbar[b]; the MMA issuer waits for them
 template <int SA>
 __device__ void fill_A_digits(Smem& S, int b, int c, const uint16_t* digits) {
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(&S.tbar[b], SA * A_SL);
 #pragma unroll
-    for (int s = 0; s < SA; ++s) {
-        const uint4* src = reinterpret_cast<const uint4*>(digits + (static_cast<size_t>(s) * NCH + c) * (A_SL / 2));
-        uint4* dst = reinterpret_cast<uint4*>(bufA(S, b, s));
-        for (int u = threadIdx.x; u < A_SL / 16; u += kThreads) dst[u] = src[u];
+        for (int s = 0; s < SA; ++s)
+            bulk_copy_g2s(bufA(S, b, s), digits + (static_cast<size_t>(s) * NCH + c) * (A_SL / 2),
+                          A_SL, &S.tbar[b]);
     }
 }
 
@@ -156,37 +159,42 @@ __device__ void fill_A_rows(Smem& S, int b, int c, const double* X) {
     }
 }
 
-// B from the columns p*64 .. p*64+63 of a row-major FP64 matrix X with column scales S.colT;
+// B from the columns p*NP .. p*NP+NP-1 of a row-major FP64 matrix X with column scales S.colT;
 // with E, row k is multiplied by e_k (significand me[k], exponent Ee[k]) exactly on the way
-template <int SB, bool E>
+template <int SB, bool E, int NP>
 __device__ void fill_B_cols(Smem& S, int b, int c, int p, const double* X,
                             const unsigned long long* me, const int* Ee) {
-    const int t = threadIdx.x;
-    const int jl = t & (NPW - 1), kg = t >> 6;
-    const int j = p * NPW + jl;
-    const int T = S.colT[j];
-    long long F[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int k = c * KC + kg * 8 + q;
-        const double x = X[static_cast<size_t>(k) * L + j];
-        if constexpr (E) {
-            const int up = S.s[k] > 0 ? 1 : 0;   // caller stores sigma s_k in S.s
-            F[q] = to_fixed_scaled(x, me[up], Ee[up], T);
-        } else {
-            F[q] = to_fixed(x, T);
+    for (int u0 = 0; u0 < NP * (KC / 8); u0 += kThreads) {
+        const int u = u0 + threadIdx.x;
+        const int jl = u & (NP - 1), kg = u / NP;
+        const int j = p * NP + jl;
+        const int T = S.colT[j];
+        double x[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) x[q] = X[static_cast<size_t>(c * KC + kg * 8 + q) * L + j];
+        long long F[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if constexpr (E) {
+                const int up = S.s[c * KC + kg * 8 + q] > 0 ? 1 : 0;   // S.s holds sigma s_k
+                F[q] = to_fixed_scaled(x[q], me[up], Ee[up], T);
+            } else {
+                F[q] = to_fixed(x[q], T);
+            }
         }
+        store_digits<SB>(F, bufB<NP>(S, b, 0), NP * KC * 2, ((jl >> 3) * 4 + kg) * 128 + (jl & 7) * 16);
     }
-    store_digits<SB>(F, bufB(S, b, 0), B_SL, ((jl >> 3) * 4 + kg) * 128 + (jl & 7) * 16);
 }
 
 // ------------------------------------------------------------------------------------------
 // one product pass: fills, MMAs, readout
 // ------------------------------------------------------------------------------------------
-template <int SA, int SB, int NL>
+template <int SA, int SB, int NL, int NP>
 __device__ void issue_chunk(Smem& S, int b, int c) {
+    constexpr uint32_t idesc = idesc_bf16_f32(128, NP);
     tc_fence_after_sync();
-    const uint32_t a0 = smem_addr(bufA(S, b, 0)), b0 = smem_addr(bufB(S, b, 0));
+    const uint32_t a0 = smem_addr(bufA(S, b, 0)), b0 = smem_addr(bufB<NP>(S, b, 0));
 #pragma unroll
     for (int n = 2; n <= NL; ++n) {
         const int smin = n - SB > 1 ? n - SB : 1;
@@ -196,20 +204,24 @@ __device__ void issue_chunk(Smem& S, int b, int c) {
 #pragma unroll
             for (int kk = 0; kk < 2; ++kk) {
                 const uint64_t ad = smem_desc(a0 + (s - 1) * A_SL + kk * 256, 128, 512);
-                const uint64_t bd = smem_desc(b0 + (t - 1) * B_SL + kk * 256, 128, 512);
-                mma_bf16(S.tmem + (n - 2) * NPW, ad, bd, kIdesc, !(c == 0 && kk == 0 && s == smin));
+                const uint64_t bd = smem_desc(b0 + (t - 1) * (NP * KC * 2) + kk * 256, 128, 512);
+                mma_bf16(S.tmem + (n - 2) * NP, ad, bd, idesc, !(c == 0 && kk == 0 && s == smin));
             }
         }
     }
     mma_commit(&S.mbar[b]);
 }
 
-// Runs one pass (output columns p*64 ...) of C = A B with the given operand fills and hands every
-// element's level sum Q (C_ij = Q 2^(rowT_i + colT_j - 54)) to epi(i, j, Q).  ph[] tracks the
-// two mbarriers' phases.  Returns false if a wait ran out (the CTA then stops using TMEM).
-template <int SA, int SB, int NL, class FA, class FB, class EPI>
-__device__ bool product_pass(Smem& S, int p, uint32_t (&ph)[2], FA fillA, FB fillB, EPI epi) {
-    static_assert(NL - 1 <= 8 && (NL - 1) * NPW <= static_cast<int>(kTmemCols), "levels fit TMEM");
+// Runs one pass (output columns p*NP ...) of C = A B with the given operand fills and hands every
+// element's level sum Q (C_ij = Q 2^(rowT_i + colT_j - 54)) to the epilogue: pre(i, j0) once per
+// 16 columns j0 ... j0+15 of row i (to load what the epilogue needs early), then epi(i, j, k, Q)
+// for each, k = j - j0.  With TMA_A the A fill is a bulk copy whose completion the MMA issuer
+// awaits.  ph[] / tph[] track the mbarriers' phases.  Returns false if a wait ran out.
+template <int SA, int SB, int NL, int NP, bool TMA_A, class FA, class FB, class PRE, class EPI>
+__device__ bool product_pass(Smem& S, int p, uint32_t (&ph)[2], uint32_t (&tph)[2], FA fillA,
+                             FB fillB, PRE pre, EPI epi) {
+    static_assert(NL - 1 <= 8 && (NL - 1) * NP <= static_cast<int>(kTmemCols), "levels fit TMEM");
+    static_assert(SB * NP * KC * 2 <= BUFB - SMAX * A_SL && SA <= SMAX, "digits fit the buffer");
     const int tid = threadIdx.x;
     bool ok = true;
     for (int c = 0; c < NCH; ++c) {
@@ -223,32 +235,41 @@ __device__ bool product_pass(Smem& S, int p, uint32_t (&ph)[2], FA fillA, FB fil
         fence_async_shared();
         tc_fence_before_sync();
         __syncthreads();
-        if (tid == 0) issue_chunk<SA, SB, NL>(S, b, c);
+        if (tid == 0) {
+            if constexpr (TMA_A) {
+                ok = mbar_wait(&S.tbar[b], tph[b]) && ok;
+            }
+            issue_chunk<SA, SB, NL, NP>(S, b, c);
+        }
+        if constexpr (TMA_A) tph[b] ^= 1u;
     }
     ok = mbar_wait(&S.mbar[0], ph[0]) && ok;
     ph[0] ^= 1u;
     ok = mbar_wait(&S.mbar[1], ph[1]) && ok;
     ph[1] ^= 1u;
-    if (!ok) return false;
+    if (__syncthreads_or(!ok)) return false;
     tc_fence_after_sync();
     const int w = tid >> 5, lane = tid & 31;
     const int i = 32 * (w & 3) + lane;
     const int cg = w >> 2;
+    constexpr int G = NP / 32;   // groups of 16 columns per warp half
     const uint32_t trow = S.tmem + (static_cast<uint32_t>(32 * (w & 3)) << 16);
 #pragma unroll 1
-    for (int g = 0; g < 2; ++g) {
+    for (int g = 0; g < G; ++g) {
+        const int jl0 = (NP / 2) * cg + 16 * g;
+        pre(i, p * NP + jl0);
         long long Q[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) Q[k] = 0;
 #pragma unroll
         for (int n = 2; n <= NL; ++n) {
             float v[16];
-            tmem_ld16(trow + (n - 2) * NPW + 32 * cg + 16 * g, v);
+            tmem_ld16(trow + (n - 2) * NP + jl0, v);
 #pragma unroll
             for (int k = 0; k < 16; ++k) Q[k] += level_shift(static_cast<long long>(__float2int_rz(v[k])), n);
         }
-#pragma unroll 4
-        for (int k = 0; k < 16; ++k) epi(i, p * NPW + 32 * cg + 16 * g + k, Q[k]);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) epi(i, p * NP + jl0 + k, k, Q[k]);
     }
     tc_fence_before_sync();
     __syncthreads();
@@ -323,8 +344,9 @@ struct SpinArgs {
 
 // R = 1 - g0^{-1} (E X) + D X for X in Xsrc, written to Rdst; returns max |R| (bit pattern key)
 template <int S_, int NL>
-__device__ bool residual(Smem& S, uint32_t (&ph)[2], const SpinArgs& a, const double* Xsrc,
-                         double* Rdst, unsigned long long& rmax) {
+__device__ bool residual(Smem& S, uint32_t (&ph)[2], uint32_t (&tph)[2], const SpinArgs& a,
+                         const double* Xsrc, double* Rdst, unsigned long long& rmax) {
+    constexpr int NP = 64;
     for (int i = threadIdx.x; i < L; i += kThreads) S.rowT[i] = a.rowTg[i];
     col_scales(S, Xsrc, a.Ee);
     if (threadIdx.x < 32) {   // largest row scale + largest column scale
@@ -341,11 +363,20 @@ __device__ bool residual(Smem& S, uint32_t (&ph)[2], const SpinArgs& a, const do
         if (threadIdx.x == 0 && mr + mc > kMaxScaleSum) S.flag = 1;
     }
     unsigned long long mx = 0;
-    for (int p = 0; p < L / NPW; ++p) {
-        const bool ok = product_pass<S_, S_, NL>(
-            S, p, ph, [&](int b, int c) { fill_A_digits<S_>(S, b, c, a.digits); },
-            [&](int b, int c) { fill_B_cols<S_, true>(S, b, c, p, Xsrc, a.me, a.Ee); },
-            [&](int i, int j, long long Q) {
+    double xr[16];
+    for (int p = 0; p < L / NP; ++p) {
+        const bool ok = product_pass<S_, S_, NL, NP, true>(
+            S, p, ph, tph, [&](int b, int c) { fill_A_digits<S_>(S, b, c, a.digits); },
+            [&](int b, int c) { fill_B_cols<S_, true, NP>(S, b, c, p, Xsrc, a.me, a.Ee); },
+            [&](int i, int j0) {
+#pragma unroll
+                for (int k = 0; k < 16; k += 2) {
+                    const double2 v = *reinterpret_cast<const double2*>(Xsrc + static_cast<size_t>(i) * L + j0 + k);
+                    xr[k] = v.x;
+                    xr[k + 1] = v.y;
+                }
+            },
+            [&](int i, int j, int k, long long Q) {
                 const int EQ = S.rowT[i] + S.colT[j] - 54;
                 long long q = -Q;
                 if (i == j) {
@@ -357,7 +388,7 @@ __device__ bool residual(Smem& S, uint32_t (&ph)[2], const SpinArgs& a, const do
                 const int T = 62 + EQ;
                 // |ev X| must lie below 2^(T - 1) for the fixed-point form; it does whenever the
                 // scales are sane, otherwise the chain falls back
-                const double x = Xsrc[static_cast<size_t>(i) * L + j];
+                const double x = xr[k];
                 const int ex = exp_of(x);
                 if (ex != kNoExp && ex + a.Eev[up] + 2 > T - 1) S.flag = 1;
                 long long v = to_fixed_scaled(x, a.mev[up], a.Eev[up], T);
@@ -374,33 +405,41 @@ __device__ bool residual(Smem& S, uint32_t (&ph)[2], const SpinArgs& a, const do
     return true;
 }
 
-// X_new = X + X R (X in Xsrc, R in Rsrc), written over Rsrc (each pass writes only the columns
-// it has finished reading)
+// X_new = X + X R (X in Xsrc, R in Rsrc), written over Rsrc, in one pass of all 128 columns
+// (4 digits, levels up to 5: the TMEM holds the four level accumulators of 128 columns)
 template <int S_, int NL>
-__device__ bool correct(Smem& S, uint32_t (&ph)[2], const double* Xsrc, double* Rsrc) {
+__device__ bool correct(Smem& S, uint32_t (&ph)[2], uint32_t (&tph)[2], const double* Xsrc,
+                        double* Rsrc) {
+    constexpr int NP = 128;
     row_scales(S, Xsrc);
     col_scales(S, Rsrc, nullptr);
-    for (int p = 0; p < L / NPW; ++p) {
-        const bool ok = product_pass<S_, S_, NL>(
-            S, p, ph, [&](int b, int c) { fill_A_rows<S_>(S, b, c, Xsrc); },
-            [&](int b, int c) { fill_B_cols<S_, false>(S, b, c, p, Rsrc, nullptr, nullptr); },
-            [&](int i, int j, long long Q) {
-                const size_t e = static_cast<size_t>(i) * L + j;
-                Rsrc[e] = Xsrc[e] + fixed_to_double(Q, S.rowT[i] + S.colT[j] - 54);
-            });
-        if (!ok) return false;
-    }
-    return true;
+    double xr[16];
+    return product_pass<S_, S_, NL, NP, false>(
+        S, 0, ph, tph, [&](int b, int c) { fill_A_rows<S_>(S, b, c, Xsrc); },
+        [&](int b, int c) { fill_B_cols<S_, false, NP>(S, b, c, 0, Rsrc, nullptr, nullptr); },
+        [&](int i, int j0) {
+#pragma unroll
+            for (int k = 0; k < 16; k += 2) {
+                const double2 v = *reinterpret_cast<const double2*>(Xsrc + static_cast<size_t>(i) * L + j0 + k);
+                xr[k] = v.x;
+                xr[k + 1] = v.y;
+            }
+        },
+        [&](int i, int j, int k, long long Q) {
+            Rsrc[static_cast<size_t>(i) * L + j] = xr[k] + fixed_to_double(Q, S.rowT[i] + S.colT[j] - 54);
+        });
 }
 
-__device__ bool refresh_spin(Smem& S, uint32_t (&ph)[2], const SpinArgs& a, int& products) {
+__device__ bool refresh_spin(Smem& S, uint32_t (&ph)[2], uint32_t (&tph)[2], const SpinArgs& a,
+                             int& products) {
     // X0 = the FP32 state
     for (int e = threadIdx.x; e < LL; e += kThreads) a.Xa[e] = static_cast<double>(a.Gf[e]);
     __syncthreads();
     unsigned long long r = 0;
     // step 0: residual to about 2^-35 of the operand scales, enough that one full step then
-    // converges from an FP32 state; correction to what that needs
-    if (!residual<7, 8>(S, ph, a, a.Xa, a.Xb, r)) return false;
+    // converges from an FP32 state; correction from 4 digits (levels up to 5), which is what a
+    // residual of that size needs
+    if (!residual<7, 8>(S, ph, tph, a, a.Xa, a.Xb, r)) return false;
     products += n_products(7, 8);
     if (S.flag) return true;                                        // scales out of range
     if (exp_of(__longlong_as_double(static_cast<long long>(r))) >= kFarExp) {
@@ -408,19 +447,19 @@ __device__ bool refresh_spin(Smem& S, uint32_t (&ph)[2], const SpinArgs& a, int&
         __syncthreads();
         return true;
     }
-    if (!correct<5, 6>(S, ph, a.Xa, a.Xb)) return false;          // X1 in Xb
-    products += n_products(5, 6);
+    if (!correct<4, 5>(S, ph, tph, a.Xa, a.Xb)) return false;     // X1 in Xb
+    products += n_products(4, 5);
     // full-accuracy steps until the residual is below 2^-24 (its square is then far below the
     // products' own error), at most two
     double* X = a.Xb;
     double* R = a.Xa;
     bool done = false;
     for (int it = 0; it < 2 && !done; ++it) {
-        if (!residual<8, 9>(S, ph, a, X, R, r)) return false;
+        if (!residual<8, 9>(S, ph, tph, a, X, R, r)) return false;
         products += n_products(8, 9);
         if (S.flag) return true;
-        if (!correct<5, 6>(S, ph, X, R)) return false;            // X + X R over R
-        products += n_products(5, 6);
+        if (!correct<4, 5>(S, ph, tph, X, R)) return false;       // X + X R over R
+        products += n_products(4, 5);
         double* t = X;
         X = R;
         R = t;
@@ -458,13 +497,15 @@ refresh_tc_kernel(const QmcProblem P, const TcRefreshArgs A) {
         S.timeout = 0;
         mbar_init(&S.mbar[0], 1);
         mbar_init(&S.mbar[1], 1);
+        mbar_init(&S.tbar[0], 1);
+        mbar_init(&S.tbar[1], 1);
         mbar_init_fence();
     }
     if (tid < 32) tmem_alloc(&S.tmem, kTmemCols);
     tc_fence_before_sync();
     __syncthreads();
     tc_fence_after_sync();
-    uint32_t ph[2] = {0u, 0u};
+    uint32_t ph[2] = {0u, 0u}, tph[2] = {0u, 0u};
     const double e_p = 1.0 + P.ev_p, e_m = 1.0 + P.ev_m;
     bool ok = true;
     int products = 0;
@@ -485,7 +526,7 @@ refresh_tc_kernel(const QmcProblem P, const TcRefreshArgs A) {
         a.evneg[0] = P.ev_m < 0.0;
         a.evneg[1] = P.ev_p < 0.0;
         __syncthreads();
-        ok = refresh_spin(S, ph, a, products);
+        ok = refresh_spin(S, ph, tph, a, products);
         if (!ok) {
             if (tid == 0) S.timeout = 1;
             break;
@@ -578,24 +619,27 @@ tc_dgemm_kernel(const double* Am, const double* Bm, double* Cm, int n, int* stat
     if (tid == 0) {
         mbar_init(&S.mbar[0], 1);
         mbar_init(&S.mbar[1], 1);
+        mbar_init(&S.tbar[0], 1);
+        mbar_init(&S.tbar[1], 1);
         mbar_init_fence();
     }
     if (tid < 32) tmem_alloc(&S.tmem, kTmemCols);
     tc_fence_before_sync();
     __syncthreads();
     tc_fence_after_sync();
-    uint32_t ph[2] = {0u, 0u};
+    uint32_t ph[2] = {0u, 0u}, tph[2] = {0u, 0u};
     const double* Ab = Am + static_cast<size_t>(m) * LL;
     const double* Bb = Bm + static_cast<size_t>(m) * LL;
     double* Cb = Cm + static_cast<size_t>(m) * LL;
     row_scales(S, Ab);
     col_scales(S, Bb, nullptr);
     bool ok = true;
-    for (int p = 0; p < L / NPW && ok; ++p)
-        ok = product_pass<SD, SD, SD + 1>(
-            S, p, ph, [&](int b, int c) { fill_A_rows<SD>(S, b, c, Ab); },
-            [&](int b, int c) { fill_B_cols<SD, false>(S, b, c, p, Bb, nullptr, nullptr); },
-            [&](int i, int j, long long Q) {
+    for (int p = 0; p < L / 64 && ok; ++p)
+        ok = product_pass<SD, SD, SD + 1, 64, false>(
+            S, p, ph, tph, [&](int b, int c) { fill_A_rows<SD>(S, b, c, Ab); },
+            [&](int b, int c) { fill_B_cols<SD, false, 64>(S, b, c, p, Bb, nullptr, nullptr); },
+            [&](int, int) {},
+            [&](int i, int j, int, long long Q) {
                 Cb[static_cast<size_t>(i) * L + j] = fixed_to_double(Q, S.rowT[i] + S.colT[j] - 54);
             });
     __syncthreads();
