@@ -39,7 +39,7 @@ namespace {
 using namespace tc;
 
 constexpr int L = kTcL, LL = L * L;
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 constexpr int KC = 32;              // K per chunk
 constexpr int NCH = L / KC;         // chunks
 constexpr int SMAX = kTcDigits;
@@ -61,6 +61,8 @@ constexpr int kMaxScaleSum = 12;
 struct Smem {
     unsigned char buf[2][BUFB];     // double-buffered digit chunks: A digits, then B digits
     int rowT[L], colT[L];           // power-of-two scales of the current operands
+    int nrowT[L], ncolT[L];         // the next product's, gathered by this product's epilogue
+    int gT[L];                      // row scales of g0^{-1} (this spin)
     int tmpT[kThreads];
     unsigned long long red[kThreads / 32];
     int8_t s[L];                    // the chain's fields
@@ -124,67 +126,87 @@ __device__ void fill_A_digits(Smem& S, int b, int c, const uint16_t* digits) {
     }
 }
 
-// 8 fixed-point values -> SD digit rows of 16 bytes at dst[d] + off
-template <int SD>
-__device__ __forceinline__ void store_digits(long long (&F)[8], unsigned char* base, int stride,
-                                             int off) {
+// NE (4 or 8) fixed-point magnitudes and signs -> SD digit rows of NE bf16 at base + (s - 1) stride
+// + off.  Digits top down: d = round(r / 2^(62 - 8 s)) of the remainder r, the eighth digit the last
+// 6 bits at weight 2^-64 (digits_of gives the same expansion bottom up).
+template <int SD, int NE>
+__device__ __forceinline__ void store_digits(const unsigned long long (&U)[NE], const bool (&neg)[NE],
+                                             unsigned char* base, int stride, int off) {
+    long long r[NE];
+#pragma unroll
+    for (int q = 0; q < NE; ++q) r[q] = static_cast<long long>(U[q]);
 #pragma unroll
     for (int s = 1; s <= SD; ++s) {
-        uint32_t w[4];
+        int d[NE];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int d0 = next_digit(F[2 * q], s);
-            const int d1 = next_digit(F[2 * q + 1], s);
-            w[q] = pack_bf16x2(bf16_of_int(d0), bf16_of_int(d1));
+        for (int q = 0; q < NE; ++q) {
+            if (s < 8) {
+                const int sh = 62 - 8 * s;
+                const long long v = (r[q] + (1ll << (sh - 1))) >> sh;
+                r[q] -= v << sh;
+                d[q] = static_cast<int>(v);
+            } else {
+                d[q] = static_cast<int>(r[q] << 2);
+            }
         }
-        *reinterpret_cast<uint4*>(base + (s - 1) * stride + off) = make_uint4(w[0], w[1], w[2], w[3]);
+        uint32_t w[NE / 2];
+#pragma unroll
+        for (int q = 0; q < NE / 2; ++q) w[q] = bf16x2_digits(d[2 * q], d[2 * q + 1], neg[2 * q], neg[2 * q + 1]);
+        unsigned char* dst = base + (s - 1) * stride + off;
+        if constexpr (NE == 8) *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+        else *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
     }
 }
 
-// A from the rows of a row-major FP64 matrix X with row scales S.rowT
+// A from the rows of a row-major FP64 matrix X with row scales S.rowT: 128 rows x 4 groups of 8
+// consecutive K, one group per thread
 template <int SA>
 __device__ void fill_A_rows(Smem& S, int b, int c, const double* X) {
-    for (int u = threadIdx.x; u < L * (KC / 8); u += kThreads) {
-        const int i = u & (L - 1), kg = u >> 7;
-        const double* src = X + static_cast<size_t>(i) * L + c * KC + kg * 8;
-        const int T = S.rowT[i];
-        long long F[8];
+    static_assert(L * (KC / 8) == kThreads, "one group per thread");
+    const int u = threadIdx.x;
+    const int i = u & (L - 1), kg = u >> 7;
+    const double* src = X + static_cast<size_t>(i) * L + c * KC + kg * 8;
+    const int T = S.rowT[i];
+    unsigned long long U[8];
+    bool neg[8];
 #pragma unroll
-        for (int q = 0; q < 8; q += 2) {
-            const double2 v = *reinterpret_cast<const double2*>(src + q);
-            F[q] = to_fixed(v.x, T);
-            F[q + 1] = to_fixed(v.y, T);
-        }
-        store_digits<SA>(F, bufA(S, b, 0), A_SL, ((i >> 3) * 4 + kg) * 128 + (i & 7) * 16);
+    for (int q = 0; q < 8; q += 2) {
+        const double2 v = *reinterpret_cast<const double2*>(src + q);
+        U[q] = to_fixed_mag(v.x, T, neg[q]);
+        U[q + 1] = to_fixed_mag(v.y, T, neg[q + 1]);
     }
+    store_digits<SA, 8>(U, neg, bufA(S, b, 0), A_SL, ((i >> 3) * 4 + kg) * 128 + (i & 7) * 16);
 }
 
 // B from the columns p*NP .. p*NP+NP-1 of a row-major FP64 matrix X with column scales S.colT;
-// with E, row k is multiplied by e_k (significand me[k], exponent Ee[k]) exactly on the way
+// with E, row k is multiplied by e_k (significand me[k], exponent Ee[k]) exactly on the way.
+// Each thread converts EPT = NP * KC / kThreads consecutive K of one column.
 template <int SB, bool E, int NP>
 __device__ void fill_B_cols(Smem& S, int b, int c, int p, const double* X,
                             const unsigned long long* me, const int* Ee) {
+    constexpr int EPT = NP * KC / kThreads;
+    static_assert(EPT == 4 || EPT == 8, "4 or 8 K per thread");
+    const int t = threadIdx.x;
+    const int jl = t & (NP - 1), seg = t / NP;
+    const int k0 = seg * EPT;                      // within the chunk
+    const int j = p * NP + jl;
+    const int T = S.colT[j];
+    double x[EPT];
 #pragma unroll
-    for (int u0 = 0; u0 < NP * (KC / 8); u0 += kThreads) {
-        const int u = u0 + threadIdx.x;
-        const int jl = u & (NP - 1), kg = u / NP;
-        const int j = p * NP + jl;
-        const int T = S.colT[j];
-        double x[8];
+    for (int q = 0; q < EPT; ++q) x[q] = X[static_cast<size_t>(c * KC + k0 + q) * L + j];
+    unsigned long long U[EPT];
+    bool neg[EPT];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) x[q] = X[static_cast<size_t>(c * KC + kg * 8 + q) * L + j];
-        long long F[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            if constexpr (E) {
-                const int up = S.s[c * KC + kg * 8 + q] > 0 ? 1 : 0;   // S.s holds sigma s_k
-                F[q] = to_fixed_scaled(x[q], me[up], Ee[up], T);
-            } else {
-                F[q] = to_fixed(x[q], T);
-            }
+    for (int q = 0; q < EPT; ++q) {
+        if constexpr (E) {
+            const int up = S.s[c * KC + k0 + q] > 0 ? 1 : 0;   // S.s holds sigma s_k
+            U[q] = to_fixed_scaled_mag(x[q], me[up], Ee[up], T, neg[q]);
+        } else {
+            U[q] = to_fixed_mag(x[q], T, neg[q]);
         }
-        store_digits<SB>(F, bufB<NP>(S, b, 0), NP * KC * 2, ((jl >> 3) * 4 + kg) * 128 + (jl & 7) * 16);
     }
+    store_digits<SB, EPT>(U, neg, bufB<NP>(S, b, 0), NP * KC * 2,
+                          ((jl >> 3) * 4 + (k0 >> 3)) * 128 + (jl & 7) * 16 + (k0 & 7) * 2);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -214,12 +236,13 @@ __device__ void issue_chunk(Smem& S, int b, int c) {
 
 // Runs one pass (output columns p*NP ...) of C = A B with the given operand fills and hands every
 // element's level sum Q (C_ij = Q 2^(rowT_i + colT_j - 54)) to the epilogue: pre(i, j0) once per
-// 16 columns j0 ... j0+15 of row i (to load what the epilogue needs early), then epi(i, j, k, Q)
-// for each, k = j - j0.  With TMA_A the A fill is a bulk copy whose completion the MMA issuer
+// 8 columns j0 ... j0+7 of row i (to load what the epilogue needs early), then epi(i, j, k, Q)
+// for each, k = j - j0, which returns an exponent whose maximum over the rows lands in ncol[j]
+// (when ncol is not null).  With TMA_A the A fill is a bulk copy whose completion the MMA issuer
 // awaits.  ph[] / tph[] track the mbarriers' phases.  Returns false if a wait ran out.
 template <int SA, int SB, int NL, int NP, bool TMA_A, class FA, class FB, class PRE, class EPI>
 __device__ bool product_pass(Smem& S, int p, uint32_t (&ph)[2], uint32_t (&tph)[2], FA fillA,
-                             FB fillB, PRE pre, EPI epi) {
+                             FB fillB, PRE pre, EPI epi, int* ncol) {
     static_assert(NL - 1 <= 8 && (NL - 1) * NP <= static_cast<int>(kTmemCols), "levels fit TMEM");
     static_assert(SB * NP * KC * 2 <= BUFB - SMAX * A_SL && SA <= SMAX, "digits fit the buffer");
     const int tid = threadIdx.x;
@@ -251,25 +274,34 @@ __device__ bool product_pass(Smem& S, int p, uint32_t (&ph)[2], uint32_t (&tph)[
     tc_fence_after_sync();
     const int w = tid >> 5, lane = tid & 31;
     const int i = 32 * (w & 3) + lane;
+    constexpr int NQ = kThreads / 128;   // warps per lane quarter
     const int cg = w >> 2;
-    constexpr int G = NP / 32;   // groups of 16 columns per warp half
+    constexpr int G = NP / NQ / 8;       // groups of 8 columns per warp
     const uint32_t trow = S.tmem + (static_cast<uint32_t>(32 * (w & 3)) << 16);
 #pragma unroll 1
     for (int g = 0; g < G; ++g) {
-        const int jl0 = (NP / 2) * cg + 16 * g;
+        const int jl0 = (NP / NQ) * cg + 8 * g;
         pre(i, p * NP + jl0);
-        long long Q[16];
+        long long Q[8];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) Q[k] = 0;
+        for (int k = 0; k < 8; ++k) Q[k] = 0;
 #pragma unroll
         for (int n = 2; n <= NL; ++n) {
-            float v[16];
-            tmem_ld16(trow + (n - 2) * NP + jl0, v);
+            float v[8];
+            tmem_ld8(trow + (n - 2) * NP + jl0, v);
 #pragma unroll
-            for (int k = 0; k < 16; ++k) Q[k] += level_shift(static_cast<long long>(__float2int_rz(v[k])), n);
+            for (int k = 0; k < 8; ++k) Q[k] += level_shift(static_cast<long long>(__float2int_rz(v[k])), n);
         }
 #pragma unroll
-        for (int k = 0; k < 16; ++k) epi(i, p * NP + jl0 + k, k, Q[k]);
+        for (int k = 0; k < 8; ++k) {
+            // the epilogue returns its output's contribution to the next product's column
+            // scale; the warp's 32 rows are folded by one redux, the four row blocks by atomics
+            const int ce = epi(i, p * NP + jl0 + k, k, Q[k]);
+            if (ncol) {
+                const int m = __reduce_max_sync(0xffffffffu, ce);
+                if (lane == 0) atomicMax(ncol + p * NP + jl0 + k, m);
+            }
+        }
     }
     tc_fence_before_sync();
     __syncthreads();
@@ -290,9 +322,10 @@ __host__ __device__ constexpr int n_products(int S, int NL) {
 // ------------------------------------------------------------------------------------------
 // colT[j] = max_k (exp(X_kj) + add_k) + 2 (+1 for the e scaling): |e_k X_kj| <= 2^(colT_j - 1)
 __device__ void col_scales(Smem& S, const double* X, const int* Ee) {
+    constexpr int NH = kThreads / L;   // threads per column
     const int t = threadIdx.x, j = t & (L - 1), h = t >> 7;
     int m = kNoExp;
-    for (int k = h * (L / 2); k < (h + 1) * (L / 2); ++k) {
+    for (int k = h * (L / NH); k < (h + 1) * (L / NH); ++k) {
         int e = exp_of(X[static_cast<size_t>(k) * L + j]);
         if (Ee && e != kNoExp) e += Ee[S.s[k] > 0 ? 1 : 0] + 1;
         m = e > m ? e : m;
@@ -300,8 +333,9 @@ __device__ void col_scales(Smem& S, const double* X, const int* Ee) {
     S.tmpT[t] = m;
     __syncthreads();
     if (t < L) {
-        const int a = S.tmpT[t], b2 = S.tmpT[t + L];
-        S.colT[t] = (a > b2 ? a : b2) + 2;
+        int a = S.tmpT[t];
+        for (int q = 1; q < NH; ++q) a = max(a, S.tmpT[t + q * L]);
+        S.colT[t] = a + 2;
     }
     __syncthreads();
 }
@@ -342,41 +376,56 @@ struct SpinArgs {
     bool evneg[2];            // e^V - 1 < 0
 };
 
-// R = 1 - g0^{-1} (E X) + D X for X in Xsrc, written to Rdst; returns max |R| (bit pattern key)
+// Moves the scales the last epilogue gathered into place: colT <- ncolT + 2 (and rowT <- nrowT +
+// 2 with rows), and clears the gathering arrays.
+__device__ void take_scales(Smem& S, bool rows) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < L; i += kThreads) {
+        S.colT[i] = S.ncolT[i] + 2;
+        S.ncolT[i] = kNoExp;
+        if (rows) {
+            S.rowT[i] = S.nrowT[i] + 2;
+            S.nrowT[i] = kNoExp;
+        }
+    }
+    __syncthreads();
+}
+
+// R = 1 - g0^{-1} (E X) + D X for X in Xsrc (column scales of E X in S.colT), written to Rdst;
+// returns max |R| (bit pattern key).  Gathers R's column scales and X's row scales for the
+// correction that follows.
 template <int S_, int NL>
 __device__ bool residual(Smem& S, uint32_t (&ph)[2], uint32_t (&tph)[2], const SpinArgs& a,
                          const double* Xsrc, double* Rdst, unsigned long long& rmax) {
     constexpr int NP = 64;
-    for (int i = threadIdx.x; i < L; i += kThreads) S.rowT[i] = a.rowTg[i];
-    col_scales(S, Xsrc, a.Ee);
+    for (int i = threadIdx.x; i < L; i += kThreads) S.rowT[i] = S.gT[i];
+    __syncthreads();
     if (threadIdx.x < 32) {   // largest row scale + largest column scale
         int mr = kNoExp, mc = kNoExp;
         for (int i = threadIdx.x; i < L; i += 32) {
             mr = S.rowT[i] > mr ? S.rowT[i] : mr;
             mc = S.colT[i] > mc ? S.colT[i] : mc;
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            mr = max(mr, __shfl_xor_sync(0xffffffffu, mr, o));
-            mc = max(mc, __shfl_xor_sync(0xffffffffu, mc, o));
-        }
+        mr = __reduce_max_sync(0xffffffffu, mr);
+        mc = __reduce_max_sync(0xffffffffu, mc);
         if (threadIdx.x == 0 && mr + mc > kMaxScaleSum) S.flag = 1;
     }
     unsigned long long mx = 0;
-    double xr[16];
+    int xrow = kNoExp;   // this thread's row of X: largest exponent seen
+    double xr[8];
     for (int p = 0; p < L / NP; ++p) {
         const bool ok = product_pass<S_, S_, NL, NP, true>(
             S, p, ph, tph, [&](int b, int c) { fill_A_digits<S_>(S, b, c, a.digits); },
             [&](int b, int c) { fill_B_cols<S_, true, NP>(S, b, c, p, Xsrc, a.me, a.Ee); },
             [&](int i, int j0) {
 #pragma unroll
-                for (int k = 0; k < 16; k += 2) {
+                for (int k = 0; k < 8; k += 2) {
                     const double2 v = *reinterpret_cast<const double2*>(Xsrc + static_cast<size_t>(i) * L + j0 + k);
                     xr[k] = v.x;
                     xr[k + 1] = v.y;
                 }
             },
-            [&](int i, int j, int k, long long Q) {
+            [&](int i, int j, int k, long long Q) -> int {
                 const int EQ = S.rowT[i] + S.colT[j] - 54;
                 long long q = -Q;
                 if (i == j) {
@@ -390,6 +439,7 @@ __device__ bool residual(Smem& S, uint32_t (&ph)[2], uint32_t (&tph)[2], const S
                 // scales are sane, otherwise the chain falls back
                 const double x = xr[k];
                 const int ex = exp_of(x);
+                xrow = ex > xrow ? ex : xrow;
                 if (ex != kNoExp && ex + a.Eev[up] + 2 > T - 1) S.flag = 1;
                 long long v = to_fixed_scaled(x, a.mev[up], a.Eev[up], T);
                 q += a.evneg[up] ? -v : v;
@@ -398,43 +448,82 @@ __device__ bool residual(Smem& S, uint32_t (&ph)[2], uint32_t (&tph)[2], const S
                 const unsigned long long key =
                     static_cast<unsigned long long>(__double_as_longlong(r)) & 0x7FFFFFFFFFFFFFFFull;
                 mx = key > mx ? key : mx;
-            });
+                return exp_of(r);
+            },
+            S.ncolT);
         if (!ok) return false;
     }
+    atomicMax(&S.nrowT[32 * ((threadIdx.x >> 5) & 3) + (threadIdx.x & 31)], xrow);
     rmax = block_max(S, mx);
+    take_scales(S, true);   // rows: X's; columns: R's
     return true;
 }
 
-// X_new = X + X R (X in Xsrc, R in Rsrc), written over Rsrc, in one pass of all 128 columns
-// (4 digits, levels up to 5: the TMEM holds the four level accumulators of 128 columns)
+// X_new = X + X R (X in Xsrc with row scales S.rowT, R in Rsrc with column scales S.colT),
+// written over Rsrc, in one pass of all 128 columns (4 digits, levels up to 5: the TMEM holds
+// the four level accumulators of 128 columns).  Gathers the column scales of E X_new for the
+// residual that follows.
 template <int S_, int NL>
-__device__ bool correct(Smem& S, uint32_t (&ph)[2], uint32_t (&tph)[2], const double* Xsrc,
-                        double* Rsrc) {
+__device__ bool correct(Smem& S, uint32_t (&ph)[2], uint32_t (&tph)[2], const SpinArgs& a,
+                        const double* Xsrc, double* Rsrc) {
     constexpr int NP = 128;
-    row_scales(S, Xsrc);
-    col_scales(S, Rsrc, nullptr);
-    double xr[16];
-    return product_pass<S_, S_, NL, NP, false>(
+    double xr[8];
+    const bool ok = product_pass<S_, S_, NL, NP, false>(
         S, 0, ph, tph, [&](int b, int c) { fill_A_rows<S_>(S, b, c, Xsrc); },
         [&](int b, int c) { fill_B_cols<S_, false, NP>(S, b, c, 0, Rsrc, nullptr, nullptr); },
         [&](int i, int j0) {
 #pragma unroll
-            for (int k = 0; k < 16; k += 2) {
+            for (int k = 0; k < 8; k += 2) {
                 const double2 v = *reinterpret_cast<const double2*>(Xsrc + static_cast<size_t>(i) * L + j0 + k);
                 xr[k] = v.x;
                 xr[k + 1] = v.y;
             }
         },
-        [&](int i, int j, int k, long long Q) {
-            Rsrc[static_cast<size_t>(i) * L + j] = xr[k] + fixed_to_double(Q, S.rowT[i] + S.colT[j] - 54);
-        });
+        [&](int i, int j, int k, long long Q) -> int {
+            const double x = xr[k] + fixed_to_double(Q, S.rowT[i] + S.colT[j] - 54);
+            Rsrc[static_cast<size_t>(i) * L + j] = x;
+            const int e = exp_of(x);
+            return e == kNoExp ? kNoExp : e + a.Ee[S.s[i] > 0 ? 1 : 0] + 1;
+        },
+        S.ncolT);
+    if (!ok) return false;
+    take_scales(S, false);  // columns: E X_new's
+    return true;
 }
 
 __device__ bool refresh_spin(Smem& S, uint32_t (&ph)[2], uint32_t (&tph)[2], const SpinArgs& a,
                              int& products) {
-    // X0 = the FP32 state
-    for (int e = threadIdx.x; e < LL; e += kThreads) a.Xa[e] = static_cast<double>(a.Gf[e]);
-    __syncthreads();
+    // X0 = the FP32 state, with the column scales of E X0; the row scales of g0^{-1}
+    {
+        constexpr int NH = kThreads / L, RH = L / NH;   // threads per column, rows per thread
+        const int t = threadIdx.x, j = t & (L - 1), h = t >> 7;
+        int m = kNoExp;
+#pragma unroll 1
+        for (int r0 = 0; r0 < RH; r0 += 16) {
+            float v[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) v[q] = a.Gf[static_cast<size_t>(h * RH + r0 + q) * L + j];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int k = h * RH + r0 + q;
+                const double x = static_cast<double>(v[q]);
+                a.Xa[static_cast<size_t>(k) * L + j] = x;
+                const int e = exp_of(x);
+                if (e != kNoExp) m = max(m, e + a.Ee[S.s[k] > 0 ? 1 : 0] + 1);
+            }
+        }
+        S.tmpT[t] = m;
+        __syncthreads();
+        if (t < L) {
+            int mm = S.tmpT[t];
+            for (int q = 1; q < NH; ++q) mm = max(mm, S.tmpT[t + q * L]);
+            S.colT[t] = mm + 2;
+            S.ncolT[t] = kNoExp;
+            S.nrowT[t] = kNoExp;
+            S.gT[t] = a.rowTg[t];
+        }
+        __syncthreads();
+    }
     unsigned long long r = 0;
     // step 0: residual to about 2^-35 of the operand scales, enough that one full step then
     // converges from an FP32 state; correction from 4 digits (levels up to 5), which is what a
@@ -447,7 +536,7 @@ __device__ bool refresh_spin(Smem& S, uint32_t (&ph)[2], uint32_t (&tph)[2], con
         __syncthreads();
         return true;
     }
-    if (!correct<4, 5>(S, ph, tph, a.Xa, a.Xb)) return false;     // X1 in Xb
+    if (!correct<4, 5>(S, ph, tph, a, a.Xa, a.Xb)) return false;  // X1 in Xb
     products += n_products(4, 5);
     // full-accuracy steps until the residual is below 2^-24 (its square is then far below the
     // products' own error), at most two
@@ -458,7 +547,7 @@ __device__ bool refresh_spin(Smem& S, uint32_t (&ph)[2], uint32_t (&tph)[2], con
         if (!residual<8, 9>(S, ph, tph, a, X, R, r)) return false;
         products += n_products(8, 9);
         if (S.flag) return true;
-        if (!correct<4, 5>(S, ph, tph, X, R)) return false;       // X + X R over R
+        if (!correct<4, 5>(S, ph, tph, a, X, R)) return false;    // X + X R over R
         products += n_products(4, 5);
         double* t = X;
         X = R;
@@ -557,11 +646,22 @@ refresh_tc_kernel(const QmcProblem P, const TcRefreshArgs A) {
     }
     // the FP32 copy (sweep state) and the drift of the state the sweeps reached
     float dv = 0.0f;
-    for (int e = tid; e < 2 * LL; e += kThreads) {
-        const double x = P.G[static_cast<size_t>(c) * 2 * LL + e];
-        float* gf = P.Gf + static_cast<size_t>(c) * 2 * LL + e;
-        if (P.drift) dv = fmaxf(dv, static_cast<float>(fabs(x - static_cast<double>(*gf))));
-        *gf = static_cast<float>(x);
+    const double* Gc = P.G + static_cast<size_t>(c) * 2 * LL;
+    float* Gfc = P.Gf + static_cast<size_t>(c) * 2 * LL;
+#pragma unroll 1
+    for (int e0 = 0; e0 < 2 * LL; e0 += 8 * kThreads) {
+        double x[8];
+        float g[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            x[q] = Gc[e0 + q * kThreads + tid];
+            g[q] = Gfc[e0 + q * kThreads + tid];
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (P.drift) dv = fmaxf(dv, static_cast<float>(fabs(x[q] - static_cast<double>(g[q]))));
+            Gfc[e0 + q * kThreads + tid] = static_cast<float>(x[q]);
+        }
     }
     if (P.drift) drift_fold(P.drift, dv, tid == 0);
     if (P.refresh_measure) {
@@ -599,11 +699,12 @@ __global__ void __launch_bounds__(kThreads) g0inv_digits_kernel(const QmcProblem
     for (int u = threadIdx.x; u < L * (L / 8); u += kThreads) {
         const int i = u & (L - 1), kg = u >> 7;
         const int c = kg >> 2, kgl = kg & 3;
-        long long F[8];
+        unsigned long long U[8];
+        bool neg[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) F[q] = to_fixed(G[static_cast<size_t>(i) * L + kg * 8 + q], T[i]);
+        for (int q = 0; q < 8; ++q) U[q] = to_fixed_mag(G[static_cast<size_t>(i) * L + kg * 8 + q], T[i], neg[q]);
         unsigned char* base = reinterpret_cast<unsigned char*>(out) + static_cast<size_t>(c) * A_SL;
-        store_digits<SMAX>(F, base, NCH * A_SL, ((i >> 3) * 4 + kgl) * 128 + (i & 7) * 16);
+        store_digits<SMAX, 8>(U, neg, base, NCH * A_SL, ((i >> 3) * 4 + kgl) * 128 + (i & 7) * 16);
     }
 }
 
@@ -639,9 +740,11 @@ tc_dgemm_kernel(const double* Am, const double* Bm, double* Cm, int n, int* stat
             S, p, ph, tph, [&](int b, int c) { fill_A_rows<SD>(S, b, c, Ab); },
             [&](int b, int c) { fill_B_cols<SD, false, 64>(S, b, c, p, Bb, nullptr, nullptr); },
             [&](int, int) {},
-            [&](int i, int j, int, long long Q) {
+            [&](int i, int j, int, long long Q) -> int {
                 Cb[static_cast<size_t>(i) * L + j] = fixed_to_double(Q, S.rowT[i] + S.colT[j] - 54);
-            });
+                return kNoExp;
+            },
+            nullptr);
     __syncthreads();
     tc_fence_after_sync();
     if (tid < 32) tmem_dealloc(S.tmem, kTmemCols);

@@ -7,8 +7,8 @@
 
 namespace hfk {
 
-// One CTA of NT threads (a multiple of 32, at most 256) measures chain c (P.L slices); red is
-// shared scratch of at least 24 doubles.  Reads the chain's FP64 G (written by this CTA before a
+// One CTA of NT threads (a multiple of 32, at most 1024) measures chain c (P.L slices); red is
+// shared scratch of at least 3 NT / 32 doubles.  Reads the chain's FP64 G (written by this CTA before a
 // __syncthreads).
 template <int NT>
 __device__ void measure_refreshed(const QmcProblem& P, int c, double* red) {
@@ -54,19 +54,20 @@ __device__ void measure_refreshed(const QmcProblem& P, int c, double* red) {
         nd += __shfl_xor_sync(0xffffffffu, nd, o);
         db += __shfl_xor_sync(0xffffffffu, db, o);
     }
+    constexpr int NW = NT / 32;
     const int w = tid >> 5;
     if ((tid & 31) == 0) {
         red[w] = nu;
-        red[8 + w] = nd;
-        red[16 + w] = db;
+        red[NW + w] = nd;
+        red[2 * NW + w] = db;
     }
     __syncthreads();
     if (tid == 0) {
         double a = 0.0, bb = 0.0, cc = 0.0;
-        for (int k = 0; k < NT / 32; ++k) {
+        for (int k = 0; k < NW; ++k) {
             a += red[k];
-            bb += red[8 + k];
-            cc += red[16 + k];
+            bb += red[NW + k];
+            cc += red[2 * NW + k];
         }
         if (b < P.max_bins) {
             bin[2 * L + 0] += a / L;

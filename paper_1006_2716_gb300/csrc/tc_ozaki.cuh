@@ -144,6 +144,19 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
 }
 
+// 8 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = __uint_as_float(r[k]);
+}
+
 // Instruction descriptor of kind::f16 with bf16 A and B (both K-major) and an FP32 accumulator.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
     return (1u << 4)                                  // D: F32
@@ -174,25 +187,6 @@ __device__ __forceinline__ int exp_of(double x) {
     return e == 0 ? kNoExp : e - 1023;
 }
 
-// round(x 2^(62 - T)) as a signed 64-bit integer, for |x| <= 2^(T-1) (so |result| <= 2^61).
-__device__ __forceinline__ long long to_fixed(double x, int T) {
-    const long long b = __double_as_longlong(x);
-    const int e = static_cast<int>((b >> 52) & 0x7FF);
-    if (e == 0) return 0;
-    const unsigned long long m = (static_cast<unsigned long long>(b) & 0xFFFFFFFFFFFFFull) |
-                                 0x10000000000000ull;          // 53-bit significand, value m 2^(e-1075)
-    const int sh = (e - 1075) + 62 - T;                          // x 2^(62-T) = m 2^sh
-    unsigned long long v;
-    if (sh >= 0) {
-        v = m << sh;                                             // sh <= 9 when |x| <= 2^(T-1)
-    } else if (sh > -64) {
-        v = (m + (1ull << (-sh - 1))) >> (-sh);                  // round half up
-    } else {
-        v = 0;
-    }
-    return b < 0 ? -static_cast<long long>(v) : static_cast<long long>(v);
-}
-
 // round(x e 2^(62 - T)) for a double x and a constant e = me 2^(Ee - 52) (me its 53-bit
 // significand), exact product of the significands on the integer pipe; |x e| <= 2^(T-1).
 __device__ __forceinline__ long long to_fixed_scaled(double x, unsigned long long me, int Ee, int T) {
@@ -214,6 +208,69 @@ __device__ __forceinline__ long long to_fixed_scaled(double x, unsigned long lon
         v = 0;
     }
     return b < 0 ? -static_cast<long long>(v) : static_cast<long long>(v);
+}
+
+// |round(x 2^(62 - T))| and the sign of x, for |x| <= 2^(T-1) (magnitude <= 2^61).
+__device__ __forceinline__ unsigned long long to_fixed_mag(double x, int T, bool& neg) {
+    const long long b = __double_as_longlong(x);
+    neg = b < 0;
+    const int e = static_cast<int>((b >> 52) & 0x7FF);
+    if (e == 0) return 0ull;
+    const unsigned long long m = (static_cast<unsigned long long>(b) & 0xFFFFFFFFFFFFFull) |
+                                 0x10000000000000ull;
+    const int sh = (e - 1075) + 62 - T;
+    if (sh >= 0) return m << sh;
+    if (sh > -64) return (m + (1ull << (-sh - 1))) >> (-sh);
+    return 0ull;
+}
+
+// |round(x e 2^(62 - T))| and the sign of x, e = me 2^(Ee - 52) > 0 (see to_fixed_scaled).
+__device__ __forceinline__ unsigned long long to_fixed_scaled_mag(double x, unsigned long long me,
+                                                                  int Ee, int T, bool& neg) {
+    const long long b = __double_as_longlong(x);
+    neg = b < 0;
+    const int e = static_cast<int>((b >> 52) & 0x7FF);
+    if (e == 0) return 0ull;
+    const unsigned long long m = (static_cast<unsigned long long>(b) & 0xFFFFFFFFFFFFFull) |
+                                 0x10000000000000ull;
+    const unsigned long long hi = __umul64hi(m << 11, me << 11);
+    const int sh = (42 + e - 1127 + Ee) + 62 - T;
+    if (sh >= 0) return hi << sh;
+    if (sh > -64) return (hi >> (-sh)) + ((hi >> (-sh - 1)) & 1ull);
+    return 0ull;
+}
+
+// The first SD balanced base-256 digits of a fixed-point magnitude u <= 2^61 (value u 2^-62 =
+// sum_s d_s 2^(-8 s) + what the dropped digits held, at most half a unit of the last digit):
+// 8-bit fields from the top (the eighth is the remaining 6 bits, scaled to weight 2^-64), made
+// balanced from the bottom up by borrowing 256 from a field above 128.  d_s in [-127, 128].
+template <int SD>
+__device__ __forceinline__ void digits_of(unsigned long long u, int (&d)[SD]) {
+    if constexpr (SD < 8) u += 1ull << (61 - 8 * SD);   // rounds the truncation to the nearest
+    int f[SD];
+#pragma unroll
+    for (int s = 1; s <= SD; ++s)
+        f[s - 1] = s < 8 ? static_cast<int>((u >> (62 - 8 * s)) & 255ull)
+                         : static_cast<int>((u & 63ull) << 2);
+    int c = 0;
+#pragma unroll
+    for (int s = SD; s >= 1; --s) {
+        const int v = f[s - 1] + c;
+        c = v > 128 ? 1 : 0;
+        d[s - 1] = c ? v - 256 : v;
+    }
+}
+
+// FP32 bit pattern of an integer |d| <= 2^22 (exact), through the binade [2^23, 2^24).
+__device__ __forceinline__ uint32_t f32bits_of_int(int d) {
+    return __float_as_uint(__int_as_float(0x4B400000 + d) - 12582912.0f);
+}
+
+// Two digits as a bf16x2 word (the upper halves of their FP32 patterns, d0 low), each negated
+// where its element is negative (bf16 sign bits).
+__device__ __forceinline__ uint32_t bf16x2_digits(int d0, int d1, bool neg0, bool neg1) {
+    const uint32_t w = __byte_perm(f32bits_of_int(d0), f32bits_of_int(d1), 0x7632);
+    return w ^ ((neg0 ? 0x8000u : 0u) | (neg1 ? 0x80000000u : 0u));
 }
 
 // q 2^E as a double (round to nearest on the integer pipe; q = 0 gives 0).
@@ -240,31 +297,6 @@ __device__ __forceinline__ double fixed_to_double(long long q, int E) {
     return __longlong_as_double(static_cast<long long>(
         sign | (static_cast<unsigned long long>(ex + 1023) << 52) | (m & 0xFFFFFFFFFFFFFull)));
 }
-
-// Digit s (1-based) of the balanced base-256 expansion of a 62-bit fixed-point value F (the
-// value F 2^-62 = sum_s d_s 2^(-8 s)): for s <= 7, d = round(F / 2^(62 - 8 s)) in [-128, 128] and
-// F keeps the remainder (|F| <= 2^(61 - 8 s)); digit 8 is what is left, scaled to weight 2^-64
-// (4 F, |4 F| <= 128), after which F is 0 and the expansion is exact.
-__device__ __forceinline__ int next_digit(long long& F, int s) {
-    const int shift = 62 - 8 * s;
-    if (shift <= 0) {
-        const long long d = F << (-shift);
-        F = 0;
-        return static_cast<int>(d);
-    }
-    const long long d = (F + (1ll << (shift - 1))) >> shift;
-    F -= d << shift;
-    return static_cast<int>(d);
-}
-
-// bf16 bit pattern of an integer |d| <= 256 (exact): through the FP32 binade [2^23, 2^24).
-__device__ __forceinline__ uint32_t bf16_of_int(int d) {
-    const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
-    return __float_as_uint(f) >> 16;
-}
-
-// Two bf16 patterns packed into one 32-bit word, lo in the low half.
-__device__ __forceinline__ uint32_t pack_bf16x2(uint32_t lo, uint32_t hi) { return lo | (hi << 16); }
 
 }  // namespace tc
 }  // namespace hfk
