@@ -401,6 +401,8 @@ size_t layout(hf_ctx& c, void* base) {
         c.tc.g0inv_rowT = cv.take<int>(static_cast<size_t>(ns) * 2 * L);
         c.tc.scratch = cv.take<double>(static_cast<size_t>(nc) * L * L);
         c.tc.fail = cv.take<int>(nc);
+        c.tc.fail_list = cv.take<int>(nc);
+        c.tc.fail_count = cv.take<int>(1);
         c.tc.products = cv.take<unsigned long long>(1);
     }
     return cv.off + 256;
@@ -535,8 +537,10 @@ hf_status launch_sweeps_f32(hf_ctx* c, int n_warmup, int n_measure, int refresh_
             if (c->tc_on) {
                 // Newton steps on the tensor cores from the sweep's FP32 state; a chain whose
                 // residual does not converge is refreshed by Gauss-Jordan right after
-                e = hfk::launch_refresh_tc(q, c->tc, c->stream);
-                if (e == cudaSuccess) e = hfk::launch_refresh_f64_only(q, c->tc.fail, c->stream);
+                e = cudaMemsetAsync(c->tc.fail_count, 0, sizeof(int), c->stream);
+                if (e == cudaSuccess) e = hfk::launch_refresh_tc(q, c->tc, c->stream);
+                if (e == cudaSuccess)
+                    e = hfk::launch_refresh_f64_listed(q, c->tc.fail_list, c->tc.fail_count, c->stream);
             } else {
                 e = hfk::launch_refresh_f64(q, c->stream);
             }

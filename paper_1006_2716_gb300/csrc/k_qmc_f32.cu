@@ -9,11 +9,14 @@
 // in shared memory), with g0^{-1} computed once per bath.  The refresh writes the FP64 G (used
 // for the measurement that follows a refresh) and its FP32 copy (the sweep state).  One block
 // of 256 threads per chain in both kernels.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 
 #include "hf_internal.cuh"
 #include "k_refresh_tc.cuh"
 #include "refresh_measure.cuh"
+#include "tc_ozaki.cuh"
 
 namespace hfk {
 namespace {
@@ -34,11 +37,25 @@ constexpr int kT32 = 256;   // threads per block
 // --------------------------------------------------------------------------------------------
 constexpr int kDK = 8;   // pending rank-1 updates per spin
 
+// L = 128: the flush G += U W runs on the tensor cores.  U and W^T are cut into three bf16 parts
+// each (exact: 8 + 8 + 8 bits of an FP32 significand), the six part products with s + t <= 4 are
+// accumulated in FP32 in TMEM (one 128 x 128 accumulator per spin; the dropped ones are below
+// 2^-24 of |U||W|), and the sums are added to G in shared memory.  Operands: K-major core
+// matrices, K = 16 (the 8 pending factors and 8 zeros).
+constexpr int kTcFlushL = 128;
+constexpr int kPartBytes = 128 * 16 * 2;   // one bf16 part of U or W^T: 128 rows x 16 K
+
+__host__ __device__ constexpr size_t flush_tc_bytes(int L) {
+    // parts[spin][U or W^T][3] + mbarrier + TMEM address
+    return L == kTcFlushL ? static_cast<size_t>(2 * 2 * 3) * kPartBytes + 16 : 0;
+}
+
 __host__ __device__ constexpr size_t sweep32_bytes(int L) {
     // G[2][L][L+1] f32, U[2][L][kDK] f32, W[2][kDK][L] f32, u[L] f32 (even count), bacc[2L+3] f64,
-    // red[32] f64, s[L] i8
-    return static_cast<size_t>(2 * L * (L + 1) + 4 * L * kDK + L + (L & 1)) * 4 +
-           static_cast<size_t>(2 * L + 3 + 32) * 8 + ((L + 15) / 16) * 16 + 16;
+    // red[32] f64, s[L] i8, then (L = 128) the tensor-core flush's operand parts
+    return (static_cast<size_t>(2 * L * (L + 1) + 4 * L * kDK + L + (L & 1)) * 4 +
+            static_cast<size_t>(2 * L + 3 + 32) * 8 + ((L + 15) / 16) * 16 + 16 + 1023) / 1024 * 1024 +
+           flush_tc_bytes(L);
 }
 
 template <int L>
@@ -136,6 +153,103 @@ __device__ __forceinline__ void flush32(float* G0, float* G1, const float* U0, c
     }
 }
 
+struct FlushTc {
+    unsigned char* parts;   // [spin][0: U, 1: W^T][3 parts] x kPartBytes, 1024-byte aligned
+    uint64_t* bar;
+    uint32_t* tmem;
+};
+
+// G_sigma += U_sigma W_sigma for the first m pending updates, on the tensor cores (L = 128).
+// ph: the mbarrier's phase, flipped here.  Returns false if the wait ran out.
+__device__ bool flush32_tc(float* G0, float* G1, const float* U0, const float* U1,
+                           const float* W0, const float* W1, int m, int tid, const FlushTc& F,
+                           uint32_t& ph) {
+    constexpr int L = kTcFlushL, LP = L + 1;
+    static_assert(kT32 == 2 * L, "one thread per (spin, row) of the operand parts");
+    // three bf16 parts of each pending factor, zero beyond the m pending ones; thread t cuts
+    // row t % 128 of U (t < 128: spin up) or of W^T (spin of t / 128 ... both spins each)
+    {
+        const int sp = tid >> 7, r = tid & 127;
+        const float* U = sp ? U1 : U0;
+        const float* W = sp ? W1 : W0;
+        float uv[kDK], wv[kDK];
+#pragma unroll
+        for (int p = 0; p < kDK; ++p) {
+            uv[p] = p < m ? U[r * kDK + p] : 0.0f;
+            wv[p] = p < m ? W[p * L + r] : 0.0f;
+        }
+        unsigned char* Ub = F.parts + (sp * 2 + 0) * 3 * kPartBytes;
+        unsigned char* Wb = F.parts + (sp * 2 + 1) * 3 * kPartBytes;
+        const int off = (r >> 3) * 256 + (r & 7) * 16;   // core (r / 8, 0), row r % 8
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            float* v = side ? wv : uv;
+            unsigned char* base = side ? Wb : Ub;
+            uint32_t w[3][4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float a0 = v[2 * q], a1 = v[2 * q + 1];
+                uint32_t lo[3], hi[3];
+#pragma unroll
+                for (int pt = 0; pt < 3; ++pt) {
+                    const __nv_bfloat16 b0 = __float2bfloat16_rn(a0), b1 = __float2bfloat16_rn(a1);
+                    lo[pt] = __bfloat16_as_ushort(b0);
+                    hi[pt] = __bfloat16_as_ushort(b1);
+                    a0 -= __bfloat162float(b0);
+                    a1 -= __bfloat162float(b1);
+                }
+#pragma unroll
+                for (int pt = 0; pt < 3; ++pt) w[pt][q] = lo[pt] | (hi[pt] << 16);
+            }
+#pragma unroll
+            for (int pt = 0; pt < 3; ++pt)
+                *reinterpret_cast<uint4*>(base + pt * kPartBytes + off) =
+                    make_uint4(w[pt][0], w[pt][1], w[pt][2], w[pt][3]);
+        }
+    }
+    tc::fence_async_shared();
+    tc::tc_fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+        tc::tc_fence_after_sync();
+        constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 128);
+        constexpr int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 2, 1, 0};
+#pragma unroll
+        for (int sp = 0; sp < 2; ++sp) {
+            const uint32_t ua = tc::smem_addr(F.parts + (sp * 2 + 0) * 3 * kPartBytes);
+            const uint32_t wa = tc::smem_addr(F.parts + (sp * 2 + 1) * 3 * kPartBytes);
+#pragma unroll
+            for (int k = 0; k < 6; ++k)
+                tc::mma_bf16(*F.tmem + sp * 128, tc::smem_desc(ua + pa[k] * kPartBytes, 128, 256),
+                             tc::smem_desc(wa + pb[k] * kPartBytes, 128, 256), idesc, k > 0);
+        }
+        tc::mma_commit(F.bar);
+    }
+    const bool ok = __syncthreads_and(tc::mbar_wait(F.bar, ph));
+    ph ^= 1u;
+    if (!ok) return false;
+    tc::tc_fence_after_sync();
+    {
+        const int w = tid >> 5, lane = tid & 31;
+        const int i = 32 * (w & 3) + lane, cg = w >> 2;
+        const uint32_t trow = *F.tmem + (static_cast<uint32_t>(32 * (w & 3)) << 16);
+#pragma unroll
+        for (int sp = 0; sp < 2; ++sp) {
+            float* G = sp ? G1 : G0;
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                const int j0 = 64 * cg + 16 * g;
+                float v[16];
+                tc::tmem_ld16(trow + sp * 128 + j0, v);
+#pragma unroll
+                for (int k = 0; k < 16; ++k) G[i * LP + j0 + k] += v[k];
+            }
+        }
+    }
+    tc::tc_fence_before_sync();
+    return true;
+}
+
 template <int L>
 __device__ void sweep32_chain(const QmcProblem& P, int c, unsigned char* base) {
     constexpr int LL = L * L;
@@ -153,6 +267,25 @@ __device__ void sweep32_chain(const QmcProblem& P, int c, unsigned char* base) {
     double* bacc = reinterpret_cast<double*>(u + L + (L & 1));
     double* red = bacc + W;
     int8_t* s = reinterpret_cast<int8_t*>(red + 32);
+    FlushTc ft{};
+    uint32_t fph = 0u;
+    bool tc_ok = true;
+    if constexpr (L == kTcFlushL) {
+        ft.parts = base + (sweep32_bytes(L) - flush_tc_bytes(L));
+        ft.bar = reinterpret_cast<uint64_t*>(ft.parts + 2 * 2 * 3 * kPartBytes);
+        ft.tmem = reinterpret_cast<uint32_t*>(ft.bar + 1);
+        // the K padding (pending factors 8..15) stays zero: clear every part once
+        for (int e = tid; e < 2 * 2 * 3 * kPartBytes / 16; e += kT32)
+            reinterpret_cast<uint4*>(ft.parts)[e] = make_uint4(0u, 0u, 0u, 0u);
+        if (tid == 0) {
+            tc::mbar_init(ft.bar, 1);
+            tc::mbar_init_fence();
+        }
+        if (tid < 32) tc::tmem_alloc(ft.tmem, 256);
+        tc::tc_fence_before_sync();
+        __syncthreads();
+        tc::tc_fence_after_sync();
+    }
 
     const int site = c / P.cps;
     const int ch = c - site * P.cps;
@@ -221,13 +354,17 @@ __device__ void sweep32_chain(const QmcProblem& P, int c, unsigned char* base) {
                 if (tid == 0) s[l] = static_cast<int8_t>(-sl);
                 ++acc;
                 if (++m == kDK) {
-                    flush32<L>(G0, G1, U0, U1, W0, W1, m, tid);
+                    if constexpr (L == kTcFlushL) tc_ok = tc_ok && flush32_tc(G0, G1, U0, U1, W0, W1, m, tid, ft, fph);
+                    else flush32<L>(G0, G1, U0, U1, W0, W1, m, tid);
                     m = 0;
                     __syncthreads();
                 }
             }
         }
-        if (m > 0) flush32<L>(G0, G1, U0, U1, W0, W1, m, tid);
+        if (m > 0) {
+            if constexpr (L == kTcFlushL) tc_ok = tc_ok && flush32_tc(G0, G1, U0, U1, W0, W1, m, tid, ft, fph);
+            else flush32<L>(G0, G1, U0, U1, W0, W1, m, tid);
+        }
         ++nsw;
         __syncthreads();
         if (k >= P.meas_from && k < P.meas_to) {
@@ -258,10 +395,16 @@ __device__ void sweep32_chain(const QmcProblem& P, int c, unsigned char* base) {
         P.nmeas[c] = nmeas;
         P.acc[c] += acc;
     }
+    if constexpr (L == kTcFlushL) {
+        __syncthreads();
+        tc::tc_fence_after_sync();
+        if (tid < 32) tc::tmem_dealloc(*ft.tmem, 256);
+        if (!tc_ok && tid == 0) atomicExch(P.status, static_cast<int>(HF_ETIMEOUT));
+    }
 }
 
 __global__ void __launch_bounds__(kT32) qmc_f32_kernel(const __grid_constant__ QmcBatch B) {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(1024) unsigned char smem[];
     int pi = 0;
     while (pi + 1 < B.nprob && static_cast<int>(blockIdx.x) >= B.p[pi + 1].block0) ++pi;
     const QmcProblem& P = B.p[pi];
@@ -453,12 +596,9 @@ __device__ bool refresh_chain(const QmcProblem& P, int c, unsigned char* smem) {
     return ok;
 }
 
-__global__ void __launch_bounds__(kT32) refresh_f64_kernel(const QmcProblem P, const int* only) {
-    extern __shared__ __align__(16) unsigned char smem[];
+// Refresh (and, with refresh_measure, measure) chain c.
+__device__ void refresh_one(const QmcProblem& P, int c, unsigned char* smem) {
     const int L = P.L;
-    const int c = blockIdx.x;
-    if (c >= P.nchain) return;
-    if (only && only[c] == 0) return;   // the tensor-core refresh already handled this chain
     const int tid = threadIdx.x;
     const int LL = L * L;
     bool ok = true;
@@ -476,6 +616,22 @@ __global__ void __launch_bounds__(kT32) refresh_f64_kernel(const QmcProblem P, c
     __threadfence_block();
     __syncthreads();
     measure_refreshed<kT32>(P, c, red);
+}
+
+// every chain (list == nullptr: one CTA per chain) or the listed ones (a wave of CTAs that take
+// list[k], k = blockIdx.x, blockIdx.x + gridDim.x, ... < *count)
+__global__ void __launch_bounds__(kT32) refresh_f64_kernel(const QmcProblem P, const int* list,
+                                                           const int* count) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    if (!list) {
+        if (static_cast<int>(blockIdx.x) < P.nchain) refresh_one(P, blockIdx.x, smem);
+        return;
+    }
+    const int n = *count;
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        refresh_one(P, list[k], smem);
+        __syncthreads();   // the next chain reuses the shared memory
+    }
 }
 
 }  // namespace
@@ -500,17 +656,22 @@ cudaError_t launch_refresh_f64(const QmcProblem& p, cudaStream_t st) {
                                          static_cast<int>(refresh_bytes(128)));
     if (e != cudaSuccess) return e;
     if (p.nchain <= 0) return cudaSuccess;
-    refresh_f64_kernel<<<p.nchain, kT32, smem, st>>>(p, nullptr);
+    refresh_f64_kernel<<<p.nchain, kT32, smem, st>>>(p, nullptr, nullptr);
     return cudaGetLastError();
 }
 
-cudaError_t launch_refresh_f64_only(const QmcProblem& p, const int* only, cudaStream_t st) {
+cudaError_t launch_refresh_f64_listed(const QmcProblem& p, const int* list, const int* count,
+                                      cudaStream_t st) {
     const size_t smem = refresh_bytes(p.L);
     cudaError_t e = cudaFuncSetAttribute(refresh_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(refresh_bytes(128)));
     if (e != cudaSuccess) return e;
     if (p.nchain <= 0) return cudaSuccess;
-    refresh_f64_kernel<<<p.nchain, kT32, smem, st>>>(p, only);
+    int dev = 0, sms = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    refresh_f64_kernel<<<std::min(p.nchain, sms), kT32, smem, st>>>(p, list, count);
     return cudaGetLastError();
 }
 

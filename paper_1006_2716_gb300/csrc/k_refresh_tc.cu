@@ -26,7 +26,7 @@
 // If the Newton residual does not fall below 2^-24 within two full steps (an FP32 state too far
 // from the inverse), or the operands' scales are too large for the residual's accuracy (a badly
 // conditioned G) or leave the fixed-point range, the chain is flagged and refreshed by the Gauss-Jordan
-// kernel instead (launch_refresh_f64_only); its outputs here are not written.
+// kernel instead (launch_refresh_f64_listed); its outputs here are not written.
 #include <algorithm>
 
 #include "k_refresh_tc.cuh"
@@ -578,7 +578,10 @@ refresh_tc_kernel(const QmcProblem P, const TcRefreshArgs A) {
     const int site = c / P.cps;
     // after a timeout anywhere in this context, leave every chain to the Gauss-Jordan refresh
     if (*reinterpret_cast<volatile const int*>(P.status) == static_cast<int>(HF_ETIMEOUT)) {
-        if (tid == 0) A.fail[c] = 1;
+        if (tid == 0) {
+            A.fail[c] = 1;
+            A.fail_list[atomicAdd(A.fail_count, 1)] = c;
+        }
         return;
     }
     if (tid == 0) {
@@ -630,12 +633,14 @@ refresh_tc_kernel(const QmcProblem P, const TcRefreshArgs A) {
         if (tid == 0) {
             atomicExch(P.status, static_cast<int>(HF_ETIMEOUT));
             A.fail[c] = 1;
+            A.fail_list[atomicAdd(A.fail_count, 1)] = c;
         }
         return;
     }
     if (S.flag) {
         if (tid == 0) {
             A.fail[c] = 1;
+            A.fail_list[atomicAdd(A.fail_count, 1)] = c;
             atomicAdd(reinterpret_cast<unsigned int*>(P.status + 7), 1u);
         }
         return;
