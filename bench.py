@@ -638,11 +638,16 @@ def run_ours(args):
 
 
 def lattice_launches(hf, cfg):
-    """Lattice-step launches of one iteration: the nspin x nw matrices in chunks of as many band
-    buffers as fit in 1 GiB (at most 2 nw)."""
+    """Lattice-step launches of one iteration, as the library plans them: the nspin x nw
+    matrices in chunks of as many band buffers as fit in 1 GiB (at most 2 nw), one launch each;
+    in the blocked band form (band half-width above 165, or lattice_form 1) as many as fit in
+    8 GiB, split evenly, two launches each (factorisation, forward solves)."""
     N, _, b, nspin, _, _, _ = hf.hf_lattice_info(hf.make_params(cfg))
     nw = cfg["n_matsubara"]
-    batch = max(1, min(2 * nw, (1 << 30) // (N * (b + 1) * 16)))
+    per = N * (b + 1) * 16
+    if b > 165 or cfg.get("lattice_form", 0) == 1:
+        return 2 * -(-nspin * nw // max(1, (8 << 30) // per))
+    batch = max(1, min(2 * nw, (1 << 30) // per))
     return -(-nspin * nw // batch)
 
 
@@ -743,7 +748,7 @@ def cpu_oracle_3d(name, n_chains_total, chains_per_core=8, freqs_per_core=1):
 
 
 def run_lattice3d(args):
-    """Three-dimensional workloads (slab16, box12): whole RDMFT iterations with the FP32-pair
+    """Three-dimensional workloads (slab16, box12, box14p, box16p): whole RDMFT iterations with the FP32-pair
     sweeps, reported with the rooflines of both the impurity sweeps and the lattice step, which
     in three dimensions is no longer small."""
     import torch
@@ -789,12 +794,17 @@ def run_lattice3d(args):
     qroof = qmc_roofline(2, L, nc, sweeps, accepts, cfg["n_measure"], n_refresh,
                          statistics.mean(qmc_ms) / 1e3, "qmc_df64_kernel")
     qroof["acceptance"] = accepts / proposals
-    fl = lattice_flops(N, b, nspin, nw)
+    lform, lat_launches, cfma = hf.hf_get_lattice_plan(ctx.handle)
+    fl = 8.0 * cfma * nspin * nw
     lat_s = phase[0] / 1e3
+    lkern = "lattice_factor_kernel + lattice_solve_kernel" if lform == 1 else "lattice_kernel"
     lroof = {"bound": "alu", "achieved": fl / lat_s / 1e12, "peak": FP64_PEAK_TFLOPS,
              "unit": "TFLOP/s", "frac": fl / lat_s / 1e12 / FP64_PEAK_TFLOPS,
              "traffic": measured_traffic("lattice_kernel:" + name),
-             "kernel": "lattice_kernel", "matrices": nspin * nw, "N": N, "band": b,
+             "kernel": lkern, "matrices": nspin * nw, "N": N, "band": b,
+             "form": "blocked band L D L^T + forward solves" if lform == 1
+             else "band L D L^T + selected inversion in a shared-memory window",
+             "seconds": lat_s,
              "peak_source": "FP64 nominal: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz"}
     dominant = lroof if phase[0] > phase[2] else qroof
     geo = ("%dx%d slab of %d layers, periodic in all directions, cylindrical trap" % (cfg["Lx"], cfg["Ly"], cfg["Lz"])
@@ -1465,7 +1475,7 @@ def main():
                          "refresh); -1 (default): FP64 with the autotuned team width")
     ap.add_argument("--workload", default="square20",
                     choices=["square20", "scan20", "square30", "disc40", "dtau_scan", "slab16",
-                             "box12", "entropy6", "fig1"])
+                             "box12", "box14p", "box16p", "entropy6", "fig1"])
     ap.add_argument("--refresh-stagger", type=int, default=0, choices=[0, 1],
                     help="1: per-chain refresh phases; 0 (default): every chain refreshes on the "
                          "same sweeps")
@@ -1493,7 +1503,7 @@ def main():
         return run_fig1(args)
     if args.workload == "entropy6":
         return run_entropy6(args)
-    if args.workload in ("slab16", "box12"):
+    if args.workload in ("slab16", "box12", "box14p", "box16p"):
         return run_lattice3d(args)
     if args.workload == "dtau_scan":
         return run_dtau_scan(args)

@@ -79,6 +79,11 @@ typedef struct hf_params {
                          /* two Newton steps on the tensor cores (products formed exactly     */
                          /* from bf16 digits), falling back to Gauss-Jordan for a chain whose */
                          /* residual does not converge; 1 always uses FP64 Gauss-Jordan       */
+    int lattice_form;    /* lattice step (eq. 2): 0 (default) picks by band half-width b: up   */
+                         /* to 165 the band L D L^T and selected inversion in a shared-memory */
+                         /* window, above it (up to 840) the blocked band L D L^T in global   */
+                         /* memory with G_ii from forward solves L^{-1} e_i at one site per    */
+                         /* orbit and spin; 1 always takes the blocked band form              */
     int delay_k;         /* delayed-update depth: 0/1 rank-1 Sherman-Morrison; 4, 8, 16, 32  */
                          /* (precision 2, one warp per chain): accepted flips gathered as    */
                          /* rank-k corrections                                              */
@@ -112,8 +117,8 @@ hf_status hf_lattice_info(const hf_params* p, int* N, int* n_sites, int* band, i
  * initial Ising fields of every chain and seed Sigma_{i,sigma}(i w_n) = U/2 - sigma h_seed
  * eps_i.  *out receives a host handle released by hf_free.  HF_EINVAL for invalid parameters,
  * including a lattice whose band half-width in the lattice step's band order (periodic axes
- * folded) exceeds 165, the largest window the step keeps in shared memory; HF_ENOMEM for a
- * workspace smaller than hf_workspace_size. */
+ * folded) exceeds 840, the widest band the blocked band form keeps buffers for; HF_ENOMEM for
+ * a workspace smaller than hf_workspace_size. */
 hf_status hf_init(const hf_params* p, void* d_ws, size_t ws_bytes, hf_ctx** out);
 
 /* Number of inequivalent sites, chains, L, lattice sites N (any pointer may be NULL). */
@@ -195,6 +200,14 @@ hf_status hf_get_accepts(hf_ctx* ctx, unsigned long long* accepts);
  * number of chain refreshes checked.  The refresh at the start of a launch is not checked (the
  * bath may have changed).  Either pointer may be NULL.  Synchronises. */
 hf_status hf_get_drift(hf_ctx* ctx, double* max_drift, unsigned long long* refreshes);
+
+/* The lattice step of this context (eq. 2; host only): *form 0 = band L D L^T with selected
+ * inversion in a shared-memory window (every diagonal element), 1 = blocked band L D L^T in
+ * global memory with forward solves L^{-1} e_k at the listed positions (see lattice_form);
+ * *launches = kernel launches per lattice step; *cfma = complex multiply-adds that the form's
+ * algorithm performs per (w_n, sigma) matrix (factorisation plus selected inversion, or plus
+ * the forward solves), averaged over the spin matrices.  Any pointer may be NULL. */
+hf_status hf_get_lattice_plan(const hf_ctx* ctx, int* form, int* launches, double* cfma);
 
 /* Refreshes of the mixed-precision form at L = 128 since the last hf_clear_measurements: chains
  * refreshed by the Newton steps on the tensor cores; chains those steps handed to the FP64

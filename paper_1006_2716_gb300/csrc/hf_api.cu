@@ -241,6 +241,9 @@ struct hf_ctx {
     cudaStream_t stream = nullptr;
     int device = 0;                 // device current at hf_init (the workspace's device)
     int lat_batch = 0;              // matrices per lattice-step launch
+    bool lat_wide = false;          // lattice step in the blocked band form
+    int wide_npos = 0;              // its listed positions per spin matrix
+    std::vector<int> wide_pos_host; // [nspin][wide_npos] host copy of wide_pos
     uint32_t nmeas = 0;             // measured sweeps since the last clear (all chains)
     uint32_t nsw_host = 0;          // sweep counter shared by all chains (FP32 path)
     std::string err;
@@ -271,6 +274,8 @@ struct hf_ctx {
     int* site_rep = nullptr;        // [N]
     int* site_dn = nullptr;         // [N]
     double2* lat_scratch = nullptr; // [lat_batch][N][b+1]
+    int* wide_pos = nullptr;        // [nspin][wide_npos] blocked band form: positions to solve for
+    int* wide_out = nullptr;        // [nspin][wide_npos] and the gloc row each one fills
     // tensor-core refresh of the mixed-precision form (precision 1, L = 128, refresh_gj = 0)
     bool tc_on = false;
     hfk::TcRefreshArgs tc{};
@@ -349,6 +354,7 @@ hf_status validate(const hf_params& p, std::string& err) {
         return HF_EINVAL;
     }
     if (!(p.check_drift == 0 || p.check_drift == 1)) { err = "check_drift must be 0 or 1"; return HF_EINVAL; }
+    if (!(p.lattice_form == 0 || p.lattice_form == 1)) { err = "lattice_form must be 0 or 1"; return HF_EINVAL; }
     if (!(p.refresh_stagger == 0 || p.refresh_stagger == 1) ||
         (p.refresh_stagger == 1 && p.precision == 1 && p.refresh_every > 1)) {
         err = "refresh_stagger must be 0 or 1; staggered phases need fused refreshes (precision 0 "
@@ -395,6 +401,8 @@ size_t layout(hf_ctx& c, void* base) {
     c.site_rep = cv.take<int>(N);
     c.site_dn = cv.take<int>(N);
     c.lat_scratch = cv.take<double2>(static_cast<size_t>(c.lat_batch) * N * bw);
+    c.wide_pos = cv.take<int>(static_cast<size_t>(4) * ns);
+    c.wide_out = cv.take<int>(static_cast<size_t>(4) * ns);
     c.tc_on = c.p.precision == 1 && L == hfk::kTcL && c.p.refresh_gj == 0;
     if (c.tc_on) {
         c.tc.g0inv_digits = cv.take<uint16_t>(hfk::tc_digits_bytes(ns) / 2);
@@ -418,16 +426,26 @@ hf_status setup_sizes(hf_ctx& c, const hf_params* p) {
     if (!hfk::lattice_band_supported(c.lat.b))
         return fail(nullptr, HF_EINVAL,
                     "the lattice's band half-width " + std::to_string(c.lat.b) +
-                        " exceeds the lattice step's shared-memory window (largest: " +
+                        " exceeds the lattice step's band buffers (largest: " +
                         std::to_string(hfk::lattice_max_band()) + ")");
+    c.lat_wide = p->lattice_form == 1 || !hfk::lattice_window_supported(c.lat.b);
     c.L = static_cast<int>(std::lround(p->beta / p->dtau));
     c.nsite = static_cast<int>(c.lat.rep.size());
     c.nchain = c.nsite * p->chains_per_site;
     c.nw = p->n_matsubara;
     // lattice step: as many (w_n, sigma) matrices per launch as fit in 1 GiB of band buffers
+    // (blocked band form: 8 GiB, split evenly over the launches, so that each launch still fills
+    // the GPU with one matrix per SM)
     const size_t per = hfk::lattice_scratch_per_matrix(c.lat.N, c.lat.b);
-    const size_t cap = (static_cast<size_t>(1) << 30) / (per ? per : 1);
-    c.lat_batch = static_cast<int>(std::max<size_t>(1, std::min<size_t>(2 * c.nw, cap)));
+    const int nq = (c.lat.gdn.empty() ? 2 : 1) * c.nw;
+    if (c.lat_wide) {
+        const size_t cap = std::max<size_t>(1, (static_cast<size_t>(8) << 30) / (per ? per : 1));
+        const size_t nl = (static_cast<size_t>(nq) + cap - 1) / cap;
+        c.lat_batch = static_cast<int>((static_cast<size_t>(nq) + nl - 1) / nl);
+    } else {
+        const size_t cap = (static_cast<size_t>(1) << 30) / (per ? per : 1);
+        c.lat_batch = static_cast<int>(std::max<size_t>(1, std::min<size_t>(2 * c.nw, cap)));
+    }
     return HF_OK;
 }
 
@@ -589,6 +607,10 @@ hfk::LatticeArgs lattice_args(const hf_ctx& c) {
     la.gloc = c.gloc;
     la.scratch = c.lat_scratch;
     la.status = c.status;
+    la.wide = c.lat_wide ? 1 : 0;
+    la.wide_npos = c.wide_npos;
+    la.wide_pos = c.wide_pos;
+    la.wide_out = c.wide_out;
     return la;
 }
 
@@ -707,6 +729,39 @@ hf_status hf_init(const hf_params* p, void* d_ws, size_t ws_bytes, hf_ctx** out)
     }
     if (!lat.gdn.empty())
         for (int r = 0; r < ns; ++r) site_dn_k[lat.pos[lat.gdn[lat.rep[r]]]] = r;
+    // blocked band form: the band position whose G_kk fills each output (r, slot).  In the
+    // matrix of spin sp the site at position k carries G of orbit rep_of_k[k] and spin
+    // sp ^ flip_k[k], the same at every such site (the symmetries mapping one onto another keep
+    // the matrix), so the member with the largest position is taken: its forward solve is the
+    // shortest.  Both spins inverted: matrix sp fills slot sp; spin-halved: the spin-up matrix
+    // fills both slots, slot 1 from the members on the other sublattice.
+    const int nspin = lat.gdn.empty() ? 2 : 1;
+    c->wide_npos = ns * (3 - nspin);
+    std::vector<int> wpos, wout;
+    for (int sp = 0; sp < nspin; ++sp) {
+        std::vector<int> best(static_cast<size_t>(ns) * 2, -1);
+        for (int k = 0; k < N; ++k) {
+            const int slot = sp ^ flip_k[k];
+            if (nspin == 2 && slot != sp) continue;
+            best[static_cast<size_t>(rep_of_k[k]) * 2 + slot] = k;   // ascending k: the largest wins
+        }
+        std::vector<std::pair<int, int>> lst;
+        for (int r = 0; r < ns; ++r)
+            for (int slot = 0; slot < 2; ++slot) {
+                if (nspin == 2 && slot != sp) continue;
+                const int k = best[static_cast<size_t>(r) * 2 + slot];
+                if (k < 0) {
+                    delete c;
+                    return fail(nullptr, HF_EINVAL, "internal: an orbit has no site for a spin slot");
+                }
+                lst.emplace_back(k, r * 2 + slot);
+            }
+        std::sort(lst.begin(), lst.end());
+        for (const auto& pr : lst) {
+            wpos.push_back(pr.first);
+            wout.push_back(pr.second);
+        }
+    }
     std::vector<double> c23(static_cast<size_t>(ns) * 2);
     std::vector<double2> sig(static_cast<size_t>(ns) * 2 * nw);
     for (int i = 0; i < ns; ++i) {
@@ -729,6 +784,9 @@ hf_status hf_init(const hf_params* p, void* d_ws, size_t ws_bytes, hf_ctx** out)
     if (e == cudaSuccess) e = up(c->flip, flip_k.data(), N * sizeof(int));
     if (e == cudaSuccess) e = up(c->site_rep, site_rep_k.data(), N * sizeof(int));
     if (e == cudaSuccess) e = up(c->site_dn, site_dn_k.data(), N * sizeof(int));
+    c->wide_pos_host = wpos;
+    if (e == cudaSuccess) e = up(c->wide_pos, wpos.data(), wpos.size() * sizeof(int));
+    if (e == cudaSuccess) e = up(c->wide_out, wout.data(), wout.size() * sizeof(int));
     if (e == cudaSuccess) e = up(c->c23, c23.data(), c23.size() * sizeof(double));
     if (e == cudaSuccess) e = up(c->sigma, sig.data(), sig.size() * sizeof(double2));
     if (e == cudaSuccess) e = cudaMemsetAsync(c->gtau, 0, sizeof(double) * ns * 2 * c->L, st0);
@@ -752,6 +810,35 @@ hf_status hf_init(const hf_params* p, void* d_ws, size_t ws_bytes, hf_ctx** out)
         return fail(nullptr, HF_ECUDA, m);
     }
     *out = c;
+    return HF_OK;
+}
+
+hf_status hf_get_lattice_plan(const hf_ctx* c, int* form, int* launches, double* cfma) {
+    if (!c) return fail(nullptr, HF_EINVAL, "null context");
+    const int N = c->lat.N, b = c->lat.b;
+    const int nspin = c->lat.gdn.empty() ? 2 : 1;
+    const int nq = nspin * c->nw;
+    const int nl = (nq + c->lat_batch - 1) / c->lat_batch;
+    double f = 0.0;   // factorisation: d (d + 1) / 2 at column k, d = min(b, N - 1 - k)
+    for (int k = 0; k < N; ++k) {
+        const double d = std::min(b, N - 1 - k);
+        f += d * (d + 1) / 2;
+    }
+    if (c->lat_wide) {   // forward solves from each listed position p: min(b, N - 1 - j), j >= p
+        std::vector<double> tail(static_cast<size_t>(N) + 1, 0.0);
+        for (int j = N - 1; j >= 0; --j) tail[j] = tail[j + 1] + std::min(b, N - 1 - j);
+        double sv = 0.0;
+        for (int p : c->wide_pos_host) sv += tail[p];
+        f += sv / nspin;
+    } else {             // selected inversion: d^2 + d at column k
+        for (int k = 0; k < N; ++k) {
+            const double d = std::min(b, N - 1 - k);
+            f += d * d + d;
+        }
+    }
+    if (form) *form = c->lat_wide ? 1 : 0;
+    if (launches) *launches = nl * (c->lat_wide ? 2 : 1);
+    if (cfma) *cfma = f;
     return HF_OK;
 }
 

@@ -34,51 +34,12 @@
 #include "hf_internal.cuh"
 
 #include "k_lattice.cuh"
+#include "k_lattice_dev.cuh"
 
 namespace hfk {
 namespace {
 
 constexpr int kNarrowBand = 32;
-
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ double2 cfms(double2 acc, double2 a, double2 b) {  // acc - a b
-    return make_double2(fma(-a.x, b.x, fma(a.y, b.y, acc.x)),
-                        fma(-a.x, b.y, fma(-a.y, b.x, acc.y)));
-}
-__device__ __forceinline__ double2 crecip(double2 a) {
-    const double d = a.x * a.x + a.y * a.y;
-    return make_double2(a.x / d, -a.y / d);
-}
-__device__ __forceinline__ double2 shfl_xor_c(double2 v, int o) {
-    return make_double2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
-}
-
-// Matrix q of the launch: spin and Matsubara index.
-__device__ __forceinline__ void item_of(const LatticeArgs& A, int q, int& sp, int& n) {
-    sp = q / A.nw;
-    n = q - sp * A.nw;
-}
-
-// Diagonal element of M at band position k.
-__device__ __forceinline__ double2 m_diag(const LatticeArgs& A, int k, int sp, int n, double wn) {
-    const int bw = A.b + 1;
-    const int r = A.rep_of[k];
-    const int s2 = sp ^ A.flip[k];
-    const double2 sg = A.sigma[(static_cast<size_t>(r) * 2 + s2) * A.nw + n];
-    return make_double2(A.mu - A.h0band[static_cast<size_t>(k) * bw] - sg.x, wn - sg.y);
-}
-
-// Writes the diagonal G_kk of the matrix to the outputs that take it.
-__device__ __forceinline__ void store_diag(const LatticeArgs& A, int k, int sp, int n, double2 z) {
-    const int r = A.site_rep[k];
-    if (r >= 0) A.gloc[(static_cast<size_t>(r) * 2 + sp) * A.nw + n] = z;
-    if (A.site_dn) {
-        const int r2 = A.site_dn[k];
-        if (r2 >= 0) A.gloc[(static_cast<size_t>(r2) * 2 + 1) * A.nw + n] = z;
-    }
-}
 
 // Packed symmetric window: the entry of slots (a, c) lives at tri(max, min).
 __device__ __forceinline__ int wtri(int a, int c) {
@@ -272,15 +233,19 @@ int block_threads(int b) {       // two threads per row of the window
 
 }  // namespace
 
-bool lattice_band_supported(int b) {
+bool lattice_window_supported(int b) {
     return b >= 0 && window_bytes(b) <= static_cast<size_t>(227) * 1024;
 }
 
-int lattice_max_band() {
+int lattice_window_max_band() {
     int b = 0;
-    while (lattice_band_supported(b + 1)) ++b;
+    while (lattice_window_supported(b + 1)) ++b;
     return b;
 }
+
+bool lattice_band_supported(int b) { return b >= 0 && b <= lattice_max_band(); }
+
+int lattice_max_band() { return std::max(lattice_window_max_band(), lattice_wide_max_band()); }
 
 size_t lattice_scratch_per_matrix(int N, int b) {
     return static_cast<size_t>(N) * (b + 1) * sizeof(double2);
@@ -288,7 +253,7 @@ size_t lattice_scratch_per_matrix(int N, int b) {
 
 cudaError_t launch_lattice(const LatticeArgs& a, int q0, int nq, cudaStream_t st) {
     if (nq <= 0) return cudaSuccess;
-    if (!lattice_band_supported(a.b)) return cudaErrorInvalidValue;
+    if (a.wide || !lattice_window_supported(a.b)) return launch_lattice_wide(a, q0, nq, st);
     const size_t smem = window_bytes(a.b);
     if (a.b > kNarrowBand) {
         cudaError_t e = cudaFuncSetAttribute(lattice_kernel<true>,

@@ -19,12 +19,26 @@ struct LatticeArgs {
     double2* gloc;            // [nsite][2][nw] output G_ii of the representatives
     double2* scratch;         // [nq][N][b+1] band factors of the matrices in flight (q = sigma nw + n)
     int* status;
+    // blocked band form (k_lattice_wide.cu): G_kk only at listed band positions, one per output
+    int wide;                 // 1: blocked band form for this lattice (always above the window)
+    int wide_npos;            // listed positions per spin matrix
+    const int* wide_pos;      // [nspin][wide_npos] band positions to solve for, ascending
+    const int* wide_out;      // [nspin][wide_npos] row r * 2 + slot of gloc that each one fills
 };
 
+// Shared-memory window form (k_lattice.cu): a (b+1)(b+2)/2-entry window per matrix.
+bool lattice_window_supported(int b);
+int lattice_window_max_band();
+// Either form: the window form up to its largest band unless a.wide, the blocked band form above.
 bool lattice_band_supported(int b);
 int lattice_max_band();
 size_t lattice_scratch_per_matrix(int N, int b);
 cudaError_t launch_lattice(const LatticeArgs& a, int q0, int nq, cudaStream_t st);
+
+// Blocked band form (k_lattice_wide.cu), every b <= lattice_wide_max_band().
+int lattice_wide_max_band();
+int lattice_wide_rhs_per_block();
+cudaError_t launch_lattice_wide(const LatticeArgs& a, int q0, int nq, cudaStream_t st);
 
 // Lattice step over all nspin * nw matrices with the band buffers in a fixed 16 MiB device array
 // (a.scratch is ignored); rejects a lattice whose single band does not fit.

@@ -31,7 +31,7 @@ class hf_params(C.Structure):
         ("beta", C.c_double), ("dtau", C.c_double),
         ("n_matsubara", C.c_int), ("chains_per_site", C.c_int), ("precision", C.c_int),
         ("refresh_every", C.c_int), ("refresh_stagger", C.c_int), ("check_drift", C.c_int),
-        ("refresh_gj", C.c_int),
+        ("refresh_gj", C.c_int), ("lattice_form", C.c_int),
         ("delay_k", C.c_int),
         ("team_warps", C.c_int),
         ("bin_size", C.c_int),
@@ -106,6 +106,7 @@ SIGNATURES = [
     ("hf_get_refresh_stats", C.c_int, [_VP, C.POINTER(C.c_ulonglong), C.POINTER(C.c_ulonglong),
                                         C.POINTER(C.c_ulonglong)]),
     ("hf_lattice_step_noalloc", C.c_int, [_VP, _VP, _VP]),
+    ("hf_get_lattice_plan", C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int), _DP]),
     ("hf_philox_blocks", C.c_int, [C.c_uint32, C.c_uint32, _VP, C.c_int, _VP, _VP]),
     ("hf_tc_dgemm128", C.c_int, [_VP, _VP, _VP, C.c_int, C.c_int, _VP, _VP]),
     ("hf_batch_create", C.c_int, [C.POINTER(_VP), C.c_int, C.c_int, C.POINTER(_VP)]),
@@ -297,6 +298,13 @@ def hf_get_drift(ctx):
     n = C.c_ulonglong()
     _check(lib().hf_get_drift(ctx, C.byref(m), C.byref(n)), ctx)
     return m.value, n.value
+
+
+def hf_get_lattice_plan(ctx):
+    """(form, kernel launches per lattice step, complex multiply-adds per (w_n, sigma) matrix)."""
+    f, n, w = C.c_int(), C.c_int(), C.c_double()
+    _check(lib().hf_get_lattice_plan(ctx, C.byref(f), C.byref(n), C.byref(w)), ctx)
+    return f.value, n.value, w.value
 
 
 def hf_get_refresh_stats(ctx):
@@ -494,6 +502,7 @@ def make_params(cfg: dict, stream=None, **over) -> hf_params:
     p.refresh_stagger = int(d.get("refresh_stagger", 0))
     p.check_drift = int(d.get("check_drift", 0))
     p.refresh_gj = int(d.get("refresh_gj", 0))
+    p.lattice_form = int(d.get("lattice_form", 0))
     p.delay_k = int(d.get("delay_k", 1))
     p.team_warps = int(d.get("team_warps", 0))
     p.bin_size = int(d.get("bin_size", 100))

@@ -27,7 +27,7 @@ from . import workloads as wl
 _KEYS = {"Lx": int, "Ly": int, "Lz": int, "geometry": int, "periodic": int, "t": float,
          "U": float, "V0": float, "mu": float, "beta": float, "dtau": float,
          "n_matsubara": int, "chains_per_site": int, "precision": int, "refresh_every": int,
-         "refresh_stagger": int, "check_drift": int, "refresh_gj": int, "delay_k": int, "team_warps": int,
+         "refresh_stagger": int, "check_drift": int, "refresh_gj": int, "lattice_form": int, "delay_k": int, "team_warps": int,
          "bin_size": int, "max_bins": int, "n_warmup": int, "n_measure": int, "seed": int,
          "h_seed": float, "mix": float}
 

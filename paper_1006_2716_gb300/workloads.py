@@ -21,6 +21,10 @@ Configurations (the trapped 2D Hubbard model of eq. 1 with V_i = V0 r_i^2, t = 1
   per inequivalent site (36 sites).
 * ``box12``     -- a 12x12x12 open box with a spherical trap V0=0.08, otherwise as slab16
   (56 inequivalent sites).
+* ``box14p``, ``box16p`` -- the periodic cubic boxes of Fig. 4: 14^3 and 16^3 sites, periodic in
+  all three directions (band half-width 392 and 512 in the folded band order), spherical trap
+  V0=0.05, U=12, T = 0.33 (beta=3), mu = U/2 (half filling at the centre; the figure does not
+  state mu), dtau=0.125 (L=24), 16 chains per inequivalent site (84 and 120 sites).
 """
 from __future__ import annotations
 
@@ -47,6 +51,14 @@ CONFIGS = {
                    beta=2.4, dtau=0.1, precision=2, team_warps=1, n_matsubara=500,
                    chains_per_site=32, n_warmup=500, n_measure=2000, refresh_every=10,
                    bin_size=100, seed=5, h_seed=0.1, mix=0.5),
+    "box14p": dict(Lx=14, Ly=14, Lz=14, geometry=2, periodic=1, t=1.0, U=12.0, V0=0.05, mu=6.0,
+                   beta=3.0, dtau=0.125, precision=2, team_warps=1, n_matsubara=500,
+                   chains_per_site=16, n_warmup=500, n_measure=2000, refresh_every=10,
+                   bin_size=100, seed=7, h_seed=0.1, mix=0.5),
+    "box16p": dict(Lx=16, Ly=16, Lz=16, geometry=2, periodic=1, t=1.0, U=12.0, V0=0.05, mu=6.0,
+                   beta=3.0, dtau=0.125, precision=2, team_warps=1, n_matsubara=500,
+                   chains_per_site=16, n_warmup=500, n_measure=2000, refresh_every=10,
+                   bin_size=100, seed=8, h_seed=0.1, mix=0.5),
     "box12": dict(Lx=12, Ly=12, Lz=12, geometry=2, periodic=0, t=1.0, U=8.0, V0=0.08, mu=4.0,
                   beta=2.4, dtau=0.1, precision=2, team_warps=1, n_matsubara=500,
                   chains_per_site=32, n_warmup=500, n_measure=2000, refresh_every=10,

@@ -2,9 +2,12 @@
 lattices ("Efficient simulations for three dimensions": trapped boxes with periodic boundaries and
 slabs periodic across their layers), through the C ABI, with the CPU oracle.
 
-Cases span both lattice kernels (one warp per matrix for band half-width b <= 32, one block per
-matrix above) and both spin treatments (spin-down matrices inverted, or read from the spin-up
-ones through a sublattice-exchanging symmetry).  Bars as for the square: G_ii(i w_n) within 1e-12
+Cases span both forms of the lattice step -- the band L D L^T and selected inversion in a
+shared-memory window (one warp per matrix for band half-width b <= 32, one block above), and the
+blocked band L D L^T in global memory with forward solves at one site per orbit and spin (taken
+above b = 165, or when asked for with lattice_form = 1) -- and both spin treatments (spin-down
+matrices inverted, or read from the spin-up ones through a sublattice-exchanging symmetry).  The
+periodic 14^3 and 16^3 boxes of Fig. 4 (b = 392, 512) run in the blocked form.  Bars as for the square: G_ii(i w_n) within 1e-12
 relative; baths within 1e-12; decisions identical; observables within 1e-10; Sigma within 1e-9
 relative.
 """
@@ -69,15 +72,18 @@ SMALL = [
 ]
 
 
-@pytest.mark.parametrize("geom,Lx,Ly,Lz,per,band,halved", SMALL)
-def test_lattice_step_all_frequencies(hf, geom, Lx, Ly, Lz, per, band, halved):
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("geom,Lx,Ly,Lz,per,band,halved",
+                         SMALL + [(0, 6, 6, 1, 0, 6, True)])   # b < panel width (blocked form)
+def test_lattice_step_all_frequencies(hf, geom, Lx, Ly, Lz, per, band, halved, form):
     """Every inequivalent site and every frequency of a set self-energy against a dense
-    inverse."""
-    cfg = _cfg(geom, Lx, Ly, Lz, per)
+    inverse, in either form of the lattice step."""
+    cfg = _cfg(geom, Lx, Ly, Lz, per, lattice_form=form)
     p = hf.make_params(cfg)
     N, ns, b, nsp, _, _, _ = hf.hf_lattice_info(p)
     assert b == band
     ctx = hf.Context(p)
+    assert hf.hf_get_lattice_plan(ctx.handle)[0] == form
     ref = _oracle_for(cfg)
     assert ns == ref.nsite and N == ref.lat.N
     has_flip = any(np.all(ref.lat.parity[im] != ref.lat.parity) for im in ref.lat._images)
@@ -102,27 +108,32 @@ def test_lattice_step_all_frequencies(hf, geom, Lx, Ly, Lz, per, band, halved):
 
 
 LARGE = [
-    (3, 24, 24, 4, 0, 96),          # slab of 2304 sites
-    (2, 8, 8, 8, 1, 128),           # periodic box of 512 sites
-    (2, 12, 12, 12, 0, 144),        # open box of 1728 sites
+    (3, 24, 24, 4, 0, 96, 0),       # slab of 2304 sites
+    (2, 8, 8, 8, 1, 128, 0),        # periodic box of 512 sites
+    (2, 12, 12, 12, 0, 144, 0),     # open box of 1728 sites
+    (2, 12, 12, 12, 0, 144, 1),     # the same in the blocked band form
+    (2, 14, 14, 14, 1, 392, 0),     # periodic boxes of Fig. 4 (blocked band form)
+    (2, 16, 16, 16, 1, 512, 0),
 ]
 
 
-@pytest.mark.parametrize("geom,Lx,Ly,Lz,per,band", LARGE)
-def test_lattice_step_large_sampled(hf, geom, Lx, Ly, Lz, per, band):
+@pytest.mark.parametrize("geom,Lx,Ly,Lz,per,band,form", LARGE)
+def test_lattice_step_large_sampled(hf, geom, Lx, Ly, Lz, per, band, form):
     """Full-size lattices at 500 frequencies: sampled (frequency, spin, orbit) entries against one
-    oracle column of M^{-1} each (sparse LU)."""
+    oracle column of M^{-1} each (sparse LU); every orbit for the blocked band form."""
     cfg = _cfg(geom, Lx, Ly, Lz, per, V0=0.03, mu=2.0, U=8.0, beta=8.0, dtau=0.25,
-               n_matsubara=500, n_measure=1, max_bins=1)
+               n_matsubara=500, n_measure=1, max_bins=1, lattice_form=form)
     p = hf.make_params(cfg)
     _, ns, b, _, _, _, _ = hf.hf_lattice_info(p)
     assert b == band
     ctx = hf.Context(p)
+    wide = hf.hf_get_lattice_plan(ctx.handle)[0]
+    assert wide == (1 if (form == 1 or band > 165) else 0)
     hf.hf_compute_baths(ctx.handle)          # lattice step from the seeded self-energy
     gloc = hf.hf_get_gloc(ctx.handle, ns, ctx.nw)
     ref = _oracle_for(cfg)
     full = ref.expand_sigma()
-    orbits = sorted({0, 1, ns // 2, ns - 1})
+    orbits = list(range(ns)) if wide else sorted({0, 1, ns // 2, ns - 1})
     sites = [int(ref.reps[o]) for o in orbits]
     for n in (0, 7, 250, 499):
         for sp in range(2):
@@ -132,12 +143,13 @@ def test_lattice_step_large_sampled(hf, geom, Lx, Ly, Lz, per, band):
     ctx.close()
 
 
-@pytest.mark.parametrize("precision", [0, 2])
-def test_rdmft_iteration_periodic_box_full(hf, precision):
+@pytest.mark.parametrize("precision,form", [(0, 0), (2, 0), (0, 1)])
+def test_rdmft_iteration_periodic_box_full(hf, precision, form):
     """4x4x4 periodic trapped box (4 inequivalent sites), U = 4, beta = 4, L = 16, 500 + 2000
-    sweeps: two complete iterations compared step by step with the oracle."""
+    sweeps: two complete iterations compared step by step with the oracle (form 1: the lattice
+    step in the blocked band form)."""
     cfg = dict(wl.CONFIGS["square6"], geometry=2, Lx=4, Ly=4, Lz=4, periodic=1, V0=0.15, mu=2.0,
-               precision=precision)
+               precision=precision, lattice_form=form)
     ctx = hf.Context(hf.make_params(cfg))
     ref = _oracle_for(cfg)
     assert ctx.n_sites == 4

@@ -59,7 +59,7 @@ def test_orbit_tables_match_the_oracle(lib, geom, Lx, Ly, Lz, per, band):
     (dict(geometry=3, Lx=6, Ly=6, Lz=3), "even length"),
     (dict(geometry=3, Lx=6, Ly=6, Lz=2), "even length"),
     (dict(geometry=2, Lx=4, Ly=4, Lz=0), ">= 1"),
-    (dict(geometry=3, Lx=48, Ly=48, Lz=4), "band half-width"),     # b = 192 > 166
+    (dict(geometry=3, Lx=212, Ly=2, Lz=4), "band half-width"),     # b = 848 > 840
 ])
 def test_invalid_three_dimensional_lattices(lib, over, frag):
     p = hf.make_params(wl.CONFIGS["square6"], **over)
@@ -80,6 +80,10 @@ def test_bench_lattice_bookkeeping(lib):
     assert bench.lattice_launches(hf, wl.CONFIGS["slab16"]) == 1
     # 12^3 box: 500 matrices of 1728 x 145 x 16 bytes = 2.0 GB -> two launches
     assert bench.lattice_launches(hf, wl.CONFIGS["box12"]) == 2
+    # periodic 16^3 box (blocked band form): 500 matrices of 4096 x 513 x 16 bytes = 16.8 GB ->
+    # two chunks of 250 under the 8 GiB cap, two launches each
+    assert bench.lattice_launches(hf, wl.CONFIGS["box16p"]) == 4
+    assert bench.lattice_launches(hf, dict(wl.CONFIGS["slab16"], lattice_form=1)) == 2
     N = 40
     exact = 8.0 * sum(d * (d + 1) // 2 + d * d + d for d in range(N))
     assert bench.lattice_flops(N, N - 1, 1, 1) == exact
@@ -87,12 +91,21 @@ def test_bench_lattice_bookkeeping(lib):
     assert abs(bench.lattice_flops(400, 399, 1, 1) / (8 * 400 ** 3 / 2) - 1) < 0.01
 
 
-def test_largest_band_is_165(lib):
-    """The lattice step keeps a (b+1)(b+2)/2-entry window in shared memory: b = 165 is the
-    largest half-width it accepts (an 11x15x3 open box has b = Lx Ly = 165; 2x83x2 has 166)."""
-    p = hf.make_params(wl.CONFIGS["square6"], geometry=2, Lx=11, Ly=15, Lz=3, periodic=0)
-    assert hf.hf_lattice_info(p)[2] == 165
-    p = hf.make_params(wl.CONFIGS["square6"], geometry=2, Lx=2, Ly=83, Lz=2, periodic=0)
+def test_band_limits(lib):
+    """The shared-memory window form takes b <= 165 (an 11x15x3 open box has b = Lx Ly = 165);
+    wider bands go to the blocked band form, up to b = 840 (a 28x30x2 box; 29x29x2 has 841 and
+    is rejected).  The periodic boxes of Fig. 4 have b = 2 n^2 in the folded band order."""
+    sq = wl.CONFIGS["square6"]
+    assert hf.hf_lattice_info(hf.make_params(sq, geometry=2, Lx=11, Ly=15, Lz=3, periodic=0))[2] == 165
+    assert hf.hf_lattice_info(hf.make_params(sq, geometry=2, Lx=2, Ly=83, Lz=2, periodic=0))[2] == 166
+    assert hf.hf_lattice_info(hf.make_params(sq, geometry=2, Lx=28, Ly=30, Lz=2, periodic=0))[2] == 840
+    for name, n, b, ns in (("box14p", 14, 392, 84), ("box16p", 16, 512, 120)):
+        N, nsite, band, nspin, _, _, _ = hf.hf_lattice_info(hf.make_params(wl.CONFIGS[name]))
+        assert (N, band, nsite, nspin) == (n ** 3, b, ns, 1)
+    p = hf.make_params(sq, geometry=2, Lx=29, Ly=29, Lz=2, periodic=0)
     with pytest.raises(hf.HFError) as e:
         hf.hf_lattice_info(p)
-    assert e.value.status == hf.HF_EINVAL and "largest: 165" in str(e.value)
+    assert e.value.status == hf.HF_EINVAL and "largest: 840" in str(e.value)
+    with pytest.raises(hf.HFError) as e:
+        hf.hf_lattice_info(hf.make_params(sq, lattice_form=2))
+    assert e.value.status == hf.HF_EINVAL

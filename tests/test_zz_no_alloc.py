@@ -26,13 +26,14 @@ def hf():
     return H
 
 
-def test_noalloc_matches_workspace_lattice_step_twice(hf):
+@pytest.mark.parametrize("form", [0, 1])
+def test_noalloc_matches_workspace_lattice_step_twice(hf, form):
     import torch
 
     # the 20x20 trap: one band is 400 x 21 complex = 134 KB, so the 1000 (w_n, sigma) matrices
-    # run in several chunks through the 16 MiB static array
+    # run in several chunks through the 16 MiB static array (form 1: blocked band form)
     cfg = dict(wl.CONFIGS["square20"], chains_per_site=1, n_warmup=2, n_measure=4, bin_size=2,
-               max_bins=2)
+               max_bins=2, lattice_form=form)
     ctx = hf.Context(hf.make_params(cfg))
     ns, nw = ctx.n_sites, ctx.nw
     d_sigma = torch.empty((ns, 2, nw), dtype=torch.complex128, device="cuda")
