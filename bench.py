@@ -401,10 +401,17 @@ DF_OPS_PER_FMA = 12          # FP32-pipe ops of one double-float multiply-add (l
 MEASURED_TRAFFIC = {"qmc_f64_kernel": (2377728 + 1792, "4d68298916e948ee"),
                     "qmc_df64_kernel": (2.628e6 + 1.452e6, "f0ade2fccbd67061"),
                     # the lattice step of the slab16 workload (N = 1024, b = 128, 500 matrices)
-                    "lattice_kernel:slab16": (652.3e6 + 947.5e6, "bce118bbe49681e3")}
+                    "lattice_kernel:slab16": (652.3e6 + 947.5e6, "bce118bbe49681e3"),
+                    # square30: one refresh launch and one sweep launch of all 1920 chains
+                    "refresh_tc_kernel": (364.8e6 + 1068.1e6, "9ba5eccb33c4df1e"),
+                    "qmc_f32_kernel": (256.3e6 + 195.5e6, "72762755cf7d94b1")}
 KERNEL_SOURCES = {"qmc_df64_kernel": ("k_qmc_df64.cu", "qmc_common.cuh", "hf_internal.cuh"),
                   "qmc_f64_kernel": ("k_qmc_f64.cu", "qmc_common.cuh", "hf_internal.cuh"),
-                  "lattice_kernel:slab16": ("k_lattice.cu", "k_lattice.cuh", "hf_internal.cuh")}
+                  "lattice_kernel:slab16": ("k_lattice.cu", "k_lattice.cuh", "hf_internal.cuh"),
+                  "refresh_tc_kernel": ("k_refresh_tc.cu", "k_refresh_tc.cuh", "tc_ozaki.cuh",
+                                        "refresh_measure.cuh", "hf_internal.cuh"),
+                  "qmc_f32_kernel": ("k_qmc_f32.cu", "tc_ozaki.cuh", "refresh_measure.cuh",
+                                     "hf_internal.cuh")}
 
 
 def measured_traffic(kernel):
@@ -764,6 +771,8 @@ def run_lattice3d(args):
         # short QMC launch for profiling captures only (not a benchmark value)
         nm = args.sweeps - args.sweeps // 5
         cfg.update(n_warmup=args.sweeps // 5, n_measure=nm, bin_size=max(1, nm // 4))
+    if args.matsubara:
+        cfg.update(n_matsubara=args.matsubara)   # profiling captures only (not a benchmark value)
     N, ns, b, nspin, _, _, _ = hf.hf_lattice_info(hf.make_params(cfg))
     nc = ns * cfg["chains_per_site"]
     cpu = None
@@ -829,8 +838,9 @@ def run_lattice3d(args):
             "roofline": dominant, "qmc_roofline": qroof, "lattice_roofline": lroof,
             "gpu_launches": (lattice_launches(hf, cfg) + 5) * args.steps,
             "cpu_baseline": cpu, "clocks": clk}
-    if args.sweeps:
-        line["profile_case"] = "sweeps overridden to %d: not a benchmark value" % args.sweeps
+    if args.sweeps or args.matsubara:
+        line["profile_case"] = ("sweeps overridden to %d, Matsubara frequencies to %d: not a "
+                                "benchmark value" % (args.sweeps, args.matsubara))
     print(json.dumps(line))
     ctx.close()
     return 0
@@ -1030,8 +1040,8 @@ def run_square30(args):
     # multiply-adds, so the FP32 pipe (128 FFMA/clk/SM), not shared memory, is the roof
     sweep_roof = {"bound": "alu", "kernel": "qmc_f32_kernel", "achieved": f_sweep / sweep_s / 1e12,
                   "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                  "frac": f_sweep / sweep_s / 1e12 / FP32_PEAK_TFLOPS, "traffic": None,
-                  "seconds": sweep_s,
+                  "frac": f_sweep / sweep_s / 1e12 / FP32_PEAK_TFLOPS,
+                  "traffic": measured_traffic("qmc_f32_kernel"), "seconds": sweep_s,
                   "peak_source": "FP32 nominal: 128 FFMA/clk/SM x 152 SMs x 2.07 GHz"}
     if tc:
         # executed tensor-core work: the digit products the Newton steps ran in the last timed
@@ -1040,7 +1050,8 @@ def run_square30(args):
         tflop = n_prod * 2.0 * L ** 3
         ref_roof = {"bound": "tensor", "kernel": "refresh_tc_kernel", "achieved": tflop / refresh_s / 1e12,
                     "peak": MEASURED_BF16_SUSTAINED, "unit": "TFLOP/s",
-                    "frac": tflop / refresh_s / 1e12 / MEASURED_BF16_SUSTAINED, "traffic": None,
+                    "frac": tflop / refresh_s / 1e12 / MEASURED_BF16_SUSTAINED,
+                    "traffic": measured_traffic("refresh_tc_kernel"),
                     "seconds": refresh_s, "algorithmic_fp64_tflops": f_ref / refresh_s / 1e12,
                     "peak_source": "measured dense bf16 (cuBLAS, sustained) of this GPU",
                     "work": "bf16 flops of the exact digit products the refreshes ran",
@@ -1490,6 +1501,9 @@ def main():
                     help="fig1: RDMFT iterations per temperature")
     ap.add_argument("--sweeps", type=int, default=0,
                     help="profiling only: override sweeps per iteration (result is not a bench value)")
+    ap.add_argument("--matsubara", type=int, default=0,
+                    help="profiling only, 3D workloads: override the Matsubara frequencies, i.e. "
+                         "the lattice step's matrices (result is not a bench value)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -276,6 +276,7 @@ struct hf_ctx {
     double2* lat_scratch = nullptr; // [lat_batch][N][b+1]
     int* wide_pos = nullptr;        // [nspin][wide_npos] blocked band form: positions to solve for
     int* wide_out = nullptr;        // [nspin][wide_npos] and the gloc row each one fills
+    int* lat_work = nullptr;        // [1 + lat_batch] its task counter and ready flags
     // tensor-core refresh of the mixed-precision form (precision 1, L = 128, refresh_gj = 0)
     bool tc_on = false;
     hfk::TcRefreshArgs tc{};
@@ -403,6 +404,7 @@ size_t layout(hf_ctx& c, void* base) {
     c.lat_scratch = cv.take<double2>(static_cast<size_t>(c.lat_batch) * N * bw);
     c.wide_pos = cv.take<int>(static_cast<size_t>(4) * ns);
     c.wide_out = cv.take<int>(static_cast<size_t>(4) * ns);
+    c.lat_work = cv.take<int>(static_cast<size_t>(c.lat_batch) + 1);
     c.tc_on = c.p.precision == 1 && L == hfk::kTcL && c.p.refresh_gj == 0;
     if (c.tc_on) {
         c.tc.g0inv_digits = cv.take<uint16_t>(hfk::tc_digits_bytes(ns) / 2);
@@ -611,6 +613,7 @@ hfk::LatticeArgs lattice_args(const hf_ctx& c) {
     la.wide_npos = c.wide_npos;
     la.wide_pos = c.wide_pos;
     la.wide_out = c.wide_out;
+    la.work = c.lat_work;
     return la;
 }
 

@@ -281,28 +281,39 @@ constexpr size_t kStaticLatticeScratchBytes = static_cast<size_t>(16) << 20;   /
 static __device__ __align__(256) double2
     g_lattice_scratch[kStaticLatticeScratchBytes / sizeof(double2)];
 
+// task counter and ready flags of the blocked band form, for chunks of up to kStaticChunk matrices
+constexpr int kStaticChunk = 4096;
+static __device__ int g_lattice_work[kStaticChunk + 1];
+
 size_t lattice_static_scratch_bytes() { return kStaticLatticeScratchBytes; }
 
-// Device address of g_lattice_scratch on the current device, looked up once per device (the
-// host-side symbol is only a stand-in and must never reach a kernel).  The per-device entries
-// are atomics: host threads that make their first call on a device at the same time each look
-// the address up and store the same value.
-static cudaError_t static_scratch_address(double2** out) {
+// Device addresses of g_lattice_scratch and g_lattice_work on the current device, looked up
+// once per device (the host-side symbols are only stand-ins and must never reach a kernel).  The
+// per-device entries are atomics: host threads that make their first call on a device at the
+// same time each look the addresses up and store the same values.
+static cudaError_t static_scratch_address(double2** out, int** work) {
     constexpr int kMaxDevices = 64;
     static std::atomic<double2*> addr[kMaxDevices] = {};
+    static std::atomic<int*> waddr[kMaxDevices] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     double2* a = addr[dev].load(std::memory_order_acquire);
-    if (a == nullptr) {
+    int* w = waddr[dev].load(std::memory_order_acquire);
+    if (a == nullptr || w == nullptr) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_lattice_scratch);
         if (e != cudaSuccess) return e;
         a = static_cast<double2*>(p);
+        e = cudaGetSymbolAddress(&p, g_lattice_work);
+        if (e != cudaSuccess) return e;
+        w = static_cast<int*>(p);
         addr[dev].store(a, std::memory_order_release);
+        waddr[dev].store(w, std::memory_order_release);
     }
     *out = a;
+    *work = w;
     return cudaSuccess;
 }
 
@@ -310,11 +321,13 @@ cudaError_t launch_lattice_static(const LatticeArgs& a_in, cudaStream_t st) {
     const size_t per = lattice_scratch_per_matrix(a_in.N, a_in.b);
     if (per == 0 || per > kStaticLatticeScratchBytes) return cudaErrorInvalidValue;
     double2* base = nullptr;
-    cudaError_t e = static_scratch_address(&base);
+    int* work = nullptr;
+    cudaError_t e = static_scratch_address(&base, &work);
     if (e != cudaSuccess) return e;
     LatticeArgs a = a_in;
     a.scratch = base;
-    const int chunk = static_cast<int>(kStaticLatticeScratchBytes / per);
+    a.work = work;
+    const int chunk = static_cast<int>(std::min<size_t>(kStaticChunk, kStaticLatticeScratchBytes / per));
     const int nq = a.nspin * a.nw;
     for (int q0 = 0; q0 < nq; q0 += chunk) {
         e = launch_lattice(a, q0, std::min(chunk, nq - q0), st);

@@ -24,6 +24,7 @@ struct LatticeArgs {
     int wide_npos;            // listed positions per spin matrix
     const int* wide_pos;      // [nspin][wide_npos] band positions to solve for, ascending
     const int* wide_out;      // [nspin][wide_npos] row r * 2 + slot of gloc that each one fills
+    int* work;                // [1 + matrices per launch] task counter and per-matrix ready flags
 };
 
 // Shared-memory window form (k_lattice.cu): a (b+1)(b+2)/2-entry window per matrix.

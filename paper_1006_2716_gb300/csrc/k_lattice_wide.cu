@@ -13,8 +13,10 @@
 //      by forward substitution from position k, for one listed position per output (orbit, spin
 //      slot).  All members of an orbit with the same sublattice relation to its representative
 //      have the same G_kk, so the host lists the member with the largest band position: its
-//      solve, which runs from k to N - 1, is the shortest.  A block solves kR positions at once,
-//      each reading of a column of L serving all of them.
+//      solve, which runs from k to N - 1, is the shortest.  A solve task takes kR positions at
+//      once, each reading of a column of L serving all of them.
+// Both run in one persistent kernel (one block per SM) that hands out the factorisations first
+// and then the solve tasks, so that the solves fill the SMs the last factorisations leave idle.
 // Work per matrix: about N b^2 / 2 complex FMA for the factorisation and (N - k) b per listed
 // position, against 1.5 N b^2 for the selected inversion of the window form, which also yields
 // every diagonal element.
@@ -29,14 +31,12 @@ namespace hfk {
 namespace {
 
 constexpr int kNB = 16;          // panel width
-constexpr int kFT = 512;         // threads of the factorisation block
-constexpr int kR = 16;           // right-hand sides per solve block
-constexpr int kST = 256;         // threads of a solve block
-constexpr int kDPT = 4;          // band entries per solve thread at most: b <= kDPT * kST
+constexpr int kT = 512;          // threads of a block (both kinds of task)
+constexpr int kR = 16;           // right-hand sides per solve task
 constexpr int kWideMaxBand = 840;
 constexpr int kSeg = 256;        // rows of a trailing-update unit (8 per lane)
 
-static_assert(kWideMaxBand <= kDPT * kST, "solve threads cover a column of L");
+static_assert(kWideMaxBand <= 2 * kT, "two band entries of a column per solve thread at most");
 
 size_t factor_smem(int b) {      // the panel and the pivot row
     return (static_cast<size_t>(kNB) * (kNB + b) + kNB) * sizeof(double2);
@@ -46,27 +46,35 @@ size_t solve_smem(int b) {       // kR windows of b + 1 entries
     return static_cast<size_t>(kR) * (b + 1) * sizeof(double2);
 }
 
+size_t wide_smem(int b) { return std::max(factor_smem(b), solve_smem(b)); }
+
 __device__ __forceinline__ double2 cfma(double2 acc, double2 a, double2 b) {  // acc + a b
     return make_double2(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
 }
 
-// One block per matrix: assembly and blocked band L D L^T into the matrix's band buffer
-// (column k: D_k at d = 0, L_{k+d,k} at d >= 1).
-__global__ void __launch_bounds__(kFT, 1) lattice_factor_kernel(const LatticeArgs A, int q0, int nq) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int qi = static_cast<int>(blockIdx.x);
-    if (qi >= nq) return;
+__device__ __forceinline__ double2 shfl_c(double2 v, int src) {
+    return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+__device__ __forceinline__ int load_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Matrix qi of the launch: assembly and blocked band L D L^T into its band buffer (column k: D_k
+// at d = 0, L_{k+d,k} at d >= 1).  Sets bad on a vanishing or non-finite pivot.
+__device__ void factor_matrix(const LatticeArgs& A, int q0, int qi, unsigned char* smem, bool& bad) {
     int sp, n;
     item_of(A, q0 + qi, sp, n);
     const int N = A.N, b = A.b, S = b + 1, RP = kNB + b;
     const int tid = static_cast<int>(threadIdx.x), lane = tid & 31, warp = tid >> 5;
-    constexpr int kWarps = kFT / 32;
+    constexpr int kWarps = kT / 32;
     const double wn = (2.0 * n + 1.0) * M_PI / A.beta;
     double2* Bq = A.scratch + static_cast<size_t>(qi) * N * S;
     double2* P = reinterpret_cast<double2*>(smem);   // [kNB][RP]: P[j][i] = entry (k0 + i, k0 + j)
     double2* vj = P + static_cast<size_t>(kNB) * RP; // [kNB] pivot row of the current column
     const double2 zero = make_double2(0.0, 0.0);
-    bool bad = false;
 
     // 1. the band of M (entries past the last row zero)
     for (int k = warp; k < N; k += kWarps)
@@ -99,7 +107,7 @@ __global__ void __launch_bounds__(kFT, 1) lattice_factor_kernel(const LatticeArg
                 bad = true;
             __syncthreads();
             const double2 inv = crecip(D);
-            for (int i = j + 1 + tid; i < rmax; i += kFT) {
+            for (int i = j + 1 + tid; i < rmax; i += kT) {
                 const double2 l = cmul(P[j * RP + i], inv);
                 P[j * RP + i] = l;
                 const int jm = min(nb - 1, i);
@@ -113,10 +121,12 @@ __global__ void __launch_bounds__(kFT, 1) lattice_factor_kernel(const LatticeArg
             for (int i = j + lane; i <= ie; i += 32) Bq[static_cast<size_t>(k0 + j) * S + (i - j)] = P[j * RP + i];
         }
         // (d) trailing triangle, rows and columns nb .. tend (relative to k0):
-        //     A[r][c] -= sum_j L_rj D_j L_cj; a warp takes a column, 256 rows at a time (8 a lane)
+        //     A[r][c] -= sum_j L_rj w_j with w_j = D_j L_cj; a warp takes a column, 256 rows at a
+        //     time (8 a lane); lane j forms w_j once and the warp reads it by shuffle
         const int tend = min(nb - 1 + b, rmax - 1);
         for (int c = nb + warp; c <= tend; c += kWarps) {
             double2* col = Bq + static_cast<size_t>(k0 + c) * S;     // col[r - c]
+            const double2 wl = lane < nb ? cmul(P[lane * RP + lane], P[lane * RP + c]) : zero;
             for (int r0 = c; r0 <= tend; r0 += kSeg) {
                 const int nqv = min(kSeg / 32, (tend - r0 + 32) >> 5);   // row groups (warp-uniform)
                 double2 a[kSeg / 32], acc[kSeg / 32];
@@ -127,7 +137,7 @@ __global__ void __launch_bounds__(kFT, 1) lattice_factor_kernel(const LatticeArg
                     acc[q] = zero;
                 }
                 for (int j = 0; j < nb; ++j) {
-                    const double2 w = cmul(P[j * RP + j], P[j * RP + c]);
+                    const double2 w = shfl_c(wl, j);
                     const double2* pj = P + j * RP;
 #pragma unroll
                     for (int q = 0; q < kSeg / 32; ++q)
@@ -142,18 +152,13 @@ __global__ void __launch_bounds__(kFT, 1) lattice_factor_kernel(const LatticeArg
         }
         __syncthreads();
     }
-    if (bad) atomicExch(A.status, static_cast<int>(HF_ENUMERIC));
 }
 
-// One block per (matrix, kR listed positions): y = L^{-1} e_p for each position p, in a window of
+// Listed positions ch * kR ... of matrix qi: y = L^{-1} e_p for each position p, in a window of
 // b + 1 entries per right-hand side (index j in slot j mod (b + 1)); G_pp = sum_j y_j^2 / D_j.
-template <int DPT>   // band entries of a column per thread: b <= DPT * kST
-__global__ void __launch_bounds__(kST, 2) lattice_solve_kernel(const LatticeArgs A, int q0, int nq,
-                                                            int nchunk) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int qi = static_cast<int>(blockIdx.x) / nchunk;
-    const int ch = static_cast<int>(blockIdx.x) - qi * nchunk;
-    if (qi >= nq) return;
+// The factors were written by another block: they are read through L2 (ld.global.cg).
+template <int DPT>   // band entries of a column per thread: b <= DPT * kT
+__device__ void solve_chunk(const LatticeArgs& A, int q0, int qi, int ch, unsigned char* smem) {
     int sp, n;
     item_of(A, q0 + qi, sp, n);
     const int N = A.N, b = A.b, S = b + 1;
@@ -164,8 +169,8 @@ __global__ void __launch_bounds__(kST, 2) lattice_solve_kernel(const LatticeArgs
     const int* out = A.wide_out + static_cast<size_t>(sp) * A.wide_npos + ch * kR;
     const int nr = min(kR, A.wide_npos - ch * kR);
     double2* Y = reinterpret_cast<double2*>(smem);   // [kR][S]
-    const int j0 = pos[0];                           // the smallest position of the block
-    for (int e = tid; e < kR * S; e += kST) Y[e] = zero;
+    const int j0 = pos[0];                           // the smallest position of the task
+    for (int e = tid; e < kR * S; e += kT) Y[e] = zero;
     __syncthreads();
     int pmine = -1;
     if (tid < nr) {
@@ -175,12 +180,12 @@ __global__ void __launch_bounds__(kST, 2) lattice_solve_kernel(const LatticeArgs
     __syncthreads();
     double2 acc = zero;
     int s = j0 % S;
-    // column j of L for this thread's entries d = 1 + tid + m kST, loaded a column ahead
+    // column j of L for this thread's entries d = 1 + tid + m kT, loaded a column ahead
     double2 l[DPT];
 #pragma unroll
     for (int m = 0; m < DPT; ++m) {
-        const int d = 1 + tid + m * kST;
-        l[m] = d <= min(b, N - 1 - j0) ? Bq[static_cast<size_t>(j0) * S + d] : zero;
+        const int d = 1 + tid + m * kT;
+        l[m] = d <= min(b, N - 1 - j0) ? __ldcg(Bq + static_cast<size_t>(j0) * S + d) : zero;
     }
     for (int j = j0; j < N; ++j) {
         const int dmax = min(b, N - 1 - j);
@@ -188,14 +193,14 @@ __global__ void __launch_bounds__(kST, 2) lattice_solve_kernel(const LatticeArgs
         const int dnext = min(b, N - 2 - j);
 #pragma unroll
         for (int m = 0; m < DPT; ++m) {
-            const int d = 1 + tid + m * kST;
-            ln[m] = d <= dnext ? Bq[static_cast<size_t>(j + 1) * S + d] : zero;
+            const int d = 1 + tid + m * kT;
+            ln[m] = d <= dnext ? __ldcg(Bq + static_cast<size_t>(j + 1) * S + d) : zero;
         }
         double2 y[kR];
 #pragma unroll
         for (int r = 0; r < kR; ++r) y[r] = r < nr ? Y[r * S + s] : zero;
         const double2 ym = tid < nr ? Y[tid * S + s] : zero;
-        const double2 Dj = tid < nr ? Bq[static_cast<size_t>(j) * S] : one;
+        const double2 Dj = tid < nr ? __ldcg(Bq + static_cast<size_t>(j) * S) : one;
         __syncthreads();                                 // slot s read by every thread
         if (tid < nr) {
             acc = cfma(acc, cmul(ym, ym), crecip(Dj));
@@ -203,7 +208,7 @@ __global__ void __launch_bounds__(kST, 2) lattice_solve_kernel(const LatticeArgs
         }
 #pragma unroll
         for (int m = 0; m < DPT; ++m) {
-            const int d = 1 + tid + m * kST;
+            const int d = 1 + tid + m * kT;
             if (d <= dmax) {
                 int sd = s + d;
                 if (sd >= S) sd -= S;
@@ -223,6 +228,53 @@ __global__ void __launch_bounds__(kST, 2) lattice_solve_kernel(const LatticeArgs
     }
 }
 
+// One persistent block per SM.  The tasks of a launch are the nq factorisations, then the
+// nq * nchunk solve tasks (matrix-major); blocks take them in order from work[0].  A block that
+// finishes a factorisation raises work[1 + qi]; a solve task waits for its matrix's flag (it was
+// handed out earlier, so a running block is factoring it), at most wait_cycles (several times
+// what one factorisation takes), after which it reports HF_ETIMEOUT and skips.  So the blocks left over when the factorisations run out take
+// the solves of the matrices already factored, instead of idling through a last partial wave.
+template <int DPT>
+__global__ void __launch_bounds__(kT, 1) lattice_wide_kernel(const LatticeArgs A, int q0, int nq,
+                                                             int nchunk, int* work,
+                                                             long long wait_cycles) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int task_s, ready_s;
+    const int tid = static_cast<int>(threadIdx.x);
+    const int ntask = nq * (1 + nchunk);
+    bool bad = false;
+    for (;;) {
+        if (tid == 0) task_s = atomicAdd(work, 1);
+        __syncthreads();
+        const int t = task_s;
+        if (t >= ntask) break;
+        if (t < nq) {
+            factor_matrix(A, q0, t, smem, bad);
+            __syncthreads();                         // every store of the factors issued
+            if (tid == 0) {
+                __threadfence();
+                atomicExch(work + 1 + t, 1);
+            }
+        } else {
+            const int u = t - nq, qi = u / nchunk, ch = u - qi * nchunk;
+            if (tid == 0) {
+                const long long t0 = clock64();
+                int r = load_acquire(work + 1 + qi);
+                while (r == 0 && clock64() - t0 < wait_cycles) {
+                    __nanosleep(1000);
+                    r = load_acquire(work + 1 + qi);
+                }
+                ready_s = r;
+            }
+            __syncthreads();
+            if (ready_s) solve_chunk<DPT>(A, q0, qi, ch, smem);
+            else if (tid == 0) atomicExch(A.status, static_cast<int>(HF_ETIMEOUT));
+        }
+        __syncthreads();                             // task_s and the shared memory are reused
+    }
+    if (bad) atomicExch(A.status, static_cast<int>(HF_ENUMERIC));
+}
+
 }  // namespace
 
 int lattice_wide_max_band() { return kWideMaxBand; }
@@ -231,25 +283,23 @@ int lattice_wide_rhs_per_block() { return kR; }
 
 cudaError_t launch_lattice_wide(const LatticeArgs& a, int q0, int nq, cudaStream_t st) {
     if (nq <= 0) return cudaSuccess;
-    if (a.b < 0 || a.b > kWideMaxBand || a.wide_npos <= 0 || !a.wide_pos || !a.wide_out)
+    if (a.b < 0 || a.b > kWideMaxBand || a.wide_npos <= 0 || !a.wide_pos || !a.wide_out || !a.work)
         return cudaErrorInvalidValue;
-    const size_t fs = factor_smem(a.b), ss = solve_smem(a.b);
-    const bool two = a.b <= 2 * kST;
-    cudaError_t e = cudaFuncSetAttribute(lattice_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(factor_smem(kWideMaxBand)));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(two ? lattice_solve_kernel<2> : lattice_solve_kernel<kDPT>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(solve_smem(kWideMaxBand)));
-    if (e != cudaSuccess) return e;
-    lattice_factor_kernel<<<nq, kFT, fs, st>>>(a, q0, nq);
-    e = cudaGetLastError();
+    const bool one = a.b <= kT;
+    auto kern = one ? lattice_wide_kernel<1> : lattice_wide_kernel<2>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(wide_smem(kWideMaxBand)));
+    int dev = 0, sms = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.work, 0, sizeof(int) * (static_cast<size_t>(nq) + 1), st);
     if (e != cudaSuccess) return e;
     const int nchunk = (a.wide_npos + kR - 1) / kR;
-    if (two)
-        lattice_solve_kernel<2><<<nq * nchunk, kST, ss, st>>>(a, q0, nq, nchunk);
-    else
-        lattice_solve_kernel<kDPT><<<nq * nchunk, kST, ss, st>>>(a, q0, nq, nchunk);
+    const int grid = static_cast<int>(std::min<long long>(sms, static_cast<long long>(nq) * (1 + nchunk)));
+    // a factorisation takes about N b^2 SM cycles (N b^2 / 2 complex multiply-adds of 4 DFMA at
+    // 2 DFMA per cycle); a solve task waits at most 8 times that, and at least 2^31 cycles
+    const long long wait = (1ll << 31) + 8ll * a.N * static_cast<long long>(a.b) * a.b;
+    kern<<<grid, kT, wide_smem(a.b), st>>>(a, q0, nq, nchunk, a.work, wait);
     return cudaGetLastError();
 }
 

@@ -620,7 +620,7 @@ __device__ void refresh_one(const QmcProblem& P, int c, unsigned char* smem) {
 
 // every chain (list == nullptr: one CTA per chain) or the listed ones (a wave of CTAs that take
 // list[k], k = blockIdx.x, blockIdx.x + gridDim.x, ... < *count)
-__global__ void __launch_bounds__(kT32) refresh_f64_kernel(const QmcProblem P, const int* list,
+__global__ void __launch_bounds__(kT32, 1) refresh_f64_kernel(const QmcProblem P, const int* list,
                                                            const int* count) {
     extern __shared__ __align__(16) unsigned char smem[];
     if (!list) {

@@ -178,12 +178,18 @@ __device__ void fill_A_rows(Smem& S, int b, int c, const double* X) {
     store_digits<SA, 8>(U, neg, bufA(S, b, 0), A_SL, ((i >> 3) * 4 + kg) * 128 + (i & 7) * 16);
 }
 
+// e_k = e^{V_k} as significand and exponent for sigma s_k = -1 (m0, E0) and +1 (m1, E1), passed
+// as scalars and selected, never indexed, so that nothing of it goes to local memory.
+struct EScale {
+    unsigned long long m0, m1;
+    int E0, E1;
+};
+
 // B from the columns p*NP .. p*NP+NP-1 of a row-major FP64 matrix X with column scales S.colT;
-// with E, row k is multiplied by e_k (significand me[k], exponent Ee[k]) exactly on the way.
+// with E, row k is multiplied by e_k (from es) exactly on the way.
 // Each thread converts EPT = NP * KC / kThreads consecutive K of one column.
 template <int SB, bool E, int NP>
-__device__ void fill_B_cols(Smem& S, int b, int c, int p, const double* X,
-                            const unsigned long long* me, const int* Ee) {
+__device__ void fill_B_cols(Smem& S, int b, int c, int p, const double* X, EScale es) {
     constexpr int EPT = NP * KC / kThreads;
     static_assert(EPT == 4 || EPT == 8, "4 or 8 K per thread");
     const int t = threadIdx.x;
@@ -199,8 +205,8 @@ __device__ void fill_B_cols(Smem& S, int b, int c, int p, const double* X,
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
         if constexpr (E) {
-            const int up = S.s[c * KC + k0 + q] > 0 ? 1 : 0;   // S.s holds sigma s_k
-            U[q] = to_fixed_scaled_mag(x[q], me[up], Ee[up], T, neg[q]);
+            const bool up = S.s[c * KC + k0 + q] > 0;   // S.s holds sigma s_k
+            U[q] = to_fixed_scaled_mag(x[q], up ? es.m1 : es.m0, up ? es.E1 : es.E0, T, neg[q]);
         } else {
             U[q] = to_fixed_mag(x[q], T, neg[q]);
         }
@@ -239,9 +245,10 @@ __device__ void issue_chunk(Smem& S, int b, int c) {
 // 8 columns j0 ... j0+7 of row i (to load what the epilogue needs early), then epi(i, j, k, Q)
 // for each, k = j - j0, which returns an exponent whose maximum over the rows lands in ncol[j]
 // (when ncol is not null).  With TMA_A the A fill is a bulk copy whose completion the MMA issuer
-// awaits.  ph[] / tph[] track the mbarriers' phases.  Returns false if a wait ran out.
+// awaits.  Bit b of ph / tph tracks the phase of mbar[b] / tbar[b] (bit masks rather than
+// arrays, so that the dynamic index b stays in registers).  Returns false if a wait ran out.
 template <int SA, int SB, int NL, int NP, bool TMA_A, class FA, class FB, class PRE, class EPI>
-__device__ bool product_pass(Smem& S, int p, uint32_t (&ph)[2], uint32_t (&tph)[2], FA fillA,
+__device__ bool product_pass(Smem& S, int p, uint32_t& ph, uint32_t& tph, FA fillA,
                              FB fillB, PRE pre, EPI epi, int* ncol) {
     static_assert(NL - 1 <= 8 && (NL - 1) * NP <= static_cast<int>(kTmemCols), "levels fit TMEM");
     static_assert(SB * NP * KC * 2 <= BUFB - SMAX * A_SL && SA <= SMAX, "digits fit the buffer");
@@ -250,8 +257,8 @@ __device__ bool product_pass(Smem& S, int p, uint32_t (&ph)[2], uint32_t (&tph)[
     for (int c = 0; c < NCH; ++c) {
         const int b = c & 1;
         if (c >= 2) {   // the MMAs that read this buffer two chunks ago must be done
-            ok = mbar_wait(&S.mbar[b], ph[b]) && ok;
-            ph[b] ^= 1u;
+            ok = mbar_wait(&S.mbar[b], (ph >> b) & 1u) && ok;
+            ph ^= 1u << b;
         }
         fillA(b, c);
         fillB(b, c);
@@ -260,16 +267,15 @@ __device__ bool product_pass(Smem& S, int p, uint32_t (&ph)[2], uint32_t (&tph)[
         __syncthreads();
         if (tid == 0) {
             if constexpr (TMA_A) {
-                ok = mbar_wait(&S.tbar[b], tph[b]) && ok;
+                ok = mbar_wait(&S.tbar[b], (tph >> b) & 1u) && ok;
             }
             issue_chunk<SA, SB, NL, NP>(S, b, c);
         }
-        if constexpr (TMA_A) tph[b] ^= 1u;
+        if constexpr (TMA_A) tph ^= 1u << b;
     }
-    ok = mbar_wait(&S.mbar[0], ph[0]) && ok;
-    ph[0] ^= 1u;
-    ok = mbar_wait(&S.mbar[1], ph[1]) && ok;
-    ph[1] ^= 1u;
+    ok = mbar_wait(&S.mbar[0], ph & 1u) && ok;
+    ok = mbar_wait(&S.mbar[1], (ph >> 1) & 1u) && ok;
+    ph ^= 3u;
     if (__syncthreads_or(!ok)) return false;
     tc_fence_after_sync();
     const int w = tid >> 5, lane = tid & 31;
@@ -369,11 +375,9 @@ struct SpinArgs {
     const float* Gf;          // FP32 state of this spin
     const uint16_t* digits;   // g0^{-1} digits of (site, spin)
     const int* rowTg;         // and its row scales
-    unsigned long long me[2]; // significands of e^V: [0] sigma s = -1, [1] sigma s = +1
-    int Ee[2];
-    unsigned long long mev[2];// significands of |e^V - 1|
-    int Eev[2];
-    bool evneg[2];            // e^V - 1 < 0
+    EScale e;                 // e^V: significands and exponents for sigma s = -1 / +1
+    EScale ev;                // |e^V - 1|
+    bool evneg0, evneg1;      // e^V - 1 < 0 for sigma s = -1 / +1
 };
 
 // Moves the scales the last epilogue gathered into place: colT <- ncolT + 2 (and rowT <- nrowT +
@@ -395,7 +399,7 @@ __device__ void take_scales(Smem& S, bool rows) {
 // returns max |R| (bit pattern key).  Gathers R's column scales and X's row scales for the
 // correction that follows.
 template <int S_, int NL>
-__device__ bool residual(Smem& S, uint32_t (&ph)[2], uint32_t (&tph)[2], const SpinArgs& a,
+__device__ bool residual(Smem& S, uint32_t& ph, uint32_t& tph, const SpinArgs& a,
                          const double* Xsrc, double* Rdst, unsigned long long& rmax) {
     constexpr int NP = 64;
     for (int i = threadIdx.x; i < L; i += kThreads) S.rowT[i] = S.gT[i];
@@ -416,7 +420,7 @@ __device__ bool residual(Smem& S, uint32_t (&ph)[2], uint32_t (&tph)[2], const S
     for (int p = 0; p < L / NP; ++p) {
         const bool ok = product_pass<S_, S_, NL, NP, true>(
             S, p, ph, tph, [&](int b, int c) { fill_A_digits<S_>(S, b, c, a.digits); },
-            [&](int b, int c) { fill_B_cols<S_, true, NP>(S, b, c, p, Xsrc, a.me, a.Ee); },
+            [&](int b, int c) { fill_B_cols<S_, true, NP>(S, b, c, p, Xsrc, a.e); },
             [&](int i, int j0) {
 #pragma unroll
                 for (int k = 0; k < 8; k += 2) {
@@ -433,16 +437,17 @@ __device__ bool residual(Smem& S, uint32_t (&ph)[2], uint32_t (&tph)[2], const S
                     if (sh < 0 || sh > 61) S.flag = 1;
                     else q += 1ll << sh;
                 }
-                const int up = S.s[i] > 0 ? 1 : 0;
+                const bool up = S.s[i] > 0;
                 const int T = 62 + EQ;
                 // |ev X| must lie below 2^(T - 1) for the fixed-point form; it does whenever the
                 // scales are sane, otherwise the chain falls back
                 const double x = xr[k];
                 const int ex = exp_of(x);
                 xrow = ex > xrow ? ex : xrow;
-                if (ex != kNoExp && ex + a.Eev[up] + 2 > T - 1) S.flag = 1;
-                long long v = to_fixed_scaled(x, a.mev[up], a.Eev[up], T);
-                q += a.evneg[up] ? -v : v;
+                const int Eev = up ? a.ev.E1 : a.ev.E0;
+                if (ex != kNoExp && ex + Eev + 2 > T - 1) S.flag = 1;
+                long long v = to_fixed_scaled(x, up ? a.ev.m1 : a.ev.m0, Eev, T);
+                q += (up ? a.evneg1 : a.evneg0) ? -v : v;
                 const double r = fixed_to_double(q, EQ);
                 Rdst[static_cast<size_t>(i) * L + j] = r;
                 const unsigned long long key =
@@ -464,13 +469,13 @@ __device__ bool residual(Smem& S, uint32_t (&ph)[2], uint32_t (&tph)[2], const S
 // the four level accumulators of 128 columns).  Gathers the column scales of E X_new for the
 // residual that follows.
 template <int S_, int NL>
-__device__ bool correct(Smem& S, uint32_t (&ph)[2], uint32_t (&tph)[2], const SpinArgs& a,
+__device__ bool correct(Smem& S, uint32_t& ph, uint32_t& tph, const SpinArgs& a,
                         const double* Xsrc, double* Rsrc) {
     constexpr int NP = 128;
     double xr[8];
     const bool ok = product_pass<S_, S_, NL, NP, false>(
         S, 0, ph, tph, [&](int b, int c) { fill_A_rows<S_>(S, b, c, Xsrc); },
-        [&](int b, int c) { fill_B_cols<S_, false, NP>(S, b, c, 0, Rsrc, nullptr, nullptr); },
+        [&](int b, int c) { fill_B_cols<S_, false, NP>(S, b, c, 0, Rsrc, EScale{}); },
         [&](int i, int j0) {
 #pragma unroll
             for (int k = 0; k < 8; k += 2) {
@@ -483,7 +488,7 @@ __device__ bool correct(Smem& S, uint32_t (&ph)[2], uint32_t (&tph)[2], const Sp
             const double x = xr[k] + fixed_to_double(Q, S.rowT[i] + S.colT[j] - 54);
             Rsrc[static_cast<size_t>(i) * L + j] = x;
             const int e = exp_of(x);
-            return e == kNoExp ? kNoExp : e + a.Ee[S.s[i] > 0 ? 1 : 0] + 1;
+            return e == kNoExp ? kNoExp : e + (S.s[i] > 0 ? a.e.E1 : a.e.E0) + 1;
         },
         S.ncolT);
     if (!ok) return false;
@@ -491,7 +496,7 @@ __device__ bool correct(Smem& S, uint32_t (&ph)[2], uint32_t (&tph)[2], const Sp
     return true;
 }
 
-__device__ bool refresh_spin(Smem& S, uint32_t (&ph)[2], uint32_t (&tph)[2], const SpinArgs& a,
+__device__ bool refresh_spin(Smem& S, uint32_t& ph, uint32_t& tph, const SpinArgs& a,
                              int& products) {
     // X0 = the FP32 state, with the column scales of E X0; the row scales of g0^{-1}
     {
@@ -509,7 +514,7 @@ __device__ bool refresh_spin(Smem& S, uint32_t (&ph)[2], uint32_t (&tph)[2], con
                 const double x = static_cast<double>(v[q]);
                 a.Xa[static_cast<size_t>(k) * L + j] = x;
                 const int e = exp_of(x);
-                if (e != kNoExp) m = max(m, e + a.Ee[S.s[k] > 0 ? 1 : 0] + 1);
+                if (e != kNoExp) m = max(m, e + (S.s[k] > 0 ? a.e.E1 : a.e.E0) + 1);
             }
         }
         S.tmpT[t] = m;
@@ -597,7 +602,7 @@ refresh_tc_kernel(const QmcProblem P, const TcRefreshArgs A) {
     tc_fence_before_sync();
     __syncthreads();
     tc_fence_after_sync();
-    uint32_t ph[2] = {0u, 0u}, tph[2] = {0u, 0u};
+    uint32_t ph = 0u, tph = 0u;
     const double e_p = 1.0 + P.ev_p, e_m = 1.0 + P.ev_m;
     bool ok = true;
     int products = 0;
@@ -611,12 +616,12 @@ refresh_tc_kernel(const QmcProblem P, const TcRefreshArgs A) {
         a.Gf = P.Gf + (static_cast<size_t>(c) * 2 + sp) * LL;
         a.digits = A.g0inv_digits + (static_cast<size_t>(site) * 2 + sp) * SMAX * LL;
         a.rowTg = A.g0inv_rowT + (static_cast<size_t>(site) * 2 + sp) * L;
-        split_e(e_m, a.me[0], a.Ee[0]);
-        split_e(e_p, a.me[1], a.Ee[1]);
-        split_e(fabs(P.ev_m), a.mev[0], a.Eev[0]);
-        split_e(fabs(P.ev_p), a.mev[1], a.Eev[1]);
-        a.evneg[0] = P.ev_m < 0.0;
-        a.evneg[1] = P.ev_p < 0.0;
+        split_e(e_m, a.e.m0, a.e.E0);
+        split_e(e_p, a.e.m1, a.e.E1);
+        split_e(fabs(P.ev_m), a.ev.m0, a.ev.E0);
+        split_e(fabs(P.ev_p), a.ev.m1, a.ev.E1);
+        a.evneg0 = P.ev_m < 0.0;
+        a.evneg1 = P.ev_p < 0.0;
         __syncthreads();
         ok = refresh_spin(S, ph, tph, a, products);
         if (!ok) {
@@ -733,7 +738,7 @@ tc_dgemm_kernel(const double* Am, const double* Bm, double* Cm, int n, int* stat
     tc_fence_before_sync();
     __syncthreads();
     tc_fence_after_sync();
-    uint32_t ph[2] = {0u, 0u}, tph[2] = {0u, 0u};
+    uint32_t ph = 0u, tph = 0u;
     const double* Ab = Am + static_cast<size_t>(m) * LL;
     const double* Bb = Bm + static_cast<size_t>(m) * LL;
     double* Cb = Cm + static_cast<size_t>(m) * LL;
@@ -743,7 +748,7 @@ tc_dgemm_kernel(const double* Am, const double* Bm, double* Cm, int n, int* stat
     for (int p = 0; p < L / 64 && ok; ++p)
         ok = product_pass<SD, SD, SD + 1, 64, false>(
             S, p, ph, tph, [&](int b, int c) { fill_A_rows<SD>(S, b, c, Ab); },
-            [&](int b, int c) { fill_B_cols<SD, false, 64>(S, b, c, p, Bb, nullptr, nullptr); },
+            [&](int b, int c) { fill_B_cols<SD, false, 64>(S, b, c, p, Bb, EScale{}); },
             [&](int, int) {},
             [&](int i, int j, int, long long Q) -> int {
                 Cb[static_cast<size_t>(i) * L + j] = fixed_to_double(Q, S.rowT[i] + S.colT[j] - 54);
