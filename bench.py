@@ -806,7 +806,7 @@ def run_lattice3d(args):
     lform, lat_launches, cfma = hf.hf_get_lattice_plan(ctx.handle)
     fl = 8.0 * cfma * nspin * nw
     lat_s = phase[0] / 1e3
-    lkern = "lattice_factor_kernel + lattice_solve_kernel" if lform == 1 else "lattice_kernel"
+    lkern = "lattice_wide_kernel" if lform == 1 else "lattice_kernel"
     lroof = {"bound": "alu", "achieved": fl / lat_s / 1e12, "peak": FP64_PEAK_TFLOPS,
              "unit": "TFLOP/s", "frac": fl / lat_s / 1e12 / FP64_PEAK_TFLOPS,
              "traffic": measured_traffic("lattice_kernel:" + name),
