@@ -181,6 +181,15 @@ hf_status hf_get_gloc(hf_ctx* ctx, double* gloc);
 /* Bath g~0(tau_m) currently set, [n_sites][2][L].  Synchronises. */
 hf_status hf_get_g0(hf_ctx* ctx, double* g0_tau);
 
+/* Frequency-domain quantities of the last hf_rdmft_step, each [n_sites][2][n_matsubara]
+ * complex (re, im interleaved), any pointer NULL to skip: the shifted Weiss field
+ * G~0(i w_n) = 1/(1/G0 - U/2) the bath was built from, 1/G0 = 1/G_ii + Sigma, the impurity
+ * G(i w_n) transformed from the measured G(tau) ("Model and Methods": G_imp = G~0 +
+ * FT[-spline(g_imp - g~0)]), and the new self-energy 1/G0 - 1/G_imp before mixing.
+ * Synchronises. */
+hf_status hf_get_impurity_iw(hf_ctx* ctx, double* gw0, double* weiss_inv, double* gimp,
+                             double* sigma_new);
+
 /* Checkpoint / resume: fields [n_chains][L] int8 (+-1), per-chain sweep counters
  * [n_chains].  Setting fields invalidates G until the next refresh (hf_sweep with
  * refresh_first = 1).  Synchronises. */

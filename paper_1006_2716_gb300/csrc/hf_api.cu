@@ -1024,6 +1024,18 @@ hf_status hf_get_gloc(hf_ctx* c, double* gloc) {
     return HF_OK;
 }
 
+hf_status hf_get_impurity_iw(hf_ctx* c, double* gw0, double* weiss_inv, double* gimp,
+                             double* sigma_new) {
+    if (!c) return fail(nullptr, HF_EINVAL, "null context");
+    const size_t n = sizeof(double2) * c->nsite * 2 * c->nw;
+    double* dst[4] = {gw0, weiss_inv, gimp, sigma_new};
+    const double2* src[4] = {c->gwt, c->weiss_inv, c->gimp, c->sigma_new};
+    for (int k = 0; k < 4; ++k)
+        if (dst[k]) HF_CUDA(c, cudaMemcpyAsync(dst[k], src[k], n, cudaMemcpyDeviceToHost, c->stream));
+    HF_CUDA(c, cudaStreamSynchronize(c->stream));
+    return HF_OK;
+}
+
 hf_status hf_get_fields(hf_ctx* c, signed char* fields, uint32_t* counters) {
     if (!c) return fail(nullptr, HF_EINVAL, "null context");
     if (fields)

@@ -218,13 +218,26 @@ __device__ void fill_B_cols(Smem& S, int b, int c, int p, const double* X, EScal
 // ------------------------------------------------------------------------------------------
 // one product pass: fills, MMAs, readout
 // ------------------------------------------------------------------------------------------
+// The MMAs of a chunk are issued by lane 0 of warps 0 .. kIssuers-1, each taking whole levels
+// (a level's accumulator is written by one thread, in order, its first product overwriting it):
+// level n goes to issuer fold(n - 2) mod kIssuers, fold pairing the first and the last levels,
+// so that the issuers' shares of the products are nearly equal.  Each issuer commits to the
+// chunk's mbarrier, which therefore expects kIssuers arrivals.
+constexpr int kIssuers = 4;
+
+__host__ __device__ constexpr int issuer_of_level(int n, int NL) {
+    const int m = n - 2, last = NL - 2;
+    return (m < last - m ? m : last - m) % kIssuers;
+}
+
 template <int SA, int SB, int NL, int NP>
-__device__ void issue_chunk(Smem& S, int b, int c) {
+__device__ void issue_chunk(Smem& S, int b, int c, int q) {
     constexpr uint32_t idesc = idesc_bf16_f32(128, NP);
     tc_fence_after_sync();
     const uint32_t a0 = smem_addr(bufA(S, b, 0)), b0 = smem_addr(bufB<NP>(S, b, 0));
 #pragma unroll
     for (int n = 2; n <= NL; ++n) {
+        if (issuer_of_level(n, NL) != q) continue;
         const int smin = n - SB > 1 ? n - SB : 1;
         const int smax = n - 1 < SA ? n - 1 : SA;
         for (int s = smin; s <= smax; ++s) {
@@ -265,11 +278,11 @@ __device__ bool product_pass(Smem& S, int p, uint32_t& ph, uint32_t& tph, FA fil
         fence_async_shared();
         tc_fence_before_sync();
         __syncthreads();
-        if (tid == 0) {
+        if ((tid & 31) == 0 && (tid >> 5) < kIssuers) {
             if constexpr (TMA_A) {
                 ok = mbar_wait(&S.tbar[b], (tph >> b) & 1u) && ok;
             }
-            issue_chunk<SA, SB, NL, NP>(S, b, c);
+            issue_chunk<SA, SB, NL, NP>(S, b, c, tid >> 5);
         }
         if constexpr (TMA_A) tph ^= 1u << b;
     }
@@ -592,8 +605,8 @@ refresh_tc_kernel(const QmcProblem P, const TcRefreshArgs A) {
     if (tid == 0) {
         S.flag = 0;
         S.timeout = 0;
-        mbar_init(&S.mbar[0], 1);
-        mbar_init(&S.mbar[1], 1);
+        mbar_init(&S.mbar[0], kIssuers);
+        mbar_init(&S.mbar[1], kIssuers);
         mbar_init(&S.tbar[0], 1);
         mbar_init(&S.tbar[1], 1);
         mbar_init_fence();
@@ -728,8 +741,8 @@ tc_dgemm_kernel(const double* Am, const double* Bm, double* Cm, int n, int* stat
     if (m >= n) return;
     const int tid = threadIdx.x;
     if (tid == 0) {
-        mbar_init(&S.mbar[0], 1);
-        mbar_init(&S.mbar[1], 1);
+        mbar_init(&S.mbar[0], kIssuers);
+        mbar_init(&S.mbar[1], kIssuers);
         mbar_init(&S.tbar[0], 1);
         mbar_init(&S.tbar[1], 1);
         mbar_init_fence();

@@ -107,6 +107,7 @@ SIGNATURES = [
                                         C.POINTER(C.c_ulonglong)]),
     ("hf_lattice_step_noalloc", C.c_int, [_VP, _VP, _VP]),
     ("hf_get_lattice_plan", C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int), _DP]),
+    ("hf_get_impurity_iw", C.c_int, [_VP, _DP, _DP, _DP, _DP]),
     ("hf_philox_blocks", C.c_int, [C.c_uint32, C.c_uint32, _VP, C.c_int, _VP, _VP]),
     ("hf_tc_dgemm128", C.c_int, [_VP, _VP, _VP, C.c_int, C.c_int, _VP, _VP]),
     ("hf_batch_create", C.c_int, [C.POINTER(_VP), C.c_int, C.c_int, C.POINTER(_VP)]),
@@ -251,6 +252,14 @@ def hf_get_gloc(ctx, n_sites, nw):
     out = np.zeros((n_sites, 2, nw), dtype=np.complex128)
     _check(lib().hf_get_gloc(ctx, out.ctypes.data_as(_DP)), ctx)
     return out
+
+
+def hf_get_impurity_iw(ctx, n_sites, nw):
+    """(G~0(i w_n), 1/G0, G_imp(i w_n), unmixed Sigma) of the last RDMFT iteration, each
+    [n_sites][2][nw] complex."""
+    out = [np.zeros((n_sites, 2, nw), dtype=np.complex128) for _ in range(4)]
+    _check(lib().hf_get_impurity_iw(ctx, *[o.ctypes.data_as(_DP) for o in out]), ctx)
+    return tuple(out)
 
 
 def hf_get_g0(ctx, n_sites, L):
