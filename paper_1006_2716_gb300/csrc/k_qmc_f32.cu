@@ -622,7 +622,7 @@ __device__ void refresh_one(const QmcProblem& P, int c, unsigned char* smem) {
 // list[k], k = blockIdx.x, blockIdx.x + gridDim.x, ... < *count)
 __global__ void __launch_bounds__(kT32, 1) refresh_f64_kernel(const QmcProblem P, const int* list,
                                                            const int* count) {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(1024) unsigned char smem[];
     if (!list) {
         if (static_cast<int>(blockIdx.x) < P.nchain) refresh_one(P, blockIdx.x, smem);
         return;

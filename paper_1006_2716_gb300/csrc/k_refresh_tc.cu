@@ -158,25 +158,49 @@ __device__ __forceinline__ void store_digits(const unsigned long long (&U)[NE], 
     }
 }
 
+// The operand fills of a K-chunk are objects with two steps: load(c) reads the chunk's FP64
+// values from global memory into registers, cut(b, c) turns them into digits in buffer b.
+// product_pass loads chunk c + 1 right after cutting chunk c, so the global reads are in flight
+// during the barrier, the MMA issue and the wait for the next buffer.
+
+// A from precomputed digit chunks (bulk copies by thread 0 in cut; nothing to load)
+template <int SA>
+struct FillADigits {
+    Smem& S;
+    const uint16_t* digits;
+    __device__ void load(int) {}
+    __device__ void cut(int b, int c) { fill_A_digits<SA>(S, b, c, digits); }
+};
+
 // A from the rows of a row-major FP64 matrix X with row scales S.rowT: 128 rows x 4 groups of 8
 // consecutive K, one group per thread
 template <int SA>
-__device__ void fill_A_rows(Smem& S, int b, int c, const double* X) {
+struct FillARows {
     static_assert(L * (KC / 8) == kThreads, "one group per thread");
-    const int u = threadIdx.x;
-    const int i = u & (L - 1), kg = u >> 7;
-    const double* src = X + static_cast<size_t>(i) * L + c * KC + kg * 8;
-    const int T = S.rowT[i];
-    unsigned long long U[8];
-    bool neg[8];
+    Smem& S;
+    const double* X;
+    double2 v[4];
+    __device__ void load(int c) {
+        const int u = threadIdx.x;
+        const int i = u & (L - 1), kg = u >> 7;
+        const double* src = X + static_cast<size_t>(i) * L + c * KC + kg * 8;
 #pragma unroll
-    for (int q = 0; q < 8; q += 2) {
-        const double2 v = *reinterpret_cast<const double2*>(src + q);
-        U[q] = to_fixed_mag(v.x, T, neg[q]);
-        U[q + 1] = to_fixed_mag(v.y, T, neg[q + 1]);
+        for (int q = 0; q < 4; ++q) v[q] = *reinterpret_cast<const double2*>(src + 2 * q);
     }
-    store_digits<SA, 8>(U, neg, bufA(S, b, 0), A_SL, ((i >> 3) * 4 + kg) * 128 + (i & 7) * 16);
-}
+    __device__ void cut(int b, int c) {
+        const int u = threadIdx.x;
+        const int i = u & (L - 1), kg = u >> 7;
+        const int T = S.rowT[i];
+        unsigned long long U[8];
+        bool neg[8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            U[2 * q] = to_fixed_mag(v[q].x, T, neg[2 * q]);
+            U[2 * q + 1] = to_fixed_mag(v[q].y, T, neg[2 * q + 1]);
+        }
+        store_digits<SA, 8>(U, neg, bufA(S, b, 0), A_SL, ((i >> 3) * 4 + kg) * 128 + (i & 7) * 16);
+    }
+};
 
 // e_k = e^{V_k} as significand and exponent for sigma s_k = -1 (m0, E0) and +1 (m1, E1), passed
 // as scalars and selected, never indexed, so that nothing of it goes to local memory.
@@ -189,31 +213,40 @@ struct EScale {
 // with E, row k is multiplied by e_k (from es) exactly on the way.
 // Each thread converts EPT = NP * KC / kThreads consecutive K of one column.
 template <int SB, bool E, int NP>
-__device__ void fill_B_cols(Smem& S, int b, int c, int p, const double* X, EScale es) {
-    constexpr int EPT = NP * KC / kThreads;
+struct FillBCols {
+    static constexpr int EPT = NP * KC / kThreads;
     static_assert(EPT == 4 || EPT == 8, "4 or 8 K per thread");
-    const int t = threadIdx.x;
-    const int jl = t & (NP - 1), seg = t / NP;
-    const int k0 = seg * EPT;                      // within the chunk
-    const int j = p * NP + jl;
-    const int T = S.colT[j];
+    Smem& S;
+    const double* X;
+    int p;
+    EScale es;
     double x[EPT];
+    __device__ void load(int c) {
+        const int t = threadIdx.x;
+        const int jl = t & (NP - 1), k0 = (t / NP) * EPT;
+        const int j = p * NP + jl;
 #pragma unroll
-    for (int q = 0; q < EPT; ++q) x[q] = X[static_cast<size_t>(c * KC + k0 + q) * L + j];
-    unsigned long long U[EPT];
-    bool neg[EPT];
-#pragma unroll
-    for (int q = 0; q < EPT; ++q) {
-        if constexpr (E) {
-            const bool up = S.s[c * KC + k0 + q] > 0;   // S.s holds sigma s_k
-            U[q] = to_fixed_scaled_mag(x[q], up ? es.m1 : es.m0, up ? es.E1 : es.E0, T, neg[q]);
-        } else {
-            U[q] = to_fixed_mag(x[q], T, neg[q]);
-        }
+        for (int q = 0; q < EPT; ++q) x[q] = X[static_cast<size_t>(c * KC + k0 + q) * L + j];
     }
-    store_digits<SB, EPT>(U, neg, bufB<NP>(S, b, 0), NP * KC * 2,
-                          ((jl >> 3) * 4 + (k0 >> 3)) * 128 + (jl & 7) * 16 + (k0 & 7) * 2);
-}
+    __device__ void cut(int b, int c) {
+        const int t = threadIdx.x;
+        const int jl = t & (NP - 1), k0 = (t / NP) * EPT;   // k0 within the chunk
+        const int T = S.colT[p * NP + jl];
+        unsigned long long U[EPT];
+        bool neg[EPT];
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+            if constexpr (E) {
+                const bool up = S.s[c * KC + k0 + q] > 0;   // S.s holds sigma s_k
+                U[q] = to_fixed_scaled_mag(x[q], up ? es.m1 : es.m0, up ? es.E1 : es.E0, T, neg[q]);
+            } else {
+                U[q] = to_fixed_mag(x[q], T, neg[q]);
+            }
+        }
+        store_digits<SB, EPT>(U, neg, bufB<NP>(S, b, 0), NP * KC * 2,
+                              ((jl >> 3) * 4 + (k0 >> 3)) * 128 + (jl & 7) * 16 + (k0 & 7) * 2);
+    }
+};
 
 // ------------------------------------------------------------------------------------------
 // one product pass: fills, MMAs, readout
@@ -253,7 +286,8 @@ __device__ void issue_chunk(Smem& S, int b, int c, int q) {
     mma_commit(&S.mbar[b]);
 }
 
-// Runs one pass (output columns p*NP ...) of C = A B with the given operand fills and hands every
+// Runs one pass (output columns p*NP ...) of C = A B with the given operand fills (load / cut
+// objects, see above) and hands every
 // element's level sum Q (C_ij = Q 2^(rowT_i + colT_j - 54)) to the epilogue: pre(i, j0) once per
 // 8 columns j0 ... j0+7 of row i (to load what the epilogue needs early), then epi(i, j, k, Q)
 // for each, k = j - j0, which returns an exponent whose maximum over the rows lands in ncol[j]
@@ -261,20 +295,26 @@ __device__ void issue_chunk(Smem& S, int b, int c, int q) {
 // awaits.  Bit b of ph / tph tracks the phase of mbar[b] / tbar[b] (bit masks rather than
 // arrays, so that the dynamic index b stays in registers).  Returns false if a wait ran out.
 template <int SA, int SB, int NL, int NP, bool TMA_A, class FA, class FB, class PRE, class EPI>
-__device__ bool product_pass(Smem& S, int p, uint32_t& ph, uint32_t& tph, FA fillA,
-                             FB fillB, PRE pre, EPI epi, int* ncol) {
+__device__ bool product_pass(Smem& S, int p, uint32_t& ph, uint32_t& tph, FA& fillA,
+                             FB& fillB, PRE pre, EPI epi, int* ncol) {
     static_assert(NL - 1 <= 8 && (NL - 1) * NP <= static_cast<int>(kTmemCols), "levels fit TMEM");
     static_assert(SB * NP * KC * 2 <= BUFB - SMAX * A_SL && SA <= SMAX, "digits fit the buffer");
     const int tid = threadIdx.x;
     bool ok = true;
+    fillA.load(0);
+    fillB.load(0);
     for (int c = 0; c < NCH; ++c) {
         const int b = c & 1;
         if (c >= 2) {   // the MMAs that read this buffer two chunks ago must be done
             ok = mbar_wait(&S.mbar[b], (ph >> b) & 1u) && ok;
             ph ^= 1u << b;
         }
-        fillA(b, c);
-        fillB(b, c);
+        fillA.cut(b, c);
+        fillB.cut(b, c);
+        if (c + 1 < NCH) {
+            fillA.load(c + 1);
+            fillB.load(c + 1);
+        }
         fence_async_shared();
         tc_fence_before_sync();
         __syncthreads();
@@ -304,12 +344,21 @@ __device__ bool product_pass(Smem& S, int p, uint32_t& ph, uint32_t& tph, FA fil
         long long Q[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) Q[k] = 0;
+        // the levels' columns in batches of up to four loads in flight per wait
 #pragma unroll
-        for (int n = 2; n <= NL; ++n) {
-            float v[8];
-            tmem_ld8(trow + (n - 2) * NP + jl0, v);
+        for (int n0 = 2; n0 <= NL; n0 += 4) {
+            uint32_t r[4][8];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) Q[k] += level_shift(static_cast<long long>(__float2int_rz(v[k])), n);
+            for (int u = 0; u < 4; ++u)
+                if (n0 + u <= NL) tmem_ld8_async(trow + (n0 + u - 2) * NP + jl0, r[u]);
+            tmem_wait_ld();
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (n0 + u <= NL) {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        Q[k] += level_shift(static_cast<long long>(__float2int_rz(__uint_as_float(r[u][k]))), n0 + u);
+                }
         }
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
@@ -431,9 +480,10 @@ __device__ bool residual(Smem& S, uint32_t& ph, uint32_t& tph, const SpinArgs& a
     int xrow = kNoExp;   // this thread's row of X: largest exponent seen
     double xr[8];
     for (int p = 0; p < L / NP; ++p) {
+        FillADigits<S_> fa{S, a.digits};
+        FillBCols<S_, true, NP> fb{S, Xsrc, p, a.e};
         const bool ok = product_pass<S_, S_, NL, NP, true>(
-            S, p, ph, tph, [&](int b, int c) { fill_A_digits<S_>(S, b, c, a.digits); },
-            [&](int b, int c) { fill_B_cols<S_, true, NP>(S, b, c, p, Xsrc, a.e); },
+            S, p, ph, tph, fa, fb,
             [&](int i, int j0) {
 #pragma unroll
                 for (int k = 0; k < 8; k += 2) {
@@ -486,9 +536,10 @@ __device__ bool correct(Smem& S, uint32_t& ph, uint32_t& tph, const SpinArgs& a,
                         const double* Xsrc, double* Rsrc) {
     constexpr int NP = 128;
     double xr[8];
+    FillARows<S_> fa{S, Xsrc};
+    FillBCols<S_, false, NP> fb{S, Rsrc, 0, EScale{}};
     const bool ok = product_pass<S_, S_, NL, NP, false>(
-        S, 0, ph, tph, [&](int b, int c) { fill_A_rows<S_>(S, b, c, Xsrc); },
-        [&](int b, int c) { fill_B_cols<S_, false, NP>(S, b, c, 0, Rsrc, EScale{}); },
+        S, 0, ph, tph, fa, fb,
         [&](int i, int j0) {
 #pragma unroll
             for (int k = 0; k < 8; k += 2) {
@@ -758,16 +809,18 @@ tc_dgemm_kernel(const double* Am, const double* Bm, double* Cm, int n, int* stat
     row_scales(S, Ab);
     col_scales(S, Bb, nullptr);
     bool ok = true;
-    for (int p = 0; p < L / 64 && ok; ++p)
+    for (int p = 0; p < L / 64 && ok; ++p) {
+        FillARows<SD> fa{S, Ab};
+        FillBCols<SD, false, 64> fb{S, Bb, p, EScale{}};
         ok = product_pass<SD, SD, SD + 1, 64, false>(
-            S, p, ph, tph, [&](int b, int c) { fill_A_rows<SD>(S, b, c, Ab); },
-            [&](int b, int c) { fill_B_cols<SD, false, 64>(S, b, c, p, Bb, EScale{}); },
+            S, p, ph, tph, fa, fb,
             [&](int, int) {},
             [&](int i, int j, int, long long Q) -> int {
                 Cb[static_cast<size_t>(i) * L + j] = fixed_to_double(Q, S.rowT[i] + S.colT[j] - 54);
                 return kNoExp;
             },
             nullptr);
+    }
     __syncthreads();
     tc_fence_after_sync();
     if (tid < 32) tmem_dealloc(S.tmem, kTmemCols);
