@@ -401,13 +401,18 @@ DF_OPS_PER_FMA = 12          # FP32-pipe ops of one double-float multiply-add (l
 MEASURED_TRAFFIC = {"qmc_f64_kernel": (2377728 + 1792, "4d68298916e948ee"),
                     "qmc_df64_kernel": (2.628e6 + 1.452e6, "f0ade2fccbd67061"),
                     # the lattice step of the slab16 workload (N = 1024, b = 128, 500 matrices)
-                    "lattice_kernel:slab16": (652.3e6 + 947.5e6, "bce118bbe49681e3"),
+                    "lattice_kernel:slab16": (652.8e6 + 941.8e6, "cb1522e9ec00d909"),
+                    # box16p (N = 4096, b = 512): one launch of 250 matrices
+                    "lattice_kernel:box16p": (155.58e9 + 138.91e9, "c90a88d2608085bc"),
                     # square30: one refresh launch and one sweep launch of all 1920 chains
-                    "refresh_tc_kernel": (364.8e6 + 1068.1e6, "9ba5eccb33c4df1e"),
-                    "qmc_f32_kernel": (256.3e6 + 195.5e6, "72762755cf7d94b1")}
+                    "refresh_tc_kernel": (350.9e6 + 1056.1e6, "d5913a6323e887aa"),
+                    "qmc_f32_kernel": (256.5e6 + 193.3e6, "f0a91e19b560c285")}
 KERNEL_SOURCES = {"qmc_df64_kernel": ("k_qmc_df64.cu", "qmc_common.cuh", "hf_internal.cuh"),
                   "qmc_f64_kernel": ("k_qmc_f64.cu", "qmc_common.cuh", "hf_internal.cuh"),
-                  "lattice_kernel:slab16": ("k_lattice.cu", "k_lattice.cuh", "hf_internal.cuh"),
+                  "lattice_kernel:slab16": ("k_lattice.cu", "k_lattice.cuh", "k_lattice_dev.cuh",
+                                            "hf_internal.cuh"),
+                  "lattice_kernel:box16p": ("k_lattice_wide.cu", "k_lattice.cuh",
+                                            "k_lattice_dev.cuh", "hf_internal.cuh"),
                   "refresh_tc_kernel": ("k_refresh_tc.cu", "k_refresh_tc.cuh", "tc_ozaki.cuh",
                                         "refresh_measure.cuh", "hf_internal.cuh"),
                   "qmc_f32_kernel": ("k_qmc_f32.cu", "tc_ozaki.cuh", "refresh_measure.cuh",
