@@ -451,6 +451,23 @@ hf_status setup_sizes(hf_ctx& c, const hf_params* p) {
     return HF_OK;
 }
 
+// Multiplier of the sweep kernels' slot-to-chain map: the smallest m > nchain / 4 coprime with
+// nchain, so that the chains of one block lie about a quarter of the chain range apart (sites
+// across the trap, whose acceptance and hence work differ).  Taken for the FP64 sweeps of one
+// context, whose blocks all run in one wave, so that the SMs finish together (measured: square20
+// QMC 615 -> 575 ms).  Not for the FP32-pair form, whose blocks gain more from sharing one site's
+// g0^{-1} in L1 (216 -> 241 ms with the map), nor for fused batches, which run several waves that
+// the block scheduler balances.
+int slot_multiplier(int nchain) {
+    if (nchain < 8) return 1;
+    for (int m = nchain / 4 + 1; m < nchain; ++m) {
+        int a = m, b = nchain;
+        while (b) { const int t = a % b; a = b; b = t; }
+        if (a == 1) return m;
+    }
+    return 1;
+}
+
 hfk::QmcProblem make_problem(const hf_ctx& c, int n_warmup, int n_measure, int refresh_first) {
     hfk::QmcProblem q{};
     q.L = c.L;
@@ -471,6 +488,7 @@ hfk::QmcProblem make_problem(const hf_ctx& c, int n_warmup, int n_measure, int r
     q.n_measure = n_measure;
     q.refresh_every = c.p.refresh_every;
     q.refresh_stagger = c.p.refresh_stagger;
+    q.slot_mult = c.p.precision == 0 ? slot_multiplier(c.nchain) : 1;
     q.bin_size = c.p.bin_size;
     q.max_bins = c.p.max_bins;
     q.refresh_first = refresh_first;
@@ -1248,6 +1266,7 @@ static hf_status enqueue_batch_qmc(hf_batch* b, int n_warmup, int n_measure, int
     for (int i = 0; i < qb.nprob; ++i) {
         hf_ctx* c = b->ctx[i];
         qb.p[i] = make_problem(*c, n_warmup, n_measure, refresh_first);
+        qb.p[i].slot_mult = 1;   // several waves: the block scheduler balances them
         qb.p[i].block0 = blocks;
         const int tw = qb.p[i].team_warps;
         const int cpb = hfk::qmc_f64_chains_per_block(c->L, tw);

@@ -76,6 +76,10 @@ struct QmcProblem {
     int site0;            // Philox site word = site0 + local site (served requests: the key's site)
     int delay_k;          // FP32-pair sweeps: delayed-update depth (<= 1: rank-1 updates)
     int refresh_stagger;  // 1: chain (site, c) refreshes when nsw + site + c = 0 mod refresh_every
+    int slot_mult;        // FP64 / FP32-pair sweeps: block slot s runs chain (s slot_mult) mod
+                          // nchain (gcd(slot_mult, nchain) = 1), so that a block's chains come
+                          // from sites across the trap and blocks carry similar work; 1: slot s
+                          // runs chain s
     const double* gtau;   // [nsite][2][L]  bath g~0(tau_m)
     double* g0inv;        // [nsite][2][L*L] inverse bath matrices (rebuilt with the bath)
     double* G;            // [nchain][2][L*L] (FP64 state, or FP64 scratch of the FP32 path)

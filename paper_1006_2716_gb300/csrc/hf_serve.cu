@@ -280,6 +280,7 @@ hf_status start_launch(hf_srv* S, Launch& Lh) {
         q.n_measure = p.n_measure;
         q.refresh_every = p.refresh_every;
         q.refresh_stagger = p.refresh_stagger;
+        q.slot_mult = 1;
         q.bin_size = p.bin_size;
         q.max_bins = S->nb;
         q.refresh_first = 1;

@@ -599,9 +599,11 @@ template <int L, int TW>
 __device__ void run_team_df(const QmcProblem& P, int blk, unsigned char* smem) {
     constexpr int per_block = kBlock / (32 * TW);
     const int team = static_cast<int>(threadIdx.x) / (32 * TW);
-    const int c = blk * per_block + team;
+    const int slot = blk * per_block + team;
+    const long long m = P.slot_mult > 0 ? P.slot_mult : 1;
+    const int c = static_cast<int>(slot * m % P.nchain);
     const size_t stride = team_bytes(L) + delayed_bytes(L, P.delay_k);
-    if (c >= P.nchain) return;
+    if (slot >= P.nchain) return;
     const int tid = static_cast<int>(threadIdx.x) % (32 * TW);
     if constexpr (TW == 1) {   // delayed updates run with one warp per chain
         if (P.delay_k > 1) {

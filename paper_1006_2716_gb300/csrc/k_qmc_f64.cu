@@ -337,8 +337,10 @@ template <int L, int TW>
 __device__ void run_team(const QmcProblem& P, int blk, unsigned char* smem) {
     constexpr int per_block = kBlock / (32 * TW);
     const int team = static_cast<int>(threadIdx.x) / (32 * TW);
-    const int c = blk * per_block + team;
-    if (c < P.nchain)
+    const int slot = blk * per_block + team;
+    const long long m = P.slot_mult > 0 ? P.slot_mult : 1;
+    const int c = static_cast<int>(slot * m % P.nchain);
+    if (slot < P.nchain)
         qmc_chain<L, TW>(P, c, smem + team * team_bytes(L), static_cast<int>(threadIdx.x) % (32 * TW));
 }
 
