@@ -398,8 +398,8 @@ DF_OPS_PER_FMA = 12          # FP32-pipe ops of one double-float multiply-add (l
 # DRAM bytes (read + write) of one full-size launch, from one ncu capture of the kernel built from
 # sources whose sha256 starts with the given prefix (the capture's command and counters are kept
 # in the profile summaries); a kernel whose sources changed since reports null.
-MEASURED_TRAFFIC = {"qmc_f64_kernel": (2377728 + 1792, "4d68298916e948ee"),
-                    "qmc_df64_kernel": (2.628e6 + 1.452e6, "f0ade2fccbd67061"),
+MEASURED_TRAFFIC = {"qmc_f64_kernel": (2295808 + 3584, "04c6f020ee92be69"),
+                    "qmc_df64_kernel": (2386432 + 3584, "5e3b37f3293b93e3"),
                     # the lattice step of the slab16 workload (N = 1024, b = 128, 500 matrices)
                     "lattice_kernel:slab16": (652.8e6 + 941.8e6, "cb1522e9ec00d909"),
                     # box16p (N = 4096, b = 512): one launch of 250 matrices
