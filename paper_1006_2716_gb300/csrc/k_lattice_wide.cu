@@ -26,6 +26,7 @@
 
 #include "k_lattice.cuh"
 #include "k_lattice_dev.cuh"
+#include "tc_ozaki.cuh"
 
 namespace hfk {
 namespace {
@@ -46,7 +47,47 @@ size_t solve_smem(int b) {       // kR windows of b + 1 entries
     return static_cast<size_t>(kR) * (b + 1) * sizeof(double2);
 }
 
-size_t wide_smem(int b) { return std::max(factor_smem(b), solve_smem(b)); }
+// ---- the trailing update on the tensor cores (128 <= b <= kTcMaxBand) ----
+// A[r][c] -= sum_j L_rj W_cj, W_cj = D_j L_cj, over the trailing triangle, as exact digit
+// products (the error-free splitting of tc_ozaki.cuh).  With A = [Re W | Im W] (128 trailing
+// columns c per tile, K = 32: the panel's 16 columns, real and imaginary parts) and
+// B_re = [Re L | -Im L], B_im = [Im L | Re L] (32 trailing rows r per tile), Re and Im of the
+// sum are A B_re^T and A B_im^T.  Each operand row gets a power-of-two scale and kTD balanced
+// base-256 digits; the levels n = s + t <= kTNL are kept (the dropped ones stay below 2^-58 of
+// the scales), each an exact FP32 accumulator in TMEM (K = 32 terms of at most 2^14, at most 7
+// per level: below 2^22), eight levels x (Re, Im) x 32 rows = all 512 TMEM columns.  The
+// epilogue combines a tile's levels in 64-bit integers and subtracts the rounded sums from the
+// band buffer in FP64: one DADD per part and entry instead of 16 complex multiply-adds.
+constexpr int kTD = 7;                  // digits of an operand
+constexpr int kTNL = kTD + 2;           // highest level kept
+constexpr int kTM = 128;                // trailing columns c per tile (MMA M)
+constexpr int kTN = 32;                 // trailing rows r per tile (MMA N)
+constexpr int kTK = 32;                 // K
+constexpr int kPlaneA = kTM * kTK * 2;  // bytes of one digit plane of A (K-major core matrices)
+constexpr int kPlaneB = kTN * kTK * 2;
+constexpr int kTcMinBand = 128;
+constexpr int kTcMaxBand = 520;
+
+struct TcSmem {                         // behind the panel, 1024-byte aligned
+    unsigned char a[kTD * kPlaneA];
+    unsigned char bre[kTD * kPlaneB];
+    unsigned char bim[kTD * kPlaneB];
+    int ta[kTM];                        // scales of A's rows (the tile's columns c)
+    int tb[kTN];                        // scales of B's rows (the tile's rows r)
+    uint64_t bar;                       // MMA completion
+    uint32_t tmem;                      // TMEM base address
+    int fail;                           // an MMA wait ran out: no more tensor-core work
+};
+
+size_t tc_offset(int b) { return (factor_smem(b) + 1023) / 1024 * 1024; }
+__device__ __forceinline__ int tc_offset_dev(int b) {
+    return ((kNB * (kNB + b) + kNB) * static_cast<int>(sizeof(double2)) + 1023) / 1024 * 1024;
+}
+
+size_t wide_smem(int b, bool tc) {
+    const size_t f = tc ? tc_offset(b) + sizeof(TcSmem) : factor_smem(b);
+    return std::max(f, solve_smem(b));
+}
 
 __device__ __forceinline__ double2 cfma(double2 acc, double2 a, double2 b) {  // acc + a b
     return make_double2(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
@@ -62,9 +103,205 @@ __device__ __forceinline__ int load_acquire(const int* p) {
     return v;
 }
 
+// kTD balanced base-256 digits of 8 fixed-point magnitudes (top down, each rounded) into the
+// digit planes at base (plane stride `plane`), 16 bytes at offset off of each.
+__device__ __forceinline__ void put_digits(const unsigned long long (&U)[8], const bool (&neg)[8],
+                                           unsigned char* base, int plane, int off) {
+    long long r[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) r[q] = static_cast<long long>(U[q]);
+#pragma unroll
+    for (int sd = 1; sd <= kTD; ++sd) {
+        const int sh = 62 - 8 * sd;
+        int d[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const long long v = (r[q] + (1ll << (sh - 1))) >> sh;
+            r[q] -= v << sh;
+            d[q] = static_cast<int>(v);
+        }
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) w[q] = tc::bf16x2_digits(d[2 * q], d[2 * q + 1], neg[2 * q], neg[2 * q + 1]);
+        *reinterpret_cast<uint4*>(base + (sd - 1) * plane + off) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// Digit-plane offset of element (row m, k) of a K-major operand with K = 32: 8-row x 16-byte
+// core matrices, 128 bytes apart along K, 512 bytes apart along the rows.
+__device__ __forceinline__ int core_off(int m, int kg) { return ((m >> 3) * 4 + kg) * 128 + (m & 7) * 16; }
+
+__device__ __forceinline__ int scale_of(int e) { return e == tc::kNoExp ? 0 : e + 2; }
+
+// The trailing update of one panel on the tensor cores: rows and columns nb .. tend of the panel
+// P (RP rows per column, L_ij scaled, D_j on the diagonal) into the band buffer Bq at k0.
+// ph: the mbarrier's phase bit, flipped by every wait.
+__device__ void trailing_tc(TcSmem& T, const double2* P, int RP, int nb, int tend, double2* Bq,
+                            int k0, int S, uint32_t& ph) {
+    const int tid = static_cast<int>(threadIdx.x), lane = tid & 31, warp = tid >> 5;
+    const int rows = tend - nb + 1;
+    if (rows <= 0) return;
+    const double2 zero = make_double2(0.0, 0.0);
+    for (int c0 = 0; c0 < rows; c0 += kTM) {
+        // A: W_cj = D_j L_cj of the tile's columns c = nb + c0 + m, m < 128 (zero past tend)
+        if (tid < kTM) {
+            const int c = nb + c0 + tid;
+            int e = tc::kNoExp;
+            if (c <= tend)
+                for (int j = 0; j < kNB; ++j) {
+                    const double2 w = cmul(P[j * RP + j], P[j * RP + c]);
+                    e = max(e, max(tc::exp_of(w.x), tc::exp_of(w.y)));
+                }
+            T.ta[tid] = scale_of(e);
+        }
+        __syncthreads();
+        {
+            const int m = tid & (kTM - 1), kg = tid >> 7;     // 8 K of one row per thread
+            const int c = nb + c0 + m;
+            const int Ta = T.ta[m];
+            unsigned long long U[8];
+            bool neg[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int j = (kg & 1) * 8 + q;
+                double x = 0.0;
+                if (c <= tend) {
+                    const double2 w = cmul(P[j * RP + j], P[j * RP + c]);
+                    x = kg < 2 ? w.x : w.y;
+                }
+                U[q] = tc::to_fixed_mag(x, Ta, neg[q]);
+            }
+            put_digits(U, neg, T.a, kPlaneA, core_off(m, kg));
+        }
+        for (int r0 = c0 - (c0 % kTN); r0 < rows; r0 += kTN) {
+            // B: L_rj of the tile's rows r = nb + r0 + n, n < 32, as [Re | -Im] and [Im | Re]
+            if (tid < kTN) {
+                const int r = nb + r0 + tid;
+                int e = tc::kNoExp;
+                if (r <= tend)
+                    for (int j = 0; j < kNB; ++j) {
+                        const double2 l = P[j * RP + r];
+                        e = max(e, max(tc::exp_of(l.x), tc::exp_of(l.y)));
+                    }
+                T.tb[tid] = scale_of(e);
+            }
+            __syncthreads();
+            if (tid < 2 * kTN * 4) {
+                const bool im = tid >= kTN * 4;
+                const int u = tid & (kTN * 4 - 1);
+                const int nr = u & (kTN - 1), kg = u >> 5;
+                const int r = nb + r0 + nr;
+                const int Tb = T.tb[nr];
+                unsigned long long U[8];
+                bool neg[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int j = (kg & 1) * 8 + q;
+                    const double2 l = r <= tend ? P[j * RP + r] : zero;
+                    // re: k < 16 Re L, k >= 16 -Im L;  im: k < 16 Im L, k >= 16 Re L
+                    double x;
+                    if (!im) x = kg < 2 ? l.x : -l.y;
+                    else x = kg < 2 ? l.y : l.x;
+                    U[q] = tc::to_fixed_mag(x, Tb, neg[q]);
+                }
+                put_digits(U, neg, im ? T.bim : T.bre, kPlaneB, core_off(nr, kg));
+            }
+            tc::fence_async_shared();
+            tc::tc_fence_before_sync();
+            __syncthreads();
+            if (tid == 0 && !T.fail) {
+                tc::tc_fence_after_sync();
+                constexpr uint32_t idesc = tc::idesc_bf16_f32(kTM, kTN);
+                const uint32_t a0 = tc::smem_addr(T.a), re0 = tc::smem_addr(T.bre), im0 = tc::smem_addr(T.bim);
+#pragma unroll
+                for (int n = 2; n <= kTNL; ++n) {
+                    const int smin = n - kTD > 1 ? n - kTD : 1, smax = n - 1 < kTD ? n - 1 : kTD;
+                    for (int sd = smin; sd <= smax; ++sd) {
+                        const int td = n - sd;
+#pragma unroll
+                        for (int kk = 0; kk < 2; ++kk) {
+                            const uint64_t ad = tc::smem_desc(a0 + (sd - 1) * kPlaneA + kk * 256, 128, 512);
+                            const bool accum = !(sd == smin && kk == 0);
+                            tc::mma_bf16(T.tmem + (n - 2) * kTN, ad,
+                                         tc::smem_desc(re0 + (td - 1) * kPlaneB + kk * 256, 128, 512), idesc, accum);
+                            tc::mma_bf16(T.tmem + 256 + (n - 2) * kTN, ad,
+                                         tc::smem_desc(im0 + (td - 1) * kPlaneB + kk * 256, 128, 512), idesc, accum);
+                        }
+                    }
+                }
+                tc::mma_commit(&T.bar);
+            }
+            // every thread waits for the MMAs (bounded; a wait that runs out stops the tensor-core
+            // work of this block, the caller reports HF_ETIMEOUT)
+            bool ok = true;
+            if (!T.fail) ok = tc::mbar_wait(&T.bar, ph);
+            ph ^= 1u;
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) T.fail = 1;
+                return;
+            }
+            tc::tc_fence_after_sync();
+            // epilogue: lane quarter (warp & 3) holds columns c = c0 + 32 (warp & 3) + lane; the
+            // four warps of a quarter take 8 rows each
+            {
+                const int ql = warp & 3, g = warp >> 2;
+                const int m = 32 * ql + lane;
+                const int c = nb + c0 + m;
+                const uint32_t trow = T.tmem + (static_cast<uint32_t>(32 * ql) << 16) + 8 * g;
+                long long Qr[8], Qi[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) Qr[k] = Qi[k] = 0;
+#pragma unroll
+                for (int n0 = 2; n0 <= kTNL; n0 += 2) {
+                    uint32_t v[4][8];
+#pragma unroll
+                    for (int u = 0; u < 2; ++u)
+                        if (n0 + u <= kTNL) {
+                            tc::tmem_ld8_async(trow + (n0 + u - 2) * kTN, v[2 * u]);
+                            tc::tmem_ld8_async(trow + 256 + (n0 + u - 2) * kTN, v[2 * u + 1]);
+                        }
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int u = 0; u < 2; ++u)
+                        if (n0 + u <= kTNL) {
+                            const int sh = 54 - 8 * (n0 + u);
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) {
+                                const long long dr = __float2int_rz(__uint_as_float(v[2 * u][k]));
+                                const long long di = __float2int_rz(__uint_as_float(v[2 * u + 1][k]));
+                                Qr[k] += sh >= 0 ? (dr << sh) : ((dr + (1ll << (-sh - 1))) >> (-sh));
+                                Qi[k] += sh >= 0 ? (di << sh) : ((di + (1ll << (-sh - 1))) >> (-sh));
+                            }
+                        }
+                }
+                if (c <= tend) {
+                    const int Ta = T.ta[m];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int nr = 8 * g + k;
+                        const int r = nb + r0 + nr;
+                        if (r >= c && r <= tend) {
+                            const int E = Ta + T.tb[nr] - 54;
+                            double2* a = Bq + static_cast<size_t>(k0 + c) * S + (r - c);
+                            const double2 x = *a;
+                            *a = make_double2(x.x - tc::fixed_to_double(Qr[k], E), x.y - tc::fixed_to_double(Qi[k], E));
+                        }
+                    }
+                }
+            }
+            tc::tc_fence_before_sync();
+            __syncthreads();   // TMEM and the B planes are reused by the next tile
+        }
+        __syncthreads();       // the A planes are reused by the next column tile
+    }
+}
+
 // Matrix qi of the launch: assembly and blocked band L D L^T into its band buffer (column k: D_k
-// at d = 0, L_{k+d,k} at d >= 1).  Sets bad on a vanishing or non-finite pivot.
-__device__ void factor_matrix(const LatticeArgs& A, int q0, int qi, unsigned char* smem, bool& bad) {
+// at d = 0, L_{k+d,k} at d >= 1).  Sets bad on a vanishing or non-finite pivot.  TC: the trailing
+// updates run on the tensor cores (T: the block's tensor-core state, ph its mbarrier phase).
+template <bool TC>
+__device__ void factor_matrix(const LatticeArgs& A, int q0, int qi, unsigned char* smem, bool& bad,
+                              TcSmem* T, uint32_t& ph) {
     int sp, n;
     item_of(A, q0 + qi, sp, n);
     const int N = A.N, b = A.b, S = b + 1, RP = kNB + b;
@@ -124,6 +361,13 @@ __device__ void factor_matrix(const LatticeArgs& A, int q0, int qi, unsigned cha
         //     A[r][c] -= sum_j L_rj w_j with w_j = D_j L_cj; a warp takes a column, 256 rows at a
         //     time (8 a lane); lane j forms w_j once and the warp reads it by shuffle
         const int tend = min(nb - 1 + b, rmax - 1);
+        if constexpr (TC) {
+            if (nb == kNB) {   // full panels; the last, narrower one (and small tails) below
+                trailing_tc(*T, P, RP, nb, tend, Bq, k0, S, ph);
+                __syncthreads();
+                continue;
+            }
+        }
         for (int c = nb + warp; c <= tend; c += kWarps) {
             double2* col = Bq + static_cast<size_t>(k0 + c) * S;     // col[r - c]
             const double2 wl = lane < nb ? cmul(P[lane * RP + lane], P[lane * RP + c]) : zero;
@@ -232,24 +476,40 @@ __device__ void solve_chunk(const LatticeArgs& A, int q0, int qi, int ch, unsign
 // nq * nchunk solve tasks (matrix-major); blocks take them in order from work[0].  A block that
 // finishes a factorisation raises work[1 + qi]; a solve task waits for its matrix's flag (it was
 // handed out earlier, so a running block is factoring it), at most wait_cycles (several times
-// what one factorisation takes), after which it reports HF_ETIMEOUT and skips.  So the blocks left over when the factorisations run out take
-// the solves of the matrices already factored, instead of idling through a last partial wave.
-template <int DPT>
+// what one factorisation takes), after which it reports HF_ETIMEOUT and skips.  So the blocks
+// left over when the factorisations run out take the solves of the matrices already factored,
+// instead of idling through a last partial wave.  TC: the block holds all of TMEM and an
+// mbarrier for the tensor-core trailing updates, from its first task to its last.
+template <int DPT, bool TC>
 __global__ void __launch_bounds__(kT, 1) lattice_wide_kernel(const LatticeArgs A, int q0, int nq,
                                                              int nchunk, int* work,
                                                              long long wait_cycles) {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ int task_s, ready_s;
     const int tid = static_cast<int>(threadIdx.x);
     const int ntask = nq * (1 + nchunk);
     bool bad = false;
+    TcSmem* T = nullptr;
+    uint32_t ph = 0u;
+    if constexpr (TC) {
+        T = reinterpret_cast<TcSmem*>(smem + tc_offset_dev(A.b));
+        if (tid == 0) {
+            T->fail = 0;
+            tc::mbar_init(&T->bar, 1);
+            tc::mbar_init_fence();
+        }
+        if (tid < 32) tc::tmem_alloc(&T->tmem, 512);
+        tc::tc_fence_before_sync();
+        __syncthreads();
+        tc::tc_fence_after_sync();
+    }
     for (;;) {
         if (tid == 0) task_s = atomicAdd(work, 1);
         __syncthreads();
         const int t = task_s;
         if (t >= ntask) break;
         if (t < nq) {
-            factor_matrix(A, q0, t, smem, bad);
+            factor_matrix<TC>(A, q0, t, smem, bad, T, ph);
             __syncthreads();                         // every store of the factors issued
             if (tid == 0) {
                 __threadfence();
@@ -272,6 +532,12 @@ __global__ void __launch_bounds__(kT, 1) lattice_wide_kernel(const LatticeArgs A
         }
         __syncthreads();                             // task_s and the shared memory are reused
     }
+    if constexpr (TC) {
+        __syncthreads();
+        tc::tc_fence_after_sync();
+        if (tid < 32) tc::tmem_dealloc(T->tmem, 512);
+        if (tid == 0 && T->fail) atomicExch(A.status, static_cast<int>(HF_ETIMEOUT));
+    }
     if (bad) atomicExch(A.status, static_cast<int>(HF_ENUMERIC));
 }
 
@@ -286,9 +552,12 @@ cudaError_t launch_lattice_wide(const LatticeArgs& a, int q0, int nq, cudaStream
     if (a.b < 0 || a.b > kWideMaxBand || a.wide_npos <= 0 || !a.wide_pos || !a.wide_out || !a.work)
         return cudaErrorInvalidValue;
     const bool one = a.b <= kT;
-    auto kern = one ? lattice_wide_kernel<1> : lattice_wide_kernel<2>;
+    const bool tcu = a.b >= kTcMinBand && a.b <= kTcMaxBand;
+    auto kern = tcu ? (one ? lattice_wide_kernel<1, true> : lattice_wide_kernel<2, true>)
+                    : (one ? lattice_wide_kernel<1, false> : lattice_wide_kernel<2, false>);
+    const size_t smax = std::max(wide_smem(kWideMaxBand, false), wide_smem(kTcMaxBand, true));
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(wide_smem(kWideMaxBand)));
+                                         static_cast<int>(smax));
     int dev = 0, sms = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -299,7 +568,7 @@ cudaError_t launch_lattice_wide(const LatticeArgs& a, int q0, int nq, cudaStream
     // a factorisation takes about N b^2 SM cycles (N b^2 / 2 complex multiply-adds of 4 DFMA at
     // 2 DFMA per cycle); a solve task waits at most 8 times that, and at least 2^31 cycles
     const long long wait = (1ll << 31) + 8ll * a.N * static_cast<long long>(a.b) * a.b;
-    kern<<<grid, kT, wide_smem(a.b), st>>>(a, q0, nq, nchunk, a.work, wait);
+    kern<<<grid, kT, wide_smem(a.b, tcu), st>>>(a, q0, nq, nchunk, a.work, wait);
     return cudaGetLastError();
 }
 
