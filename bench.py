@@ -808,18 +808,33 @@ def run_lattice3d(args):
     qroof = qmc_roofline(2, L, nc, sweeps, accepts, cfg["n_measure"], n_refresh,
                          statistics.mean(qmc_ms) / 1e3, "qmc_df64_kernel")
     qroof["acceptance"] = accepts / proposals
-    lform, lat_launches, cfma = hf.hf_get_lattice_plan(ctx.handle)
+    lform, lat_launches, cfma, tc_flops = hf.hf_get_lattice_plan(ctx.handle)
     fl = 8.0 * cfma * nspin * nw
     lat_s = phase[0] / 1e3
     lkern = "lattice_wide_kernel" if lform == 1 else "lattice_kernel"
-    lroof = {"bound": "alu", "achieved": fl / lat_s / 1e12, "peak": FP64_PEAK_TFLOPS,
-             "unit": "TFLOP/s", "frac": fl / lat_s / 1e12 / FP64_PEAK_TFLOPS,
-             "traffic": measured_traffic("lattice_kernel:" + name),
-             "kernel": lkern, "matrices": nspin * nw, "N": N, "band": b,
-             "form": "blocked band L D L^T + forward solves" if lform == 1
-             else "band L D L^T + selected inversion in a shared-memory window",
-             "seconds": lat_s,
-             "peak_source": "FP64 nominal: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz"}
+    form = ("blocked band L D L^T + forward solves" if lform == 1
+            else "band L D L^T + selected inversion in a shared-memory window")
+    if tc_flops > 0:
+        # trailing updates as exact digit products on the tensor cores: the roof is the bf16
+        # pipe; the FP64-equivalent rate of the algorithm is reported beside it
+        tfl = tc_flops * nspin * nw
+        lroof = {"bound": "tensor", "achieved": tfl / lat_s / 1e12, "peak": MEASURED_BF16_SUSTAINED,
+                 "unit": "TFLOP/s", "frac": tfl / lat_s / 1e12 / MEASURED_BF16_SUSTAINED,
+                 "traffic": measured_traffic("lattice_kernel:" + name),
+                 "kernel": lkern, "matrices": nspin * nw, "N": N, "band": b,
+                 "form": form + ", trailing updates on the tensor cores", "seconds": lat_s,
+                 "work": "bf16 flops of the trailing updates' digit products (the panel "
+                         "factorisations and forward solves run on the FP64 pipe)",
+                 "algorithmic_fp64_tflops": fl / lat_s / 1e12,
+                 "algorithmic_fp64_vs_fp64_nominal": fl / lat_s / 1e12 / FP64_PEAK_TFLOPS,
+                 "peak_source": "measured dense bf16 (cuBLAS, sustained) of this GPU"}
+    else:
+        lroof = {"bound": "alu", "achieved": fl / lat_s / 1e12, "peak": FP64_PEAK_TFLOPS,
+                 "unit": "TFLOP/s", "frac": fl / lat_s / 1e12 / FP64_PEAK_TFLOPS,
+                 "traffic": measured_traffic("lattice_kernel:" + name),
+                 "kernel": lkern, "matrices": nspin * nw, "N": N, "band": b,
+                 "form": form, "seconds": lat_s,
+                 "peak_source": "FP64 nominal: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz"}
     dominant = lroof if phase[0] > phase[2] else qroof
     geo = ("%dx%d slab of %d layers, periodic in all directions, cylindrical trap" % (cfg["Lx"], cfg["Ly"], cfg["Lz"])
            if cfg["geometry"] == 3 else

@@ -215,8 +215,11 @@ hf_status hf_get_drift(hf_ctx* ctx, double* max_drift, unsigned long long* refre
  * global memory with forward solves L^{-1} e_k at the listed positions (see lattice_form);
  * *launches = kernel launches per lattice step; *cfma = complex multiply-adds that the form's
  * algorithm performs per (w_n, sigma) matrix (factorisation plus selected inversion, or plus
- * the forward solves), averaged over the spin matrices.  Any pointer may be NULL. */
-hf_status hf_get_lattice_plan(const hf_ctx* ctx, int* form, int* launches, double* cfma);
+ * the forward solves), averaged over the spin matrices; *tc_flops = bf16 flops per matrix of
+ * the exact digit products with which the blocked form runs its trailing updates on the tensor
+ * cores (band half-widths 128 .. 520; 0 otherwise).  Any pointer may be NULL. */
+hf_status hf_get_lattice_plan(const hf_ctx* ctx, int* form, int* launches, double* cfma,
+                              double* tc_flops);
 
 /* Refreshes of the mixed-precision form at L = 128 since the last hf_clear_measurements: chains
  * refreshed by the Newton steps on the tensor cores; chains those steps handed to the FP64

@@ -834,7 +834,8 @@ hf_status hf_init(const hf_params* p, void* d_ws, size_t ws_bytes, hf_ctx** out)
     return HF_OK;
 }
 
-hf_status hf_get_lattice_plan(const hf_ctx* c, int* form, int* launches, double* cfma) {
+hf_status hf_get_lattice_plan(const hf_ctx* c, int* form, int* launches, double* cfma,
+                              double* tc_flops) {
     if (!c) return fail(nullptr, HF_EINVAL, "null context");
     const int N = c->lat.N, b = c->lat.b;
     const int nspin = c->lat.gdn.empty() ? 2 : 1;
@@ -860,6 +861,7 @@ hf_status hf_get_lattice_plan(const hf_ctx* c, int* form, int* launches, double*
     if (form) *form = c->lat_wide ? 1 : 0;
     if (launches) *launches = nl * (c->lat_wide ? 2 : 1);
     if (cfma) *cfma = f;
+    if (tc_flops) *tc_flops = c->lat_wide ? hfk::lattice_wide_tc_flops(N, b) : 0.0;
     return HF_OK;
 }
 

@@ -39,6 +39,8 @@ cudaError_t launch_lattice(const LatticeArgs& a, int q0, int nq, cudaStream_t st
 // Blocked band form (k_lattice_wide.cu), every b <= lattice_wide_max_band().
 int lattice_wide_max_band();
 int lattice_wide_rhs_per_block();
+// bf16 flops of the tensor-core trailing updates per matrix (0 where the band keeps DFMA)
+double lattice_wide_tc_flops(int N, int b);
 cudaError_t launch_lattice_wide(const LatticeArgs& a, int q0, int nq, cudaStream_t st);
 
 // Lattice step over all nspin * nw matrices with the band buffers in a fixed 16 MiB device array

@@ -127,6 +127,27 @@ __device__ __forceinline__ void put_digits(const unsigned long long (&U)[8], con
     }
 }
 
+// The same for 4 values (8 bytes at off of each plane).
+__device__ __forceinline__ void put_digits4(const unsigned long long (&U)[4], const bool (&neg)[4],
+                                            unsigned char* base, int plane, int off) {
+    long long r[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) r[q] = static_cast<long long>(U[q]);
+#pragma unroll
+    for (int sd = 1; sd <= kTD; ++sd) {
+        const int sh = 62 - 8 * sd;
+        int d[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const long long v = (r[q] + (1ll << (sh - 1))) >> sh;
+            r[q] -= v << sh;
+            d[q] = static_cast<int>(v);
+        }
+        *reinterpret_cast<uint2*>(base + (sd - 1) * plane + off) =
+            make_uint2(tc::bf16x2_digits(d[0], d[1], neg[0], neg[1]), tc::bf16x2_digits(d[2], d[3], neg[2], neg[3]));
+    }
+}
+
 // Digit-plane offset of element (row m, k) of a K-major operand with K = 32: 8-row x 16-byte
 // core matrices, 128 bytes apart along K, 512 bytes apart along the rows.
 __device__ __forceinline__ int core_off(int m, int kg) { return ((m >> 3) * 4 + kg) * 128 + (m & 7) * 16; }
@@ -143,16 +164,22 @@ __device__ void trailing_tc(TcSmem& T, const double2* P, int RP, int nb, int ten
     if (rows <= 0) return;
     const double2 zero = make_double2(0.0, 0.0);
     for (int c0 = 0; c0 < rows; c0 += kTM) {
-        // A: W_cj = D_j L_cj of the tile's columns c = nb + c0 + m, m < 128 (zero past tend)
-        if (tid < kTM) {
-            const int c = nb + c0 + tid;
+        // A: W_cj = D_j L_cj of the tile's columns c = nb + c0 + m, m < 128 (zero past tend);
+        // scales from 4 threads per column (4 j each, adjacent lanes)
+        {
+            const int m = tid >> 2, part = tid & 3;
+            const int c = nb + c0 + m;
             int e = tc::kNoExp;
             if (c <= tend)
-                for (int j = 0; j < kNB; ++j) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int j = 4 * part + q;
                     const double2 w = cmul(P[j * RP + j], P[j * RP + c]);
                     e = max(e, max(tc::exp_of(w.x), tc::exp_of(w.y)));
                 }
-            T.ta[tid] = scale_of(e);
+            e = max(e, __shfl_xor_sync(0xffffffffu, e, 1));
+            e = max(e, __shfl_xor_sync(0xffffffffu, e, 2));
+            if (part == 0) T.ta[m] = scale_of(e);
         }
         __syncthreads();
         {
@@ -174,29 +201,33 @@ __device__ void trailing_tc(TcSmem& T, const double2* P, int RP, int nb, int ten
             put_digits(U, neg, T.a, kPlaneA, core_off(m, kg));
         }
         for (int r0 = c0 - (c0 % kTN); r0 < rows; r0 += kTN) {
-            // B: L_rj of the tile's rows r = nb + r0 + n, n < 32, as [Re | -Im] and [Im | Re]
-            if (tid < kTN) {
-                const int r = nb + r0 + tid;
+            // B: L_rj of the tile's rows r = nb + r0 + n, n < 32, as [Re | -Im] and [Im | Re];
+            // scales from 16 threads per row (one j each, a half warp), digits 4 K per thread
+            {
+                const int nr = tid >> 4, j = tid & 15;
+                const int r = nb + r0 + nr;
                 int e = tc::kNoExp;
-                if (r <= tend)
-                    for (int j = 0; j < kNB; ++j) {
-                        const double2 l = P[j * RP + r];
-                        e = max(e, max(tc::exp_of(l.x), tc::exp_of(l.y)));
-                    }
-                T.tb[tid] = scale_of(e);
+                if (r <= tend) {
+                    const double2 l = P[j * RP + r];
+                    e = max(tc::exp_of(l.x), tc::exp_of(l.y));
+                }
+#pragma unroll
+                for (int o = 1; o < 16; o <<= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+                if (j == 0) T.tb[nr] = scale_of(e);
             }
             __syncthreads();
-            if (tid < 2 * kTN * 4) {
-                const bool im = tid >= kTN * 4;
-                const int u = tid & (kTN * 4 - 1);
-                const int nr = u & (kTN - 1), kg = u >> 5;
+            {
+                const bool im = tid >= 256;
+                const int u = tid & 255;
+                const int nr = u & (kTN - 1), kq = u >> 5;   // K quarter-group: 4 K at 4 kq
+                const int kg = kq >> 1;
                 const int r = nb + r0 + nr;
                 const int Tb = T.tb[nr];
-                unsigned long long U[8];
-                bool neg[8];
+                unsigned long long U[4];
+                bool neg[4];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int j = (kg & 1) * 8 + q;
+                for (int q = 0; q < 4; ++q) {
+                    const int j = ((4 * kq + q) & 15);
                     const double2 l = r <= tend ? P[j * RP + r] : zero;
                     // re: k < 16 Re L, k >= 16 -Im L;  im: k < 16 Im L, k >= 16 Re L
                     double x;
@@ -204,17 +235,20 @@ __device__ void trailing_tc(TcSmem& T, const double2* P, int RP, int nb, int ten
                     else x = kg < 2 ? l.y : l.x;
                     U[q] = tc::to_fixed_mag(x, Tb, neg[q]);
                 }
-                put_digits(U, neg, im ? T.bim : T.bre, kPlaneB, core_off(nr, kg));
+                put_digits4(U, neg, im ? T.bim : T.bre, kPlaneB, core_off(nr, kg) + (kq & 1) * 8);
             }
             tc::fence_async_shared();
             tc::tc_fence_before_sync();
             __syncthreads();
-            if (tid == 0 && !T.fail) {
+            // the MMAs: lane 0 of warps 0 .. 3, each owning whole levels (first and last paired:
+            // 2+9, 3+8, 4+7, 5+6), committing to the mbarrier (which expects four arrivals)
+            if ((tid & 31) == 0 && warp < 4 && !T.fail) {
                 tc::tc_fence_after_sync();
                 constexpr uint32_t idesc = tc::idesc_bf16_f32(kTM, kTN);
                 const uint32_t a0 = tc::smem_addr(T.a), re0 = tc::smem_addr(T.bre), im0 = tc::smem_addr(T.bim);
 #pragma unroll
                 for (int n = 2; n <= kTNL; ++n) {
+                    if (((n - 2) < (kTNL - n) ? (n - 2) : (kTNL - n)) != warp) continue;
                     const int smin = n - kTD > 1 ? n - kTD : 1, smax = n - 1 < kTD ? n - 1 : kTD;
                     for (int sd = smin; sd <= smax; ++sd) {
                         const int td = n - sd;
@@ -472,6 +506,227 @@ __device__ void solve_chunk(const LatticeArgs& A, int q0, int qi, int ch, unsign
     }
 }
 
+// The same forward solves with the bulk of each 16-column step on the tensor cores (128 <= b <=
+// kTcMaxBand).  Step J: (i) the panel's own triangle column by column (DFMA), which finishes
+// y_J .. y_{J+15} and adds their y^2 / D to G; (ii) their slots are cut into the digits of
+// B_re = [Re y | -Im y], B_im = [Im y | Re y] (16 right-hand sides, K = 32) and then freed for
+// the indices J + S .. J + S + 15; (iii) the rows J + 16 .. J + 15 + b lose
+// sum_j L_rj y_j, formed as in trailing_tc with A = [Re L | Im L] (128 rows per tile) and
+// N = 16 (levels x (Re, Im) x 16 = 256 TMEM columns), and subtracted from their window slots.
+constexpr int kSN = 16;                      // right-hand sides = MMA N of the solve
+constexpr int kPlaneS = kSN * kTK * 2;       // one digit plane of the y panel
+static_assert(kSN == kR && 2 * kTD * kPlaneS <= 2 * kTD * kPlaneB, "solve planes fit");
+
+__device__ void solve_chunk_tc(const LatticeArgs& A, int q0, int qi, int ch, unsigned char* smem,
+                               TcSmem& T, uint32_t& ph) {
+    int sp, n;
+    item_of(A, q0 + qi, sp, n);
+    const int N = A.N, b = A.b, S = b + 1;
+    const int tid = static_cast<int>(threadIdx.x), lane = tid & 31, warp = tid >> 5;
+    const double2 zero = make_double2(0.0, 0.0), one = make_double2(1.0, 0.0);
+    const double2* Bq = A.scratch + static_cast<size_t>(qi) * N * S;
+    const int* pos = A.wide_pos + static_cast<size_t>(sp) * A.wide_npos + ch * kR;
+    const int* out = A.wide_out + static_cast<size_t>(sp) * A.wide_npos + ch * kR;
+    const int nr = min(kR, A.wide_npos - ch * kR);
+    double2* Y = reinterpret_cast<double2*>(smem);   // [kR][S], index j in slot j mod S
+    const int j0 = pos[0];
+    for (int e = tid; e < kR * S; e += kT) Y[e] = zero;
+    __syncthreads();
+    int pmine = -1;
+    if (tid < nr) {
+        pmine = pos[tid];
+        if (pmine - j0 < S) Y[tid * S + pmine % S] = one;
+    }
+    __syncthreads();
+    double2 acc = zero;
+    unsigned char* bre = T.bre;
+    unsigned char* bim = T.bim;
+    for (int J = j0; J < N; J += kNB) {
+        const int nb = min(kNB, N - J);
+        // (i) the panel's triangle: thread (rhs r, panel row i)
+        for (int jj = 0; jj < nb; ++jj) {
+            const int j = J + jj, sj = j % S;
+            if (tid < kR * kNB) {
+                const int r = tid >> 4, i = tid & 15;
+                const double2 yj = Y[r * S + sj];
+                if (i > jj && i < nb) {
+                    const int si = (J + i) % S;
+                    Y[r * S + si] = cfms(Y[r * S + si], __ldcg(Bq + static_cast<size_t>(j) * S + (i - jj)), yj);
+                }
+            }
+            if (tid < nr) {
+                const double2 yj = Y[tid * S + sj];
+                acc = cfma(acc, cmul(yj, yj), crecip(__ldcg(Bq + static_cast<size_t>(j) * S)));
+            }
+            __syncthreads();
+        }
+        const int rows = min(b, N - J - nb);   // rows J + nb .. J + nb + rows - 1 below the panel
+        const bool bulk = nb == kNB && rows > 0 && !T.fail;
+        // (ii) B digits of the finished panel, then its slots take the indices J + S ...
+        if (bulk) {
+            {   // scales: 16 threads per right-hand side (one panel row each)
+                const int r = tid >> 4, i = tid & 15;
+                int e = tc::kNoExp;
+                if (tid < kR * kNB) {
+                    const double2 y = Y[r * S + (J + i) % S];
+                    e = max(tc::exp_of(y.x), tc::exp_of(y.y));
+                }
+#pragma unroll
+                for (int o = 1; o < 16; o <<= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+                if (tid < kR * kNB && i == 0) T.tb[r] = scale_of(e);
+            }
+            __syncthreads();
+            if (tid < 2 * kSN * 8) {
+                const bool im = tid >= kSN * 8;
+                const int u = tid & (kSN * 8 - 1);
+                const int r = u & (kSN - 1), kq = u >> 4, kg = kq >> 1;
+                const int Tb = T.tb[r];
+                unsigned long long U[4];
+                bool neg[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int i = (4 * kq + q) & 15;
+                    const double2 y = Y[r * S + (J + i) % S];
+                    double x;
+                    if (!im) x = kg < 2 ? y.x : -y.y;
+                    else x = kg < 2 ? y.y : y.x;
+                    U[q] = tc::to_fixed_mag(x, Tb, neg[q]);
+                }
+                put_digits4(U, neg, im ? bim : bre, kPlaneS, core_off(r, kg) + (kq & 1) * 8);
+            }
+            __syncthreads();
+        }
+        if (tid < nr)
+            for (int i = 0; i < nb; ++i) Y[tid * S + (J + i) % S] = (J + i + S == pmine) ? one : zero;
+        __syncthreads();
+        // no rows below a short last panel; after a failed MMA wait the block does no more
+        // tensor-core work (the launch reports HF_ETIMEOUT)
+        if (!bulk) continue;
+        // (iii) rows below, 128 per tile
+        for (int m0 = 0; m0 < rows; m0 += kTM) {
+            {   // A scales: 4 threads per row (4 panel columns each)
+                const int m = tid >> 2, part = tid & 3;
+                const int r = J + nb + m0 + m;
+                int e = tc::kNoExp;
+                if (m0 + m < rows)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int jj = 4 * part + q, d = r - (J + jj);
+                        if (d <= b) {
+                            const double2 l = __ldcg(Bq + static_cast<size_t>(J + jj) * S + d);
+                            e = max(e, max(tc::exp_of(l.x), tc::exp_of(l.y)));
+                        }
+                    }
+                e = max(e, __shfl_xor_sync(0xffffffffu, e, 1));
+                e = max(e, __shfl_xor_sync(0xffffffffu, e, 2));
+                if (part == 0) T.ta[m] = scale_of(e);
+            }
+            __syncthreads();
+            {
+                const int m = tid & (kTM - 1), kg = tid >> 7;
+                const int r = J + nb + m0 + m;
+                const int Ta = T.ta[m];
+                unsigned long long U[8];
+                bool neg[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int jj = (kg & 1) * 8 + q, d = r - (J + jj);
+                    double x = 0.0;
+                    if (m0 + m < rows && d <= b) {
+                        const double2 l = __ldcg(Bq + static_cast<size_t>(J + jj) * S + d);
+                        x = kg < 2 ? l.x : l.y;
+                    }
+                    U[q] = tc::to_fixed_mag(x, Ta, neg[q]);
+                }
+                put_digits(U, neg, T.a, kPlaneA, core_off(m, kg));
+            }
+            tc::fence_async_shared();
+            tc::tc_fence_before_sync();
+            __syncthreads();
+            if ((tid & 31) == 0 && warp < 4 && !T.fail) {
+                tc::tc_fence_after_sync();
+                constexpr uint32_t idesc = tc::idesc_bf16_f32(kTM, kSN);
+                const uint32_t a0 = tc::smem_addr(T.a), re0 = tc::smem_addr(bre), im0 = tc::smem_addr(bim);
+#pragma unroll
+                for (int lv = 2; lv <= kTNL; ++lv) {
+                    if (((lv - 2) < (kTNL - lv) ? (lv - 2) : (kTNL - lv)) != warp) continue;
+                    const int smin = lv - kTD > 1 ? lv - kTD : 1, smax = lv - 1 < kTD ? lv - 1 : kTD;
+                    for (int sd = smin; sd <= smax; ++sd) {
+                        const int td = lv - sd;
+#pragma unroll
+                        for (int kk = 0; kk < 2; ++kk) {
+                            const uint64_t ad = tc::smem_desc(a0 + (sd - 1) * kPlaneA + kk * 256, 128, 512);
+                            const bool accum = !(sd == smin && kk == 0);
+                            tc::mma_bf16(T.tmem + (lv - 2) * kSN, ad,
+                                         tc::smem_desc(re0 + (td - 1) * kPlaneS + kk * 256, 128, 512), idesc, accum);
+                            tc::mma_bf16(T.tmem + 128 + (lv - 2) * kSN, ad,
+                                         tc::smem_desc(im0 + (td - 1) * kPlaneS + kk * 256, 128, 512), idesc, accum);
+                        }
+                    }
+                }
+                tc::mma_commit(&T.bar);
+            }
+            bool ok = true;
+            if (!T.fail) ok = tc::mbar_wait(&T.bar, ph);
+            ph ^= 1u;
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) T.fail = 1;
+                break;
+            }
+            tc::tc_fence_after_sync();
+            {   // lane quarter (warp & 3): rows m = 32 (warp & 3) + lane; warp >> 2: rhs 4 g ...
+                const int ql = warp & 3, g = warp >> 2;
+                const int m = 32 * ql + lane;
+                const uint32_t trow = T.tmem + (static_cast<uint32_t>(32 * ql) << 16) + 4 * g;
+                long long Qr[4], Qi[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) Qr[k] = Qi[k] = 0;
+#pragma unroll
+                for (int l0 = 2; l0 <= kTNL; l0 += 4) {
+                    uint32_t v[8][4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (l0 + u <= kTNL) {
+                            tc::tmem_ld4_async(trow + (l0 + u - 2) * kSN, v[2 * u]);
+                            tc::tmem_ld4_async(trow + 128 + (l0 + u - 2) * kSN, v[2 * u + 1]);
+                        }
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (l0 + u <= kTNL) {
+                            const int sh = 54 - 8 * (l0 + u);
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                const long long dr = __float2int_rz(__uint_as_float(v[2 * u][k]));
+                                const long long di = __float2int_rz(__uint_as_float(v[2 * u + 1][k]));
+                                Qr[k] += sh >= 0 ? (dr << sh) : ((dr + (1ll << (-sh - 1))) >> (-sh));
+                                Qi[k] += sh >= 0 ? (di << sh) : ((di + (1ll << (-sh - 1))) >> (-sh));
+                            }
+                        }
+                }
+                if (m0 + m < rows) {
+                    const int r = J + nb + m0 + m, sr = r % S;
+                    const int Ta = T.ta[m];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int rh = 4 * g + k;
+                        const int E = Ta + T.tb[rh] - 54;
+                        double2* y = Y + rh * S + sr;
+                        const double2 x = *y;
+                        *y = make_double2(x.x - tc::fixed_to_double(Qr[k], E), x.y - tc::fixed_to_double(Qi[k], E));
+                    }
+                }
+            }
+            tc::tc_fence_before_sync();
+            __syncthreads();
+        }
+    }
+    if (tid < nr) {
+        A.gloc[static_cast<size_t>(out[tid]) * A.nw + n] = acc;
+        if (!isfinite(acc.x) || !isfinite(acc.y)) atomicExch(A.status, static_cast<int>(HF_ENUMERIC));
+    }
+}
+
 // One persistent block per SM.  The tasks of a launch are the nq factorisations, then the
 // nq * nchunk solve tasks (matrix-major); blocks take them in order from work[0].  A block that
 // finishes a factorisation raises work[1 + qi]; a solve task waits for its matrix's flag (it was
@@ -495,7 +750,7 @@ __global__ void __launch_bounds__(kT, 1) lattice_wide_kernel(const LatticeArgs A
         T = reinterpret_cast<TcSmem*>(smem + tc_offset_dev(A.b));
         if (tid == 0) {
             T->fail = 0;
-            tc::mbar_init(&T->bar, 1);
+            tc::mbar_init(&T->bar, 4);   // one commit per MMA issuer
             tc::mbar_init_fence();
         }
         if (tid < 32) tc::tmem_alloc(&T->tmem, 512);
@@ -527,7 +782,10 @@ __global__ void __launch_bounds__(kT, 1) lattice_wide_kernel(const LatticeArgs A
                 ready_s = r;
             }
             __syncthreads();
-            if (ready_s) solve_chunk<DPT>(A, q0, qi, ch, smem);
+            if (ready_s) {
+                if constexpr (TC) solve_chunk_tc(A, q0, qi, ch, smem, *T, ph);
+                else solve_chunk<DPT>(A, q0, qi, ch, smem);
+            }
             else if (tid == 0) atomicExch(A.status, static_cast<int>(HF_ETIMEOUT));
         }
         __syncthreads();                             // task_s and the shared memory are reused
@@ -546,6 +804,24 @@ __global__ void __launch_bounds__(kT, 1) lattice_wide_kernel(const LatticeArgs A
 int lattice_wide_max_band() { return kWideMaxBand; }
 
 int lattice_wide_rhs_per_block() { return kR; }
+
+double lattice_wide_tc_flops(int N, int b) {
+    if (b < kTcMinBand || b > kTcMaxBand) return 0.0;
+    // per full panel: column tiles of 128, row tiles of 32 from the tile's first column on;
+    // 2 (Re, Im) x 2 (K halves) x the digit pairs of levels <= kTNL MMAs of 128 x 32 x 16
+    int pairs = 0;
+    for (int sd = 1; sd <= kTD; ++sd)
+        for (int td = 1; td <= kTD; ++td)
+            if (sd + td <= kTNL) ++pairs;
+    const double per_tile = 4.0 * pairs * 2.0 * kTM * kTN * 16;
+    double f = 0.0;
+    for (int k0 = 0; k0 + kNB <= N; k0 += kNB) {
+        const int rmax = std::min(kNB + b, N - k0);
+        const int rows = std::min(kNB - 1 + b, rmax - 1) - kNB + 1;
+        for (int c0 = 0; c0 < rows; c0 += kTM) f += per_tile * ((rows - c0 + kTN - 1) / kTN);
+    }
+    return f;
+}
 
 cudaError_t launch_lattice_wide(const LatticeArgs& a, int q0, int nq, cudaStream_t st) {
     if (nq <= 0) return cudaSuccess;

@@ -106,7 +106,7 @@ SIGNATURES = [
     ("hf_get_refresh_stats", C.c_int, [_VP, C.POINTER(C.c_ulonglong), C.POINTER(C.c_ulonglong),
                                         C.POINTER(C.c_ulonglong)]),
     ("hf_lattice_step_noalloc", C.c_int, [_VP, _VP, _VP]),
-    ("hf_get_lattice_plan", C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int), _DP]),
+    ("hf_get_lattice_plan", C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int), _DP, _DP]),
     ("hf_get_impurity_iw", C.c_int, [_VP, _DP, _DP, _DP, _DP]),
     ("hf_philox_blocks", C.c_int, [C.c_uint32, C.c_uint32, _VP, C.c_int, _VP, _VP]),
     ("hf_tc_dgemm128", C.c_int, [_VP, _VP, _VP, C.c_int, C.c_int, _VP, _VP]),
@@ -310,10 +310,11 @@ def hf_get_drift(ctx):
 
 
 def hf_get_lattice_plan(ctx):
-    """(form, kernel launches per lattice step, complex multiply-adds per (w_n, sigma) matrix)."""
-    f, n, w = C.c_int(), C.c_int(), C.c_double()
-    _check(lib().hf_get_lattice_plan(ctx, C.byref(f), C.byref(n), C.byref(w)), ctx)
-    return f.value, n.value, w.value
+    """(form, kernel launches per lattice step, complex multiply-adds per (w_n, sigma) matrix,
+    bf16 flops per matrix of the tensor-core trailing updates)."""
+    f, n, w, t = C.c_int(), C.c_int(), C.c_double(), C.c_double()
+    _check(lib().hf_get_lattice_plan(ctx, C.byref(f), C.byref(n), C.byref(w), C.byref(t)), ctx)
+    return f.value, n.value, w.value, t.value
 
 
 def hf_get_refresh_stats(ctx):
