@@ -265,6 +265,20 @@ __device__ void trailing_tc(TcSmem& T, const double2* P, int RP, int nb, int ten
                 }
                 tc::mma_commit(&T.bar);
             }
+            // the band entries this thread updates, loaded while the MMAs run: lane quarter
+            // (warp & 3) holds columns c = c0 + 32 (warp & 3) + lane; the four warps of a quarter
+            // take 8 rows each (contiguous in column c)
+            const int ql = warp & 3, g = warp >> 2;
+            const int m = 32 * ql + lane;
+            const int c = nb + c0 + m;
+            const int rlo = nb + r0 + 8 * g;
+            double2* col = Bq + (static_cast<size_t>(k0 + c) * S - c);   // col[r] = A[r][c]
+            double2 x[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int r = rlo + k;
+                x[k] = (c <= tend && r >= c && r <= tend) ? col[r] : make_double2(0.0, 0.0);
+            }
             // every thread waits for the MMAs (bounded; a wait that runs out stops the tensor-core
             // work of this block, the caller reports HF_ETIMEOUT)
             bool ok = true;
@@ -275,50 +289,36 @@ __device__ void trailing_tc(TcSmem& T, const double2* P, int RP, int nb, int ten
                 return;
             }
             tc::tc_fence_after_sync();
-            // epilogue: lane quarter (warp & 3) holds columns c = c0 + 32 (warp & 3) + lane; the
-            // four warps of a quarter take 8 rows each
+            // epilogue: the level sums of this thread's 8 entries from TMEM
             {
-                const int ql = warp & 3, g = warp >> 2;
-                const int m = 32 * ql + lane;
-                const int c = nb + c0 + m;
                 const uint32_t trow = T.tmem + (static_cast<uint32_t>(32 * ql) << 16) + 8 * g;
                 long long Qr[8], Qi[8];
 #pragma unroll
                 for (int k = 0; k < 8; ++k) Qr[k] = Qi[k] = 0;
 #pragma unroll
-                for (int n0 = 2; n0 <= kTNL; n0 += 2) {
-                    uint32_t v[4][8];
-#pragma unroll
-                    for (int u = 0; u < 2; ++u)
-                        if (n0 + u <= kTNL) {
-                            tc::tmem_ld8_async(trow + (n0 + u - 2) * kTN, v[2 * u]);
-                            tc::tmem_ld8_async(trow + 256 + (n0 + u - 2) * kTN, v[2 * u + 1]);
-                        }
+                for (int n = 2; n <= kTNL; ++n) {
+                    uint32_t vr[8], vi[8];
+                    tc::tmem_ld8_async(trow + (n - 2) * kTN, vr);
+                    tc::tmem_ld8_async(trow + 256 + (n - 2) * kTN, vi);
                     tc::tmem_wait_ld();
+                    const int sh = 54 - 8 * n;
 #pragma unroll
-                    for (int u = 0; u < 2; ++u)
-                        if (n0 + u <= kTNL) {
-                            const int sh = 54 - 8 * (n0 + u);
-#pragma unroll
-                            for (int k = 0; k < 8; ++k) {
-                                const long long dr = __float2int_rz(__uint_as_float(v[2 * u][k]));
-                                const long long di = __float2int_rz(__uint_as_float(v[2 * u + 1][k]));
-                                Qr[k] += sh >= 0 ? (dr << sh) : ((dr + (1ll << (-sh - 1))) >> (-sh));
-                                Qi[k] += sh >= 0 ? (di << sh) : ((di + (1ll << (-sh - 1))) >> (-sh));
-                            }
-                        }
+                    for (int k = 0; k < 8; ++k) {
+                        const long long dr = __float2int_rz(__uint_as_float(vr[k]));
+                        const long long di = __float2int_rz(__uint_as_float(vi[k]));
+                        Qr[k] += sh >= 0 ? (dr << sh) : ((dr + (1ll << (-sh - 1))) >> (-sh));
+                        Qi[k] += sh >= 0 ? (di << sh) : ((di + (1ll << (-sh - 1))) >> (-sh));
+                    }
                 }
                 if (c <= tend) {
                     const int Ta = T.ta[m];
 #pragma unroll
                     for (int k = 0; k < 8; ++k) {
-                        const int nr = 8 * g + k;
-                        const int r = nb + r0 + nr;
+                        const int r = rlo + k;
                         if (r >= c && r <= tend) {
-                            const int E = Ta + T.tb[nr] - 54;
-                            double2* a = Bq + static_cast<size_t>(k0 + c) * S + (r - c);
-                            const double2 x = *a;
-                            *a = make_double2(x.x - tc::fixed_to_double(Qr[k], E), x.y - tc::fixed_to_double(Qi[k], E));
+                            const int E = Ta + T.tb[8 * g + k] - 54;
+                            col[r] = make_double2(x[k].x - tc::fixed_to_double(Qr[k], E),
+                                                  x[k].y - tc::fixed_to_double(Qi[k], E));
                         }
                     }
                 }
@@ -532,76 +532,72 @@ __device__ void solve_chunk_tc(const LatticeArgs& A, int q0, int qi, int ch, uns
     const int j0 = pos[0];
     for (int e = tid; e < kR * S; e += kT) Y[e] = zero;
     __syncthreads();
-    int pmine = -1;
-    if (tid < nr) {
-        pmine = pos[tid];
-        if (pmine - j0 < S) Y[tid * S + pmine % S] = one;
-    }
-    __syncthreads();
+    if (tid < nr && pos[tid] - j0 < S) Y[tid * S + pos[tid] % S] = one;
+    // the panel's L triangle, Lp[16 jj + i] = L_{J+i, J+jj} (i > jj), and 1 / D_{J+jj} at i = jj:
+    // the 256 entries behind the windows
+    double2* Lp = Y + kR * S;
+    // thread (rhs r = tid >> 4, panel row i = tid & 15), tid < 256: the position of its
+    // right-hand side, and sum_i y_i^2 / D_i over its panel rows (the 16 partial sums of a
+    // right-hand side are added at the end)
+    const int pr = (tid < kR * kNB && (tid >> 4) < nr) ? pos[tid >> 4] : -1;
     double2 acc = zero;
     unsigned char* bre = T.bre;
     unsigned char* bim = T.bim;
     for (int J = j0; J < N; J += kNB) {
         const int nb = min(kNB, N - J);
-        // (i) the panel's triangle: thread (rhs r, panel row i)
-        for (int jj = 0; jj < nb; ++jj) {
-            const int j = J + jj, sj = j % S;
-            if (tid < kR * kNB) {
-                const int r = tid >> 4, i = tid & 15;
-                const double2 yj = Y[r * S + sj];
-                if (i > jj && i < nb) {
-                    const int si = (J + i) % S;
-                    Y[r * S + si] = cfms(Y[r * S + si], __ldcg(Bq + static_cast<size_t>(j) * S + (i - jj)), yj);
-                }
-            }
-            if (tid < nr) {
-                const double2 yj = Y[tid * S + sj];
-                acc = cfma(acc, cmul(yj, yj), crecip(__ldcg(Bq + static_cast<size_t>(j) * S)));
-            }
-            __syncthreads();
-        }
         const int rows = min(b, N - J - nb);   // rows J + nb .. J + nb + rows - 1 below the panel
         const bool bulk = nb == kNB && rows > 0 && !T.fail;
-        // (ii) B digits of the finished panel, then its slots take the indices J + S ...
-        if (bulk) {
-            {   // scales: 16 threads per right-hand side (one panel row each)
-                const int r = tid >> 4, i = tid & 15;
-                int e = tc::kNoExp;
-                if (tid < kR * kNB) {
-                    const double2 y = Y[r * S + (J + i) % S];
-                    e = max(tc::exp_of(y.x), tc::exp_of(y.y));
-                }
+        if (tid < kNB * kNB) {
+            const int jj = tid >> 4, i = tid & 15;
+            if (jj < nb && i < nb && i >= jj) {
+                const double2 l = __ldcg(Bq + static_cast<size_t>(J + jj) * S + (i - jj));
+                Lp[tid] = i == jj ? crecip(l) : l;
+            }
+        }
+        __syncthreads();
+        // (i) the panel's triangle in registers, y_{J+jj} of a right-hand side passed along its
+        // half warp by shuffle; (ii) its B digits straight from the registers; then the panel's
+        // window slots take the indices J + S ...  No barrier: the next one (before the MMAs) also
+        // publishes the digits, and each thread touches only its own slot.
+        if (tid < kR * kNB) {
+            const int r = tid >> 4, i = tid & 15, half = tid & 16;
+            const int si = (J + i) % S;
+            double2 y = i < nb ? Y[r * S + si] : zero;
+            for (int jj = 0; jj < nb; ++jj) {
+                const double2 yj = shfl_c(y, half | jj);
+                if (i > jj && i < nb) y = cfms(y, Lp[16 * jj + i], yj);
+            }
+            if (i < nb) {
+                acc = cfma(acc, cmul(y, y), Lp[17 * i]);
+                Y[r * S + si] = (J + i + S == pr) ? one : zero;
+            }
+            if (bulk) {
+                int e = max(tc::exp_of(y.x), tc::exp_of(y.y));   // the row's scale: its half warp
 #pragma unroll
                 for (int o = 1; o < 16; o <<= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
-                if (tid < kR * kNB && i == 0) T.tb[r] = scale_of(e);
-            }
-            __syncthreads();
-            if (tid < 2 * kSN * 8) {
-                const bool im = tid >= kSN * 8;
-                const int u = tid & (kSN * 8 - 1);
-                const int r = u & (kSN - 1), kq = u >> 4, kg = kq >> 1;
-                const int Tb = T.tb[r];
+                const int Tb = scale_of(e);
+                if (i == 0) T.tb[r] = Tb;   // for the epilogues
+                // lane i = 4 a + c cuts K quad a of part c: B_re = [Re y | -Im y] (c = 0, 1),
+                // B_im = [Im y | Re y] (c = 2, 3)
+                const int a = i >> 2, c = i & 3;
                 unsigned long long U[4];
                 bool neg[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const int i = (4 * kq + q) & 15;
-                    const double2 y = Y[r * S + (J + i) % S];
-                    double x;
-                    if (!im) x = kg < 2 ? y.x : -y.y;
-                    else x = kg < 2 ? y.y : y.x;
+                    const double2 v = shfl_c(y, half | (4 * a + q));
+                    const double x = c == 0 ? v.x : c == 1 ? -v.y : c == 2 ? v.y : v.x;
                     U[q] = tc::to_fixed_mag(x, Tb, neg[q]);
                 }
-                put_digits4(U, neg, im ? bim : bre, kPlaneS, core_off(r, kg) + (kq & 1) * 8);
+                const int kq = (c & 1) * 4 + a;
+                put_digits4(U, neg, c < 2 ? bre : bim, kPlaneS, core_off(r, kq >> 1) + (kq & 1) * 8);
             }
-            __syncthreads();
         }
-        if (tid < nr)
-            for (int i = 0; i < nb; ++i) Y[tid * S + (J + i) % S] = (J + i + S == pmine) ? one : zero;
-        __syncthreads();
         // no rows below a short last panel; after a failed MMA wait the block does no more
         // tensor-core work (the launch reports HF_ETIMEOUT)
-        if (!bulk) continue;
+        if (!bulk) {
+            __syncthreads();   // Lp is restaged by the next panel
+            continue;
+        }
         // (iii) rows below, 128 per tile
         for (int m0 = 0; m0 < rows; m0 += kTM) {
             {   // A scales: 4 threads per row (4 panel columns each)
@@ -721,8 +717,13 @@ __device__ void solve_chunk_tc(const LatticeArgs& A, int q0, int qi, int ch, uns
             __syncthreads();
         }
     }
-    if (tid < nr) {
-        A.gloc[static_cast<size_t>(out[tid]) * A.nw + n] = acc;
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (tid < kR * kNB && (tid & 15) == 0 && (tid >> 4) < nr) {
+        A.gloc[static_cast<size_t>(out[tid >> 4]) * A.nw + n] = acc;
         if (!isfinite(acc.x) || !isfinite(acc.y)) atomicExch(A.status, static_cast<int>(HF_ENUMERIC));
     }
 }
