@@ -859,8 +859,12 @@ def run_lattice3d(args):
             "gpu_launches": (lattice_launches(hf, cfg) + 5) * args.steps,
             "cpu_baseline": cpu, "clocks": clk}
     if args.sweeps or args.matsubara:
-        line["profile_case"] = ("sweeps overridden to %d, Matsubara frequencies to %d: not a "
-                                "benchmark value" % (args.sweeps, args.matsubara))
+        over = []
+        if args.sweeps:
+            over.append("sweeps to %d" % args.sweeps)
+        if args.matsubara:
+            over.append("Matsubara frequencies to %d" % args.matsubara)
+        line["profile_case"] = "overridden: %s; not a benchmark value" % ", ".join(over)
     print(json.dumps(line))
     ctx.close()
     return 0

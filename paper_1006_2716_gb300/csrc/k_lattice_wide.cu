@@ -39,8 +39,12 @@ constexpr int kSeg = 256;        // rows of a trailing-update unit (8 per lane)
 
 static_assert(kWideMaxBand <= 2 * kT, "two band entries of a column per solve thread at most");
 
+// Row stride of the staged panel: kNB + b rows, rounded up to an odd count so that the 16
+// columns of one row fall in different shared-memory banks.
+__host__ __device__ constexpr int panel_stride(int b) { return (kNB + b) | 1; }
+
 size_t factor_smem(int b) {      // the panel and the pivot row
-    return (static_cast<size_t>(kNB) * (kNB + b) + kNB) * sizeof(double2);
+    return (static_cast<size_t>(kNB) * panel_stride(b) + kNB) * sizeof(double2);
 }
 
 size_t solve_smem(int b) {       // kR windows of b + 1 entries
@@ -55,25 +59,30 @@ size_t solve_smem(int b) {       // kR windows of b + 1 entries
 // sum are A B_re^T and A B_im^T.  Each operand row gets a power-of-two scale and kTD balanced
 // base-256 digits; the levels n = s + t <= kTNL are kept (the dropped ones stay below 2^-58 of
 // the scales), each an exact FP32 accumulator in TMEM (K = 32 terms of at most 2^14, at most 7
-// per level: below 2^22), eight levels x (Re, Im) x 32 rows = all 512 TMEM columns.  The
-// epilogue combines a tile's levels in 64-bit integers and subtracts the rounded sums from the
-// band buffer in FP64: one DADD per part and entry instead of 16 complex multiply-adds.
+// per level: below 2^22).  A digit plane of B holds the B_re and B_im rows of the tile's 32
+// rows r, interleaved by eights (row 16 (r / 8) + 8 part + r % 8), so a level's accumulator is
+// 64 TMEM columns in which each thread's 8 rows r have their Re and Im sums side by side; the
+// eight levels fill all 512 columns.  For each digit s of A the digits t of B are stacked along
+// N (up to four planes, 256 columns, per MMA): 23 MMAs per tile, each reading its A plane once
+// for up to 256 columns.  The epilogue combines a tile's levels in 64-bit integers and
+// subtracts the rounded sums from the band buffer in FP64: one DADD per part and entry per
+// panel, against 16 complex multiply-adds.
 constexpr int kTD = 7;                  // digits of an operand
 constexpr int kTNL = kTD + 2;           // highest level kept
 constexpr int kTM = 128;                // trailing columns c per tile (MMA M)
-constexpr int kTN = 32;                 // trailing rows r per tile (MMA N)
+constexpr int kTN = 32;                 // trailing rows r per tile
 constexpr int kTK = 32;                 // K
 constexpr int kPlaneA = kTM * kTK * 2;  // bytes of one digit plane of A (K-major core matrices)
-constexpr int kPlaneB = kTN * kTK * 2;
+constexpr int kPlaneB = 2 * kTN * kTK * 2;   // one digit plane of B: 32 rows r x (Re, Im)
 constexpr int kTcMinBand = 128;
 constexpr int kTcMaxBand = 520;
 
 struct TcSmem {                         // behind the panel, 1024-byte aligned
     unsigned char a[kTD * kPlaneA];
-    unsigned char bre[kTD * kPlaneB];
-    unsigned char bim[kTD * kPlaneB];
+    unsigned char b[kTD * kPlaneB];
     int ta[kTM];                        // scales of A's rows (the tile's columns c)
-    int tb[kTN];                        // scales of B's rows (the tile's rows r)
+    int tb[kNB + kTcMaxBand];           // scales of the B rows: the panel's rows (trailing
+                                        // update), the right-hand sides (solve)
     uint64_t bar;                       // MMA completion
     uint32_t tmem;                      // TMEM base address
     int fail;                           // an MMA wait ran out: no more tensor-core work
@@ -81,7 +90,7 @@ struct TcSmem {                         // behind the panel, 1024-byte aligned
 
 size_t tc_offset(int b) { return (factor_smem(b) + 1023) / 1024 * 1024; }
 __device__ __forceinline__ int tc_offset_dev(int b) {
-    return ((kNB * (kNB + b) + kNB) * static_cast<int>(sizeof(double2)) + 1023) / 1024 * 1024;
+    return ((kNB * panel_stride(b) + kNB) * static_cast<int>(sizeof(double2)) + 1023) / 1024 * 1024;
 }
 
 size_t wide_smem(int b, bool tc) {
@@ -103,31 +112,8 @@ __device__ __forceinline__ int load_acquire(const int* p) {
     return v;
 }
 
-// kTD balanced base-256 digits of 8 fixed-point magnitudes (top down, each rounded) into the
-// digit planes at base (plane stride `plane`), 16 bytes at offset off of each.
-__device__ __forceinline__ void put_digits(const unsigned long long (&U)[8], const bool (&neg)[8],
-                                           unsigned char* base, int plane, int off) {
-    long long r[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) r[q] = static_cast<long long>(U[q]);
-#pragma unroll
-    for (int sd = 1; sd <= kTD; ++sd) {
-        const int sh = 62 - 8 * sd;
-        int d[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const long long v = (r[q] + (1ll << (sh - 1))) >> sh;
-            r[q] -= v << sh;
-            d[q] = static_cast<int>(v);
-        }
-        uint32_t w[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) w[q] = tc::bf16x2_digits(d[2 * q], d[2 * q + 1], neg[2 * q], neg[2 * q + 1]);
-        *reinterpret_cast<uint4*>(base + (sd - 1) * plane + off) = make_uint4(w[0], w[1], w[2], w[3]);
-    }
-}
-
-// The same for 4 values (8 bytes at off of each plane).
+// kTD balanced base-256 digits of 4 fixed-point magnitudes (top down, each rounded) into the
+// digit planes at base (plane stride `plane`), 8 bytes at offset off of each.
 __device__ __forceinline__ void put_digits4(const unsigned long long (&U)[4], const bool (&neg)[4],
                                             unsigned char* base, int plane, int off) {
     long long r[4];
@@ -154,8 +140,62 @@ __device__ __forceinline__ int core_off(int m, int kg) { return ((m >> 3) * 4 + 
 
 __device__ __forceinline__ int scale_of(int e) { return e == tc::kNoExp ? 0 : e + 2; }
 
+// The sign-flipped bit pattern of x (no FP64 instruction).
+__device__ __forceinline__ double neg_bits(double x) {
+    return __longlong_as_double(__double_as_longlong(x) ^ static_cast<long long>(0x8000000000000000ull));
+}
+
+// Level n of a product lives in TMEM columns W (n - 2) ... (W per level).  The digit products of
+// one tile: for each digit s of A (planes (s - 1) planeA) the digits t = 1 .. min(kTD, kTNL - s)
+// of B (planes (t - 1) planeB, W rows each) in runs of at most 256 / W planes, one MMA per run and
+// K half, writing the level blocks s + t .. in one go.  The first product of each level
+// (s = max(1, n - kTD), first K half) starts its accumulator: a run never mixes first products
+// with later ones.  The schedule is fixed at compile time.
+struct MmaRun {
+    int kk, sd, t, nt;
+    bool first;
+};
+template <int G>
+struct MmaSchedule {
+    MmaRun run[32];
+    int n;
+};
+template <int G>
+__host__ __device__ constexpr MmaSchedule<G> mma_schedule() {
+    MmaSchedule<G> S{};
+    for (int kk = 0; kk < 2; ++kk)
+        for (int sd = 1; sd <= kTD; ++sd) {
+            const int tmax = kTD < kTNL - sd ? kTD : kTNL - sd;
+            int t = 1;
+            while (t <= tmax) {
+                const auto first_of = [&](int tt) { return kk == 0 && sd == (sd + tt - kTD > 1 ? sd + tt - kTD : 1); };
+                const bool first = first_of(t);
+                int e = t;
+                while (e < tmax && e - t + 1 < G && first_of(e + 1) == first) ++e;
+                S.run[S.n++] = MmaRun{kk, sd, t, e - t + 1, first};
+                t = e + 1;
+            }
+        }
+    return S;
+}
+
+// Issued by one thread.  adesc / bdesc: descriptors of the first A and B planes (K-major, core
+// matrices 128 bytes apart along K and 512 along the rows); an offset of o bytes adds o / 16.
+template <int W, int PlaneA, int PlaneB>
+__device__ __forceinline__ void issue_levels(uint32_t tmem, uint64_t adesc, uint64_t bdesc) {
+    constexpr MmaSchedule<256 / W> S = mma_schedule<256 / W>();
+    static_assert(S.n <= 32, "schedule fits");
+#pragma unroll
+    for (int i = 0; i < S.n; ++i) {
+        const MmaRun r = S.run[i];
+        tc::mma_bf16(tmem + (r.sd + r.t - 2) * W, adesc + (((r.sd - 1) * PlaneA + r.kk * 256) >> 4),
+                     bdesc + (((r.t - 1) * PlaneB + r.kk * 256) >> 4), tc::idesc_bf16_f32(kTM, r.nt * W),
+                     !r.first);
+    }
+}
+
 // The trailing update of one panel on the tensor cores: rows and columns nb .. tend of the panel
-// P (RP rows per column, L_ij scaled, D_j on the diagonal) into the band buffer Bq at k0.
+// P (RP the row stride, L_ij scaled, D_j on the diagonal) into the band buffer Bq at k0.
 // ph: the mbarrier's phase bit, flipped by every wait.
 __device__ void trailing_tc(TcSmem& T, const double2* P, int RP, int nb, int tend, double2* Bq,
                             int k0, int S, uint32_t& ph) {
@@ -163,108 +203,73 @@ __device__ void trailing_tc(TcSmem& T, const double2* P, int RP, int nb, int ten
     const int rows = tend - nb + 1;
     if (rows <= 0) return;
     const double2 zero = make_double2(0.0, 0.0);
+    // the B scales of every trailing row, once for the panel (a thread per row)
+    for (int i = nb + tid; i <= tend; i += kT) {
+        int e = tc::kNoExp;
+#pragma unroll
+        for (int j = 0; j < kNB; ++j) {
+            const double2 l = P[j * RP + i];
+            e = max(e, max(tc::exp_of(l.x), tc::exp_of(l.y)));
+        }
+        T.tb[i] = scale_of(e);
+    }
+    __syncthreads();
     for (int c0 = 0; c0 < rows; c0 += kTM) {
-        // A: W_cj = D_j L_cj of the tile's columns c = nb + c0 + m, m < 128 (zero past tend);
-        // scales from 4 threads per column (4 j each, adjacent lanes)
+        // A: W_cj = D_j L_cj of the tile's columns c = nb + c0 + m, m < 128 (zero past tend):
+        // four threads per column (adjacent lanes, four j each) form their W once, agree on the
+        // column's scale by shuffle and cut the Re and Im digits
         {
             const int m = tid >> 2, part = tid & 3;
             const int c = nb + c0 + m;
+            double2 w[4];
             int e = tc::kNoExp;
-            if (c <= tend)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int j = 4 * part + q;
-                    const double2 w = cmul(P[j * RP + j], P[j * RP + c]);
-                    e = max(e, max(tc::exp_of(w.x), tc::exp_of(w.y)));
-                }
+            for (int q = 0; q < 4; ++q) {
+                const int j = 4 * part + q;
+                w[q] = c <= tend ? cmul(P[j * RP + j], P[j * RP + c]) : zero;
+                e = max(e, max(tc::exp_of(w[q].x), tc::exp_of(w[q].y)));
+            }
             e = max(e, __shfl_xor_sync(0xffffffffu, e, 1));
             e = max(e, __shfl_xor_sync(0xffffffffu, e, 2));
-            if (part == 0) T.ta[m] = scale_of(e);
-        }
-        __syncthreads();
-        {
-            const int m = tid & (kTM - 1), kg = tid >> 7;     // 8 K of one row per thread
-            const int c = nb + c0 + m;
-            const int Ta = T.ta[m];
-            unsigned long long U[8];
-            bool neg[8];
+            const int Ta = scale_of(e);
+            if (part == 0) T.ta[m] = Ta;
+            unsigned long long U[4];
+            bool neg[4];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int j = (kg & 1) * 8 + q;
-                double x = 0.0;
-                if (c <= tend) {
-                    const double2 w = cmul(P[j * RP + j], P[j * RP + c]);
-                    x = kg < 2 ? w.x : w.y;
-                }
-                U[q] = tc::to_fixed_mag(x, Ta, neg[q]);
-            }
-            put_digits(U, neg, T.a, kPlaneA, core_off(m, kg));
+            for (int q = 0; q < 4; ++q) U[q] = tc::to_fixed_mag(w[q].x, Ta, neg[q]);
+            put_digits4(U, neg, T.a, kPlaneA, core_off(m, part >> 1) + (part & 1) * 8);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) U[q] = tc::to_fixed_mag(w[q].y, Ta, neg[q]);
+            put_digits4(U, neg, T.a, kPlaneA, core_off(m, 2 + (part >> 1)) + (part & 1) * 8);
         }
         for (int r0 = c0 - (c0 % kTN); r0 < rows; r0 += kTN) {
-            // B: L_rj of the tile's rows r = nb + r0 + n, n < 32, as [Re | -Im] and [Im | Re];
-            // scales from 16 threads per row (one j each, a half warp), digits 4 K per thread
+            // B: L_rj of the tile's rows r = nb + r0 + nr, nr < 32, as [Re | -Im] (part 0) and
+            // [Im | Re] (part 1), 4 K a thread
             {
-                const int nr = tid >> 4, j = tid & 15;
-                const int r = nb + r0 + nr;
-                int e = tc::kNoExp;
-                if (r <= tend) {
-                    const double2 l = P[j * RP + r];
-                    e = max(tc::exp_of(l.x), tc::exp_of(l.y));
-                }
-#pragma unroll
-                for (int o = 1; o < 16; o <<= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
-                if (j == 0) T.tb[nr] = scale_of(e);
-            }
-            __syncthreads();
-            {
-                const bool im = tid >= 256;
+                const int part = tid >> 8;
                 const int u = tid & 255;
                 const int nr = u & (kTN - 1), kq = u >> 5;   // K quarter-group: 4 K at 4 kq
                 const int kg = kq >> 1;
                 const int r = nb + r0 + nr;
-                const int Tb = T.tb[nr];
+                const int Tb = r <= tend ? T.tb[r] : 0;
                 unsigned long long U[4];
                 bool neg[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int j = ((4 * kq + q) & 15);
                     const double2 l = r <= tend ? P[j * RP + r] : zero;
-                    // re: k < 16 Re L, k >= 16 -Im L;  im: k < 16 Im L, k >= 16 Re L
+                    // part 0: k < 16 Re L, k >= 16 -Im L;  part 1: k < 16 Im L, k >= 16 Re L
                     double x;
-                    if (!im) x = kg < 2 ? l.x : -l.y;
+                    if (part == 0) x = kg < 2 ? l.x : neg_bits(l.y);
                     else x = kg < 2 ? l.y : l.x;
                     U[q] = tc::to_fixed_mag(x, Tb, neg[q]);
                 }
-                put_digits4(U, neg, im ? T.bim : T.bre, kPlaneB, core_off(nr, kg) + (kq & 1) * 8);
+                const int mb = 16 * (nr >> 3) + 8 * part + (nr & 7);
+                put_digits4(U, neg, T.b, kPlaneB, core_off(mb, kg) + (kq & 1) * 8);
             }
             tc::fence_async_shared();
             tc::tc_fence_before_sync();
             __syncthreads();
-            // the MMAs: lane 0 of warps 0 .. 3, each owning whole levels (first and last paired:
-            // 2+9, 3+8, 4+7, 5+6), committing to the mbarrier (which expects four arrivals)
-            if ((tid & 31) == 0 && warp < 4 && !T.fail) {
-                tc::tc_fence_after_sync();
-                constexpr uint32_t idesc = tc::idesc_bf16_f32(kTM, kTN);
-                const uint32_t a0 = tc::smem_addr(T.a), re0 = tc::smem_addr(T.bre), im0 = tc::smem_addr(T.bim);
-#pragma unroll
-                for (int n = 2; n <= kTNL; ++n) {
-                    if (((n - 2) < (kTNL - n) ? (n - 2) : (kTNL - n)) != warp) continue;
-                    const int smin = n - kTD > 1 ? n - kTD : 1, smax = n - 1 < kTD ? n - 1 : kTD;
-                    for (int sd = smin; sd <= smax; ++sd) {
-                        const int td = n - sd;
-#pragma unroll
-                        for (int kk = 0; kk < 2; ++kk) {
-                            const uint64_t ad = tc::smem_desc(a0 + (sd - 1) * kPlaneA + kk * 256, 128, 512);
-                            const bool accum = !(sd == smin && kk == 0);
-                            tc::mma_bf16(T.tmem + (n - 2) * kTN, ad,
-                                         tc::smem_desc(re0 + (td - 1) * kPlaneB + kk * 256, 128, 512), idesc, accum);
-                            tc::mma_bf16(T.tmem + 256 + (n - 2) * kTN, ad,
-                                         tc::smem_desc(im0 + (td - 1) * kPlaneB + kk * 256, 128, 512), idesc, accum);
-                        }
-                    }
-                }
-                tc::mma_commit(&T.bar);
-            }
             // the band entries this thread updates, loaded while the MMAs run: lane quarter
             // (warp & 3) holds columns c = c0 + 32 (warp & 3) + lane; the four warps of a quarter
             // take 8 rows each (contiguous in column c)
@@ -277,7 +282,14 @@ __device__ void trailing_tc(TcSmem& T, const double2* P, int RP, int nb, int ten
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const int r = rlo + k;
-                x[k] = (c <= tend && r >= c && r <= tend) ? col[r] : make_double2(0.0, 0.0);
+                x[k] = (c <= tend && r >= c && r <= tend) ? col[r] : zero;
+            }
+            // the MMAs, issued by one thread and committed to the mbarrier
+            if (tid == 0 && !T.fail) {
+                tc::tc_fence_after_sync();
+                issue_levels<2 * kTN, kPlaneA, kPlaneB>(T.tmem, tc::smem_desc(tc::smem_addr(T.a), 128, 512),
+                                                        tc::smem_desc(tc::smem_addr(T.b), 128, 512));
+                tc::mma_commit(&T.bar);
             }
             // every thread waits for the MMAs (bounded; a wait that runs out stops the tensor-core
             // work of this block, the caller reports HF_ETIMEOUT)
@@ -289,23 +301,22 @@ __device__ void trailing_tc(TcSmem& T, const double2* P, int RP, int nb, int ten
                 return;
             }
             tc::tc_fence_after_sync();
-            // epilogue: the level sums of this thread's 8 entries from TMEM
+            // epilogue: the level sums of this thread's 8 rows (Re and Im side by side)
             {
-                const uint32_t trow = T.tmem + (static_cast<uint32_t>(32 * ql) << 16) + 8 * g;
+                const uint32_t trow = T.tmem + (static_cast<uint32_t>(32 * ql) << 16) + 16 * g;
                 long long Qr[8], Qi[8];
 #pragma unroll
                 for (int k = 0; k < 8; ++k) Qr[k] = Qi[k] = 0;
 #pragma unroll
                 for (int n = 2; n <= kTNL; ++n) {
-                    uint32_t vr[8], vi[8];
-                    tc::tmem_ld8_async(trow + (n - 2) * kTN, vr);
-                    tc::tmem_ld8_async(trow + 256 + (n - 2) * kTN, vi);
+                    uint32_t v[16];
+                    tc::tmem_ld16_async(trow + (n - 2) * (2 * kTN), v);
                     tc::tmem_wait_ld();
                     const int sh = 54 - 8 * n;
 #pragma unroll
                     for (int k = 0; k < 8; ++k) {
-                        const long long dr = __float2int_rz(__uint_as_float(vr[k]));
-                        const long long di = __float2int_rz(__uint_as_float(vi[k]));
+                        const long long dr = __float2int_rz(__uint_as_float(v[k]));
+                        const long long di = __float2int_rz(__uint_as_float(v[8 + k]));
                         Qr[k] += sh >= 0 ? (dr << sh) : ((dr + (1ll << (-sh - 1))) >> (-sh));
                         Qi[k] += sh >= 0 ? (di << sh) : ((di + (1ll << (-sh - 1))) >> (-sh));
                     }
@@ -316,7 +327,7 @@ __device__ void trailing_tc(TcSmem& T, const double2* P, int RP, int nb, int ten
                     for (int k = 0; k < 8; ++k) {
                         const int r = rlo + k;
                         if (r >= c && r <= tend) {
-                            const int E = Ta + T.tb[8 * g + k] - 54;
+                            const int E = Ta + T.tb[r] - 54;
                             col[r] = make_double2(x[k].x - tc::fixed_to_double(Qr[k], E),
                                                   x[k].y - tc::fixed_to_double(Qi[k], E));
                         }
@@ -338,7 +349,7 @@ __device__ void factor_matrix(const LatticeArgs& A, int q0, int qi, unsigned cha
                               TcSmem* T, uint32_t& ph) {
     int sp, n;
     item_of(A, q0 + qi, sp, n);
-    const int N = A.N, b = A.b, S = b + 1, RP = kNB + b;
+    const int N = A.N, b = A.b, S = b + 1, RP = panel_stride(b);
     const int tid = static_cast<int>(threadIdx.x), lane = tid & 31, warp = tid >> 5;
     constexpr int kWarps = kT / 32;
     const double wn = (2.0 * n + 1.0) * M_PI / A.beta;
@@ -360,7 +371,7 @@ __device__ void factor_matrix(const LatticeArgs& A, int q0, int qi, unsigned cha
     // 2. panels of kNB columns
     for (int k0 = 0; k0 < N; k0 += kNB) {
         const int nb = min(kNB, N - k0);
-        const int rmax = min(RP, N - k0);            // rows k0 .. k0 + rmax - 1 exist
+        const int rmax = min(kNB + b, N - k0);       // rows k0 .. k0 + rmax - 1 exist
         // (a) stage the panel, zero outside each column's band
         for (int j = warp; j < kNB; j += kWarps)
             for (int i = lane; i < RP; i += 32) {
@@ -507,15 +518,16 @@ __device__ void solve_chunk(const LatticeArgs& A, int q0, int qi, int ch, unsign
 }
 
 // The same forward solves with the bulk of each 16-column step on the tensor cores (128 <= b <=
-// kTcMaxBand).  Step J: (i) the panel's own triangle column by column (DFMA), which finishes
-// y_J .. y_{J+15} and adds their y^2 / D to G; (ii) their slots are cut into the digits of
-// B_re = [Re y | -Im y], B_im = [Im y | Re y] (16 right-hand sides, K = 32) and then freed for
-// the indices J + S .. J + S + 15; (iii) the rows J + 16 .. J + 15 + b lose
-// sum_j L_rj y_j, formed as in trailing_tc with A = [Re L | Im L] (128 rows per tile) and
-// N = 16 (levels x (Re, Im) x 16 = 256 TMEM columns), and subtracted from their window slots.
-constexpr int kSN = 16;                      // right-hand sides = MMA N of the solve
-constexpr int kPlaneS = kSN * kTK * 2;       // one digit plane of the y panel
-static_assert(kSN == kR && 2 * kTD * kPlaneS <= 2 * kTD * kPlaneB, "solve planes fit");
+// kTcMaxBand).  Step J: (i) the panel's own triangle (DFMA, in registers), which finishes
+// y_J .. y_{J+15} and adds their y^2 / D to G; (ii) they are cut into the digits of
+// B_re = [Re y | -Im y], B_im = [Im y | Re y] (16 right-hand sides, K = 32; a plane holds both,
+// interleaved by fours: row 8 (r / 4) + 4 part + r % 4) and their slots freed for the indices
+// J + S .. J + S + 15; (iii) the rows J + 16 .. J + 15 + b lose sum_j L_rj y_j, formed as in
+// trailing_tc with A = [Re L | Im L] (128 rows per tile) and 32 TMEM columns per level (eight
+// levels: 256 columns), and subtracted from their window slots.
+constexpr int kSN = 16;                          // right-hand sides
+constexpr int kPlaneS = 2 * kSN * kTK * 2;       // one digit plane of the y panel (Re and Im rows)
+static_assert(kSN == kR && kPlaneS <= kPlaneB, "solve planes fit");
 
 __device__ void solve_chunk_tc(const LatticeArgs& A, int q0, int qi, int ch, unsigned char* smem,
                                TcSmem& T, uint32_t& ph) {
@@ -541,8 +553,6 @@ __device__ void solve_chunk_tc(const LatticeArgs& A, int q0, int qi, int ch, uns
     // right-hand side are added at the end)
     const int pr = (tid < kR * kNB && (tid >> 4) < nr) ? pos[tid >> 4] : -1;
     double2 acc = zero;
-    unsigned char* bre = T.bre;
-    unsigned char* bim = T.bim;
     for (int J = j0; J < N; J += kNB) {
         const int nb = min(kNB, N - J);
         const int rows = min(b, N - J - nb);   // rows J + nb .. J + nb + rows - 1 below the panel
@@ -589,7 +599,8 @@ __device__ void solve_chunk_tc(const LatticeArgs& A, int q0, int qi, int ch, uns
                     U[q] = tc::to_fixed_mag(x, Tb, neg[q]);
                 }
                 const int kq = (c & 1) * 4 + a;
-                put_digits4(U, neg, c < 2 ? bre : bim, kPlaneS, core_off(r, kq >> 1) + (kq & 1) * 8);
+                const int mb = 8 * (r >> 2) + 4 * (c >> 1) + (r & 3);
+                put_digits4(U, neg, T.b, kPlaneS, core_off(mb, kq >> 1) + (kq & 1) * 8);
             }
         }
         // no rows below a short last panel; after a failed MMA wait the block does no more
@@ -600,66 +611,38 @@ __device__ void solve_chunk_tc(const LatticeArgs& A, int q0, int qi, int ch, uns
         }
         // (iii) rows below, 128 per tile
         for (int m0 = 0; m0 < rows; m0 += kTM) {
-            {   // A scales: 4 threads per row (4 panel columns each)
+            {   // A: the rows' L entries, four threads per row (four panel columns each, adjacent
+                // lanes), which agree on the row's scale by shuffle and cut the Re and Im digits
                 const int m = tid >> 2, part = tid & 3;
                 const int r = J + nb + m0 + m;
+                double2 l[4];
                 int e = tc::kNoExp;
-                if (m0 + m < rows)
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int jj = 4 * part + q, d = r - (J + jj);
-                        if (d <= b) {
-                            const double2 l = __ldcg(Bq + static_cast<size_t>(J + jj) * S + d);
-                            e = max(e, max(tc::exp_of(l.x), tc::exp_of(l.y)));
-                        }
-                    }
+                for (int q = 0; q < 4; ++q) {
+                    const int jj = 4 * part + q, d = r - (J + jj);
+                    l[q] = (m0 + m < rows && d <= b) ? __ldcg(Bq + static_cast<size_t>(J + jj) * S + d) : zero;
+                    e = max(e, max(tc::exp_of(l[q].x), tc::exp_of(l[q].y)));
+                }
                 e = max(e, __shfl_xor_sync(0xffffffffu, e, 1));
                 e = max(e, __shfl_xor_sync(0xffffffffu, e, 2));
-                if (part == 0) T.ta[m] = scale_of(e);
-            }
-            __syncthreads();
-            {
-                const int m = tid & (kTM - 1), kg = tid >> 7;
-                const int r = J + nb + m0 + m;
-                const int Ta = T.ta[m];
-                unsigned long long U[8];
-                bool neg[8];
+                const int Ta = scale_of(e);
+                if (part == 0) T.ta[m] = Ta;
+                unsigned long long U[4];
+                bool neg[4];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int jj = (kg & 1) * 8 + q, d = r - (J + jj);
-                    double x = 0.0;
-                    if (m0 + m < rows && d <= b) {
-                        const double2 l = __ldcg(Bq + static_cast<size_t>(J + jj) * S + d);
-                        x = kg < 2 ? l.x : l.y;
-                    }
-                    U[q] = tc::to_fixed_mag(x, Ta, neg[q]);
-                }
-                put_digits(U, neg, T.a, kPlaneA, core_off(m, kg));
+                for (int q = 0; q < 4; ++q) U[q] = tc::to_fixed_mag(l[q].x, Ta, neg[q]);
+                put_digits4(U, neg, T.a, kPlaneA, core_off(m, part >> 1) + (part & 1) * 8);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) U[q] = tc::to_fixed_mag(l[q].y, Ta, neg[q]);
+                put_digits4(U, neg, T.a, kPlaneA, core_off(m, 2 + (part >> 1)) + (part & 1) * 8);
             }
             tc::fence_async_shared();
             tc::tc_fence_before_sync();
             __syncthreads();
-            if ((tid & 31) == 0 && warp < 4 && !T.fail) {
+            if (tid == 0 && !T.fail) {
                 tc::tc_fence_after_sync();
-                constexpr uint32_t idesc = tc::idesc_bf16_f32(kTM, kSN);
-                const uint32_t a0 = tc::smem_addr(T.a), re0 = tc::smem_addr(bre), im0 = tc::smem_addr(bim);
-#pragma unroll
-                for (int lv = 2; lv <= kTNL; ++lv) {
-                    if (((lv - 2) < (kTNL - lv) ? (lv - 2) : (kTNL - lv)) != warp) continue;
-                    const int smin = lv - kTD > 1 ? lv - kTD : 1, smax = lv - 1 < kTD ? lv - 1 : kTD;
-                    for (int sd = smin; sd <= smax; ++sd) {
-                        const int td = lv - sd;
-#pragma unroll
-                        for (int kk = 0; kk < 2; ++kk) {
-                            const uint64_t ad = tc::smem_desc(a0 + (sd - 1) * kPlaneA + kk * 256, 128, 512);
-                            const bool accum = !(sd == smin && kk == 0);
-                            tc::mma_bf16(T.tmem + (lv - 2) * kSN, ad,
-                                         tc::smem_desc(re0 + (td - 1) * kPlaneS + kk * 256, 128, 512), idesc, accum);
-                            tc::mma_bf16(T.tmem + 128 + (lv - 2) * kSN, ad,
-                                         tc::smem_desc(im0 + (td - 1) * kPlaneS + kk * 256, 128, 512), idesc, accum);
-                        }
-                    }
-                }
+                issue_levels<2 * kSN, kPlaneA, kPlaneS>(T.tmem, tc::smem_desc(tc::smem_addr(T.a), 128, 512),
+                                                        tc::smem_desc(tc::smem_addr(T.b), 128, 512));
                 tc::mma_commit(&T.bar);
             }
             bool ok = true;
@@ -671,34 +654,30 @@ __device__ void solve_chunk_tc(const LatticeArgs& A, int q0, int qi, int ch, uns
             }
             tc::tc_fence_after_sync();
             {   // lane quarter (warp & 3): rows m = 32 (warp & 3) + lane; warp >> 2: rhs 4 g ...
+                // 4 g + 3, their Re and Im sums side by side
                 const int ql = warp & 3, g = warp >> 2;
                 const int m = 32 * ql + lane;
-                const uint32_t trow = T.tmem + (static_cast<uint32_t>(32 * ql) << 16) + 4 * g;
+                const uint32_t trow = T.tmem + (static_cast<uint32_t>(32 * ql) << 16) + 8 * g;
                 long long Qr[4], Qi[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) Qr[k] = Qi[k] = 0;
 #pragma unroll
-                for (int l0 = 2; l0 <= kTNL; l0 += 4) {
-                    uint32_t v[8][4];
+                for (int l0 = 2; l0 <= kTNL; l0 += 2) {
+                    uint32_t v[2][8];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (l0 + u <= kTNL) {
-                            tc::tmem_ld4_async(trow + (l0 + u - 2) * kSN, v[2 * u]);
-                            tc::tmem_ld4_async(trow + 128 + (l0 + u - 2) * kSN, v[2 * u + 1]);
-                        }
+                    for (int u = 0; u < 2; ++u) tc::tmem_ld8_async(trow + (l0 + u - 2) * (2 * kSN), v[u]);
                     tc::tmem_wait_ld();
 #pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (l0 + u <= kTNL) {
-                            const int sh = 54 - 8 * (l0 + u);
+                    for (int u = 0; u < 2; ++u) {
+                        const int sh = 54 - 8 * (l0 + u);
 #pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                const long long dr = __float2int_rz(__uint_as_float(v[2 * u][k]));
-                                const long long di = __float2int_rz(__uint_as_float(v[2 * u + 1][k]));
-                                Qr[k] += sh >= 0 ? (dr << sh) : ((dr + (1ll << (-sh - 1))) >> (-sh));
-                                Qi[k] += sh >= 0 ? (di << sh) : ((di + (1ll << (-sh - 1))) >> (-sh));
-                            }
+                        for (int k = 0; k < 4; ++k) {
+                            const long long dr = __float2int_rz(__uint_as_float(v[u][k]));
+                            const long long di = __float2int_rz(__uint_as_float(v[u][4 + k]));
+                            Qr[k] += sh >= 0 ? (dr << sh) : ((dr + (1ll << (-sh - 1))) >> (-sh));
+                            Qi[k] += sh >= 0 ? (di << sh) : ((di + (1ll << (-sh - 1))) >> (-sh));
                         }
+                    }
                 }
                 if (m0 + m < rows) {
                     const int r = J + nb + m0 + m, sr = r % S;
@@ -751,7 +730,7 @@ __global__ void __launch_bounds__(kT, 1) lattice_wide_kernel(const LatticeArgs A
         T = reinterpret_cast<TcSmem*>(smem + tc_offset_dev(A.b));
         if (tid == 0) {
             T->fail = 0;
-            tc::mbar_init(&T->bar, 4);   // one commit per MMA issuer
+            tc::mbar_init(&T->bar, 1);   // one commit per tile
             tc::mbar_init_fence();
         }
         if (tid < 32) tc::tmem_alloc(&T->tmem, 512);
