@@ -815,16 +815,17 @@ def run_lattice3d(args):
     form = ("blocked band L D L^T + forward solves" if lform == 1
             else "band L D L^T + selected inversion in a shared-memory window")
     if tc_flops > 0:
-        # trailing updates as exact digit products on the tensor cores: the roof is the bf16
-        # pipe; the FP64-equivalent rate of the algorithm is reported beside it
+        # panels, trailing updates and solves as exact digit products on the tensor cores: the
+        # roof is the bf16 pipe; the FP64-equivalent rate of the algorithm is reported beside it
         tfl = tc_flops * nspin * nw
         lroof = {"bound": "tensor", "achieved": tfl / lat_s / 1e12, "peak": MEASURED_BF16_SUSTAINED,
                  "unit": "TFLOP/s", "frac": tfl / lat_s / 1e12 / MEASURED_BF16_SUSTAINED,
                  "traffic": measured_traffic("lattice_kernel:" + name),
                  "kernel": lkern, "matrices": nspin * nw, "N": N, "band": b,
-                 "form": form + ", trailing updates on the tensor cores", "seconds": lat_s,
-                 "work": "bf16 flops of the trailing updates' digit products (the panel "
-                         "factorisations and forward solves run on the FP64 pipe)",
+                 "form": form + ", products on the tensor cores", "seconds": lat_s,
+                 "work": "bf16 flops of the exact digit products (panels below their diagonal "
+                         "blocks, trailing updates, forward solves); the diagonal blocks and the "
+                         "solves' own triangles run on the FP64 pipe",
                  "algorithmic_fp64_tflops": fl / lat_s / 1e12,
                  "algorithmic_fp64_vs_fp64_nominal": fl / lat_s / 1e12 / FP64_PEAK_TFLOPS,
                  "peak_source": "measured dense bf16 (cuBLAS, sustained) of this GPU"}

@@ -216,8 +216,9 @@ hf_status hf_get_drift(hf_ctx* ctx, double* max_drift, unsigned long long* refre
  * *launches = kernel launches per lattice step; *cfma = complex multiply-adds that the form's
  * algorithm performs per (w_n, sigma) matrix (factorisation plus selected inversion, or plus
  * the forward solves), averaged over the spin matrices; *tc_flops = bf16 flops per matrix of
- * the exact digit products with which the blocked form runs its trailing updates on the tensor
- * cores (band half-widths 128 .. 520; 0 otherwise).  Any pointer may be NULL. */
+ * the exact digit products with which the blocked form runs its panels, trailing updates and
+ * forward solves on the tensor cores (band half-widths 128 .. 520; 0 otherwise), averaged over
+ * the spin matrices.  Any pointer may be NULL. */
 hf_status hf_get_lattice_plan(const hf_ctx* ctx, int* form, int* launches, double* cfma,
                               double* tc_flops);
 

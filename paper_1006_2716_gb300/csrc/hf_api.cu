@@ -861,7 +861,9 @@ hf_status hf_get_lattice_plan(const hf_ctx* c, int* form, int* launches, double*
     if (form) *form = c->lat_wide ? 1 : 0;
     if (launches) *launches = nl * (c->lat_wide ? 2 : 1);
     if (cfma) *cfma = f;
-    if (tc_flops) *tc_flops = c->lat_wide ? hfk::lattice_wide_tc_flops(N, b) : 0.0;
+    if (tc_flops)
+        *tc_flops = c->lat_wide ? hfk::lattice_wide_tc_flops(N, b, c->wide_pos_host.data(), c->wide_npos, nspin)
+                                : 0.0;
     return HF_OK;
 }
 

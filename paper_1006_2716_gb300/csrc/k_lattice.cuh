@@ -40,7 +40,7 @@ cudaError_t launch_lattice(const LatticeArgs& a, int q0, int nq, cudaStream_t st
 int lattice_wide_max_band();
 int lattice_wide_rhs_per_block();
 // bf16 flops of the tensor-core trailing updates per matrix (0 where the band keeps DFMA)
-double lattice_wide_tc_flops(int N, int b);
+double lattice_wide_tc_flops(int N, int b, const int* pos, int npos, int nspin);
 cudaError_t launch_lattice_wide(const LatticeArgs& a, int q0, int nq, cudaStream_t st);
 
 // Lattice step over all nspin * nw matrices with the band buffers in a fixed 16 MiB device array

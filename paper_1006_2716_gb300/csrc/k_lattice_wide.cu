@@ -76,6 +76,11 @@ constexpr int kPlaneA = kTM * kTK * 2;  // bytes of one digit plane of A (K-majo
 constexpr int kPlaneB = 2 * kTN * kTK * 2;   // one digit plane of B: 32 rows r x (Re, Im)
 constexpr int kTcMinBand = 128;
 constexpr int kTcMaxBand = 520;
+// the products with 16 columns on the B side (the panel's rows below its diagonal block, the
+// forward solves): a digit plane holds the Re and Im rows of the 16 columns
+constexpr int kSN = 16;                          // B columns (right-hand sides of the solves)
+constexpr int kPlaneS = 2 * kSN * kTK * 2;       // one digit plane of the y panel (Re and Im rows)
+static_assert(kSN == kR && kPlaneS <= kPlaneB, "solve planes fit");
 
 struct TcSmem {                         // behind the panel, 1024-byte aligned
     unsigned char a[kTD * kPlaneA];
@@ -341,6 +346,172 @@ __device__ void trailing_tc(TcSmem& T, const double2* P, int RP, int nb, int ten
     }
 }
 
+// The panel of a full step with the tensor cores.  (1) Its 16 x 16 diagonal block is factored in
+// FP64, a thread per pair (jp, i) of the block's lower triangle in order of falling jp, so that
+// the pairs a step updates are packed into the fewest warps; the thread of the next pivot also
+// forms its reciprocal, and column j - 1 is scaled during step j.  (2) X = L11^{-1} by forward
+// substitution, a half warp per column of X (X[k][m] passed by shuffle).  (3) The rows below,
+// L21 = A21 (D L11^T)^{-1} = A21 Z with Z[m][c] = X[c][m] / D_c, as exact digit products with
+// A = [Re A21 | Im A21] (128 rows per tile) and B = [Re Z | -Im Z], [Im Z | Re Z] (the solves'
+// layout), each entry rounded once.  P: the staged panel (row stride RP, rmax rows); on return
+// it holds D on the diagonal and L below.  Returns false if an MMA wait ran out.
+__device__ bool panel_tc(TcSmem& T, double2* P, int RP, int rmax, bool& bad, uint32_t& ph) {
+    const int tid = static_cast<int>(threadIdx.x), lane = tid & 31, warp = tid >> 5;
+    const double2 zero = make_double2(0.0, 0.0);
+    // scratch behind the 7 B planes of the product: Z (then X) and the pivots' reciprocals
+    double2* Zs = reinterpret_cast<double2*>(T.b + kTD * kPlaneS);   // [c][m]
+    double2* inv = Zs + kNB * kNB;
+    static_assert(kTD * kPlaneS + (kNB * kNB + kNB) * static_cast<int>(sizeof(double2)) <= kTD * kPlaneB,
+                  "panel scratch fits behind the B planes");
+    // (1) pair p < 120 of the pairs with jp >= 1: jp = 15 (1 pair), 14 (2), ...
+    int jp = -1, i = -1;
+    if (tid < kNB * (kNB - 1) / 2) {
+        int base = 0, c = kNB - 1;
+        while (tid >= base + (kNB - c)) {
+            base += kNB - c;
+            --c;
+        }
+        jp = c;
+        i = c + (tid - base);
+    }
+    const int sc = tid - 128;   // the scaling threads 128 .. 143: row sc of the column before
+    for (int j = 0; j < kNB; ++j) {
+        const double2 D = P[j * RP + j];
+        if (tid == 0 && (!(fabs(D.x) + fabs(D.y) > 0.0) || !isfinite(D.x) || !isfinite(D.y))) bad = true;
+        if (jp > j) {
+            const double2 r = j == 0 ? crecip(D) : inv[j];
+            const double2 l = cmul(P[j * RP + i], r);
+            const double2 t = cfms(P[jp * RP + i], l, P[j * RP + jp]);
+            P[jp * RP + i] = t;
+            if (i == jp && jp == j + 1) inv[jp] = crecip(t);   // the next pivot is final
+        }
+        if (j == 0 && sc == 0) inv[0] = crecip(D);
+        if (j > 0 && sc > j - 1 && sc < kNB) P[(j - 1) * RP + sc] = cmul(P[(j - 1) * RP + sc], inv[j - 1]);
+        __syncthreads();
+    }
+    // (2) X = L11^{-1}: half warp m (tid >> 4) holds column m, lane c = tid & 15 the entry X[c][m];
+    // then Z[m][c] = X[c][m] / D_c and the B scales (a thread per column c)
+    if (tid < kNB * kNB) {
+        const int m = tid >> 4, c = tid & 15, half = tid & 16;
+        double2 x = c == m ? make_double2(1.0, 0.0) : zero;
+        for (int k = 2 * (warp); k < kNB - 1; ++k) {   // columns m < 2 warp + 2 start at k = m
+            const double2 xk = shfl_c(x, half | k);
+            if (c > k && k >= m) x = cfms(x, P[k * RP + c], xk);
+        }
+        Zs[c * kNB + m] = c >= m ? cmul(x, inv[c]) : zero;
+    }
+    __syncthreads();
+    if (tid < kNB) {
+        int e = tc::kNoExp;
+        for (int m = 0; m < kNB; ++m) {
+            const double2 z = Zs[tid * kNB + m];
+            e = max(e, max(tc::exp_of(z.x), tc::exp_of(z.y)));
+        }
+        T.tb[tid] = scale_of(e);
+    }
+    __syncthreads();
+    // (3) B digits (256 threads, 4 K each: part, column c, K quarter-group kq)
+    if (tid < 2 * kSN * 8) {
+        const int part = tid >> 7, u = tid & 127;
+        const int c = u & 15, kq = u >> 4, kg = kq >> 1;
+        const int Tb = T.tb[c];
+        unsigned long long U[4];
+        bool neg[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const double2 z = Zs[c * kNB + ((4 * kq + q) & 15)];
+            double x;
+            if (part == 0) x = kg < 2 ? z.x : neg_bits(z.y);
+            else x = kg < 2 ? z.y : z.x;
+            U[q] = tc::to_fixed_mag(x, Tb, neg[q]);
+        }
+        const int mb = 8 * (c >> 2) + 4 * part + (c & 3);
+        put_digits4(U, neg, T.b, kPlaneS, core_off(mb, kg) + (kq & 1) * 8);
+    }
+    const int rows = rmax - kNB;   // rows kNB .. rmax - 1
+    for (int m0 = 0; m0 < rows; m0 += kTM) {
+        {   // A: four threads per row (four panel columns each) agree on the row's scale
+            const int m = tid >> 2, part = tid & 3;
+            const int r = kNB + m0 + m;
+            double2 a[4];
+            int e = tc::kNoExp;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                a[q] = m0 + m < rows ? P[(4 * part + q) * RP + r] : zero;
+                e = max(e, max(tc::exp_of(a[q].x), tc::exp_of(a[q].y)));
+            }
+            e = max(e, __shfl_xor_sync(0xffffffffu, e, 1));
+            e = max(e, __shfl_xor_sync(0xffffffffu, e, 2));
+            const int Ta = scale_of(e);
+            if (part == 0) T.ta[m] = Ta;
+            unsigned long long U[4];
+            bool neg[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) U[q] = tc::to_fixed_mag(a[q].x, Ta, neg[q]);
+            put_digits4(U, neg, T.a, kPlaneA, core_off(m, part >> 1) + (part & 1) * 8);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) U[q] = tc::to_fixed_mag(a[q].y, Ta, neg[q]);
+            put_digits4(U, neg, T.a, kPlaneA, core_off(m, 2 + (part >> 1)) + (part & 1) * 8);
+        }
+        tc::fence_async_shared();
+        tc::tc_fence_before_sync();
+        __syncthreads();
+        if (tid == 0 && !T.fail) {
+            tc::tc_fence_after_sync();
+            issue_levels<2 * kSN, kPlaneA, kPlaneS>(T.tmem, tc::smem_desc(tc::smem_addr(T.a), 128, 512),
+                                                    tc::smem_desc(tc::smem_addr(T.b), 128, 512));
+            tc::mma_commit(&T.bar);
+        }
+        bool ok = true;
+        if (!T.fail) ok = tc::mbar_wait(&T.bar, ph);
+        ph ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) T.fail = 1;
+            return false;
+        }
+        tc::tc_fence_after_sync();
+        {   // rows m = 32 (warp & 3) + lane, columns c = 4 (warp >> 2) ...: L21 = the rounded sums
+            const int ql = warp & 3, g = warp >> 2;
+            const int m = 32 * ql + lane;
+            const uint32_t trow = T.tmem + (static_cast<uint32_t>(32 * ql) << 16) + 8 * g;
+            long long Qr[4], Qi[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) Qr[k] = Qi[k] = 0;
+#pragma unroll
+            for (int l0 = 2; l0 <= kTNL; l0 += 2) {
+                uint32_t v[2][8];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) tc::tmem_ld8_async(trow + (l0 + u - 2) * (2 * kSN), v[u]);
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int sh = 54 - 8 * (l0 + u);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const long long dr = __float2int_rz(__uint_as_float(v[u][k]));
+                        const long long di = __float2int_rz(__uint_as_float(v[u][4 + k]));
+                        Qr[k] += sh >= 0 ? (dr << sh) : ((dr + (1ll << (-sh - 1))) >> (-sh));
+                        Qi[k] += sh >= 0 ? (di << sh) : ((di + (1ll << (-sh - 1))) >> (-sh));
+                    }
+                }
+            }
+            if (m0 + m < rows) {
+                const int r = kNB + m0 + m;
+                const int Ta = T.ta[m];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int c = 4 * g + k;
+                    const int E = Ta + T.tb[c] - 54;
+                    P[c * RP + r] = make_double2(tc::fixed_to_double(Qr[k], E), tc::fixed_to_double(Qi[k], E));
+                }
+            }
+        }
+        tc::tc_fence_before_sync();
+        __syncthreads();   // TMEM and the A planes are reused by the next tile
+    }
+    return true;
+}
+
 // Matrix qi of the launch: assembly and blocked band L D L^T into its band buffer (column k: D_k
 // at d = 0, L_{k+d,k} at d >= 1).  Sets bad on a vanishing or non-finite pivot.  TC: the trailing
 // updates run on the tensor cores (T: the block's tensor-core state, ph its mbarrier phase).
@@ -381,8 +552,13 @@ __device__ void factor_matrix(const LatticeArgs& A, int q0, int qi, unsigned cha
                 P[j * RP + i] = v;
             }
         __syncthreads();
-        // (b) factor it: column j -> L (scaled by 1/D_j); A[i][j'] -= L_ij v_j' (v = D_j L_j'j)
-        for (int j = 0; j < nb; ++j) {
+        // (b) factor it: column j -> L (scaled by 1/D_j); A[i][j'] -= L_ij v_j' (v = D_j L_j'j);
+        //     full panels with rows below their diagonal block on the tensor cores (TC)
+        bool panel_done = false;
+        if constexpr (TC) {
+            if (nb == kNB && rmax > kNB && !T->fail) panel_done = panel_tc(*T, P, RP, rmax, bad, ph);
+        }
+        for (int j = 0; j < nb && !panel_done; ++j) {
             const double2 D = P[j * RP + j];
             if (tid > j && tid < nb) vj[tid] = P[j * RP + tid];
             if (tid == 0 && (!(fabs(D.x) + fabs(D.y) > 0.0) || !isfinite(D.x) || !isfinite(D.y)))
@@ -525,9 +701,6 @@ __device__ void solve_chunk(const LatticeArgs& A, int q0, int qi, int ch, unsign
 // J + S .. J + S + 15; (iii) the rows J + 16 .. J + 15 + b lose sum_j L_rj y_j, formed as in
 // trailing_tc with A = [Re L | Im L] (128 rows per tile) and 32 TMEM columns per level (eight
 // levels: 256 columns), and subtracted from their window slots.
-constexpr int kSN = 16;                          // right-hand sides
-constexpr int kPlaneS = 2 * kSN * kTK * 2;       // one digit plane of the y panel (Re and Im rows)
-static_assert(kSN == kR && kPlaneS <= kPlaneB, "solve planes fit");
 
 __device__ void solve_chunk_tc(const LatticeArgs& A, int q0, int qi, int ch, unsigned char* smem,
                                TcSmem& T, uint32_t& ph) {
@@ -785,22 +958,37 @@ int lattice_wide_max_band() { return kWideMaxBand; }
 
 int lattice_wide_rhs_per_block() { return kR; }
 
-double lattice_wide_tc_flops(int N, int b) {
+double lattice_wide_tc_flops(int N, int b, const int* pos, int npos, int nspin) {
     if (b < kTcMinBand || b > kTcMaxBand) return 0.0;
-    // per full panel: column tiles of 128, row tiles of 32 from the tile's first column on;
-    // 2 (Re, Im) x 2 (K halves) x the digit pairs of levels <= kTNL MMAs of 128 x 32 x 16
+    // one tile of 128 rows with W columns on the B side: 2 flops x 2 K halves x the digit pairs
+    // of levels <= kTNL x 128 x W x 16
     int pairs = 0;
     for (int sd = 1; sd <= kTD; ++sd)
         for (int td = 1; td <= kTD; ++td)
             if (sd + td <= kTNL) ++pairs;
-    const double per_tile = 4.0 * pairs * 2.0 * kTM * kTN * 16;
+    const double tile64 = 4.0 * pairs * kTM * (2 * kTN) * 16;
+    const double tile32 = 4.0 * pairs * kTM * (2 * kSN) * 16;
     double f = 0.0;
-    for (int k0 = 0; k0 + kNB <= N; k0 += kNB) {
+    for (int k0 = 0; k0 + kNB <= N; k0 += kNB) {   // full panels
         const int rmax = std::min(kNB + b, N - k0);
+        // the rows below the diagonal block: tiles of 128 with the 16 columns of Z
+        f += tile32 * ((rmax - kNB + kTM - 1) / kTM);
+        // the trailing update: column tiles of 128, row tiles of 32 from the tile's first column on
         const int rows = std::min(kNB - 1 + b, rmax - 1) - kNB + 1;
-        for (int c0 = 0; c0 < rows; c0 += kTM) f += per_tile * ((rows - c0 + kTN - 1) / kTN);
+        for (int c0 = 0; c0 < rows; c0 += kTM) f += tile64 * ((rows - c0 + kTN - 1) / kTN);
     }
-    return f;
+    // the forward solves: per task of kR positions (ascending), from its first position, the rows
+    // below each full step in tiles of 128
+    double sv = 0.0;
+    for (int sp = 0; sp < nspin; ++sp)
+        for (int ch = 0; ch * kR < npos; ++ch) {
+            const int j0 = pos[static_cast<size_t>(sp) * npos + ch * kR];
+            for (int J = j0; J + kNB <= N; J += kNB) {
+                const int rows = std::min(b, N - J - kNB);
+                if (rows > 0) sv += tile32 * ((rows + kTM - 1) / kTM);
+            }
+        }
+    return f + sv / std::max(nspin, 1);
 }
 
 cudaError_t launch_lattice_wide(const LatticeArgs& a, int q0, int nq, cudaStream_t st) {
