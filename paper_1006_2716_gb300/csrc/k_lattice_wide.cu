@@ -51,44 +51,45 @@ size_t solve_smem(int b) {       // kR windows of b + 1 entries
     return static_cast<size_t>(kR) * (b + 1) * sizeof(double2);
 }
 
-// ---- the trailing update on the tensor cores (128 <= b <= kTcMaxBand) ----
-// A[r][c] -= sum_j L_rj W_cj, W_cj = D_j L_cj, over the trailing triangle, as exact digit
-// products (the error-free splitting of tc_ozaki.cuh).  With A = [Re W | Im W] (128 trailing
+// ---- the products on the tensor cores (128 <= b <= kTcMaxBand) ----
+// The trailing update A[r][c] -= sum_j L_rj W_cj, W_cj = D_j L_cj, the panel's rows below its
+// diagonal block and the forward solves' updates run as exact digit products (the error-free
+// splitting of tc_ozaki.cuh).  For the trailing update, with A = [Re W | Im W] (128 trailing
 // columns c per tile, K = 32: the panel's 16 columns, real and imaginary parts) and
-// B_re = [Re L | -Im L], B_im = [Im L | Re L] (32 trailing rows r per tile), Re and Im of the
+// B_re = [Re L | -Im L], B_im = [Im L | Re L] (16 trailing rows r per tile), Re and Im of the
 // sum are A B_re^T and A B_im^T.  Each operand row gets a power-of-two scale and kTD balanced
 // base-256 digits; the levels n = s + t <= kTNL are kept (the dropped ones stay below 2^-58 of
 // the scales), each an exact FP32 accumulator in TMEM (K = 32 terms of at most 2^14, at most 7
-// per level: below 2^22).  A digit plane of B holds the B_re and B_im rows of the tile's 32
+// per level: below 2^22).  A digit plane of B holds the B_re and B_im rows of the tile's 16
 // rows r, interleaved by eights (row 16 (r / 8) + 8 part + r % 8), so a level's accumulator is
-// 64 TMEM columns in which each thread's 8 rows r have their Re and Im sums side by side; the
-// eight levels fill all 512 columns.  For each digit s of A the digits t of B are stacked along
-// N (up to four planes, 256 columns, per MMA): 23 MMAs per tile, each reading its A plane once
-// for up to 256 columns.  The epilogue combines a tile's levels in 64-bit integers and
+// 32 TMEM columns in which each thread's 8 rows r have their Re and Im sums side by side; eight
+// levels take 256 columns, half of TMEM.  For each digit s of A the digits t of B are stacked
+// along N (up to eight planes, 256 columns, per MMA): 15 MMAs per tile, each reading its A plane
+// once for up to 256 columns.  The epilogue combines a tile's levels in 64-bit integers and
 // subtracts the rounded sums from the band buffer in FP64: one DADD per part and entry per
 // panel, against 16 complex multiply-adds.
 constexpr int kTD = 7;                  // digits of an operand
 constexpr int kTNL = kTD + 2;           // highest level kept
-constexpr int kTM = 128;                // trailing columns c per tile (MMA M)
-constexpr int kTN = 32;                 // trailing rows r per tile
+static_assert((kTNL - 1) % 2 == 0, "the levels 2 .. kTNL pair up");
+constexpr int kTM = 128;                // rows of A per tile (MMA M): trailing columns c, rows
 constexpr int kTK = 32;                 // K
 constexpr int kPlaneA = kTM * kTK * 2;  // bytes of one digit plane of A (K-major core matrices)
-constexpr int kPlaneB = 2 * kTN * kTK * 2;   // one digit plane of B: 32 rows r x (Re, Im)
 constexpr int kTcMinBand = 128;
 constexpr int kTcMaxBand = 520;
-// the products with 16 columns on the B side (the panel's rows below its diagonal block, the
-// forward solves): a digit plane holds the Re and Im rows of the 16 columns
-constexpr int kSN = 16;                          // B columns (right-hand sides of the solves)
-constexpr int kPlaneS = 2 * kSN * kTK * 2;       // one digit plane of the y panel (Re and Im rows)
-static_assert(kSN == kR && kPlaneS <= kPlaneB, "solve planes fit");
+// Every product has 16 complex columns on the B side (16 trailing rows, the panel's 16 columns
+// of Z, 16 right-hand sides): a digit plane of B holds their Re and Im rows, 32 rows of K = 32.
+constexpr int kSN = 16;
+constexpr int kPlaneS = 2 * kSN * kTK * 2;
+static_assert(kSN == kR, "a solve task's right-hand sides fill the B side");
 
 struct TcSmem {                         // behind the panel, 1024-byte aligned
     unsigned char a[kTD * kPlaneA];
-    unsigned char b[kTD * kPlaneB];
+    unsigned char b[2 * kTD * kPlaneS];  // B planes: one set per warp group (trailing update)
     int ta[kTM];                        // scales of A's rows (the tile's columns c)
     int tb[kNB + kTcMaxBand];           // scales of the B rows: the panel's rows (trailing
                                         // update), the right-hand sides (solve)
-    uint64_t bar;                       // MMA completion
+    uint64_t bar[2];                    // MMA completion (the trailing update's two warp
+                                        // groups; the panels and solves use bar[0])
     uint32_t tmem;                      // TMEM base address
     int fail;                           // an MMA wait ran out: no more tensor-core work
 };
@@ -145,6 +146,22 @@ __device__ __forceinline__ int core_off(int m, int kg) { return ((m >> 3) * 4 + 
 
 __device__ __forceinline__ int scale_of(int e) { return e == tc::kNoExp ? 0 : e + 2; }
 
+// A level accumulator of these products (an integer below 2^22 in magnitude: K = 32 terms of at
+// most 2^14, at most 7 digit pairs) as an int: adding 1.5 2^23 moves it, exactly, into the low
+// bits of the significand.
+__device__ __forceinline__ int level_int(uint32_t bits) {
+    return __float_as_int(__uint_as_float(bits) + 12582912.0f) - 0x4B400000;
+}
+
+// Adds the levels n and n + 1 (n even), combined exactly in 32 bits as d_n 2^8 + d_{n+1}
+// (below 2^31), to a 64-bit sum in units of 2^-54 of the scales (rounded where the pair's
+// weight 2^(54 - 8 (n + 1)) is below one unit).
+__device__ __forceinline__ void add_level_pair(long long& Q, int dn, int dn1, int n) {
+    const long long p = static_cast<long long>(dn * 256 + dn1);
+    const int sh = 54 - 8 * (n + 1);
+    Q += sh >= 0 ? (p << sh) : ((p + (1ll << (-sh - 1))) >> (-sh));
+}
+
 // The sign-flipped bit pattern of x (no FP64 instruction).
 __device__ __forceinline__ double neg_bits(double x) {
     return __longlong_as_double(__double_as_longlong(x) ^ static_cast<long long>(0x8000000000000000ull));
@@ -199,15 +216,25 @@ __device__ __forceinline__ void issue_levels(uint32_t tmem, uint64_t adesc, uint
     }
 }
 
+// Named barrier `id` over the `count` threads of a warp group.
+__device__ __forceinline__ void group_sync(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
 // The trailing update of one panel on the tensor cores: rows and columns nb .. tend of the panel
 // P (RP the row stride, L_ij scaled, D_j on the diagonal) into the band buffer Bq at k0.
-// ph: the mbarrier's phase bit, flipped by every wait.
+// Per column tile of 128 all 512 threads cut the A digits; its row tiles of 16 go alternately to
+// the two warp groups (threads 0 .. 255 and 256 .. 511), each with its own B planes, its own half
+// of TMEM (eight levels x 32 columns), its own mbarrier and a named barrier, so that one group's
+// epilogue runs while the other cuts digits and waits for its MMAs.  ph: bit g the phase of
+// mbarrier g, flipped by every tile of group g (in every thread).
 __device__ void trailing_tc(TcSmem& T, const double2* P, int RP, int nb, int tend, double2* Bq,
                             int k0, int S, uint32_t& ph) {
+    constexpr int kRT = 16;                       // trailing rows r per tile
     const int tid = static_cast<int>(threadIdx.x), lane = tid & 31, warp = tid >> 5;
+    const int grp = tid >> 8, u = tid & 255;      // warp group, thread within it
     const int rows = tend - nb + 1;
     if (rows <= 0) return;
-    const double2 zero = make_double2(0.0, 0.0);
     // the B scales of every trailing row, once for the panel (a thread per row)
     for (int i = nb + tid; i <= tend; i += kT) {
         int e = tc::kNoExp;
@@ -218,7 +245,8 @@ __device__ void trailing_tc(TcSmem& T, const double2* P, int RP, int nb, int ten
         }
         T.tb[i] = scale_of(e);
     }
-    __syncthreads();
+    unsigned char* bplanes = T.b + grp * (kTD * kPlaneS);
+    const uint32_t tmem = T.tmem + 256 * grp;
     for (int c0 = 0; c0 < rows; c0 += kTM) {
         // A: W_cj = D_j L_cj of the tile's columns c = nb + c0 + m, m < 128 (zero past tend):
         // four threads per column (adjacent lanes, four j each) form their W once, agree on the
@@ -231,7 +259,7 @@ __device__ void trailing_tc(TcSmem& T, const double2* P, int RP, int nb, int ten
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int j = 4 * part + q;
-                w[q] = c <= tend ? cmul(P[j * RP + j], P[j * RP + c]) : zero;
+                w[q] = c <= tend ? cmul(P[j * RP + j], P[j * RP + c]) : make_double2(0.0, 0.0);
                 e = max(e, max(tc::exp_of(w[q].x), tc::exp_of(w[q].y)));
             }
             e = max(e, __shfl_xor_sync(0xffffffffu, e, 1));
@@ -247,14 +275,20 @@ __device__ void trailing_tc(TcSmem& T, const double2* P, int RP, int nb, int ten
             for (int q = 0; q < 4; ++q) U[q] = tc::to_fixed_mag(w[q].y, Ta, neg[q]);
             put_digits4(U, neg, T.a, kPlaneA, core_off(m, 2 + (part >> 1)) + (part & 1) * 8);
         }
-        for (int r0 = c0 - (c0 % kTN); r0 < rows; r0 += kTN) {
-            // B: L_rj of the tile's rows r = nb + r0 + nr, nr < 32, as [Re | -Im] (part 0) and
-            // [Im | Re] (part 1), 4 K a thread
+        tc::fence_async_shared();
+        __syncthreads();   // the A planes and scales (and, first time round, the B scales)
+        const int nt = (rows - c0 + kRT - 1) / kRT;
+        for (int t = 0; t < nt; ++t) {
+            const int g = t & 1;
+            if (g != grp) {            // the other group's tile: only its phase bit
+                ph ^= 1u << g;
+                continue;
+            }
+            const int r0 = c0 + t * kRT;
+            // B: L_rj of the tile's rows r = nb + r0 + nr, nr < 16, as [Re | -Im] (part 0) and
+            // [Im | Re] (part 1), 4 K a thread; plane row 16 (nr / 8) + 8 part + nr % 8
             {
-                const int part = tid >> 8;
-                const int u = tid & 255;
-                const int nr = u & (kTN - 1), kq = u >> 5;   // K quarter-group: 4 K at 4 kq
-                const int kg = kq >> 1;
+                const int part = u >> 7, nr = u & 15, kq = (u >> 4) & 7, kg = kq >> 1;
                 const int r = nb + r0 + nr;
                 const int Tb = r <= tend ? T.tb[r] : 0;
                 unsigned long long U[4];
@@ -262,70 +296,62 @@ __device__ void trailing_tc(TcSmem& T, const double2* P, int RP, int nb, int ten
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int j = ((4 * kq + q) & 15);
-                    const double2 l = r <= tend ? P[j * RP + r] : zero;
-                    // part 0: k < 16 Re L, k >= 16 -Im L;  part 1: k < 16 Im L, k >= 16 Re L
+                    const double2 l = r <= tend ? P[j * RP + r] : make_double2(0.0, 0.0);
                     double x;
                     if (part == 0) x = kg < 2 ? l.x : neg_bits(l.y);
                     else x = kg < 2 ? l.y : l.x;
                     U[q] = tc::to_fixed_mag(x, Tb, neg[q]);
                 }
                 const int mb = 16 * (nr >> 3) + 8 * part + (nr & 7);
-                put_digits4(U, neg, T.b, kPlaneB, core_off(mb, kg) + (kq & 1) * 8);
+                put_digits4(U, neg, bplanes, kPlaneS, core_off(mb, kg) + (kq & 1) * 8);
             }
             tc::fence_async_shared();
             tc::tc_fence_before_sync();
-            __syncthreads();
+            group_sync(1 + grp, 256);
+            // the MMAs, issued by the group's first thread and committed to its mbarrier
+            if (u == 0 && !T.fail) {
+                tc::tc_fence_after_sync();
+                issue_levels<2 * kSN, kPlaneA, kPlaneS>(tmem, tc::smem_desc(tc::smem_addr(T.a), 128, 512),
+                                                        tc::smem_desc(tc::smem_addr(bplanes), 128, 512));
+                tc::mma_commit(&T.bar[grp]);
+            }
             // the band entries this thread updates, loaded while the MMAs run: lane quarter
-            // (warp & 3) holds columns c = c0 + 32 (warp & 3) + lane; the four warps of a quarter
-            // take 8 rows each (contiguous in column c)
-            const int ql = warp & 3, g = warp >> 2;
+            // (warp & 3) holds columns c = c0 + 32 (warp & 3) + lane, the group's two warps of a
+            // quarter 8 rows each (contiguous in column c); loaded unconditionally (entries
+            // outside the triangle clamped onto it, their values unused)
+            const int ql = warp & 3, h = (warp >> 2) & 1;
             const int m = 32 * ql + lane;
             const int c = nb + c0 + m;
-            const int rlo = nb + r0 + 8 * g;
+            const int rlo = nb + r0 + 8 * h;
             double2* col = Bq + (static_cast<size_t>(k0 + c) * S - c);   // col[r] = A[r][c]
+            const int cc = min(c, tend);
+            const double2* colc = Bq + (static_cast<size_t>(k0 + cc) * S - cc);
             double2 x[8];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int r = rlo + k;
-                x[k] = (c <= tend && r >= c && r <= tend) ? col[r] : zero;
-            }
-            // the MMAs, issued by one thread and committed to the mbarrier
-            if (tid == 0 && !T.fail) {
-                tc::tc_fence_after_sync();
-                issue_levels<2 * kTN, kPlaneA, kPlaneB>(T.tmem, tc::smem_desc(tc::smem_addr(T.a), 128, 512),
-                                                        tc::smem_desc(tc::smem_addr(T.b), 128, 512));
-                tc::mma_commit(&T.bar);
-            }
-            // every thread waits for the MMAs (bounded; a wait that runs out stops the tensor-core
-            // work of this block, the caller reports HF_ETIMEOUT)
-            bool ok = true;
-            if (!T.fail) ok = tc::mbar_wait(&T.bar, ph);
-            ph ^= 1u;
-            if (__syncthreads_or(!ok)) {
-                if (tid == 0) T.fail = 1;
-                return;
-            }
+            for (int k = 0; k < 8; ++k) x[k] = colc[min(max(rlo + k, cc), tend)];
+            // wait for the group's MMAs (bounded; a wait that runs out stops the tensor-core
+            // work of this block, the launch reports HF_ETIMEOUT)
+            if (!T.fail && !tc::mbar_wait(&T.bar[grp], (ph >> grp) & 1u)) T.fail = 1;
+            ph ^= 1u << grp;
             tc::tc_fence_after_sync();
             // epilogue: the level sums of this thread's 8 rows (Re and Im side by side)
             {
-                const uint32_t trow = T.tmem + (static_cast<uint32_t>(32 * ql) << 16) + 16 * g;
+                const uint32_t trow = tmem + (static_cast<uint32_t>(32 * ql) << 16) + 16 * h;
                 long long Qr[8], Qi[8];
 #pragma unroll
                 for (int k = 0; k < 8; ++k) Qr[k] = Qi[k] = 0;
 #pragma unroll
-                for (int n = 2; n <= kTNL; ++n) {
-                    uint32_t v[16];
-                    tc::tmem_ld16_async(trow + (n - 2) * (2 * kTN), v);
-                    tc::tmem_wait_ld();
-                    const int sh = 54 - 8 * n;
+                for (int n = 2; n <= kTNL; n += 2)
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        const long long dr = __float2int_rz(__uint_as_float(v[k]));
-                        const long long di = __float2int_rz(__uint_as_float(v[8 + k]));
-                        Qr[k] += sh >= 0 ? (dr << sh) : ((dr + (1ll << (-sh - 1))) >> (-sh));
-                        Qi[k] += sh >= 0 ? (di << sh) : ((di + (1ll << (-sh - 1))) >> (-sh));
+                    for (int part = 0; part < 2; ++part) {   // Re, then Im, of the levels n, n + 1
+                        uint32_t v0[8], v1[8];
+                        tc::tmem_ld8_async(trow + (n - 2) * (2 * kSN) + 8 * part, v0);
+                        tc::tmem_ld8_async(trow + (n - 1) * (2 * kSN) + 8 * part, v1);
+                        tc::tmem_wait_ld();
+#pragma unroll
+                        for (int k = 0; k < 8; ++k)
+                            add_level_pair(part == 0 ? Qr[k] : Qi[k], level_int(v0[k]), level_int(v1[k]), n);
                     }
-                }
                 if (c <= tend) {
                     const int Ta = T.ta[m];
 #pragma unroll
@@ -340,9 +366,9 @@ __device__ void trailing_tc(TcSmem& T, const double2* P, int RP, int nb, int ten
                 }
             }
             tc::tc_fence_before_sync();
-            __syncthreads();   // TMEM and the B planes are reused by the next tile
+            group_sync(1 + grp, 256);   // the group's TMEM half and B planes are reused
         }
-        __syncthreads();       // the A planes are reused by the next column tile
+        __syncthreads();                // the A planes are reused by the next column tile
     }
 }
 
@@ -361,7 +387,7 @@ __device__ bool panel_tc(TcSmem& T, double2* P, int RP, int rmax, bool& bad, uin
     // scratch behind the 7 B planes of the product: Z (then X) and the pivots' reciprocals
     double2* Zs = reinterpret_cast<double2*>(T.b + kTD * kPlaneS);   // [c][m]
     double2* inv = Zs + kNB * kNB;
-    static_assert(kTD * kPlaneS + (kNB * kNB + kNB) * static_cast<int>(sizeof(double2)) <= kTD * kPlaneB,
+    static_assert((kNB * kNB + kNB) * static_cast<int>(sizeof(double2)) <= kTD * kPlaneS,
                   "panel scratch fits behind the B planes");
     // (1) pair p < 120 of the pairs with jp >= 1: jp = 15 (1 pair), 14 (2), ...
     int jp = -1, i = -1;
@@ -460,10 +486,10 @@ __device__ bool panel_tc(TcSmem& T, double2* P, int RP, int rmax, bool& bad, uin
             tc::tc_fence_after_sync();
             issue_levels<2 * kSN, kPlaneA, kPlaneS>(T.tmem, tc::smem_desc(tc::smem_addr(T.a), 128, 512),
                                                     tc::smem_desc(tc::smem_addr(T.b), 128, 512));
-            tc::mma_commit(&T.bar);
+            tc::mma_commit(&T.bar[0]);
         }
         bool ok = true;
-        if (!T.fail) ok = tc::mbar_wait(&T.bar, ph);
+        if (!T.fail) ok = tc::mbar_wait(&T.bar[0], ph & 1u);
         ph ^= 1u;
         if (__syncthreads_or(!ok)) {
             if (tid == 0) T.fail = 1;
@@ -484,15 +510,9 @@ __device__ bool panel_tc(TcSmem& T, double2* P, int RP, int rmax, bool& bad, uin
                 for (int u = 0; u < 2; ++u) tc::tmem_ld8_async(trow + (l0 + u - 2) * (2 * kSN), v[u]);
                 tc::tmem_wait_ld();
 #pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const int sh = 54 - 8 * (l0 + u);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const long long dr = __float2int_rz(__uint_as_float(v[u][k]));
-                        const long long di = __float2int_rz(__uint_as_float(v[u][4 + k]));
-                        Qr[k] += sh >= 0 ? (dr << sh) : ((dr + (1ll << (-sh - 1))) >> (-sh));
-                        Qi[k] += sh >= 0 ? (di << sh) : ((di + (1ll << (-sh - 1))) >> (-sh));
-                    }
+                for (int k = 0; k < 4; ++k) {
+                    add_level_pair(Qr[k], level_int(v[0][k]), level_int(v[1][k]), l0);
+                    add_level_pair(Qi[k], level_int(v[0][4 + k]), level_int(v[1][4 + k]), l0);
                 }
             }
             if (m0 + m < rows) {
@@ -816,10 +836,10 @@ __device__ void solve_chunk_tc(const LatticeArgs& A, int q0, int qi, int ch, uns
                 tc::tc_fence_after_sync();
                 issue_levels<2 * kSN, kPlaneA, kPlaneS>(T.tmem, tc::smem_desc(tc::smem_addr(T.a), 128, 512),
                                                         tc::smem_desc(tc::smem_addr(T.b), 128, 512));
-                tc::mma_commit(&T.bar);
+                tc::mma_commit(&T.bar[0]);
             }
             bool ok = true;
-            if (!T.fail) ok = tc::mbar_wait(&T.bar, ph);
+            if (!T.fail) ok = tc::mbar_wait(&T.bar[0], ph & 1u);
             ph ^= 1u;
             if (__syncthreads_or(!ok)) {
                 if (tid == 0) T.fail = 1;
@@ -841,15 +861,9 @@ __device__ void solve_chunk_tc(const LatticeArgs& A, int q0, int qi, int ch, uns
                     for (int u = 0; u < 2; ++u) tc::tmem_ld8_async(trow + (l0 + u - 2) * (2 * kSN), v[u]);
                     tc::tmem_wait_ld();
 #pragma unroll
-                    for (int u = 0; u < 2; ++u) {
-                        const int sh = 54 - 8 * (l0 + u);
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            const long long dr = __float2int_rz(__uint_as_float(v[u][k]));
-                            const long long di = __float2int_rz(__uint_as_float(v[u][4 + k]));
-                            Qr[k] += sh >= 0 ? (dr << sh) : ((dr + (1ll << (-sh - 1))) >> (-sh));
-                            Qi[k] += sh >= 0 ? (di << sh) : ((di + (1ll << (-sh - 1))) >> (-sh));
-                        }
+                    for (int k = 0; k < 4; ++k) {
+                        add_level_pair(Qr[k], level_int(v[0][k]), level_int(v[1][k]), l0);
+                        add_level_pair(Qi[k], level_int(v[0][4 + k]), level_int(v[1][4 + k]), l0);
                     }
                 }
                 if (m0 + m < rows) {
@@ -903,7 +917,8 @@ __global__ void __launch_bounds__(kT, 1) lattice_wide_kernel(const LatticeArgs A
         T = reinterpret_cast<TcSmem*>(smem + tc_offset_dev(A.b));
         if (tid == 0) {
             T->fail = 0;
-            tc::mbar_init(&T->bar, 1);   // one commit per tile
+            tc::mbar_init(&T->bar[0], 1);   // one commit per tile
+            tc::mbar_init(&T->bar[1], 1);
             tc::mbar_init_fence();
         }
         if (tid < 32) tc::tmem_alloc(&T->tmem, 512);
@@ -966,16 +981,15 @@ double lattice_wide_tc_flops(int N, int b, const int* pos, int npos, int nspin) 
     for (int sd = 1; sd <= kTD; ++sd)
         for (int td = 1; td <= kTD; ++td)
             if (sd + td <= kTNL) ++pairs;
-    const double tile64 = 4.0 * pairs * kTM * (2 * kTN) * 16;
     const double tile32 = 4.0 * pairs * kTM * (2 * kSN) * 16;
     double f = 0.0;
     for (int k0 = 0; k0 + kNB <= N; k0 += kNB) {   // full panels
         const int rmax = std::min(kNB + b, N - k0);
         // the rows below the diagonal block: tiles of 128 with the 16 columns of Z
         f += tile32 * ((rmax - kNB + kTM - 1) / kTM);
-        // the trailing update: column tiles of 128, row tiles of 32 from the tile's first column on
+        // the trailing update: column tiles of 128, row tiles of 16 from the tile's first column on
         const int rows = std::min(kNB - 1 + b, rmax - 1) - kNB + 1;
-        for (int c0 = 0; c0 < rows; c0 += kTM) f += tile64 * ((rows - c0 + kTN - 1) / kTN);
+        for (int c0 = 0; c0 < rows; c0 += kTM) f += tile32 * ((rows - c0 + kSN - 1) / kSN);
     }
     // the forward solves: per task of kR positions (ascending), from its first position, the rows
     // below each full step in tiles of 128
