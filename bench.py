@@ -401,18 +401,18 @@ DF_OPS_PER_FMA = 12          # FP32-pipe ops of one double-float multiply-add (l
 MEASURED_TRAFFIC = {"qmc_f64_kernel": (2295808 + 3584, "04c6f020ee92be69"),
                     "qmc_df64_kernel": (2386432 + 3584, "5e3b37f3293b93e3"),
                     # the lattice step of the slab16 workload (N = 1024, b = 128, 500 matrices)
-                    "lattice_kernel:slab16": (652.8e6 + 941.8e6, "cb1522e9ec00d909"),
+                    "lattice_kernel:slab16": (660.0e6 + 948.7e6, "e12e5007b95a53a0"),
                     # box16p (N = 4096, b = 512): one launch of 250 matrices
-                    "lattice_kernel:box16p": (155.58e9 + 138.91e9, "c90a88d2608085bc"),
+                    "lattice_kernel:box16p": (153.75e9 + 139.17e9, "1253e00c30993a68"),
                     # square30: one refresh launch and one sweep launch of all 1920 chains
-                    "refresh_tc_kernel": (350.9e6 + 1056.1e6, "d5913a6323e887aa"),
-                    "qmc_f32_kernel": (256.5e6 + 193.3e6, "f0a91e19b560c285")}
+                    "refresh_tc_kernel": (353.4e6 + 1056.3e6, "2f07ba98ff78531d"),
+                    "qmc_f32_kernel": (256.6e6 + 193.5e6, "a376070c58476eac")}
 KERNEL_SOURCES = {"qmc_df64_kernel": ("k_qmc_df64.cu", "qmc_common.cuh", "hf_internal.cuh"),
                   "qmc_f64_kernel": ("k_qmc_f64.cu", "qmc_common.cuh", "hf_internal.cuh"),
                   "lattice_kernel:slab16": ("k_lattice.cu", "k_lattice.cuh", "k_lattice_dev.cuh",
                                             "hf_internal.cuh"),
                   "lattice_kernel:box16p": ("k_lattice_wide.cu", "k_lattice.cuh",
-                                            "k_lattice_dev.cuh", "hf_internal.cuh"),
+                                            "k_lattice_dev.cuh", "tc_ozaki.cuh", "hf_internal.cuh"),
                   "refresh_tc_kernel": ("k_refresh_tc.cu", "k_refresh_tc.cuh", "tc_ozaki.cuh",
                                         "refresh_measure.cuh", "hf_internal.cuh"),
                   "qmc_f32_kernel": ("k_qmc_f32.cu", "tc_ozaki.cuh", "refresh_measure.cuh",

@@ -83,7 +83,9 @@ typedef struct hf_params {
                          /* to 165 the band L D L^T and selected inversion in a shared-memory */
                          /* window, above it (up to 840) the blocked band L D L^T in global   */
                          /* memory with G_ii from forward solves L^{-1} e_i at one site per    */
-                         /* orbit and spin; 1 always takes the blocked band form              */
+                         /* orbit and spin (for 128 <= b <= 520 its products run as exact    */
+                         /* bf16 digit products on the tensor cores, each entry rounded once */
+                         /* to FP64); 1 always takes the blocked band form                   */
     int delay_k;         /* delayed-update depth: 0/1 rank-1 Sherman-Morrison; 4, 8, 16, 32  */
                          /* (precision 2, one warp per chain): accepted flips gathered as    */
                          /* rank-k corrections                                              */

@@ -802,18 +802,30 @@ __device__ void solve_chunk_tc(const LatticeArgs& A, int q0, int qi, int ch, uns
             __syncthreads();   // Lp is restaged by the next panel
             continue;
         }
-        // (iii) rows below, 128 per tile
+        // (iii) rows below, 128 per tile.  A: the rows' L entries, four threads per row (four panel
+        // columns each, adjacent lanes); the next tile's are loaded while this tile's MMAs run,
+        // from clamped positions (the entries outside the band zeroed at use)
+        const int am = tid >> 2, apart = tid & 3;
+        double2 lnext[4];
+        const auto load_rows = [&](int mt) {
+            const int r = J + nb + min(mt + am, rows - 1);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int jj = 4 * apart + q;
+                lnext[q] = __ldcg(Bq + static_cast<size_t>(J + jj) * S + min(r - (J + jj), b));
+            }
+        };
+        load_rows(0);
         for (int m0 = 0; m0 < rows; m0 += kTM) {
-            {   // A: the rows' L entries, four threads per row (four panel columns each, adjacent
-                // lanes), which agree on the row's scale by shuffle and cut the Re and Im digits
-                const int m = tid >> 2, part = tid & 3;
+            {   // the rows agree on their scales by shuffle and cut the Re and Im digits
+                const int m = am, part = apart;
                 const int r = J + nb + m0 + m;
                 double2 l[4];
                 int e = tc::kNoExp;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int jj = 4 * part + q, d = r - (J + jj);
-                    l[q] = (m0 + m < rows && d <= b) ? __ldcg(Bq + static_cast<size_t>(J + jj) * S + d) : zero;
+                    l[q] = (m0 + m < rows && d <= b) ? lnext[q] : zero;
                     e = max(e, max(tc::exp_of(l[q].x), tc::exp_of(l[q].y)));
                 }
                 e = max(e, __shfl_xor_sync(0xffffffffu, e, 1));
@@ -838,6 +850,7 @@ __device__ void solve_chunk_tc(const LatticeArgs& A, int q0, int qi, int ch, uns
                                                         tc::smem_desc(tc::smem_addr(T.b), 128, 512));
                 tc::mma_commit(&T.bar[0]);
             }
+            if (m0 + kTM < rows) load_rows(m0 + kTM);
             bool ok = true;
             if (!T.fail) ok = tc::mbar_wait(&T.bar[0], ph & 1u);
             ph ^= 1u;
