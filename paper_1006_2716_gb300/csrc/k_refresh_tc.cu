@@ -251,38 +251,63 @@ struct FillBCols {
 // ------------------------------------------------------------------------------------------
 // one product pass: fills, MMAs, readout
 // ------------------------------------------------------------------------------------------
-// The MMAs of a chunk are issued by lane 0 of warps 0 .. kIssuers-1, each taking whole levels
-// (a level's accumulator is written by one thread, in order, its first product overwriting it):
-// level n goes to issuer fold(n - 2) mod kIssuers, fold pairing the first and the last levels,
-// so that the issuers' shares of the products are nearly equal.  Each issuer commits to the
-// chunk's mbarrier, which therefore expects kIssuers arrivals.
-constexpr int kIssuers = 4;
+// The MMAs of a chunk are issued by one thread.  Level n's accumulator is TMEM columns
+// (n - 2) NP ...; for each digit s of A the digits t of B (whose chunk planes lie one after the
+// other, NP rows each) are stacked along N in runs of at most 256 columns, one MMA per run and
+// K half, writing the level blocks s + t ... in one go.  The first product of each level
+// (s = max(1, n - SB), first chunk, first K half) overwrites its accumulator, and a run never
+// mixes first products with later ones.  The schedules (first chunk, later chunks) are fixed at
+// compile time.
+struct ChunkRun {
+    int kk, s, t, nt;
+    bool first;
+};
+struct ChunkSchedule {
+    ChunkRun run[64];
+    int n;
+};
+template <int SA, int SB, int NL, int NP>
+__host__ __device__ constexpr ChunkSchedule chunk_schedule(bool first_chunk) {
+    constexpr int G = 256 / NP;
+    ChunkSchedule S{};
+    for (int kk = 0; kk < 2; ++kk)
+        for (int s = 1; s <= SA; ++s) {
+            const int tmax = SB < NL - s ? SB : NL - s;
+            int t = 1;
+            while (t <= tmax) {
+                const auto first_of = [&](int tt) {
+                    return first_chunk && kk == 0 && s == (s + tt - SB > 1 ? s + tt - SB : 1);
+                };
+                const bool first = first_of(t);
+                int e = t;
+                while (e < tmax && e - t + 1 < G && first_of(e + 1) == first) ++e;
+                S.run[S.n++] = ChunkRun{kk, s, t, e - t + 1, first};
+                t = e + 1;
+            }
+        }
+    return S;
+}
 
-__host__ __device__ constexpr int issuer_of_level(int n, int NL) {
-    const int m = n - 2, last = NL - 2;
-    return (m < last - m ? m : last - m) % kIssuers;
+template <int SA, int SB, int NL, int NP, bool FIRST>
+__device__ __forceinline__ void issue_runs(uint32_t tmem, uint64_t adesc, uint64_t bdesc) {
+    constexpr ChunkSchedule S = chunk_schedule<SA, SB, NL, NP>(FIRST);
+    static_assert(S.n <= 64, "schedule fits");
+#pragma unroll
+    for (int i = 0; i < S.n; ++i) {
+        const ChunkRun r = S.run[i];
+        mma_bf16(tmem + (r.s + r.t - 2) * NP, adesc + (((r.s - 1) * A_SL + r.kk * 256) >> 4),
+                 bdesc + (((r.t - 1) * (NP * KC * 2) + r.kk * 256) >> 4), idesc_bf16_f32(128, r.nt * NP),
+                 !r.first);
+    }
 }
 
 template <int SA, int SB, int NL, int NP>
-__device__ void issue_chunk(Smem& S, int b, int c, int q) {
-    constexpr uint32_t idesc = idesc_bf16_f32(128, NP);
+__device__ void issue_chunk(Smem& S, int b, int c) {
     tc_fence_after_sync();
-    const uint32_t a0 = smem_addr(bufA(S, b, 0)), b0 = smem_addr(bufB<NP>(S, b, 0));
-#pragma unroll
-    for (int n = 2; n <= NL; ++n) {
-        if (issuer_of_level(n, NL) != q) continue;
-        const int smin = n - SB > 1 ? n - SB : 1;
-        const int smax = n - 1 < SA ? n - 1 : SA;
-        for (int s = smin; s <= smax; ++s) {
-            const int t = n - s;
-#pragma unroll
-            for (int kk = 0; kk < 2; ++kk) {
-                const uint64_t ad = smem_desc(a0 + (s - 1) * A_SL + kk * 256, 128, 512);
-                const uint64_t bd = smem_desc(b0 + (t - 1) * (NP * KC * 2) + kk * 256, 128, 512);
-                mma_bf16(S.tmem + (n - 2) * NP, ad, bd, idesc, !(c == 0 && kk == 0 && s == smin));
-            }
-        }
-    }
+    const uint64_t ad = smem_desc(smem_addr(bufA(S, b, 0)), 128, 512);
+    const uint64_t bd = smem_desc(smem_addr(bufB<NP>(S, b, 0)), 128, 512);
+    if (c == 0) issue_runs<SA, SB, NL, NP, true>(S.tmem, ad, bd);
+    else issue_runs<SA, SB, NL, NP, false>(S.tmem, ad, bd);
     mma_commit(&S.mbar[b]);
 }
 
@@ -318,11 +343,11 @@ __device__ bool product_pass(Smem& S, int p, uint32_t& ph, uint32_t& tph, FA& fi
         fence_async_shared();
         tc_fence_before_sync();
         __syncthreads();
-        if ((tid & 31) == 0 && (tid >> 5) < kIssuers) {
+        if (tid == 0) {
             if constexpr (TMA_A) {
                 ok = mbar_wait(&S.tbar[b], (tph >> b) & 1u) && ok;
             }
-            issue_chunk<SA, SB, NL, NP>(S, b, c, tid >> 5);
+            issue_chunk<SA, SB, NL, NP>(S, b, c);
         }
         if constexpr (TMA_A) tph ^= 1u << b;
     }
@@ -656,8 +681,8 @@ refresh_tc_kernel(const QmcProblem P, const TcRefreshArgs A) {
     if (tid == 0) {
         S.flag = 0;
         S.timeout = 0;
-        mbar_init(&S.mbar[0], kIssuers);
-        mbar_init(&S.mbar[1], kIssuers);
+        mbar_init(&S.mbar[0], 1);
+        mbar_init(&S.mbar[1], 1);
         mbar_init(&S.tbar[0], 1);
         mbar_init(&S.tbar[1], 1);
         mbar_init_fence();
@@ -792,8 +817,8 @@ tc_dgemm_kernel(const double* Am, const double* Bm, double* Cm, int n, int* stat
     if (m >= n) return;
     const int tid = threadIdx.x;
     if (tid == 0) {
-        mbar_init(&S.mbar[0], kIssuers);
-        mbar_init(&S.mbar[1], kIssuers);
+        mbar_init(&S.mbar[0], 1);
+        mbar_init(&S.mbar[1], 1);
         mbar_init(&S.tbar[0], 1);
         mbar_init(&S.tbar[1], 1);
         mbar_init_fence();
