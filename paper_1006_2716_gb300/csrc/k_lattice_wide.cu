@@ -88,8 +88,8 @@ struct TcSmem {                         // behind the panel, 1024-byte aligned
     int ta[kTM];                        // scales of A's rows (the tile's columns c)
     int tb[kNB + kTcMaxBand];           // scales of the B rows: the panel's rows (trailing
                                         // update), the right-hand sides (solve)
-    uint64_t bar[2];                    // MMA completion (the trailing update's two warp
-                                        // groups; the panels and solves use bar[0])
+    uint64_t bar[4];                    // MMA completion (the trailing update's warp groups;
+                                        // the panels and solves use bar[0])
     uint32_t tmem;                      // TMEM base address
     int fail;                           // an MMA wait ran out: no more tensor-core work
 };
@@ -223,16 +223,22 @@ __device__ __forceinline__ void group_sync(int id, int count) {
 
 // The trailing update of one panel on the tensor cores: rows and columns nb .. tend of the panel
 // P (RP the row stride, L_ij scaled, D_j on the diagonal) into the band buffer Bq at k0.
-// Per column tile of 128 all 512 threads cut the A digits; its row tiles of 16 go alternately to
-// the two warp groups (threads 0 .. 255 and 256 .. 511), each with its own B planes, its own half
-// of TMEM (eight levels x 32 columns), its own mbarrier and a named barrier, so that one group's
-// epilogue runs while the other cuts digits and waits for its MMAs.  ph: bit g the phase of
-// mbarrier g, flipped by every tile of group g (in every thread).
+// Per column tile of 128 all 512 threads cut the A digits; its row tiles of kRT = 8 rows go in
+// turn to the kGroups = 4 warp groups (128 threads each), each with its own B planes, its own
+// quarter of TMEM (eight levels x 16 columns), its own mbarrier and a named barrier, so that one
+// group's epilogue runs while the others cut digits and wait for their MMAs.  ph: bit g the phase
+// of mbarrier g, flipped by every tile of group g (in every thread).
+constexpr int kGroups = 4;
+constexpr int kGT = kT / kGroups;                // threads of a group
+constexpr int kRT = 32 / kGroups;                // trailing rows r per tile: 8 entries a thread
+constexpr int kPlaneT = 2 * kRT * kTK * 2;       // one B digit plane of a trailing tile
+static_assert(kRT % 8 == 0 && kGT == 16 * kRT, "a group cuts a tile's B digits, 4 K a thread");
+static_assert(kGroups * kTD * kPlaneT <= 2 * kTD * kPlaneS, "the groups' B planes fit");
+
 __device__ void trailing_tc(TcSmem& T, const double2* P, int RP, int nb, int tend, double2* Bq,
                             int k0, int S, uint32_t& ph) {
-    constexpr int kRT = 16;                       // trailing rows r per tile
     const int tid = static_cast<int>(threadIdx.x), lane = tid & 31, warp = tid >> 5;
-    const int grp = tid >> 8, u = tid & 255;      // warp group, thread within it
+    const int grp = tid / kGT, u = tid % kGT;     // warp group, thread within it
     const int rows = tend - nb + 1;
     if (rows <= 0) return;
     // the B scales of every trailing row, once for the panel (a thread per row)
@@ -245,8 +251,8 @@ __device__ void trailing_tc(TcSmem& T, const double2* P, int RP, int nb, int ten
         }
         T.tb[i] = scale_of(e);
     }
-    unsigned char* bplanes = T.b + grp * (kTD * kPlaneS);
-    const uint32_t tmem = T.tmem + 256 * grp;
+    unsigned char* bplanes = T.b + grp * (kTD * kPlaneT);
+    const uint32_t tmem = T.tmem + (512 / kGroups) * grp;
     for (int c0 = 0; c0 < rows; c0 += kTM) {
         // A: W_cj = D_j L_cj of the tile's columns c = nb + c0 + m, m < 128 (zero past tend):
         // four threads per column (adjacent lanes, four j each) form their W once, agree on the
@@ -279,16 +285,16 @@ __device__ void trailing_tc(TcSmem& T, const double2* P, int RP, int nb, int ten
         __syncthreads();   // the A planes and scales (and, first time round, the B scales)
         const int nt = (rows - c0 + kRT - 1) / kRT;
         for (int t = 0; t < nt; ++t) {
-            const int g = t & 1;
-            if (g != grp) {            // the other group's tile: only its phase bit
+            const int g = t % kGroups;
+            if (g != grp) {            // another group's tile: only its phase bit
                 ph ^= 1u << g;
                 continue;
             }
             const int r0 = c0 + t * kRT;
-            // B: L_rj of the tile's rows r = nb + r0 + nr, nr < 16, as [Re | -Im] (part 0) and
+            // B: L_rj of the tile's rows r = nb + r0 + nr, nr < kRT, as [Re | -Im] (part 0) and
             // [Im | Re] (part 1), 4 K a thread; plane row 16 (nr / 8) + 8 part + nr % 8
             {
-                const int part = u >> 7, nr = u & 15, kq = (u >> 4) & 7, kg = kq >> 1;
+                const int part = u / (8 * kRT), nr = u % kRT, kq = (u / kRT) % 8, kg = kq >> 1;
                 const int r = nb + r0 + nr;
                 const int Tb = r <= tend ? T.tb[r] : 0;
                 unsigned long long U[4];
@@ -303,23 +309,23 @@ __device__ void trailing_tc(TcSmem& T, const double2* P, int RP, int nb, int ten
                     U[q] = tc::to_fixed_mag(x, Tb, neg[q]);
                 }
                 const int mb = 16 * (nr >> 3) + 8 * part + (nr & 7);
-                put_digits4(U, neg, bplanes, kPlaneS, core_off(mb, kg) + (kq & 1) * 8);
+                put_digits4(U, neg, bplanes, kPlaneT, core_off(mb, kg) + (kq & 1) * 8);
             }
             tc::fence_async_shared();
             tc::tc_fence_before_sync();
-            group_sync(1 + grp, 256);
+            group_sync(1 + grp, kGT);
             // the MMAs, issued by the group's first thread and committed to its mbarrier
             if (u == 0 && !T.fail) {
                 tc::tc_fence_after_sync();
-                issue_levels<2 * kSN, kPlaneA, kPlaneS>(tmem, tc::smem_desc(tc::smem_addr(T.a), 128, 512),
+                issue_levels<2 * kRT, kPlaneA, kPlaneT>(tmem, tc::smem_desc(tc::smem_addr(T.a), 128, 512),
                                                         tc::smem_desc(tc::smem_addr(bplanes), 128, 512));
                 tc::mma_commit(&T.bar[grp]);
             }
             // the band entries this thread updates, loaded while the MMAs run: lane quarter
-            // (warp & 3) holds columns c = c0 + 32 (warp & 3) + lane, the group's two warps of a
+            // (warp & 3) holds columns c = c0 + 32 (warp & 3) + lane, the group's warps of a
             // quarter 8 rows each (contiguous in column c); loaded unconditionally (entries
             // outside the triangle clamped onto it, their values unused)
-            const int ql = warp & 3, h = (warp >> 2) & 1;
+            const int ql = warp & 3, h = (u >> 7);
             const int m = 32 * ql + lane;
             const int c = nb + c0 + m;
             const int rlo = nb + r0 + 8 * h;
@@ -345,8 +351,8 @@ __device__ void trailing_tc(TcSmem& T, const double2* P, int RP, int nb, int ten
 #pragma unroll
                     for (int part = 0; part < 2; ++part) {   // Re, then Im, of the levels n, n + 1
                         uint32_t v0[8], v1[8];
-                        tc::tmem_ld8_async(trow + (n - 2) * (2 * kSN) + 8 * part, v0);
-                        tc::tmem_ld8_async(trow + (n - 1) * (2 * kSN) + 8 * part, v1);
+                        tc::tmem_ld8_async(trow + (n - 2) * (2 * kRT) + 8 * part, v0);
+                        tc::tmem_ld8_async(trow + (n - 1) * (2 * kRT) + 8 * part, v1);
                         tc::tmem_wait_ld();
 #pragma unroll
                         for (int k = 0; k < 8; ++k)
@@ -366,7 +372,7 @@ __device__ void trailing_tc(TcSmem& T, const double2* P, int RP, int nb, int ten
                 }
             }
             tc::tc_fence_before_sync();
-            group_sync(1 + grp, 256);   // the group's TMEM half and B planes are reused
+            group_sync(1 + grp, kGT);   // the group's TMEM share and B planes are reused
         }
         __syncthreads();                // the A planes are reused by the next column tile
     }
@@ -930,8 +936,7 @@ __global__ void __launch_bounds__(kT, 1) lattice_wide_kernel(const LatticeArgs A
         T = reinterpret_cast<TcSmem*>(smem + tc_offset_dev(A.b));
         if (tid == 0) {
             T->fail = 0;
-            tc::mbar_init(&T->bar[0], 1);   // one commit per tile
-            tc::mbar_init(&T->bar[1], 1);
+            for (int g = 0; g < 4; ++g) tc::mbar_init(&T->bar[g], 1);   // one commit per tile
             tc::mbar_init_fence();
         }
         if (tid < 32) tc::tmem_alloc(&T->tmem, 512);
@@ -995,14 +1000,15 @@ double lattice_wide_tc_flops(int N, int b, const int* pos, int npos, int nspin) 
         for (int td = 1; td <= kTD; ++td)
             if (sd + td <= kTNL) ++pairs;
     const double tile32 = 4.0 * pairs * kTM * (2 * kSN) * 16;
+    const double tile_rt = 4.0 * pairs * kTM * (2 * kRT) * 16;
     double f = 0.0;
     for (int k0 = 0; k0 + kNB <= N; k0 += kNB) {   // full panels
         const int rmax = std::min(kNB + b, N - k0);
         // the rows below the diagonal block: tiles of 128 with the 16 columns of Z
         f += tile32 * ((rmax - kNB + kTM - 1) / kTM);
-        // the trailing update: column tiles of 128, row tiles of 16 from the tile's first column on
+        // the trailing update: column tiles of 128, row tiles of kRT from the tile's first column on
         const int rows = std::min(kNB - 1 + b, rmax - 1) - kNB + 1;
-        for (int c0 = 0; c0 < rows; c0 += kTM) f += tile32 * ((rows - c0 + kSN - 1) / kSN);
+        for (int c0 = 0; c0 < rows; c0 += kTM) f += tile_rt * ((rows - c0 + kRT - 1) / kRT);
     }
     // the forward solves: per task of kR positions (ascending), from its first position, the rows
     // below each full step in tiles of 128
