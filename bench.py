@@ -403,10 +403,10 @@ MEASURED_TRAFFIC = {"qmc_f64_kernel": (2295808 + 3584, "04c6f020ee92be69"),
                     # the lattice step of the slab16 workload (N = 1024, b = 128, 500 matrices)
                     "lattice_kernel:slab16": (660.0e6 + 948.7e6, "e12e5007b95a53a0"),
                     # box16p (N = 4096, b = 512): one launch of 250 matrices
-                    "lattice_kernel:box16p": (153.75e9 + 139.17e9, "1253e00c30993a68"),
+                    "lattice_kernel:box16p": (153.74e9 + 139.22e9, "62dbcc64f8cec42c"),
                     # square30: one refresh launch and one sweep launch of all 1920 chains
-                    "refresh_tc_kernel": (353.4e6 + 1056.3e6, "2f07ba98ff78531d"),
-                    "qmc_f32_kernel": (256.6e6 + 193.5e6, "a376070c58476eac")}
+                    "refresh_tc_kernel": (351.7e6 + 1055.7e6, "6ebecb2c46502445"),
+                    "qmc_f32_kernel": (256.3e6 + 193.2e6, "a376070c58476eac")}
 KERNEL_SOURCES = {"qmc_df64_kernel": ("k_qmc_df64.cu", "qmc_common.cuh", "hf_internal.cuh"),
                   "qmc_f64_kernel": ("k_qmc_f64.cu", "qmc_common.cuh", "hf_internal.cuh"),
                   "lattice_kernel:slab16": ("k_lattice.cu", "k_lattice.cuh", "k_lattice_dev.cuh",
@@ -477,6 +477,33 @@ def qmc_roofline(form, L, nchain, sweeps, accepts, n_measure, n_refresh, qmc_s, 
             "frac": achieved / peak, "traffic": measured_traffic(kernel),
             "algorithmic_bytes": alg_bytes,
             "kernel": kernel, "executed_tflops": executed, "peak_source": src, **extra}
+
+
+def e2e_iterations(hf, ctx, dev, steps, proposals):
+    """The same RDMFT iterations end to end through the public API with host buffers: per step the
+    self-energy from pinned host memory (H2D), the iteration, and the observables and the new
+    self-energy back to pinned host memory (D2H); wall clock over the steps."""
+    import numpy as np
+    import torch
+
+    L, ns, nw = ctx.L, ctx.n_sites, ctx.nw
+    pin_sig = torch.empty(ns * 2 * nw * 2, dtype=torch.float64, pin_memory=True)
+    pin_obs = torch.empty(2 * ns * (2 * L + 4), dtype=torch.float64, pin_memory=True)
+    sig_np = pin_sig.numpy().view(np.complex128).reshape(ns, 2, nw)
+    sig_np[:] = hf.hf_get_sigma(ctx.handle, ns, nw)
+    obs = pin_obs.numpy()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        hf.lib().hf_set_sigma(ctx.handle, sig_np.ctypes.data_as(hf._DP))
+        hf.hf_rdmft_step(ctx.handle)
+        hf.lib().hf_get_observables(ctx.handle, obs.ctypes.data_as(hf._DP),
+                                    obs[ns * (2 * L + 4):].ctypes.data_as(hf._DP))
+        hf.lib().hf_get_sigma(ctx.handle, sig_np.ctypes.data_as(hf._DP))
+    torch.cuda.synchronize(dev)
+    secs = (time.perf_counter() - t0) / steps
+    return {"value": proposals / secs, "unit": "proposals/s", "h2d_bytes_per_step": sig_np.nbytes,
+            "d2h_bytes_per_step": obs.nbytes + sig_np.nbytes}
 
 
 def _time_iterations(hf, ctx, stream, flush, steps):
@@ -805,6 +832,7 @@ def run_lattice3d(args):
     accepts = int(hf.hf_get_accepts(ctx.handle, nc).sum() - acc0) / args.steps
     ms_per = statistics.mean(ms_steps)
     phase = phase / args.steps
+    e2e = e2e_iterations(hf, ctx, dev, args.steps, proposals)
     qroof = qmc_roofline(2, L, nc, sweeps, accepts, cfg["n_measure"], n_refresh,
                          statistics.mean(qmc_ms) / 1e3, "qmc_df64_kernel")
     qroof["acceptance"] = accepts / proposals
@@ -858,7 +886,7 @@ def run_lattice3d(args):
                                  [float(x) for x in phase])),
             "roofline": dominant, "qmc_roofline": qroof, "lattice_roofline": lroof,
             "gpu_launches": (lattice_launches(hf, cfg) + 5) * args.steps,
-            "cpu_baseline": cpu, "clocks": clk}
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk}
     if args.sweeps or args.matsubara:
         over = []
         if args.sweeps:
@@ -1048,6 +1076,8 @@ def run_square30(args):
     accepts = int(hf.hf_get_accepts(ctx.handle, nc).sum() - acc0) / args.steps
     ms_per = statistics.mean(ms_steps)
     qmc_s = statistics.mean(qmc_ms) / 1e3
+    n_tc, n_fb, n_prod = hf.hf_get_refresh_stats(ctx.handle)   # of the last timed iteration
+    e2e = e2e_iterations(hf, ctx, dev, args.steps, proposals)
     # the sweeps alone, timed live on a twin context that never refreshes within the launch: the
     # refresh kernels' share of the QMC phase is the difference
     twin = hf.Context(hf.make_params(dict(cfg, refresh_every=100000)), device=dev, stream=stream)
@@ -1071,7 +1101,6 @@ def run_square30(args):
     if tc:
         # executed tensor-core work: the digit products the Newton steps ran in the last timed
         # iteration (the library counts them), 2 x 128^3 bf16 flops each
-        n_tc, n_fb, n_prod = hf.hf_get_refresh_stats(ctx.handle)
         tflop = n_prod * 2.0 * L ** 3
         ref_roof = {"bound": "tensor", "kernel": "refresh_tc_kernel", "achieved": tflop / refresh_s / 1e12,
                     "peak": MEASURED_BF16_SUSTAINED, "unit": "TFLOP/s",
@@ -1108,7 +1137,7 @@ def run_square30(args):
             # alone), the first refresh, g0^-1 (and its digits), lattice step, Weiss/tau,
             # reduction, self-energy update
             "gpu_launches": (((3 if tc else 2) * sweeps) + (7 if tc else 6)) * args.steps,
-            "cpu_baseline": cpu, "clocks": clk}
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk}
     if args.sweeps:
         line["profile_case"] = "sweeps overridden to %d: not a benchmark value" % args.sweeps
     print(json.dumps(line))

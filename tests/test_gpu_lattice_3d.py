@@ -74,7 +74,9 @@ SMALL = [
 
 @pytest.mark.parametrize("form", [0, 1])
 @pytest.mark.parametrize("geom,Lx,Ly,Lz,per,band,halved",
-                         SMALL + [(0, 6, 6, 1, 0, 6, True)])   # b < panel width (blocked form)
+                         SMALL + [(0, 6, 6, 1, 0, 6, True),     # b < panel width (blocked form)
+                                  (2, 8, 8, 8, 1, 128, True)])  # b = 128: the blocked form's
+                                                                # products on the tensor cores
 def test_lattice_step_all_frequencies(hf, geom, Lx, Ly, Lz, per, band, halved, form):
     """Every inequivalent site and every frequency of a set self-energy against a dense
     inverse, in either form of the lattice step."""
