@@ -680,12 +680,13 @@ def lattice_launches(hf, cfg):
     """Lattice-step launches of one iteration, as the library plans them: the nspin x nw
     matrices in chunks of as many band buffers as fit in 1 GiB (at most 2 nw), one launch each;
     in the blocked band form (band half-width above 165, or lattice_form 1) as many as fit in
-    8 GiB, split evenly, two launches each (factorisation, forward solves)."""
+    24 GiB, split evenly, one launch each (factorisations and forward solves as the tasks of one
+    persistent kernel)."""
     N, _, b, nspin, _, _, _ = hf.hf_lattice_info(hf.make_params(cfg))
     nw = cfg["n_matsubara"]
     per = N * (b + 1) * 16
     if b > 165 or cfg.get("lattice_form", 0) == 1:
-        return 2 * -(-nspin * nw // max(1, (8 << 30) // per))
+        return -(-nspin * nw // max(1, (24 << 30) // per))
     batch = max(1, min(2 * nw, (1 << 30) // per))
     return -(-nspin * nw // batch)
 

@@ -436,12 +436,12 @@ hf_status setup_sizes(hf_ctx& c, const hf_params* p) {
     c.nchain = c.nsite * p->chains_per_site;
     c.nw = p->n_matsubara;
     // lattice step: as many (w_n, sigma) matrices per launch as fit in 1 GiB of band buffers
-    // (blocked band form: 8 GiB, split evenly over the launches, so that each launch still fills
-    // the GPU with one matrix per SM)
+    // (blocked band form: 24 GiB, split evenly over the launches, so that each launch still fills
+    // the GPU with one matrix per SM; one launch holds the 500 matrices of the periodic 16^3 box)
     const size_t per = hfk::lattice_scratch_per_matrix(c.lat.N, c.lat.b);
     const int nq = (c.lat.gdn.empty() ? 2 : 1) * c.nw;
     if (c.lat_wide) {
-        const size_t cap = std::max<size_t>(1, (static_cast<size_t>(8) << 30) / (per ? per : 1));
+        const size_t cap = std::max<size_t>(1, (static_cast<size_t>(24) << 30) / (per ? per : 1));
         const size_t nl = (static_cast<size_t>(nq) + cap - 1) / cap;
         c.lat_batch = static_cast<int>((static_cast<size_t>(nq) + nl - 1) / nl);
     } else {
@@ -859,7 +859,7 @@ hf_status hf_get_lattice_plan(const hf_ctx* c, int* form, int* launches, double*
         }
     }
     if (form) *form = c->lat_wide ? 1 : 0;
-    if (launches) *launches = nl * (c->lat_wide ? 2 : 1);
+    if (launches) *launches = nl;
     if (cfma) *cfma = f;
     if (tc_flops)
         *tc_flops = c->lat_wide ? hfk::lattice_wide_tc_flops(N, b, c->wide_pos_host.data(), c->wide_npos, nspin)

@@ -80,10 +80,12 @@ def test_bench_lattice_bookkeeping(lib):
     assert bench.lattice_launches(hf, wl.CONFIGS["slab16"]) == 1
     # 12^3 box: 500 matrices of 1728 x 145 x 16 bytes = 2.0 GB -> two launches
     assert bench.lattice_launches(hf, wl.CONFIGS["box12"]) == 2
-    # periodic 16^3 box (blocked band form): 500 matrices of 4096 x 513 x 16 bytes = 16.8 GB ->
-    # two chunks of 250 under the 8 GiB cap, two launches each
-    assert bench.lattice_launches(hf, wl.CONFIGS["box16p"]) == 4
-    assert bench.lattice_launches(hf, dict(wl.CONFIGS["slab16"], lattice_form=1)) == 2
+    # periodic 16^3 box (blocked band form): 500 matrices of 4096 x 513 x 16 bytes = 16.8 GB,
+    # under the 24 GiB cap: one launch of the persistent kernel
+    assert bench.lattice_launches(hf, wl.CONFIGS["box16p"]) == 1
+    assert bench.lattice_launches(hf, dict(wl.CONFIGS["slab16"], lattice_form=1)) == 1
+    # above the cap, split evenly: 1000 matrices of the 16^3 box (33.6 GB) -> two launches of 500
+    assert bench.lattice_launches(hf, dict(wl.CONFIGS["box16p"], n_matsubara=1000)) == 2
     N = 40
     exact = 8.0 * sum(d * (d + 1) // 2 + d * d + d for d in range(N))
     assert bench.lattice_flops(N, N - 1, 1, 1) == exact
