@@ -402,8 +402,8 @@ MEASURED_TRAFFIC = {"qmc_f64_kernel": (2295808 + 3584, "04c6f020ee92be69"),
                     "qmc_df64_kernel": (2386432 + 3584, "5e3b37f3293b93e3"),
                     # the lattice step of the slab16 workload (N = 1024, b = 128, 500 matrices)
                     "lattice_kernel:slab16": (660.0e6 + 948.7e6, "e12e5007b95a53a0"),
-                    # box16p (N = 4096, b = 512): one launch of 250 matrices
-                    "lattice_kernel:box16p": (153.74e9 + 139.22e9, "62dbcc64f8cec42c"),
+                    # box16p (N = 4096, b = 512): one launch of all 500 matrices
+                    "lattice_kernel:box16p": (310.47e9 + 279.17e9, "ad50b4cea79d5a37"),
                     # square30: one refresh launch and one sweep launch of all 1920 chains
                     "refresh_tc_kernel": (351.7e6 + 1055.7e6, "6ebecb2c46502445"),
                     "qmc_f32_kernel": (256.3e6 + 193.2e6, "a376070c58476eac")}

@@ -19,7 +19,9 @@
 // and then the solve tasks, so that the solves fill the SMs the last factorisations leave idle.
 // Work per matrix: about N b^2 / 2 complex FMA for the factorisation and (N - k) b per listed
 // position, against 1.5 N b^2 for the selected inversion of the window form, which also yields
-// every diagonal element.
+// every diagonal element.  For 128 <= b <= kTcMaxBand the products (a panel's rows below its
+// diagonal block, the trailing updates, the solves' row updates) run on the tensor cores as
+// exact digit products, each entry rounded once to FP64; the rest stays on the FP64 pipe.
 #include <algorithm>
 
 #include "hf_internal.cuh"
@@ -919,8 +921,9 @@ __device__ void solve_chunk_tc(const LatticeArgs& A, int q0, int qi, int ch, uns
 // handed out earlier, so a running block is factoring it), at most wait_cycles (several times
 // what one factorisation takes), after which it reports HF_ETIMEOUT and skips.  So the blocks
 // left over when the factorisations run out take the solves of the matrices already factored,
-// instead of idling through a last partial wave.  TC: the block holds all of TMEM and an
-// mbarrier for the tensor-core trailing updates, from its first task to its last.
+// instead of idling through a last partial wave.  TC: the block holds all of TMEM and the
+// mbarriers of the tensor-core products (one per warp group of the trailing update), from its
+// first task to its last.
 template <int DPT, bool TC>
 __global__ void __launch_bounds__(kT, 1) lattice_wide_kernel(const LatticeArgs A, int q0, int nq,
                                                              int nchunk, int* work,
