@@ -400,18 +400,18 @@ DF_OPS_PER_FMA = 12          # FP32-pipe ops of one double-float multiply-add (l
 # in the profile summaries); a kernel whose sources changed since reports null.
 MEASURED_TRAFFIC = {"qmc_f64_kernel": (2295808 + 3584, "04c6f020ee92be69"),
                     "qmc_df64_kernel": (2386432 + 3584, "5e3b37f3293b93e3"),
-                    # the lattice step of the slab16 workload (N = 1024, b = 128, 500 matrices)
-                    "lattice_kernel:slab16": (660.0e6 + 948.7e6, "e12e5007b95a53a0"),
-                    # box16p (N = 4096, b = 512): one launch of all 500 matrices
-                    "lattice_kernel:box16p": (310.47e9 + 279.17e9, "ad50b4cea79d5a37"),
+                    # the blocked lattice step, one launch of all 500 matrices: slab16 (N = 1024,
+                    # b = 128) and box16p (N = 4096, b = 512)
+                    "lattice_wide_kernel:slab16": (2160.4e6 + 2092.8e6, "9b62c014a9ceece6"),
+                    "lattice_wide_kernel:box16p": (310.53e9 + 279.17e9, "9b62c014a9ceece6"),
                     # square30: one refresh launch and one sweep launch of all 1920 chains
                     "refresh_tc_kernel": (351.7e6 + 1055.7e6, "6ebecb2c46502445"),
                     "qmc_f32_kernel": (256.3e6 + 193.2e6, "a376070c58476eac")}
 KERNEL_SOURCES = {"qmc_df64_kernel": ("k_qmc_df64.cu", "qmc_common.cuh", "hf_internal.cuh"),
                   "qmc_f64_kernel": ("k_qmc_f64.cu", "qmc_common.cuh", "hf_internal.cuh"),
-                  "lattice_kernel:slab16": ("k_lattice.cu", "k_lattice.cuh", "k_lattice_dev.cuh",
-                                            "hf_internal.cuh"),
-                  "lattice_kernel:box16p": ("k_lattice_wide.cu", "k_lattice.cuh",
+                  "lattice_wide_kernel:slab16": ("k_lattice_wide.cu", "k_lattice.cuh",
+                                                 "k_lattice_dev.cuh", "tc_ozaki.cuh", "hf_internal.cuh"),
+                  "lattice_wide_kernel:box16p": ("k_lattice_wide.cu", "k_lattice.cuh",
                                             "k_lattice_dev.cuh", "tc_ozaki.cuh", "hf_internal.cuh"),
                   "refresh_tc_kernel": ("k_refresh_tc.cu", "k_refresh_tc.cuh", "tc_ozaki.cuh",
                                         "refresh_measure.cuh", "hf_internal.cuh"),
@@ -679,13 +679,14 @@ def run_ours(args):
 def lattice_launches(hf, cfg):
     """Lattice-step launches of one iteration, as the library plans them: the nspin x nw
     matrices in chunks of as many band buffers as fit in 1 GiB (at most 2 nw), one launch each;
-    in the blocked band form (band half-width above 165, or lattice_form 1) as many as fit in
-    24 GiB, split evenly, one launch each (factorisations and forward solves as the tasks of one
-    persistent kernel)."""
+    in the blocked band form (band half-width 128 and above unless lattice_form 2 asks for the
+    window, or lattice_form 1) as many as fit in 24 GiB, split evenly, one launch each
+    (factorisations and forward solves as the tasks of one persistent kernel)."""
     N, _, b, nspin, _, _, _ = hf.hf_lattice_info(hf.make_params(cfg))
     nw = cfg["n_matsubara"]
     per = N * (b + 1) * 16
-    if b > 165 or cfg.get("lattice_form", 0) == 1:
+    form = cfg.get("lattice_form", 0)
+    if b > 165 or form == 1 or (form == 0 and b >= 128):
         return -(-nspin * nw // max(1, (24 << 30) // per))
     batch = max(1, min(2 * nw, (1 << 30) // per))
     return -(-nspin * nw // batch)
@@ -806,6 +807,8 @@ def run_lattice3d(args):
         cfg.update(n_warmup=args.sweeps // 5, n_measure=nm, bin_size=max(1, nm // 4))
     if args.matsubara:
         cfg.update(n_matsubara=args.matsubara)   # profiling captures only (not a benchmark value)
+    if args.lattice_form:
+        cfg.update(lattice_form=args.lattice_form)
     N, ns, b, nspin, _, _, _ = hf.hf_lattice_info(hf.make_params(cfg))
     nc = ns * cfg["chains_per_site"]
     cpu = None
@@ -849,7 +852,7 @@ def run_lattice3d(args):
         tfl = tc_flops * nspin * nw
         lroof = {"bound": "tensor", "achieved": tfl / lat_s / 1e12, "peak": MEASURED_BF16_SUSTAINED,
                  "unit": "TFLOP/s", "frac": tfl / lat_s / 1e12 / MEASURED_BF16_SUSTAINED,
-                 "traffic": measured_traffic("lattice_kernel:" + name),
+                 "traffic": measured_traffic(lkern + ":" + name),
                  "kernel": lkern, "matrices": nspin * nw, "N": N, "band": b,
                  "form": form + ", products on the tensor cores", "seconds": lat_s,
                  "work": "bf16 flops of the exact digit products (panels below their diagonal "
@@ -861,7 +864,7 @@ def run_lattice3d(args):
     else:
         lroof = {"bound": "alu", "achieved": fl / lat_s / 1e12, "peak": FP64_PEAK_TFLOPS,
                  "unit": "TFLOP/s", "frac": fl / lat_s / 1e12 / FP64_PEAK_TFLOPS,
-                 "traffic": measured_traffic("lattice_kernel:" + name),
+                 "traffic": measured_traffic(lkern + ":" + name),
                  "kernel": lkern, "matrices": nspin * nw, "N": N, "band": b,
                  "form": form, "seconds": lat_s,
                  "peak_source": "FP64 nominal: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz"}
@@ -1559,6 +1562,9 @@ def main():
     ap.add_argument("--matsubara", type=int, default=0,
                     help="profiling only, 3D workloads: override the Matsubara frequencies, i.e. "
                          "the lattice step's matrices (result is not a bench value)")
+    ap.add_argument("--lattice-form", type=int, default=0, choices=(0, 1, 2),
+                    help="3D workloads: the lattice step's form (0 automatic, 1 blocked band "
+                         "form, 2 shared-memory window form)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -79,13 +79,14 @@ typedef struct hf_params {
                          /* two Newton steps on the tensor cores (products formed exactly     */
                          /* from bf16 digits), falling back to Gauss-Jordan for a chain whose */
                          /* residual does not converge; 1 always uses FP64 Gauss-Jordan       */
-    int lattice_form;    /* lattice step (eq. 2): 0 (default) picks by band half-width b: up   */
-                         /* to 165 the band L D L^T and selected inversion in a shared-memory */
-                         /* window, above it (up to 840) the blocked band L D L^T in global   */
+    int lattice_form;    /* lattice step (eq. 2): 0 (default) picks by band half-width b: below */
+                         /* 128 the band L D L^T and selected inversion in a shared-memory    */
+                         /* window, from 128 on (up to 840) the blocked band L D L^T in global */
                          /* memory with G_ii from forward solves L^{-1} e_i at one site per    */
                          /* orbit and spin (for 128 <= b <= 520 its products run as exact    */
                          /* bf16 digit products on the tensor cores, each entry rounded once */
-                         /* to FP64); 1 always takes the blocked band form                   */
+                         /* to FP64); 1 always takes the blocked band form; 2 always the      */
+                         /* window form (b <= 165, HF_EINVAL above)                            */
     int delay_k;         /* delayed-update depth: 0/1 rank-1 Sherman-Morrison; 4, 8, 16, 32  */
                          /* (precision 2, one warp per chain): accepted flips gathered as    */
                          /* rank-k corrections                                              */

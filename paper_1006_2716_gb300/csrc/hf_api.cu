@@ -355,7 +355,7 @@ hf_status validate(const hf_params& p, std::string& err) {
         return HF_EINVAL;
     }
     if (!(p.check_drift == 0 || p.check_drift == 1)) { err = "check_drift must be 0 or 1"; return HF_EINVAL; }
-    if (!(p.lattice_form == 0 || p.lattice_form == 1)) { err = "lattice_form must be 0 or 1"; return HF_EINVAL; }
+    if (!(p.lattice_form >= 0 && p.lattice_form <= 2)) { err = "lattice_form must be 0, 1 or 2"; return HF_EINVAL; }
     if (!(p.refresh_stagger == 0 || p.refresh_stagger == 1) ||
         (p.refresh_stagger == 1 && p.precision == 1 && p.refresh_every > 1)) {
         err = "refresh_stagger must be 0 or 1; staggered phases need fused refreshes (precision 0 "
@@ -430,7 +430,14 @@ hf_status setup_sizes(hf_ctx& c, const hf_params* p) {
                     "the lattice's band half-width " + std::to_string(c.lat.b) +
                         " exceeds the lattice step's band buffers (largest: " +
                         std::to_string(hfk::lattice_max_band()) + ")");
-    c.lat_wide = p->lattice_form == 1 || !hfk::lattice_window_supported(c.lat.b);
+    // automatic: the window form below the bands whose products run on the tensor cores, the
+    // blocked form from there on (and wherever the window does not fit)
+    if (p->lattice_form == 2 && !hfk::lattice_window_supported(c.lat.b))
+        return fail(nullptr, HF_EINVAL, "lattice_form 2 (the window form) needs a band half-width <= " +
+                                             std::to_string(hfk::lattice_window_max_band()));
+    c.lat_wide = p->lattice_form == 1 ||
+                 (p->lattice_form == 0 && c.lat.b >= hfk::lattice_wide_tc_min_band()) ||
+                 !hfk::lattice_window_supported(c.lat.b);
     c.L = static_cast<int>(std::lround(p->beta / p->dtau));
     c.nsite = static_cast<int>(c.lat.rep.size());
     c.nchain = c.nsite * p->chains_per_site;

@@ -38,6 +38,8 @@ cudaError_t launch_lattice(const LatticeArgs& a, int q0, int nq, cudaStream_t st
 
 // Blocked band form (k_lattice_wide.cu), every b <= lattice_wide_max_band().
 int lattice_wide_max_band();
+// Smallest band half-width whose products the blocked form runs on the tensor cores.
+int lattice_wide_tc_min_band();
 int lattice_wide_rhs_per_block();
 // bf16 flops of the tensor-core trailing updates per matrix (0 where the band keeps DFMA)
 double lattice_wide_tc_flops(int N, int b, const int* pos, int npos, int nspin);

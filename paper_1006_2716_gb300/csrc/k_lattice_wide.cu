@@ -992,6 +992,8 @@ __global__ void __launch_bounds__(kT, 1) lattice_wide_kernel(const LatticeArgs A
 
 int lattice_wide_max_band() { return kWideMaxBand; }
 
+int lattice_wide_tc_min_band() { return kTcMinBand; }
+
 int lattice_wide_rhs_per_block() { return kR; }
 
 double lattice_wide_tc_flops(int N, int b, const int* pos, int npos, int nspin) {

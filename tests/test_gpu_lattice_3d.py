@@ -3,10 +3,12 @@ lattices ("Efficient simulations for three dimensions": trapped boxes with perio
 slabs periodic across their layers), through the C ABI, with the CPU oracle.
 
 Cases span both forms of the lattice step -- the band L D L^T and selected inversion in a
-shared-memory window (one warp per matrix for band half-width b <= 32, one block above), and the
-blocked band L D L^T in global memory with forward solves at one site per orbit and spin (taken
-above b = 165, or when asked for with lattice_form = 1) -- and both spin treatments (spin-down
-matrices inverted, or read from the spin-up ones through a sublattice-exchanging symmetry).  The
+shared-memory window (one warp per matrix for band half-width b <= 32, one block above; taken
+below b = 128, or when asked for with lattice_form = 2), and the blocked band L D L^T in global
+memory with forward solves at one site per orbit and spin (taken from b = 128 on, its products
+on the tensor cores up to b = 520, or when asked for with lattice_form = 1) -- and both spin
+treatments (spin-down matrices inverted, or read from the spin-up ones through a
+sublattice-exchanging symmetry).  The
 periodic 14^3 and 16^3 boxes of Fig. 4 (b = 392, 512) run in the blocked form.  Bars as for the square: G_ii(i w_n) within 1e-12
 relative; baths within 1e-12; decisions identical; observables within 1e-10; Sigma within 1e-9
 relative.
@@ -72,7 +74,7 @@ SMALL = [
 ]
 
 
-@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("form", [2, 1])   # the window form, the blocked form
 @pytest.mark.parametrize("geom,Lx,Ly,Lz,per,band,halved",
                          SMALL + [(0, 6, 6, 1, 0, 6, True),     # b < panel width (blocked form)
                                   (2, 8, 8, 8, 1, 128, True)])  # b = 128: the blocked form's
@@ -85,7 +87,7 @@ def test_lattice_step_all_frequencies(hf, geom, Lx, Ly, Lz, per, band, halved, f
     N, ns, b, nsp, _, _, _ = hf.hf_lattice_info(p)
     assert b == band
     ctx = hf.Context(p)
-    assert hf.hf_get_lattice_plan(ctx.handle)[0] == form
+    assert hf.hf_get_lattice_plan(ctx.handle)[0] == (1 if form == 1 else 0)
     ref = _oracle_for(cfg)
     assert ns == ref.nsite and N == ref.lat.N
     has_flip = any(np.all(ref.lat.parity[im] != ref.lat.parity) for im in ref.lat._images)
@@ -110,10 +112,10 @@ def test_lattice_step_all_frequencies(hf, geom, Lx, Ly, Lz, per, band, halved, f
 
 
 LARGE = [
-    (3, 24, 24, 4, 0, 96, 0),       # slab of 2304 sites
-    (2, 8, 8, 8, 1, 128, 0),        # periodic box of 512 sites
-    (2, 12, 12, 12, 0, 144, 0),     # open box of 1728 sites
-    (2, 12, 12, 12, 0, 144, 1),     # the same in the blocked band form
+    (3, 24, 24, 4, 0, 96, 0),       # slab of 2304 sites (window form)
+    (2, 8, 8, 8, 1, 128, 2),        # periodic box of 512 sites, in the window form
+    (2, 12, 12, 12, 0, 144, 2),     # open box of 1728 sites, in the window form
+    (2, 12, 12, 12, 0, 144, 0),     # the same in the form taken by default (blocked band form)
     (2, 14, 14, 14, 1, 392, 0),     # periodic boxes of Fig. 4 (blocked band form)
     (2, 16, 16, 16, 1, 512, 0),
 ]
@@ -130,7 +132,7 @@ def test_lattice_step_large_sampled(hf, geom, Lx, Ly, Lz, per, band, form):
     assert b == band
     ctx = hf.Context(p)
     wide = hf.hf_get_lattice_plan(ctx.handle)[0]
-    assert wide == (1 if (form == 1 or band > 165) else 0)
+    assert wide == (1 if (form == 1 or (form == 0 and band >= 128) or band > 165) else 0)
     hf.hf_compute_baths(ctx.handle)          # lattice step from the seeded self-energy
     gloc = hf.hf_get_gloc(ctx.handle, ns, ctx.nw)
     ref = _oracle_for(cfg)

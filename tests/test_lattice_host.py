@@ -78,8 +78,10 @@ def test_bench_lattice_bookkeeping(lib):
 
     assert bench.lattice_launches(hf, wl.CONFIGS["square20"]) == 1
     assert bench.lattice_launches(hf, wl.CONFIGS["slab16"]) == 1
-    # 12^3 box: 500 matrices of 1728 x 145 x 16 bytes = 2.0 GB -> two launches
-    assert bench.lattice_launches(hf, wl.CONFIGS["box12"]) == 2
+    # 12^3 box (b = 144): the blocked form by default, 500 matrices of 1728 x 145 x 16 bytes =
+    # 2.0 GB in one launch; in the window form (lattice_form 2) two launches under 1 GiB
+    assert bench.lattice_launches(hf, wl.CONFIGS["box12"]) == 1
+    assert bench.lattice_launches(hf, dict(wl.CONFIGS["box12"], lattice_form=2)) == 2
     # periodic 16^3 box (blocked band form): 500 matrices of 4096 x 513 x 16 bytes = 16.8 GB,
     # under the 24 GiB cap: one launch of the persistent kernel
     assert bench.lattice_launches(hf, wl.CONFIGS["box16p"]) == 1
@@ -109,5 +111,10 @@ def test_band_limits(lib):
         hf.hf_lattice_info(p)
     assert e.value.status == hf.HF_EINVAL and "largest: 840" in str(e.value)
     with pytest.raises(hf.HFError) as e:
-        hf.hf_lattice_info(hf.make_params(sq, lattice_form=2))
+        hf.hf_lattice_info(hf.make_params(sq, lattice_form=3))
     assert e.value.status == hf.HF_EINVAL
+    # the window form asked for where it does not fit
+    with pytest.raises(hf.HFError) as e:
+        hf.hf_lattice_info(hf.make_params(sq, geometry=2, Lx=2, Ly=83, Lz=2, periodic=0, lattice_form=2))
+    assert e.value.status == hf.HF_EINVAL and "window form" in str(e.value)
+    hf.hf_lattice_info(hf.make_params(sq, geometry=2, Lx=11, Ly=15, Lz=3, periodic=0, lattice_form=2))
